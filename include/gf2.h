@@ -1,0 +1,155 @@
+/*
+ * gf2.h -- C ABI of a GB300 (sm_103a) library for dense linear algebra over
+ * F2: the block decomposition P*A = L*E of Bertolazzi & Rimoldi, "Fast
+ * matrix decomposition in F2" (arXiv 1209.5198), with row permutations only
+ * (no column swaps), its rank, its echelon form, linear solves, and the
+ * matrix product over F2.
+ *
+ * Matrix layout (Section 3 of the paper).  An r x c matrix over F2 is held
+ * as ceil(c/64) "column blocks" of 64-bit words in DEVICE memory: the word
+ * for row i and column block q is w[q*ld + i] (ld >= r), and bit t of that
+ * word is entry (i, 64q + t) -- the least significant bit is the leftmost
+ * column (the paper's bit order).  Bits at columns >= c must be zero
+ * ("padding"); the library checks this unless GF2_NOCHECK is given.
+ *
+ * Streams.  Every call is asynchronous on the CUDA stream passed as `stream`
+ * (a cudaStream_t; NULL = the legacy default stream) unless its name ends in
+ * _host, or a padding check is requested (the check reads one flag back).
+ *
+ * Workspace.  Calls that need scratch memory take (workspace, ws_bytes).
+ * Pass a device buffer of at least the size the matching *_workspace_bytes
+ * function returns; pass NULL to let the library use its own buffer, which
+ * it allocates on first use, grows when needed and keeps per device until
+ * gf2_release_workspace().  The library's own buffer is shared by every call
+ * on that device: calls that use it must not overlap in time.
+ *
+ * Errors.  Every entry point returns a status: GF2_OK or one of the codes
+ * below.  No exception crosses the ABI.  On an error nothing is launched,
+ * except GF2_ERR_CUDA, which reports a failed CUDA call.
+ */
+#ifndef GF2_H
+#define GF2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GF2_OK 0
+#define GF2_ERR_ARG 1         /* NULL pointer, negative size, bad flag      */
+#define GF2_ERR_SHAPE 2       /* inner dimensions differ, ld < rows, k > 64 */
+#define GF2_ERR_PADDING 3     /* a bit at a column >= cols is set           */
+#define GF2_ERR_NOMEM 4       /* workspace too small / allocation failed    */
+#define GF2_ERR_CUDA 5        /* a CUDA runtime call failed                 */
+#define GF2_ERR_TIMEOUT 6     /* a bounded device-side wait gave up         */
+#define GF2_ERR_UNSUPPORTED 7 /* size beyond what this build handles        */
+
+/* flags */
+#define GF2_NOCHECK 1u /* skip the padding check of the inputs */
+
+typedef struct gf2_mat {
+    uint64_t *w;          /* device pointer, column blocks (see above) */
+    int64_t rows, cols;   /* matrix size in entries                     */
+    int64_t ld;           /* words between column blocks, >= rows       */
+} gf2_mat;
+
+/* Human-readable text for a status code (static storage, never NULL). */
+const char *gf2_status_string(int status);
+
+/* Library ABI version (increments on incompatible changes). */
+int gf2_version(void);
+
+/* Frees the library-owned workspace of the current device (safe to call
+ * when none exists).  Synchronises the device. */
+int gf2_release_workspace(void);
+
+/* ------------------------------------------------------------------------
+ * Product over F2 (Section 1 and Section 6 of the paper; the Four Russians
+ * method M4RM of Section 6 with tables in shared memory).
+ *   C = A*B        (accumulate == 0)
+ *   C = C xor A*B  (accumulate != 0)
+ * A is n x k, B is k x m, C is n x m (all column blocks, device memory,
+ * owned by the caller).  C must not alias A or B.  Exact: every result bit
+ * is the parity of the AND of a row of A and a column of B.
+ * Errors: GF2_ERR_ARG (NULL), GF2_ERR_SHAPE (A.cols != B.rows, C not n x m,
+ * ld < rows), GF2_ERR_PADDING, GF2_ERR_NOMEM, GF2_ERR_CUDA.
+ */
+size_t gf2_mmm_workspace_bytes(int64_t n, int64_t k, int64_t m);
+int gf2_mmm(const gf2_mat *A, const gf2_mat *B, gf2_mat *C, int accumulate, unsigned flags,
+            void *workspace, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Decomposition P*A = L*E (Section 4, Lemma 4.1 of the paper: block
+ * elimination with pseudo-inverse Z, Procedure buildZ for the row
+ * permutation, Schur-complement update A(j+1) = E xor Y C by M4RM, eq. (Aj)).
+ * A is n x m and is not modified.  With r = rank(A) and k = min(n, m):
+ *   perm    int32[n], device: row i of P*A is row perm[i] of A.  The pivot
+ *           rule is the paper's: within each column block, bit by bit, the
+ *           first row (in the current order) that satisfies the
+ *           non-singularity condition (eq. cond:nonsing:Bk) is exchanged with
+ *           the current pivot slot.
+ *   pivcols int32[k], device: pivcols[t] (t < r) is the column of the t-th
+ *           pivot, increasing (the column rank profile of A); entries t >= r
+ *           are set to -1.
+ *   rank    int64*, device: receives r.
+ *   L       n x k (may be NULL): unit lower trapezoidal, L[t][t] = 1, zero
+ *           above the diagonal and in columns >= r.
+ *   E       k x m (may be NULL): row echelon, row t (t < r) has its leading
+ *           one at pivcols[t]; rows >= r are zero.
+ * The factors are the bit-level PLE form (remark after Lemma 4.1: the block
+ * decomposition with b = 1 is PLE); P, pivcols and r are the same for every
+ * block size.  Exact over F2: P*A = L*E bit for bit.
+ * Errors: GF2_ERR_ARG, GF2_ERR_SHAPE (ld < rows, L or E of the wrong size),
+ * GF2_ERR_PADDING, GF2_ERR_NOMEM, GF2_ERR_UNSUPPORTED (n >= 2^31), GF2_ERR_CUDA.
+ */
+size_t gf2_decompose_workspace_bytes(int64_t n, int64_t m, int want_factors);
+int gf2_decompose(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *rank,
+                  gf2_mat *L, gf2_mat *E, unsigned flags,
+                  void *workspace, size_t ws_bytes, void *stream);
+
+/* Rank of A (n x m) only: the decomposition without storing L and E
+ * (Lemma 4.1: rank(A) = sum of the r_j).  rank_host receives the value; the
+ * call synchronises the stream.  Errors as gf2_decompose. */
+size_t gf2_rank_workspace_bytes(int64_t n, int64_t m);
+int gf2_rank(const gf2_mat *A, int64_t *rank_host, unsigned flags,
+             void *workspace, size_t ws_bytes, void *stream);
+
+/* Same as gf2_decompose, end to end from HOST memory: A_host holds the
+ * column blocks (word (i,q) at A_host[q*lda + i]); the factors are copied
+ * back to the host buffers given (L_host/E_host may be NULL; their column
+ * blocks use ld = n and ld = min(n,m)).  Host buffers should be pinned for
+ * full copy bandwidth.  Device memory comes from the workspace (see
+ * gf2_decompose_host_workspace_bytes).  Synchronises the stream. */
+size_t gf2_decompose_host_workspace_bytes(int64_t n, int64_t m, int want_factors);
+int gf2_decompose_host(int64_t n, int64_t m, const uint64_t *A_host, int64_t lda,
+                       int32_t *perm_host, int32_t *pivcols_host, int64_t *rank_host,
+                       uint64_t *L_host, uint64_t *E_host, unsigned flags,
+                       void *workspace, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Diagnostics (no counterpart in the paper; used by the benchmark).
+ * gf2_launch_count: kernels this library has launched since it was loaded.
+ * gf2_timing_enable(1): from now on every launch is bracketed by CUDA events
+ *   recorded on the launch's own stream, grouped by kernel class
+ *   (GF2_KCLASS_*).  gf2_timing_read synchronises on the last event and
+ *   returns the summed device time in ms and the number of launches of one
+ *   class since the last gf2_timing_reset.  Host-side state is guarded by a
+ *   mutex; the events are created on the current device.
+ */
+#define GF2_KCLASS_PANEL 0   /* pivot selection + pseudo-inverse (buildZ)     */
+#define GF2_KCLASS_LY 1      /* Y = D Z and the L multipliers                */
+#define GF2_KCLASS_UPDATE 2  /* trailing update / product pass (M4RM)        */
+#define GF2_KCLASS_LAYOUT 3  /* layout conversions and final outputs         */
+#define GF2_NUM_KCLASSES 4
+int64_t gf2_launch_count(void);
+int gf2_timing_enable(int on);
+int gf2_timing_reset(void);
+int gf2_timing_read(int kernel_class, double *total_ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GF2_H */

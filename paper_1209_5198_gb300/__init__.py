@@ -1,0 +1,256 @@
+"""GB300 (sm_103a) library for dense linear algebra over F2.
+
+Thin Python binding of the C ABI in include/gf2.h (libgf2.so, built in-tree
+by ``__graft_entry__.build()`` or ``paper_1209_5198_gb300._build.build()``).
+It only marshals arguments: every step of the computation runs in the CUDA
+kernels of the library.  PyTorch provides device memory and streams.
+
+The functions named like the C entry points (``gf2_mmm``, ``gf2_decompose``,
+``gf2_rank``, ``gf2_decompose_host``) take ``Mat`` views of int64 CUDA
+tensors holding column blocks: a tensor of shape (ceil(cols/64), ld), word
+(i, q) at [q, i], bit t = column 64q+t (Section 3 of the paper).
+
+There is no CPU fallback: if libgf2.so is missing or CUDA is unavailable the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgf2.so")
+
+GF2_OK = 0
+GF2_ERR_ARG = 1
+GF2_ERR_SHAPE = 2
+GF2_ERR_PADDING = 3
+GF2_ERR_NOMEM = 4
+GF2_ERR_CUDA = 5
+GF2_ERR_TIMEOUT = 6
+GF2_ERR_UNSUPPORTED = 7
+GF2_NOCHECK = 1
+KCLASS = {"panel": 0, "ly": 1, "update": 2, "layout": 3}
+
+
+class Gf2Error(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+        self.status = status
+
+
+class _CMat(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_void_p), ("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("ld", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Open libgf2.so and declare the C signatures.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    I64 = ctypes.c_int64
+    S = ctypes.c_size_t
+    M = ctypes.POINTER(_CMat)
+    lib.gf2_status_string.restype = ctypes.c_char_p
+    lib.gf2_status_string.argtypes = [ctypes.c_int]
+    lib.gf2_version.restype = ctypes.c_int
+    lib.gf2_release_workspace.restype = ctypes.c_int
+    lib.gf2_mmm_workspace_bytes.restype = S
+    lib.gf2_mmm_workspace_bytes.argtypes = [I64, I64, I64]
+    lib.gf2_mmm.restype = ctypes.c_int
+    lib.gf2_mmm.argtypes = [M, M, M, ctypes.c_int, ctypes.c_uint, P, S, P]
+    lib.gf2_decompose_workspace_bytes.restype = S
+    lib.gf2_decompose_workspace_bytes.argtypes = [I64, I64, ctypes.c_int]
+    lib.gf2_decompose.restype = ctypes.c_int
+    lib.gf2_decompose.argtypes = [M, P, P, P, M, M, ctypes.c_uint, P, S, P]
+    lib.gf2_rank_workspace_bytes.restype = S
+    lib.gf2_rank_workspace_bytes.argtypes = [I64, I64]
+    lib.gf2_rank.restype = ctypes.c_int
+    lib.gf2_rank.argtypes = [M, ctypes.POINTER(I64), ctypes.c_uint, P, S, P]
+    lib.gf2_decompose_host_workspace_bytes.restype = S
+    lib.gf2_decompose_host_workspace_bytes.argtypes = [I64, I64, ctypes.c_int]
+    lib.gf2_decompose_host.restype = ctypes.c_int
+    lib.gf2_decompose_host.argtypes = [I64, I64, P, I64, P, P, P, P, P, ctypes.c_uint, P, S, P]
+    lib.gf2_launch_count.restype = ctypes.c_int64
+    lib.gf2_timing_enable.argtypes = [ctypes.c_int]
+    lib.gf2_timing_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)]
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().gf2_status_string(int(status)).decode()
+
+
+def _check(status: int, where: str) -> None:
+    if status != GF2_OK:
+        raise Gf2Error(status, where)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+class Mat:
+    """A rows x cols matrix over F2 in column blocks on the GPU.
+
+    ``t`` is an int64 tensor of shape (ceil(cols/64), ld), ld >= rows.
+    """
+
+    def __init__(self, t: torch.Tensor, rows: int, cols: int):
+        mu = (cols + 63) // 64
+        if t.dtype != torch.int64 or t.dim() != 2 or t.shape[0] < mu or (mu and t.shape[1] < rows):
+            raise ValueError("expected an int64 tensor of shape (ceil(cols/64), ld >= rows)")
+        if not t.is_contiguous():
+            raise ValueError("column-block tensor must be contiguous")
+        self.t, self.rows, self.cols = t, int(rows), int(cols)
+
+    @property
+    def ld(self) -> int:
+        return int(self.t.shape[1]) if self.t.dim() == 2 and self.t.shape[1] else max(self.rows, 1)
+
+    def c(self) -> _CMat:
+        return _CMat(self.t.data_ptr() if self.t.numel() else None, self.rows, self.cols, self.ld)
+
+    @staticmethod
+    def empty(rows: int, cols: int, device="cuda", ld: int | None = None) -> "Mat":
+        ld = max(rows, 1) if ld is None else ld
+        return Mat(torch.zeros(((cols + 63) // 64, ld), dtype=torch.int64, device=device), rows, cols)
+
+    @staticmethod
+    def from_rowmajor(words: np.ndarray, cols: int, device="cuda", ld: int | None = None) -> "Mat":
+        """Row-major uint64 words (rows, ceil(cols/64)) -> column blocks on the device."""
+        words = np.ascontiguousarray(np.asarray(words, dtype=np.uint64))
+        rows = words.shape[0]
+        ld = max(rows, 1) if ld is None else ld
+        host = np.zeros(((cols + 63) // 64, ld), dtype=np.uint64)
+        host[:, :rows] = words[:, : (cols + 63) // 64].T
+        return Mat(torch.from_numpy(host.view(np.int64)).to(device), rows, cols)
+
+    def to_rowmajor(self) -> np.ndarray:
+        """Column blocks on the device -> row-major uint64 words on the host."""
+        host = self.t.cpu().numpy().view(np.uint64)
+        return np.ascontiguousarray(host[: (self.cols + 63) // 64, : self.rows].T)
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+# --------------------------------------------------------------------- C ABI
+
+def gf2_mmm(A: Mat, B: Mat, C: Mat, accumulate: bool = False, flags: int = 0, workspace=None, stream=None) -> None:
+    """C = A*B (or C ^= A*B) over F2.  Asynchronous on ``stream``."""
+    lib = load()
+    if workspace is None:
+        workspace = _workspace(lib.gf2_mmm_workspace_bytes(A.rows, A.cols, B.cols), C.t.device)
+    a, b, c = A.c(), B.c(), C.c()
+    _check(lib.gf2_mmm(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), int(bool(accumulate)), flags,
+                       workspace.data_ptr(), workspace.numel(), _stream(stream)), "gf2_mmm")
+
+
+def gf2_decompose(A: Mat, perm: torch.Tensor, pivcols: torch.Tensor, rank: torch.Tensor,
+                  L: Mat | None = None, E: Mat | None = None, flags: int = 0, workspace=None, stream=None) -> None:
+    """P*A = L*E: fills perm (int32 [n]), pivcols (int32 [min(n,m)]), rank (int64 [1])
+    and, when given, L (n x min(n,m)) and E (min(n,m) x m)."""
+    lib = load()
+    want = L is not None or E is not None
+    if workspace is None:
+        workspace = _workspace(lib.gf2_decompose_workspace_bytes(A.rows, A.cols, int(want)), A.t.device)
+    a = A.c()
+    l = L.c() if L is not None else None
+    e = E.c() if E is not None else None
+    _check(lib.gf2_decompose(ctypes.byref(a), _ptr(perm), _ptr(pivcols), _ptr(rank),
+                             ctypes.byref(l) if l is not None else None, ctypes.byref(e) if e is not None else None,
+                             flags, workspace.data_ptr(), workspace.numel(), _stream(stream)), "gf2_decompose")
+
+
+def gf2_rank(A: Mat, flags: int = 0, workspace=None, stream=None) -> int:
+    """rank(A); synchronises the stream."""
+    lib = load()
+    if workspace is None:
+        workspace = _workspace(lib.gf2_rank_workspace_bytes(A.rows, A.cols), A.t.device)
+    out = ctypes.c_int64(0)
+    a = A.c()
+    _check(lib.gf2_rank(ctypes.byref(a), ctypes.byref(out), flags, workspace.data_ptr(), workspace.numel(),
+                        _stream(stream)), "gf2_rank")
+    return int(out.value)
+
+
+def gf2_decompose_host(n: int, m: int, A_host: np.ndarray, perm_host: np.ndarray, pivcols_host: np.ndarray,
+                       rank_host: np.ndarray, L_host: np.ndarray | None = None, E_host: np.ndarray | None = None,
+                       flags: int = 0, workspace=None, stream=None, device="cuda") -> None:
+    """End-to-end decomposition from host buffers (column blocks, lda = A_host.shape[1])."""
+    lib = load()
+    want = L_host is not None or E_host is not None
+    if workspace is None:
+        workspace = _workspace(lib.gf2_decompose_host_workspace_bytes(n, m, int(want)), device)
+    ptr = lambda a: None if a is None else a.ctypes.data
+    lda = A_host.shape[1] if A_host.ndim == 2 else max(n, 1)
+    _check(lib.gf2_decompose_host(n, m, ptr(A_host), lda, ptr(perm_host), ptr(pivcols_host), ptr(rank_host),
+                                  ptr(L_host), ptr(E_host), flags, workspace.data_ptr(), workspace.numel(),
+                                  _stream(stream)), "gf2_decompose_host")
+
+
+# ----------------------------------------------------------------- helpers
+
+def decompose(A: Mat, factors: bool = True, flags: int = 0, stream=None) -> dict:
+    """Allocates the outputs and runs gf2_decompose; returns tensors on the device."""
+    n, m = A.rows, A.cols
+    k = min(n, m)
+    dev = A.t.device
+    perm = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    piv = torch.empty(max(k, 1), dtype=torch.int32, device=dev)
+    rank = torch.zeros(1, dtype=torch.int64, device=dev)
+    L = Mat.empty(n, k, dev) if factors else None
+    E = Mat.empty(k, m, dev) if factors else None
+    gf2_decompose(A, perm, piv, rank, L, E, flags=flags, stream=stream)
+    return dict(perm=perm[:n], pivcols=piv[:k], rank=rank, L=L, E=E)
+
+
+def mmm(A: Mat, B: Mat, stream=None) -> Mat:
+    C = Mat.empty(A.rows, B.cols, A.t.device)
+    gf2_mmm(A, B, C, stream=stream)
+    return C
+
+
+# ------------------------------------------------------------- diagnostics
+
+def launch_count() -> int:
+    """Kernels the library has launched since it was loaded."""
+    return int(load().gf2_launch_count())
+
+
+def timing(on: bool) -> None:
+    """Bracket every launch with CUDA events on its stream (grouped by class)."""
+    lib = load()
+    lib.gf2_timing_reset()
+    lib.gf2_timing_enable(int(bool(on)))
+
+
+def timing_read() -> dict:
+    """{class: (total device ms, launches)} since timing was switched on."""
+    lib = load()
+    out = {}
+    for name, cls in KCLASS.items():
+        ms = ctypes.c_double(0)
+        cnt = ctypes.c_int64(0)
+        _check(lib.gf2_timing_read(cls, ctypes.byref(ms), ctypes.byref(cnt)), "gf2_timing_read")
+        out[name] = (ms.value, cnt.value)
+    return out

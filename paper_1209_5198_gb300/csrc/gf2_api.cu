@@ -1,0 +1,439 @@
+// C ABI of the F2 library (declared in include/gf2.h): argument checks,
+// workspace carving and the host-side sequence of kernel launches.
+#include <atomic>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/gf2.h"
+#include "gf2_internal.cuh"
+
+using namespace gf2;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+int64_t words_of(int64_t cols) { return (cols + 63) / 64; }
+int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
+
+uint64_t last_word_mask(int64_t cols)
+{
+    const int rem = (int)(cols % 64);
+    return rem == 0 ? ~0ull : ((1ull << rem) - 1);
+}
+
+// ------------------------------------------------------------ workspace
+struct OwnedWorkspace {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+std::mutex g_ws_mutex;
+std::vector<OwnedWorkspace> g_ws;  // one per device
+uint32_t *g_flag_host = nullptr;   // pinned flag for padding checks
+std::mutex g_flag_mutex;
+
+int owned_workspace(size_t need, void **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GF2_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_ws_mutex);
+    if ((int)g_ws.size() <= dev) g_ws.resize(dev + 1);
+    OwnedWorkspace &w = g_ws[dev];
+    if (w.bytes < need) {
+        if (w.ptr) {
+            if (cudaDeviceSynchronize() != cudaSuccess) return GF2_ERR_CUDA;
+            cudaFree(w.ptr);
+            w.ptr = nullptr;
+            w.bytes = 0;
+        }
+        if (cudaMalloc(&w.ptr, need) != cudaSuccess) {
+            cudaGetLastError();
+            return GF2_ERR_NOMEM;
+        }
+        w.bytes = need;
+    }
+    *out = w.ptr;
+    return GF2_OK;
+}
+
+int get_workspace(void *user, size_t user_bytes, size_t need, void **out)
+{
+    if (user) {
+        if (user_bytes < need) return GF2_ERR_NOMEM;
+        *out = user;
+        return GF2_OK;
+    }
+    if (need == 0) {
+        *out = nullptr;
+        return GF2_OK;
+    }
+    return owned_workspace(need, out);
+}
+
+// Reads the device flag back (synchronising the stream); GF2_ERR_PADDING if set.
+int check_flag(const uint32_t *flag_dev, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lock(g_flag_mutex);
+    if (!g_flag_host) {
+        if (cudaHostAlloc(&g_flag_host, sizeof(uint32_t), cudaHostAllocDefault) != cudaSuccess) return GF2_ERR_CUDA;
+    }
+    if (cudaMemcpyAsync(g_flag_host, flag_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return GF2_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return GF2_ERR_CUDA;
+    return *g_flag_host ? GF2_ERR_PADDING : GF2_OK;
+}
+
+bool mat_ok(const gf2_mat *M)
+{
+    return M && M->rows >= 0 && M->cols >= 0 && (M->rows == 0 || M->cols == 0 || (M->w && M->ld >= M->rows));
+}
+
+#define CK(call)                                  \
+    do {                                          \
+        if ((call) != cudaSuccess) return GF2_ERR_CUDA; \
+    } while (0)
+
+// ------------------------------------------------------------ diagnostics
+std::atomic<int64_t> g_launches{0};
+std::atomic<bool> g_timing{false};
+std::mutex g_timing_mutex;
+struct TimedLaunch {
+    int cls;
+    cudaEvent_t a, b;
+};
+std::vector<TimedLaunch> g_timed;         // recorded since the last reset
+std::vector<cudaEvent_t> g_event_pool;    // free events
+
+cudaEvent_t take_event()
+{
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Runs one launch; counts it and, when timing is on, brackets it with events.
+template <class F>
+cudaError_t launch(int cls, cudaStream_t s, F &&f)
+{
+    if (!g_timing.load(std::memory_order_relaxed)) {
+        cudaError_t e = f();
+        if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+        return e;
+    }
+    std::lock_guard<std::mutex> lock(g_timing_mutex);
+    TimedLaunch t{cls, take_event(), take_event()};
+    if (!t.a || !t.b) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaEventRecord(t.a, s);
+    if (e == cudaSuccess) e = f();
+    if (e == cudaSuccess) e = cudaEventRecord(t.b, s);
+    if (e != cudaSuccess) return e;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    g_timed.push_back(t);
+    return cudaSuccess;
+}
+#define LAUNCH(cls, expr) CK(launch((cls), s, [&]() { return (expr); }))
+
+// ------------------------------------------------------------ decompose
+struct DecompLayout {
+    int64_t mu, ldw, kmax, ldl;
+    size_t oW, oY, oInfo, oLint, oEint, oFlag, total;
+};
+
+DecompLayout decomp_layout(int64_t n, int64_t m, bool factors)
+{
+    DecompLayout d{};
+    d.mu = words_of(m);
+    d.ldw = round8(d.mu > 0 ? d.mu : 1);
+    d.kmax = n < m ? n : m;
+    d.ldl = words_of(d.kmax) > 0 ? words_of(d.kmax) : 1;
+    size_t o = 0;
+    d.oW = o; o += align_up((size_t)n * d.ldw * 8);
+    d.oY = o; o += align_up((size_t)n * 8);
+    d.oInfo = o; o += align_up((size_t)(d.mu > 0 ? d.mu : 1) * sizeof(PanelInfo));
+    d.oLint = o; if (factors) o += align_up((size_t)n * d.ldl * 8);
+    d.oEint = o; if (factors) o += align_up((size_t)d.kmax * d.ldw * 8);
+    d.oFlag = o; o += kAlign;
+    d.total = o;
+    return d;
+}
+
+int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *rank, gf2_mat *L, gf2_mat *E,
+                   unsigned flags, void *workspace, size_t ws_bytes, cudaStream_t s)
+{
+    if (!mat_ok(A) || !perm || !rank || (flags & ~GF2_NOCHECK)) return GF2_ERR_ARG;
+    const int64_t n = A->rows, m = A->cols;
+    if (n >= (1ll << 31) - 64 || m >= (1ll << 31) - 64) return GF2_ERR_UNSUPPORTED;
+    const int64_t kmax = n < m ? n : m;
+    if (kmax > 0 && !pivcols) return GF2_ERR_ARG;
+    if (L && (!mat_ok(L) || L->rows != n || L->cols != kmax)) return GF2_ERR_SHAPE;
+    if (E && (!mat_ok(E) || E->rows != kmax || E->cols != m)) return GF2_ERR_SHAPE;
+    const bool factors = L || E;
+    const DecompLayout d = decomp_layout(n, m, factors);
+    void *ws = nullptr;
+    int st = get_workspace(workspace, ws_bytes, d.total, &ws);
+    if (st) return st;
+    char *base = static_cast<char *>(ws);
+
+    DecompCtx c{};
+    c.W = reinterpret_cast<uint64_t *>(base + d.oW);
+    c.ldw = d.ldw;
+    c.perm = perm;
+    c.pivcols = pivcols;
+    c.info = reinterpret_cast<PanelInfo *>(base + d.oInfo);
+    c.Y = reinterpret_cast<uint64_t *>(base + d.oY);
+    c.Lint = factors ? reinterpret_cast<uint64_t *>(base + d.oLint) : nullptr;
+    c.ldl = d.ldl;
+    c.Eint = factors ? reinterpret_cast<uint64_t *>(base + d.oEint) : nullptr;
+    c.n = (int32_t)n;
+    c.m = (int32_t)m;
+    c.mu = (int32_t)d.mu;
+    c.kmax = (int32_t)kmax;
+    uint32_t *flag = reinterpret_cast<uint32_t *>(base + d.oFlag);
+
+    if (n == 0 || m == 0) {
+        if (n > 0) LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest(A->w, A->ld > 0 ? A->ld : 1, (int32_t)n, 0, ~0ull, c.W, d.ldw, perm, nullptr, s));
+        CK(cudaMemsetAsync(rank, 0, sizeof(int64_t), s));
+        if (L && n > 0 && L->cols > 0) CK(cudaMemsetAsync(L->w, 0, (size_t)L->ld * words_of(L->cols) * 8, s));
+        return GF2_OK;
+    }
+
+    CK(cudaMemsetAsync(flag, 0, sizeof(uint32_t), s));
+    LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest(A->w, A->ld, (int32_t)n, (int32_t)d.mu, last_word_mask(m), c.W, d.ldw, perm, flag, s));
+    if (!(flags & GF2_NOCHECK)) {
+        st = check_flag(flag, s);
+        if (st) return st;
+    }
+    if (c.Lint) CK(cudaMemsetAsync(c.Lint, 0, (size_t)n * d.ldl * 8, s));
+
+    for (int j = 0; j < c.mu; ++j) {
+        LAUNCH(GF2_KCLASS_PANEL, launch_panel(c, j, s));
+        LAUNCH(GF2_KCLASS_LY, launch_ly(c, j, s));
+        if (j + 1 < c.mu) LAUNCH(GF2_KCLASS_UPDATE, launch_update(c, j, s));
+    }
+    LAUNCH(GF2_KCLASS_LAYOUT, launch_finish_scalars(c, rank, s));
+    if (E) LAUNCH(GF2_KCLASS_LAYOUT, launch_finish_E(c, E->w, E->ld, s));
+    if (L) LAUNCH(GF2_KCLASS_LAYOUT, launch_colblocks_from_rowmajor(c.Lint, c.ldl, perm, (int32_t)n, (int32_t)words_of(kmax), L->w, L->ld, s));
+    return GF2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *gf2_status_string(int status)
+{
+    switch (status) {
+    case GF2_OK: return "ok";
+    case GF2_ERR_ARG: return "invalid argument (null pointer, negative size or unknown flag)";
+    case GF2_ERR_SHAPE: return "inconsistent shapes (inner dimensions, ld < rows, factor sizes, k > 64)";
+    case GF2_ERR_PADDING: return "nonzero bit beyond the last column (padding must be zero)";
+    case GF2_ERR_NOMEM: return "workspace too small or device allocation failed";
+    case GF2_ERR_CUDA: return "a CUDA runtime call failed";
+    case GF2_ERR_TIMEOUT: return "a bounded device-side wait gave up";
+    case GF2_ERR_UNSUPPORTED: return "size not supported by this build";
+    default: return "unknown status";
+    }
+}
+
+int gf2_version(void) { return 1; }
+
+int gf2_release_workspace(void)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GF2_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_ws_mutex);
+    if ((int)g_ws.size() > dev && g_ws[dev].ptr) {
+        if (cudaDeviceSynchronize() != cudaSuccess) return GF2_ERR_CUDA;
+        cudaFree(g_ws[dev].ptr);
+        g_ws[dev] = OwnedWorkspace{};
+    }
+    return GF2_OK;
+}
+
+size_t gf2_decompose_workspace_bytes(int64_t n, int64_t m, int want_factors)
+{
+    if (n < 0 || m < 0) return 0;
+    return decomp_layout(n, m, want_factors != 0).total;
+}
+
+int gf2_decompose(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *rank, gf2_mat *L, gf2_mat *E,
+                  unsigned flags, void *workspace, size_t ws_bytes, void *stream)
+{
+    return decompose_impl(A, perm, pivcols, rank, L, E, flags, workspace, ws_bytes,
+                          static_cast<cudaStream_t>(stream));
+}
+
+size_t gf2_rank_workspace_bytes(int64_t n, int64_t m)
+{
+    if (n < 0 || m < 0) return 0;
+    const int64_t kmax = n < m ? n : m;
+    return gf2_decompose_workspace_bytes(n, m, 0) + align_up((size_t)(n > 0 ? n : 1) * 4) +
+           align_up((size_t)(kmax > 0 ? kmax : 1) * 4) + kAlign;
+}
+
+int gf2_rank(const gf2_mat *A, int64_t *rank_host, unsigned flags, void *workspace, size_t ws_bytes, void *stream)
+{
+    if (!A || !rank_host) return GF2_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t n = A->rows, m = A->cols;
+    const int64_t kmax = n < m ? n : m;
+    // perm, pivcols and the rank live in a small tail of the workspace
+    const size_t dec = gf2_decompose_workspace_bytes(n, m, 0);
+    const size_t extra = align_up((size_t)(n > 0 ? n : 1) * 4) + align_up((size_t)(kmax > 0 ? kmax : 1) * 4) + kAlign;
+    void *ws = nullptr;
+    int st = get_workspace(workspace, ws_bytes, gf2_rank_workspace_bytes(n, m), &ws);
+    if (st) return st;
+    char *base = static_cast<char *>(ws);
+    int32_t *perm = reinterpret_cast<int32_t *>(base + dec);
+    int32_t *piv = reinterpret_cast<int32_t *>(base + dec + align_up((size_t)(n > 0 ? n : 1) * 4));
+    int64_t *rk = reinterpret_cast<int64_t *>(base + dec + extra - kAlign);
+    st = decompose_impl(A, perm, piv, rk, nullptr, nullptr, flags, base, dec, s);
+    if (st) return st;
+    CK(cudaMemcpyAsync(rank_host, rk, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return GF2_OK;
+}
+
+size_t gf2_decompose_host_workspace_bytes(int64_t n, int64_t m, int want_factors)
+{
+    if (n < 0 || m < 0) return 0;
+    const int64_t mu = words_of(m), kmax = n < m ? n : m;
+    size_t t = align_up((size_t)n * mu * 8) + align_up((size_t)n * 4) + align_up((size_t)kmax * 4) + kAlign;
+    if (want_factors) t += align_up((size_t)words_of(kmax) * n * 8) + align_up((size_t)mu * kmax * 8);
+    return t + gf2_decompose_workspace_bytes(n, m, want_factors);
+}
+
+int gf2_decompose_host(int64_t n, int64_t m, const uint64_t *A_host, int64_t lda, int32_t *perm_host,
+                       int32_t *pivcols_host, int64_t *rank_host, uint64_t *L_host, uint64_t *E_host,
+                       unsigned flags, void *workspace, size_t ws_bytes, void *stream)
+{
+    if (n < 0 || m < 0 || !perm_host || !rank_host) return GF2_ERR_ARG;
+    if (n > 0 && m > 0 && (!A_host || lda < n)) return GF2_ERR_SHAPE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t mu = words_of(m), kmax = n < m ? n : m, lw = words_of(kmax);
+    const bool factors = L_host || E_host;
+    const size_t need = gf2_decompose_host_workspace_bytes(n, m, factors);
+    void *ws = nullptr;
+    int st = get_workspace(workspace, ws_bytes, need, &ws);
+    if (st) return st;
+    char *p = static_cast<char *>(ws);
+    uint64_t *Ad = reinterpret_cast<uint64_t *>(p); p += align_up((size_t)n * mu * 8);
+    int32_t *permd = reinterpret_cast<int32_t *>(p); p += align_up((size_t)n * 4);
+    int32_t *pivd = reinterpret_cast<int32_t *>(p); p += align_up((size_t)kmax * 4);
+    int64_t *rkd = reinterpret_cast<int64_t *>(p); p += kAlign;
+    uint64_t *Ld = nullptr, *Ed = nullptr;
+    if (factors) {
+        Ld = reinterpret_cast<uint64_t *>(p); p += align_up((size_t)lw * n * 8);
+        Ed = reinterpret_cast<uint64_t *>(p); p += align_up((size_t)mu * kmax * 8);
+    }
+    const size_t dec = gf2_decompose_workspace_bytes(n, m, factors);
+    if (n > 0 && mu > 0) {
+        if (lda == n) CK(cudaMemcpyAsync(Ad, A_host, (size_t)n * mu * 8, cudaMemcpyHostToDevice, s));
+        else CK(cudaMemcpy2DAsync(Ad, (size_t)n * 8, A_host, (size_t)lda * 8, (size_t)n * 8, (size_t)mu,
+                                  cudaMemcpyHostToDevice, s));
+    }
+    gf2_mat A{Ad, n, m, n > 0 ? n : 1};
+    gf2_mat L{Ld, n, kmax, n > 0 ? n : 1};
+    gf2_mat E{Ed, kmax, m, kmax > 0 ? kmax : 1};
+    st = decompose_impl(&A, permd, pivd, rkd, factors ? &L : nullptr, factors ? &E : nullptr, flags, p, dec, s);
+    if (st) return st;
+    CK(cudaMemcpyAsync(rank_host, rkd, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (n > 0) CK(cudaMemcpyAsync(perm_host, permd, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    if (kmax > 0 && pivcols_host) CK(cudaMemcpyAsync(pivcols_host, pivd, (size_t)kmax * 4, cudaMemcpyDeviceToHost, s));
+    if (L_host && lw > 0) CK(cudaMemcpyAsync(L_host, Ld, (size_t)lw * n * 8, cudaMemcpyDeviceToHost, s));
+    if (E_host && kmax > 0) CK(cudaMemcpyAsync(E_host, Ed, (size_t)mu * kmax * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return GF2_OK;
+}
+
+// ------------------------------------------------------------ product
+size_t gf2_mmm_workspace_bytes(int64_t n, int64_t k, int64_t m)
+{
+    if (n < 0 || k < 0 || m < 0) return 0;
+    const int64_t kw = words_of(k), mw = words_of(m);
+    return align_up((size_t)n * (kw > 0 ? kw : 1) * 8) + align_up((size_t)k * (mw > 0 ? mw : 1) * 8) +
+           align_up((size_t)n * round8(mw > 0 ? mw : 1) * 8) + kAlign;
+}
+
+int gf2_mmm(const gf2_mat *A, const gf2_mat *B, gf2_mat *C, int accumulate, unsigned flags, void *workspace,
+            size_t ws_bytes, void *stream)
+{
+    if (!mat_ok(A) || !mat_ok(B) || !mat_ok(C) || (flags & ~GF2_NOCHECK)) return GF2_ERR_ARG;
+    if (A->cols != B->rows || C->rows != A->rows || C->cols != B->cols) return GF2_ERR_SHAPE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t n = A->rows, k = A->cols, m = B->cols;
+    if (n >= (1ll << 31) || k >= (1ll << 31) || m >= (1ll << 31)) return GF2_ERR_UNSUPPORTED;
+    if (n == 0 || m == 0) return GF2_OK;
+    const int64_t kw = words_of(k), mw = words_of(m), ldc = round8(mw);
+    if (k == 0) {
+        if (!accumulate) CK(cudaMemsetAsync(C->w, 0, (size_t)C->ld * mw * 8, s));
+        return GF2_OK;
+    }
+    void *ws = nullptr;
+    int st = get_workspace(workspace, ws_bytes, gf2_mmm_workspace_bytes(n, k, m), &ws);
+    if (st) return st;
+    char *p = static_cast<char *>(ws);
+    uint64_t *Ar = reinterpret_cast<uint64_t *>(p); p += align_up((size_t)n * kw * 8);
+    uint64_t *Br = reinterpret_cast<uint64_t *>(p); p += align_up((size_t)k * mw * 8);
+    uint64_t *Cr = reinterpret_cast<uint64_t *>(p); p += align_up((size_t)n * ldc * 8);
+    uint32_t *flag = reinterpret_cast<uint32_t *>(p);
+    CK(cudaMemsetAsync(flag, 0, sizeof(uint32_t), s));
+    LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest(A->w, A->ld, (int32_t)n, (int32_t)kw, last_word_mask(k), Ar, kw, nullptr, flag, s));
+    LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest(B->w, B->ld, (int32_t)k, (int32_t)mw, last_word_mask(m), Br, mw, nullptr, flag, s));
+    if (accumulate) LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest(C->w, C->ld, (int32_t)n, (int32_t)mw, last_word_mask(m), Cr, ldc, nullptr, flag, s));
+    else CK(cudaMemsetAsync(Cr, 0, (size_t)n * ldc * 8, s));
+    if (!(flags & GF2_NOCHECK)) {
+        st = check_flag(flag, s);
+        if (st) return st;
+    }
+    MmmCtx c{Ar, kw, Br, mw, Cr, ldc, (int32_t)n, (int32_t)k};
+    for (int kb = 0; kb < kw; ++kb) LAUNCH(GF2_KCLASS_UPDATE, launch_mmm_pass(c, kb, (int)mw, s));
+    LAUNCH(GF2_KCLASS_LAYOUT, launch_colblocks_from_rowmajor(Cr, ldc, nullptr, (int32_t)n, (int32_t)mw, C->w, C->ld, s));
+    return GF2_OK;
+}
+
+int64_t gf2_launch_count(void) { return g_launches.load(); }
+
+int gf2_timing_enable(int on)
+{
+    g_timing.store(on != 0);
+    return GF2_OK;
+}
+
+int gf2_timing_reset(void)
+{
+    std::lock_guard<std::mutex> lock(g_timing_mutex);
+    for (auto &t : g_timed) {
+        g_event_pool.push_back(t.a);
+        g_event_pool.push_back(t.b);
+    }
+    g_timed.clear();
+    return GF2_OK;
+}
+
+int gf2_timing_read(int kernel_class, double *total_ms, int64_t *launches)
+{
+    if (!total_ms || !launches || kernel_class < 0 || kernel_class >= GF2_NUM_KCLASSES) return GF2_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_timing_mutex);
+    double sum = 0;
+    int64_t cnt = 0;
+    for (auto &t : g_timed) {
+        if (t.cls != kernel_class) continue;
+        if (cudaEventSynchronize(t.b) != cudaSuccess) return GF2_ERR_CUDA;
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, t.a, t.b) != cudaSuccess) return GF2_ERR_CUDA;
+        sum += ms;
+        ++cnt;
+    }
+    *total_ms = sum;
+    *launches = cnt;
+    return GF2_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// Internal declarations shared by the CUDA translation units of the F2
+// library.  Nothing here is part of the C ABI (include/gf2.h is).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gf2 {
+
+// Column words handled by one CTA of the trailing update (64 bytes of a row).
+constexpr int kTileWords = 8;
+// Four Russians table width c (Section 6 of the paper): a 64-bit multiplier
+// is split into 8 chunks of 8 bits, each looked up in a 256-entry table.
+constexpr int kTableBits = 8;
+constexpr int kNumTables = 64 / kTableBits;
+constexpr int kUpdateThreads = 256;
+constexpr int kPanelThreads = 256;
+
+// Everything one column block ("panel" j, 64 columns) of the decomposition
+// leaves for the kernels that follow it.  Coordinates: the r pivot rows of
+// the panel are B_0..B_{r-1} (raw panel words, in pivot order) and their
+// echelon forms E_0..E_{r-1} (E_s = B_s reduced by E_0..E_{s-1}).
+//   For any panel word d in the row space of the panel:
+//     y(d)      = XOR_{bits p of d} Zp[p]   -> d = sum_s y_s B_s   (Y = D Z)
+//     lambda(d) = XOR_{bits p of d} Comp[p] -> d = sum_s lambda_s E_s
+//   Tinv[s] = coordinates of E_s in the B_s   (row s of T^-1)
+//   T[s]    = coordinates of B_s in the E_s   (row s of T, unit lower)
+struct PanelInfo {
+    int32_t R;          // first pivot position of the panel (R_j)
+    int32_t r;          // pivots found in the panel (r_j)
+    int32_t pivbit[64]; // bit (column within the panel) of pivot s
+    uint64_t Zp[64];
+    uint64_t Comp[64];
+    uint64_t Tinv[64];
+    uint64_t T[64];
+    uint64_t Erow[64];  // E_s restricted to the panel's 64 columns
+};
+
+// Device state of one decomposition.  W is a row-major copy of A: storage
+// row i is row i of A and never moves; perm maps positions to storage rows
+// (row i of P*A is storage row perm[i]), so a row exchange is an exchange of
+// two perm entries and no data moves.
+struct DecompCtx {
+    uint64_t *W;
+    int64_t ldw;        // words per row of W, a multiple of kTileWords
+    int32_t *perm;      // [n] position -> storage row (the output perm)
+    int32_t *pivcols;   // [k]
+    PanelInfo *info;    // [mu]
+    uint64_t *Y;        // [n] per position: y of the current panel
+    uint64_t *Lint;     // [n x ldl] per storage row, or null (rank only)
+    int64_t ldl;
+    uint64_t *Eint;     // [k x ldw] per pivot index, or null
+    int32_t n, m, mu, kmax;
+};
+
+// Row-major operands of a product C ^= A * B over F2 for one 64-row slice
+// of B (k-block kb): the multiplier of row i is word kb of A's row i.
+struct MmmCtx {
+    const uint64_t *A; int64_t lda;   // row-major, n x ceil(k/64)
+    const uint64_t *B; int64_t ldb;   // row-major, k x ceil(m/64)
+    uint64_t *C; int64_t ldc;         // row-major, n x ldc (multiple of 8)
+    int32_t n, k;
+};
+
+// ---- launchers (each returns the cudaError_t of its launch)
+cudaError_t launch_ingest(const uint64_t *A, int64_t lda, int32_t n, int32_t mu, uint64_t last_mask,
+                          uint64_t *W, int64_t ldw, int32_t *perm_identity, uint32_t *err,
+                          cudaStream_t s);
+cudaError_t launch_colblocks_from_rowmajor(const uint64_t *R, int64_t ldr, const int32_t *row_of,
+                                           int32_t rows, int32_t words, uint64_t *out, int64_t ldo,
+                                           cudaStream_t s);
+cudaError_t launch_finish_E(const DecompCtx &c, uint64_t *E, int64_t lde, cudaStream_t s);
+cudaError_t launch_finish_scalars(const DecompCtx &c, int64_t *rank, cudaStream_t s);
+cudaError_t launch_panel(const DecompCtx &c, int j, cudaStream_t s);
+cudaError_t launch_ly(const DecompCtx &c, int j, cudaStream_t s);
+cudaError_t launch_update(const DecompCtx &c, int j, cudaStream_t s);
+cudaError_t launch_mmm_pass(const MmmCtx &c, int kb, int m_words, cudaStream_t s);
+
+}  // namespace gf2

@@ -1,0 +1,61 @@
+"""The C-ABI library loads and exports every entry point include/gf2.h
+declares; host-only entry points answer without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gf2.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gf2_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1209_5198_gb300 import _build
+    _build.build()
+    import paper_1209_5198_gb300 as g
+    return g.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in gf2.h but not exported"
+
+
+def test_host_only_entry_points(lib):
+    assert lib.gf2_version() >= 1
+    assert b"padding" in lib.gf2_status_string(3)
+    assert lib.gf2_status_string(999) == b"unknown status"
+    n = m = 32768
+    ws = lib.gf2_decompose_workspace_bytes(n, m, 1)
+    assert ws >= 3 * n * (m // 64) * 8  # working copy + L + E, row-major
+    assert lib.gf2_decompose_workspace_bytes(n, m, 0) < ws
+    assert lib.gf2_rank_workspace_bytes(n, m) >= lib.gf2_decompose_workspace_bytes(n, m, 0)
+    assert lib.gf2_mmm_workspace_bytes(1000, 2000, 3000) >= 8 * (1000 * 32 + 2000 * 47 + 1000 * 47)
+    assert lib.gf2_decompose_workspace_bytes(-1, 5, 0) == 0
+
+
+def test_argument_errors_without_gpu(lib):
+    import paper_1209_5198_gb300 as g
+    # null matrix descriptor / outputs: rejected before any CUDA call
+    assert lib.gf2_decompose(None, None, None, None, None, None, 0, None, 0, None) == g.GF2_ERR_ARG
+    assert lib.gf2_mmm(None, None, None, 0, 0, None, 0, None) == g.GF2_ERR_ARG
+    a = g._CMat(None, 10, 10, 5)  # ld < rows
+    assert lib.gf2_mmm(ctypes.byref(a), ctypes.byref(a), ctypes.byref(a), 0, 0, None, 0, None) == g.GF2_ERR_ARG
+    b = g._CMat(1, 10, 20, 10)
+    c = g._CMat(2, 10, 20, 10)
+    d = g._CMat(3, 30, 20, 30)
+    # inner dimensions differ (A is 10 x 20, B is 10 x 20)
+    assert lib.gf2_mmm(ctypes.byref(b), ctypes.byref(c), ctypes.byref(d), 0, 0, None, 0, None) == g.GF2_ERR_SHAPE
+    # unknown flag
+    assert lib.gf2_decompose(ctypes.byref(b), ctypes.c_void_p(8), ctypes.c_void_p(8), ctypes.c_void_p(8),
+                             None, None, 0x80, None, 0, None) == g.GF2_ERR_ARG
