@@ -139,8 +139,8 @@ int gf2_decompose_host(int64_t n, int64_t m, const uint64_t *A_host, int64_t lda
  *   mutex; the events are created on the current device.
  */
 #define GF2_KCLASS_PANEL 0   /* pivot selection + pseudo-inverse (buildZ)     */
-#define GF2_KCLASS_LY 1      /* Y = D Z and the L multipliers                */
-#define GF2_KCLASS_UPDATE 2  /* trailing update / product pass (M4RM)        */
+#define GF2_KCLASS_NEXT 1    /* Y = D Z, L multipliers, next column tile     */
+#define GF2_KCLASS_UPDATE 2  /* wide trailing update / product pass (M4RM)   */
 #define GF2_KCLASS_LAYOUT 3  /* layout conversions and final outputs         */
 #define GF2_NUM_KCLASSES 4
 int64_t gf2_launch_count(void);

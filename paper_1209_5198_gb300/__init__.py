@@ -33,7 +33,7 @@ GF2_ERR_CUDA = 5
 GF2_ERR_TIMEOUT = 6
 GF2_ERR_UNSUPPORTED = 7
 GF2_NOCHECK = 1
-KCLASS = {"panel": 0, "ly": 1, "update": 2, "layout": 3}
+KCLASS = {"panel": 0, "next": 1, "update": 2, "layout": 3}
 
 
 class Gf2Error(RuntimeError):

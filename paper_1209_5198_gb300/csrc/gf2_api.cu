@@ -138,11 +138,44 @@ cudaError_t launch(int cls, cudaStream_t s, F &&f)
     return cudaSuccess;
 }
 #define LAUNCH(cls, expr) CK(launch((cls), s, [&]() { return (expr); }))
+#define LAUNCH_ON(cls, strm, expr) CK(launch((cls), (strm), [&]() { return (expr); }))
+
+// ------------------------------------------------------------ side stream
+// Per device: a high-priority non-blocking stream for the panel chain and a
+// pool of events for the cross-stream dependencies.  Enqueueing a
+// decomposition holds g_side_mutex, so the events are used by one call at a
+// time (a wait captures the event's state when it is enqueued).
+struct SideResources {
+    cudaStream_t stream = nullptr;
+    std::vector<cudaEvent_t> events;
+};
+std::mutex g_side_mutex;
+std::vector<SideResources> g_side;
+
+int side_resources(int nevents, SideResources **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GF2_ERR_CUDA;
+    if ((int)g_side.size() <= dev) g_side.resize(dev + 1);
+    SideResources &r = g_side[dev];
+    if (!r.stream) {
+        int lo = 0, hi = 0;
+        if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) return GF2_ERR_CUDA;
+        if (cudaStreamCreateWithPriority(&r.stream, cudaStreamNonBlocking, hi) != cudaSuccess) return GF2_ERR_CUDA;
+    }
+    while ((int)r.events.size() < nevents) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return GF2_ERR_CUDA;
+        r.events.push_back(e);
+    }
+    *out = &r;
+    return GF2_OK;
+}
 
 // ------------------------------------------------------------ decompose
 struct DecompLayout {
     int64_t mu, ldw, kmax, ldl;
-    size_t oW, oY, oInfo, oLint, oEint, oFlag, total;
+    size_t oW, oY, oPP, oInfo, oLint, oEint, oFlag, total;
 };
 
 DecompLayout decomp_layout(int64_t n, int64_t m, bool factors)
@@ -154,7 +187,8 @@ DecompLayout decomp_layout(int64_t n, int64_t m, bool factors)
     d.ldl = words_of(d.kmax) > 0 ? words_of(d.kmax) : 1;
     size_t o = 0;
     d.oW = o; o += align_up((size_t)n * d.ldw * 8);
-    d.oY = o; o += align_up((size_t)n * 8);
+    d.oY = o; o += align_up((size_t)n * 2 * 8);
+    d.oPP = o; o += align_up((size_t)n * 4);
     d.oInfo = o; o += align_up((size_t)(d.mu > 0 ? d.mu : 1) * sizeof(PanelInfo));
     d.oLint = o; if (factors) o += align_up((size_t)n * d.ldl * 8);
     d.oEint = o; if (factors) o += align_up((size_t)d.kmax * d.ldw * 8);
@@ -187,6 +221,7 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
     c.pivcols = pivcols;
     c.info = reinterpret_cast<PanelInfo *>(base + d.oInfo);
     c.Y = reinterpret_cast<uint64_t *>(base + d.oY);
+    c.pivpanel = reinterpret_cast<int32_t *>(base + d.oPP);
     c.Lint = factors ? reinterpret_cast<uint64_t *>(base + d.oLint) : nullptr;
     c.ldl = d.ldl;
     c.Eint = factors ? reinterpret_cast<uint64_t *>(base + d.oEint) : nullptr;
@@ -197,25 +232,52 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
     uint32_t *flag = reinterpret_cast<uint32_t *>(base + d.oFlag);
 
     if (n == 0 || m == 0) {
-        if (n > 0) LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest(A->w, A->ld > 0 ? A->ld : 1, (int32_t)n, 0, ~0ull, c.W, d.ldw, perm, nullptr, s));
+        if (n > 0) LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest(A->w, A->ld > 0 ? A->ld : 1, (int32_t)n, 0, ~0ull, c.W, d.ldw, perm, nullptr, nullptr, s));
         CK(cudaMemsetAsync(rank, 0, sizeof(int64_t), s));
         if (L && n > 0 && L->cols > 0) CK(cudaMemsetAsync(L->w, 0, (size_t)L->ld * words_of(L->cols) * 8, s));
         return GF2_OK;
     }
 
     CK(cudaMemsetAsync(flag, 0, sizeof(uint32_t), s));
-    LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest(A->w, A->ld, (int32_t)n, (int32_t)d.mu, last_word_mask(m), c.W, d.ldw, perm, flag, s));
+    LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest(A->w, A->ld, (int32_t)n, (int32_t)d.mu, last_word_mask(m), c.W, d.ldw, perm, c.pivpanel, flag, s));
     if (!(flags & GF2_NOCHECK)) {
         st = check_flag(flag, s);
         if (st) return st;
     }
     if (c.Lint) CK(cudaMemsetAsync(c.Lint, 0, (size_t)n * d.ldl * 8, s));
 
+    // Panel chain (pivot selection, next column tile, Y and L) on a side
+    // stream P, the wide trailing updates on the caller's stream s:
+    //   next(j) waits for rest(j-2) (it reuses Y[j % 2]) and, when column
+    //   j+1 opens a new tile, for rest(j-1) (which updated that tile);
+    //   rest(j) waits for next(j) (its Y).
+    std::lock_guard<std::mutex> lock(g_side_mutex);
+    SideResources *side = nullptr;
+    st = side_resources(2 * c.mu + 2, &side);
+    if (st) return st;
+    cudaStream_t P = side->stream;
+    cudaEvent_t *evNext = side->events.data(), *evRest = evNext + c.mu;
+    cudaEvent_t evFork = evRest[c.mu], evJoin = evRest[c.mu + 1];
+    std::vector<char> rest_launched(c.mu, 0);
+    CK(cudaEventRecord(evFork, s));
+    CK(cudaStreamWaitEvent(P, evFork, 0));
     for (int j = 0; j < c.mu; ++j) {
-        LAUNCH(GF2_KCLASS_PANEL, launch_panel(c, j, s));
-        LAUNCH(GF2_KCLASS_LY, launch_ly(c, j, s));
-        if (j + 1 < c.mu) LAUNCH(GF2_KCLASS_UPDATE, launch_update(c, j, s));
+        LAUNCH_ON(GF2_KCLASS_PANEL, P, launch_panel(c, j, P));
+        if (j >= 2 && rest_launched[j - 2]) CK(cudaStreamWaitEvent(P, evRest[j - 2], 0));
+        if (j >= 1 && (j + 1) % kTileWords == 0 && rest_launched[j - 1]) CK(cudaStreamWaitEvent(P, evRest[j - 1], 0));
+        LAUNCH_ON(GF2_KCLASS_NEXT, P, launch_next(c, j, P));
+        int tile_first = 0;
+        if (rest_tiles(c, j, &tile_first) > 0) {
+            CK(cudaEventRecord(evNext[j], P));
+            CK(cudaStreamWaitEvent(s, evNext[j], 0));
+            int est = (int)(n - 64 * (int64_t)(j + 1));
+            LAUNCH(GF2_KCLASS_UPDATE, launch_rest(c, j, est, s));
+            CK(cudaEventRecord(evRest[j], s));
+            rest_launched[j] = 1;
+        }
     }
+    CK(cudaEventRecord(evJoin, P));
+    CK(cudaStreamWaitEvent(s, evJoin, 0));
     LAUNCH(GF2_KCLASS_LAYOUT, launch_finish_scalars(c, rank, s));
     if (E) LAUNCH(GF2_KCLASS_LAYOUT, launch_finish_E(c, E->w, E->ld, s));
     if (L) LAUNCH(GF2_KCLASS_LAYOUT, launch_colblocks_from_rowmajor(c.Lint, c.ldl, perm, (int32_t)n, (int32_t)words_of(kmax), L->w, L->ld, s));
@@ -384,9 +446,9 @@ int gf2_mmm(const gf2_mat *A, const gf2_mat *B, gf2_mat *C, int accumulate, unsi
     uint64_t *Cr = reinterpret_cast<uint64_t *>(p); p += align_up((size_t)n * ldc * 8);
     uint32_t *flag = reinterpret_cast<uint32_t *>(p);
     CK(cudaMemsetAsync(flag, 0, sizeof(uint32_t), s));
-    LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest(A->w, A->ld, (int32_t)n, (int32_t)kw, last_word_mask(k), Ar, kw, nullptr, flag, s));
-    LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest(B->w, B->ld, (int32_t)k, (int32_t)mw, last_word_mask(m), Br, mw, nullptr, flag, s));
-    if (accumulate) LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest(C->w, C->ld, (int32_t)n, (int32_t)mw, last_word_mask(m), Cr, ldc, nullptr, flag, s));
+    LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest(A->w, A->ld, (int32_t)n, (int32_t)kw, last_word_mask(k), Ar, kw, nullptr, nullptr, flag, s));
+    LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest(B->w, B->ld, (int32_t)k, (int32_t)mw, last_word_mask(m), Br, mw, nullptr, nullptr, flag, s));
+    if (accumulate) LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest(C->w, C->ld, (int32_t)n, (int32_t)mw, last_word_mask(m), Cr, ldc, nullptr, nullptr, flag, s));
     else CK(cudaMemsetAsync(Cr, 0, (size_t)n * ldc * 8, s));
     if (!(flags & GF2_NOCHECK)) {
         st = check_flag(flag, s);

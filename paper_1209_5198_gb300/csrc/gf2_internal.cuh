@@ -13,8 +13,7 @@ constexpr int kTileWords = 8;
 // is split into 8 chunks of 8 bits, each looked up in a 256-entry table.
 constexpr int kTableBits = 8;
 constexpr int kNumTables = 64 / kTableBits;
-constexpr int kUpdateThreads = 256;
-constexpr int kPanelThreads = 256;
+constexpr int kPanelThreads = 128;
 
 // Everything one column block ("panel" j, 64 columns) of the decomposition
 // leaves for the kernels that follow it.  Coordinates: the r pivot rows of
@@ -46,7 +45,8 @@ struct DecompCtx {
     int32_t *perm;      // [n] position -> storage row (the output perm)
     int32_t *pivcols;   // [k]
     PanelInfo *info;    // [mu]
-    uint64_t *Y;        // [n] per position: y of the current panel
+    uint64_t *Y;        // [2][n] per storage row: y of panel j in Y[j % 2]; 0 for pivot rows
+    int32_t *pivpanel;  // [n] per storage row: panel where it became a pivot (INT32_MAX: not yet)
     uint64_t *Lint;     // [n x ldl] per storage row, or null (rank only)
     int64_t ldl;
     uint64_t *Eint;     // [k x ldw] per pivot index, or null
@@ -64,16 +64,17 @@ struct MmmCtx {
 
 // ---- launchers (each returns the cudaError_t of its launch)
 cudaError_t launch_ingest(const uint64_t *A, int64_t lda, int32_t n, int32_t mu, uint64_t last_mask,
-                          uint64_t *W, int64_t ldw, int32_t *perm_identity, uint32_t *err,
-                          cudaStream_t s);
+                          uint64_t *W, int64_t ldw, int32_t *perm_identity, int32_t *pivpanel_init,
+                          uint32_t *err, cudaStream_t s);
 cudaError_t launch_colblocks_from_rowmajor(const uint64_t *R, int64_t ldr, const int32_t *row_of,
                                            int32_t rows, int32_t words, uint64_t *out, int64_t ldo,
                                            cudaStream_t s);
 cudaError_t launch_finish_E(const DecompCtx &c, uint64_t *E, int64_t lde, cudaStream_t s);
 cudaError_t launch_finish_scalars(const DecompCtx &c, int64_t *rank, cudaStream_t s);
 cudaError_t launch_panel(const DecompCtx &c, int j, cudaStream_t s);
-cudaError_t launch_ly(const DecompCtx &c, int j, cudaStream_t s);
-cudaError_t launch_update(const DecompCtx &c, int j, cudaStream_t s);
+cudaError_t launch_next(const DecompCtx &c, int j, cudaStream_t s);
+cudaError_t launch_rest(const DecompCtx &c, int j, int est_active_rows, cudaStream_t s);
+int rest_tiles(const DecompCtx &c, int j, int *tile_first);
 cudaError_t launch_mmm_pass(const MmmCtx &c, int kb, int m_words, cudaStream_t s);
 
 }  // namespace gf2

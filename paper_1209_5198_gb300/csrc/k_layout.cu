@@ -19,7 +19,8 @@ constexpr int kTy = 8;     // threads in y; each thread moves kT / kTy words
 // the last block are checked against last_mask; any violation sets *err.
 __global__ void k_ingest(const uint64_t *__restrict__ A, int64_t lda, int32_t n, int32_t mu,
                          uint64_t last_mask, uint64_t *__restrict__ W, int64_t ldw,
-                         int32_t *__restrict__ perm, uint32_t *__restrict__ err)
+                         int32_t *__restrict__ perm, int32_t *__restrict__ pivpanel,
+                         uint32_t *__restrict__ err)
 {
     __shared__ uint64_t tile[kT][kT + 1];
     const int i0 = blockIdx.x * kT, q0 = blockIdx.y * kT;
@@ -42,7 +43,10 @@ __global__ void k_ingest(const uint64_t *__restrict__ A, int64_t lda, int32_t n,
         const int i = i0 + ty + k * kTy, q = q0 + tx;
         if (i < n && q < ldw) W[(int64_t)i * ldw + q] = tile[tx][ty + k * kTy];
     }
-    if (perm && blockIdx.y == 0 && ty == 0 && i0 + tx < n) perm[i0 + tx] = i0 + tx;
+    if (blockIdx.y == 0 && ty == 0 && i0 + tx < n) {
+        if (perm) perm[i0 + tx] = i0 + tx;
+        if (pivpanel) pivpanel[i0 + tx] = 0x7fffffff;
+    }
 }
 
 // out (column blocks, `rows` rows, `words` blocks) from row-major R, where
@@ -109,12 +113,12 @@ __global__ void k_finish_scalars(const PanelInfo *__restrict__ last, int32_t *__
 }  // namespace
 
 cudaError_t launch_ingest(const uint64_t *A, int64_t lda, int32_t n, int32_t mu, uint64_t last_mask,
-                          uint64_t *W, int64_t ldw, int32_t *perm_identity, uint32_t *err,
-                          cudaStream_t s)
+                          uint64_t *W, int64_t ldw, int32_t *perm_identity, int32_t *pivpanel_init,
+                          uint32_t *err, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     dim3 grid((n + kT - 1) / kT, (unsigned)((ldw + kT - 1) / kT)), block(kT, kTy);
-    k_ingest<<<grid, block, 0, s>>>(A, lda, n, mu, last_mask, W, ldw, perm_identity, err);
+    k_ingest<<<grid, block, 0, s>>>(A, lda, n, mu, last_mask, W, ldw, perm_identity, pivpanel_init, err);
     return cudaGetLastError();
 }
 

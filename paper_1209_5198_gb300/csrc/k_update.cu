@@ -1,202 +1,221 @@
 // Trailing update A(j+1) = E xor Y C (eq. (Aj) of the paper) by the Method
-// of Four Russians (M4RM, Section 6): the r <= 64 pivot rows C of the panel
-// are combined into 8 tables of 2^8 entries per 8-word column tile (one XOR
-// per entry), and every row of E then takes 8 table lookups and XORs per
-// word, indexed by the 8 bytes of its multiplier y.
+// of Four Russians (M4RM, Section 6): the r <= 64 pivot rows C of panel j
+// are combined, per 8-word column tile, into 64/c tables of 2^c entries (one
+// XOR per entry), and every other row then takes 64/c table lookups and
+// XORs per word, indexed by the c-bit chunks of its multiplier y.
 //
-// GB300 layout choices:
-//   * rows are row-major inside the library, so one row's 8-word tile is 64
-//     contiguous bytes; a warp covers 8 rows x 8 words with 128-bit accesses
-//     (lane = row slot (lane/4) x word pair (lane%4)) -- full sectors, no
-//     re-reads;
-//   * the tables sit in shared memory as [table pair][x][half][8 words]: the
-//     two rows of a quarter-warp (one LDS.128 phase) read tables g and g^1,
-//     which live in opposite 64-byte halves of the bank space, so every
-//     lookup is conflict-free whatever the bytes of y are;
-//   * a CTA owns one column tile and a contiguous chunk of rows, so each
-//     table build (2048 x 8 XORs) is amortised over thousands of rows.
-// The same kernel serves the standalone product C ^= A B (one launch per
-// 64-row slice of B).
+// Two kernels per panel:
+//   k_next  the column tile holding column j+1 (the next panel), plus
+//           y = d Z and lambda = d Comp for every row (d = the row's word in
+//           column j; Y is kept per storage row for k_rest) and the L
+//           multipliers; small, on the critical path of the panel chain.
+//   k_rest  every column tile after that one; persistent (one CTA per SM),
+//           each CTA takes a contiguous range of (tile, row chunk) items and
+//           rebuilds its tables only when the tile changes.
+// Rows are visited in STORAGE order (row-major W, storage row = row of A):
+// the multiplier array is indexed by storage row and is zero for rows that
+// are already pivots, so no position->row indirection sits in the hot loop.
+//
+// GB300 layout choices: one row's 8-word tile is 64 contiguous bytes; a warp
+// covers 8 rows x 8 words with 128-bit accesses (lane = row slot (lane/4) x
+// word pair (lane%4)); the tables sit in shared memory as
+// [table pair][x][half][8 words], and the two rows of a quarter-warp (one
+// 128-bit shared-memory phase) read tables g and g^1, which live in opposite
+// 64-byte halves of the bank space, so lookups are conflict-free for any y.
+// The same tile code serves the standalone product C ^= A B.
 #include "gf2_internal.cuh"
 
 namespace gf2 {
 namespace {
 
-constexpr int kTabWords = kNumTables * 256 * kTileWords;          // 16384 words = 128 KB
-constexpr int kSmemBytes = (kTabWords + 64 * kTileWords) * 8;      // + C rows
+template <int C>
+struct Tabs {
+    static constexpr int K = 64 / C;                 // tables
+    static constexpr int X = 1 << C;                 // entries per table
+    static constexpr int Words = K * X * kTileWords; // shared-memory words
+};
 
 // index (in 8-word entries) of entry x of table g
-__device__ __forceinline__ int tab_entry(int g, int x) { return (((g >> 1) * 256 + x) << 1) | (g & 1); }
+template <int C>
+__device__ __forceinline__ int tab_entry(int g, int x)
+{
+    return ((((g >> 1) << C) + x) << 1) | (g & 1);
+}
 
+// Tables of the 64 x 8-word rows in crow (rows beyond r are zero).
+// Thread -> (word w, table g, sub-range of x); each sub-range walks its low
+// bits in Gray order, one XOR per entry.
+template <int C, int T>
 __device__ __forceinline__ void build_tables(uint64_t *tab, const uint64_t *crow)
 {
-    // warp g builds table g; lane = word w (lane & 7) x quarter qq (lane >> 3);
-    // each quarter fixes the top 2 bits of x and walks the low 6 in Gray order.
-    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-    const int w = lane & 7, qq = lane >> 3;
-    uint64_t cb[8];
+    constexpr int K = Tabs<C>::K, X = Tabs<C>::X;
+    constexpr int PAIRS = K * kTileWords;
+    static_assert(T % PAIRS == 0, "thread count must cover every (table, word)");
+    constexpr int SUBS = T / PAIRS;
+    static_assert(SUBS <= X, "too many threads for this table size");
+    constexpr int Q = X / SUBS;
+    constexpr int LQ = (Q >= 256) ? 8 : (Q >= 128) ? 7 : (Q >= 64) ? 6 : (Q >= 32) ? 5 : (Q >= 16) ? 4 : (Q >= 8) ? 3 : (Q >= 4) ? 2 : (Q >= 2) ? 1 : 0;
+    const int tid = threadIdx.x;
+    const int w = tid % kTileWords, g = (tid / kTileWords) % K, sub = tid / (kTileWords * K);
+    uint64_t cb[C];
 #pragma unroll
-    for (int b = 0; b < 8; ++b) cb[b] = crow[(8 * g + b) * kTileWords + w];
-    uint64_t v = ((qq & 1) ? cb[6] : 0) ^ ((qq & 2) ? cb[7] : 0);
-    tab[tab_entry(g, qq * 64) * kTileWords + w] = v;
+    for (int b = 0; b < C; ++b) cb[b] = crow[(C * g + b) * kTileWords + w];
+    const int x0 = sub * Q;
+    uint64_t v = 0;
 #pragma unroll
-    for (int i = 1; i < 64; ++i) {
-        const int b = (i & 1) ? 0 : (i & 2) ? 1 : (i & 4) ? 2 : (i & 8) ? 3 : (i & 16) ? 4 : 5;
+    for (int b = LQ; b < C; ++b)
+        if ((x0 >> b) & 1) v ^= cb[b];
+    tab[tab_entry<C>(g, x0) * kTileWords + w] = v;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const int b = (i & 1) ? 0 : (i & 2) ? 1 : (i & 4) ? 2 : (i & 8) ? 3 : (i & 16) ? 4 : (i & 32) ? 5 : (i & 64) ? 6 : 7;
         v ^= cb[b];
-        tab[tab_entry(g, qq * 64 + (i ^ (i >> 1))) * kTileWords + w] = v;
+        tab[tab_entry<C>(g, x0 + (i ^ (i >> 1))) * kTileWords + w] = v;
     }
 }
 
-template <bool kDecomp>
-__global__ void __launch_bounds__(kUpdateThreads, 1)
-k_update(DecompCtx dc, MmmCtx mc, int j, int tile0, int m_words)
+// a ^= y * C for this lane's word pair (tables of C in tab2).
+template <int C>
+__device__ __forceinline__ void lookup(const ulonglong2 *tab2, uint64_t y, int wp, int swp, int ng, ulonglong2 &a)
 {
-    extern __shared__ __align__(16) uint64_t smem[];
-    uint64_t *tab = smem;
-    uint64_t *crow = smem + kTabWords;
-    const int tid = threadIdx.x;
-    const int q0 = (tile0 + blockIdx.x) * kTileWords;
-
-    int r, R = 0, row_begin, row_end, live_from;
-    if (kDecomp) {
-        R = dc.info[j].R;
-        r = dc.info[j].r;
-        if (r == 0) return;
-        row_begin = R + r;
-        row_end = dc.n;
-        live_from = j + 1;
-    } else {
-        r = min(64, mc.k - 64 * j);
-        row_begin = 0;
-        row_end = mc.n;
-        live_from = 0;
+    constexpr int X = Tabs<C>::X;
+    for (int g = 0; g < ng; ++g) {
+        const int gg = g ^ swp;
+        const int x = (int)((y >> (C * gg)) & (X - 1));
+        const ulonglong2 t = tab2[tab_entry<C>(gg, x) * (kTileWords / 2) + wp];
+        a.x ^= t.x;
+        a.y ^= t.y;
     }
+}
 
-    // C rows of this column tile (zero beyond r)
-    for (int idx = tid; idx < 64 * kTileWords; idx += kUpdateThreads) {
+// Loads the C rows of panel j for the tile starting at word q0 (zero beyond r).
+template <int T>
+__device__ __forceinline__ void load_pivot_rows(const DecompCtx &c, int R, int r, int q0, uint64_t *crow)
+{
+    for (int idx = threadIdx.x; idx < 64 * kTileWords; idx += T) {
         const int t = idx / kTileWords, w = idx % kTileWords;
         uint64_t v = 0;
-        if (t < r) {
-            if (kDecomp) {
-                const int64_t srow = dc.perm[R + t];
-                v = dc.W[srow * dc.ldw + q0 + w];
-            } else if (q0 + w < m_words) {
-                v = mc.B[(int64_t)(64 * j + t) * mc.ldb + q0 + w];
-            }
-        }
+        if (t < r) v = c.W[(int64_t)c.perm[R + t] * c.ldw + q0 + w];
         crow[idx] = v;
-    }
-    __syncthreads();
-    build_tables(tab, crow);
-    __syncthreads();
-
-    const ulonglong2 *tab2 = reinterpret_cast<const ulonglong2 *>(tab);
-    const int ng2 = ((r + 7) / 8 + 1) & ~1;  // tables in use, rounded to pairs
-    const int lane = tid & 31, warp = tid >> 5;
-    const int rs = lane >> 2, wp = lane & 3, swp = rs & 1;
-    const int col = q0 + 2 * wp;
-    const bool live = (col + 1 >= live_from) && (kDecomp || col < m_words);
-
-    uint64_t *T;
-    int64_t ldt;
-    if (kDecomp) { T = dc.W; ldt = dc.ldw; }
-    else { T = mc.C; ldt = mc.ldc; }
-
-    const int rows = row_end - row_begin;
-    const int chunk = (rows + gridDim.y - 1) / gridDim.y;
-    const int rb = row_begin + blockIdx.y * chunk;
-    const int re = min(row_end, rb + chunk);
-
-    constexpr int U = 4;
-    for (int base = rb + warp * 8 * U; base < re; base += 8 * U * (kUpdateThreads / 32)) {
-        int64_t off[U];
-        uint64_t y[U];
-        ulonglong2 a[U];
-        bool ok[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int i = base + u * 8 + rs;
-            ok[u] = i < re;
-            y[u] = 0;
-            off[u] = 0;
-            if (ok[u]) {
-                if (kDecomp) {
-                    off[u] = (int64_t)dc.perm[i] * ldt + col;
-                    y[u] = dc.Y[i];
-                } else {
-                    off[u] = (int64_t)i * ldt + col;
-                    y[u] = mc.A[(int64_t)i * mc.lda + j];
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            a[u] = make_ulonglong2(0, 0);
-            if (ok[u] && live) a[u] = *reinterpret_cast<const ulonglong2 *>(T + off[u]);
-        }
-        for (int g = 0; g < ng2; ++g) {
-            const int gg = g ^ swp;
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int x = (int)((y[u] >> (8 * gg)) & 255);
-                const ulonglong2 t = tab2[tab_entry(gg, x) * (kTileWords / 2) + wp];
-                a[u].x ^= t.x;
-                a[u].y ^= t.y;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (ok[u] && live) *reinterpret_cast<ulonglong2 *>(T + off[u]) = a[u];
-    }
-
-    // Echelon rows of the panel's pivots: E_s = T^-1[s] * C on this tile.
-    if (kDecomp && dc.Eint && blockIdx.y == 0) {
-        const PanelInfo *pi = dc.info + j;
-        for (int idx = tid; idx < r * kTileWords; idx += kUpdateThreads) {
-            const int t = idx / kTileWords, w = idx % kTileWords;
-            const int q = q0 + w;
-            if (q < live_from || q >= dc.mu) continue;
-            const uint64_t ym = pi->Tinv[t];
-            uint64_t acc = 0;
-            for (int g = 0; g < ng2; ++g) acc ^= tab[tab_entry(g, (int)((ym >> (8 * g)) & 255)) * kTileWords + w];
-            dc.Eint[(int64_t)(R + t) * dc.ldw + q] = acc;
-        }
     }
 }
 
-// Y (per position) and the L multipliers (per storage row) of panel j.
-__global__ void __launch_bounds__(256) k_ly(DecompCtx c, int j)
+// Echelon rows of the panel's pivots on one tile: E_s = Tinv[s] * C.
+template <int C, int T>
+__device__ __forceinline__ void echelon_rows(const DecompCtx &c, const PanelInfo *pi, int R, int r, int q0,
+                                             int live_from, int ng, const uint64_t *tab)
 {
+    for (int idx = threadIdx.x; idx < r * kTileWords; idx += T) {
+        const int t = idx / kTileWords, w = idx % kTileWords;
+        const int q = q0 + w;
+        if (q < live_from || q >= c.mu) continue;
+        const uint64_t ym = pi->Tinv[t];
+        uint64_t acc = 0;
+        for (int g = 0; g < ng; ++g)
+            acc ^= tab[tab_entry<C>(g, (int)((ym >> (C * g)) & (Tabs<C>::X - 1))) * kTileWords + w];
+        c.Eint[(int64_t)(R + t) * c.ldw + q] = acc;
+    }
+}
+
+// -------------------------------------------------------------------- k_next
+constexpr int kNextThreads = 256;
+constexpr int kNextRows = 256;  // storage rows per CTA
+constexpr int kNextC = 4;
+constexpr int kNextSmemWords = Tabs<kNextC>::Words + 64 * kTileWords + 16 * 16 * 2;
+
+__global__ void __launch_bounds__(kNextThreads) k_next(DecompCtx c, int j)
+{
+    __shared__ __align__(16) uint64_t smem[kNextSmemWords];
+    uint64_t *tab = smem;
+    uint64_t *crow = smem + Tabs<kNextC>::Words;
+    uint64_t *zc = crow + 64 * kTileWords;  // [g][x][y, lambda], 16 tables of 16 entries
     const PanelInfo *pi = c.info + j;
     const int R = pi->R, r = pi->r;
     if (r == 0) return;
-    __shared__ uint64_t zp[64], cp[64];
-    if (threadIdx.x < 64) {
-        zp[threadIdx.x] = pi->Zp[threadIdx.x];
-        cp[threadIdx.x] = pi->Comp[threadIdx.x];
-    }
-    __syncthreads();
+    const int tid = threadIdx.x;
+    const bool has_tile = j + 1 < c.mu;
+    const int q0 = ((j + 1) / kTileWords) * kTileWords;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int rs = lane >> 2, wp = lane & 3, swp = rs & 1;
+    const int col = q0 + 2 * wp;
+    const bool live = has_tile && (col + 1 >= j + 1);
     const int wq = R >> 6, sh = R & 63;
     const bool two = sh + r > 64;
-    const int stride = gridDim.x * blockDim.x;
-    for (int i = R + r + blockIdx.x * blockDim.x + threadIdx.x; i < c.n; i += stride) {
-        const int srow = c.perm[i];
-        const uint64_t d = c.W[(int64_t)srow * c.ldw + j];
-        uint64_t y = 0, l = 0;
-        for (uint64_t x = d; x; x &= x - 1) {
-            const int p = __ffsll((long long)x) - 1;
-            y ^= zp[p];
-            l ^= cp[p];
-        }
-        c.Y[i] = y;
-        if (c.Lint) {
-            uint64_t *Lr = c.Lint + (int64_t)srow * c.ldl;
-            Lr[wq] |= l << sh;
-            if (two) Lr[wq + 1] |= l >> (64 - sh);
+    const int rb = blockIdx.x * kNextRows, re = min(c.n, rb + kNextRows);
+    constexpr int U = kNextRows / (8 * (kNextThreads / 32));  // row groups per warp
+
+    // 1. every load of this thread's rows, issued before anything waits
+    int row[U];
+    bool active[U];
+    uint64_t d[U], l0[U], l1[U];
+    ulonglong2 a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        row[u] = rb + (warp * U + u) * 8 + rs;
+        const bool in = row[u] < re;
+        const uint64_t *Wr = c.W + (int64_t)(in ? row[u] : 0) * c.ldw;
+        active[u] = in && c.pivpanel[row[u]] > j;
+        d[u] = in ? Wr[j] : 0;
+        a[u] = (in && live) ? *reinterpret_cast<const ulonglong2 *>(Wr + col) : make_ulonglong2(0, 0);
+        l0[u] = l1[u] = 0;
+        if (in && c.Lint && wp == 0) {
+            const uint64_t *Lr = c.Lint + (int64_t)row[u] * c.ldl;
+            l0[u] = Lr[wq];
+            if (two) l1[u] = Lr[wq + 1];
         }
     }
+    // 2. tables of (Zp, Comp) for y and lambda, and of C for the tile
+    {
+        const int g = tid >> 4, x = tid & 15;
+        uint64_t y = 0, l = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            if ((x >> b) & 1) {
+                y ^= pi->Zp[4 * g + b];
+                l ^= pi->Comp[4 * g + b];
+            }
+        zc[2 * tid] = y;
+        zc[2 * tid + 1] = l;
+    }
+    if (has_tile) load_pivot_rows<kNextThreads>(c, R, r, q0, crow);
+    __syncthreads();
+    if (has_tile) build_tables<kNextC, kNextThreads>(tab, crow);
+    __syncthreads();
+
+    // 3. compute and store
+    const ulonglong2 *zc2 = reinterpret_cast<const ulonglong2 *>(zc);
+    const ulonglong2 *tab2 = reinterpret_cast<const ulonglong2 *>(tab);
+    const int ng = ((r + kNextC - 1) / kNextC + 1) & ~1;
+    uint64_t *Ynext = c.Y + (int64_t)(j & 1) * c.n;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (row[u] >= re) continue;
+        uint64_t y = 0, l = 0;
+        if (active[u]) {
+#pragma unroll
+            for (int g = 0; g < 16; ++g) {
+                const ulonglong2 t = zc2[g * 16 + (int)((d[u] >> (4 * g)) & 15)];
+                y ^= t.x;
+                l ^= t.y;
+            }
+        }
+        if (wp == 0) {
+            Ynext[row[u]] = y;
+            if (c.Lint && l) {
+                uint64_t *Lr = c.Lint + (int64_t)row[u] * c.ldl;
+                Lr[wq] = l0[u] | (l << sh);
+                if (two) Lr[wq + 1] = l1[u] | (l >> (64 - sh));
+            }
+        }
+        if (live && y) {
+            lookup<kNextC>(tab2, y, wp, swp, ng, a[u]);
+            *reinterpret_cast<ulonglong2 *>(c.W + (int64_t)row[u] * c.ldw + col) = a[u];
+        }
+    }
+
     if (blockIdx.x == 0) {
-        for (int t = threadIdx.x; t < r; t += blockDim.x) {
+        // the pivot rows: their L rows (T) and echelon words
+        for (int t = tid; t < r; t += kNextThreads) {
             const int srow = c.perm[R + t];
             if (c.Lint) {
                 const uint64_t l = pi->T[t];
@@ -205,6 +224,150 @@ __global__ void __launch_bounds__(256) k_ly(DecompCtx c, int j)
                 if (two) Lr[wq + 1] |= l >> (64 - sh);
             }
             if (c.Eint) c.Eint[(int64_t)(R + t) * c.ldw + j] = pi->Erow[t];
+        }
+        if (c.Eint && has_tile) echelon_rows<kNextC, kNextThreads>(c, pi, R, r, q0, j + 1, ng, tab);
+    }
+}
+
+// -------------------------------------------------------------------- k_rest
+constexpr int kRestThreads = 512;
+constexpr int kRestChunk = 256;  // storage rows per work item
+constexpr int kRestU = 6;        // row groups of 8 rows per warp and iteration
+
+template <int C, int U>
+// at most 96 registers: 512 x 96 leaves room on the SM for a k_next or k_panel CTA
+// (128 threads) next to this persistent CTA
+__global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int ntiles)
+{
+    extern __shared__ __align__(16) uint64_t smem[];
+    uint64_t *tab = smem;
+    uint64_t *crow = smem + Tabs<C>::Words;
+    const PanelInfo *pi = c.info + j;
+    const int R = pi->R, r = pi->r;
+    if (r == 0) return;
+    const int nchunks = (c.n + kRestChunk - 1) / kRestChunk;
+    const int64_t items = (int64_t)ntiles * nchunks;
+    const int64_t i0 = items * blockIdx.x / gridDim.x, i1 = items * (blockIdx.x + 1) / gridDim.x;
+    const uint64_t *__restrict__ Yj = c.Y + (int64_t)(j & 1) * c.n;
+    uint64_t *__restrict__ W = c.W;
+    const int64_t ldw = c.ldw;
+    const int ng = ((r + C - 1) / C + 1) & ~1;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int rs = lane >> 2, wp = lane & 3, swp = rs & 1;
+    constexpr int NW = kRestThreads / 32;
+    const ulonglong2 *tab2 = reinterpret_cast<const ulonglong2 *>(tab);
+    // The item range is split into segments of one tile each: one table
+    // build per segment, then one pipelined pass over its contiguous rows.
+    for (int64_t it = i0; it < i1;) {
+        const int tile = tile_first + (int)(it / nchunks);
+        const int chunk = (int)(it % nchunks);
+        const int64_t seg_end = min(i1, (int64_t)(tile - tile_first + 1) * nchunks);
+        const int chunk_end = (int)((seg_end - 1) % nchunks) + 1;
+        it = seg_end;
+        const int q0 = tile * kTileWords;
+        __syncthreads();
+        load_pivot_rows<kRestThreads>(c, R, r, q0, crow);
+        __syncthreads();
+        build_tables<C, kRestThreads>(tab, crow);
+        __syncthreads();
+        if (c.Eint && chunk == 0) echelon_rows<C, kRestThreads>(c, pi, R, r, q0, 0, ng, tab);
+        const int col = q0 + 2 * wp;
+        const int rb = chunk * kRestChunk, re = min(c.n, chunk_end * kRestChunk);
+        constexpr int STEP = 8 * U * NW;
+        uint64_t yn[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int row = rb + warp * 8 * U + u * 8 + rs;
+            yn[u] = row < re ? Yj[row] : 0;
+        }
+        for (int base = rb + warp * 8 * U; base < re; base += STEP) {
+            uint64_t y[U];
+            ulonglong2 a[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                y[u] = yn[u];
+                const int nrow = base + STEP + u * 8 + rs;
+                yn[u] = nrow < re ? Yj[nrow] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int row = base + u * 8 + rs;
+                a[u] = make_ulonglong2(0, 0);
+                if (y[u]) a[u] = *reinterpret_cast<const ulonglong2 *>(W + (int64_t)row * ldw + col);
+            }
+            for (int g = 0; g < ng; ++g) {
+                const int gg = g ^ swp;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int x = (int)((y[u] >> (C * gg)) & (Tabs<C>::X - 1));
+                    const ulonglong2 t = tab2[tab_entry<C>(gg, x) * (kTileWords / 2) + wp];
+                    a[u].x ^= t.x;
+                    a[u].y ^= t.y;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int row = base + u * 8 + rs;
+                if (y[u]) *reinterpret_cast<ulonglong2 *>(W + (int64_t)row * ldw + col) = a[u];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ product
+constexpr int kMmmThreads = 256;
+constexpr int kMmmC = 8;
+constexpr int kMmmSmemBytes = (Tabs<kMmmC>::Words + 64 * kTileWords) * 8;
+
+__global__ void __launch_bounds__(kMmmThreads, 1) k_mmm_pass(MmmCtx mc, int kb, int m_words)
+{
+    extern __shared__ __align__(16) uint64_t smem[];
+    uint64_t *tab = smem;
+    uint64_t *crow = smem + Tabs<kMmmC>::Words;
+    const int tid = threadIdx.x;
+    const int q0 = blockIdx.x * kTileWords;
+    const int r = min(64, mc.k - 64 * kb);
+    for (int idx = tid; idx < 64 * kTileWords; idx += kMmmThreads) {
+        const int t = idx / kTileWords, w = idx % kTileWords;
+        crow[idx] = (t < r && q0 + w < m_words) ? mc.B[(int64_t)(64 * kb + t) * mc.ldb + q0 + w] : 0;
+    }
+    __syncthreads();
+    build_tables<kMmmC, kMmmThreads>(tab, crow);
+    __syncthreads();
+    const ulonglong2 *tab2 = reinterpret_cast<const ulonglong2 *>(tab);
+    const int ng = ((r + kMmmC - 1) / kMmmC + 1) & ~1;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int rs = lane >> 2, wp = lane & 3, swp = rs & 1;
+    const int col = q0 + 2 * wp;
+    const bool live = col < m_words;
+    const int rows = mc.n;
+    const int chunk = (rows + gridDim.y - 1) / gridDim.y;
+    const int rb = blockIdx.y * chunk, re = min(rows, rb + chunk);
+    constexpr int U = 4;
+    for (int base = rb + warp * 8 * U; base < re; base += 8 * U * (kMmmThreads / 32)) {
+        uint64_t y[U];
+        ulonglong2 a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = base + u * 8 + rs;
+            y[u] = i < re ? mc.A[(int64_t)i * mc.lda + kb] : 0;
+            a[u] = make_ulonglong2(0, 0);
+            if (i < re && live) a[u] = *reinterpret_cast<const ulonglong2 *>(mc.C + (int64_t)i * mc.ldc + col);
+        }
+        for (int g = 0; g < ng; ++g) {
+            const int gg = g ^ swp;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int x = (int)((y[u] >> (kMmmC * gg)) & 255);
+                const ulonglong2 t = tab2[tab_entry<kMmmC>(gg, x) * (kTileWords / 2) + wp];
+                a[u].x ^= t.x;
+                a[u].y ^= t.y;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = base + u * 8 + rs;
+            if (i < re && live) *reinterpret_cast<ulonglong2 *>(mc.C + (int64_t)i * mc.ldc + col) = a[u];
         }
     }
 }
@@ -222,53 +385,50 @@ int num_sms()
     return g_num_sms;
 }
 
-template <bool kDecomp>
-cudaError_t set_smem_attr()
+template <class K>
+cudaError_t allow_smem(K kernel, int bytes)
 {
-    static bool done = false;
-    if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(k_update<kDecomp>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-        if (e != cudaSuccess) return e;
-        done = true;
-    }
-    return cudaSuccess;
-}
-
-int row_chunks(int ntiles, int est_rows)
-{
-    const int target = 2 * num_sms();
-    int chunks = (target + ntiles - 1) / ntiles;
-    const int max_chunks = est_rows / 256 > 1 ? est_rows / 256 : 1;
-    if (chunks > max_chunks) chunks = max_chunks;
-    if (chunks < 1) chunks = 1;
-    if (chunks > 65535) chunks = 65535;
-    return chunks;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 }  // namespace
 
-cudaError_t launch_ly(const DecompCtx &c, int j, cudaStream_t s)
+cudaError_t launch_next(const DecompCtx &c, int j, cudaStream_t s)
 {
-    int blocks = (c.n + 255) / 256;
-    const int cap = 2 * num_sms();
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    k_ly<<<blocks, 256, 0, s>>>(c, j);
+    const int blocks = (c.n + kNextRows - 1) / kNextRows;
+    k_next<<<blocks, kNextThreads, 0, s>>>(c, j);
     return cudaGetLastError();
 }
 
-cudaError_t launch_update(const DecompCtx &c, int j, cudaStream_t s)
+int rest_tiles(const DecompCtx &c, int j, int *tile_first)
 {
-    const int tile0 = (j + 1) / kTileWords;
-    const int ntiles = (c.mu + kTileWords - 1) / kTileWords - tile0;
+    *tile_first = (j + 1) / kTileWords + 1;
+    const int tiles = (c.mu + kTileWords - 1) / kTileWords - *tile_first;
+    return tiles > 0 ? tiles : 0;
+}
+
+cudaError_t launch_rest(const DecompCtx &c, int j, int est_active_rows, cudaStream_t s)
+{
+    int tile_first = 0;
+    const int ntiles = rest_tiles(c, j, &tile_first);
     if (ntiles <= 0) return cudaSuccess;
-    cudaError_t e = set_smem_attr<true>();
-    if (e != cudaSuccess) return e;
-    int est = c.n - 64 * j;
-    if (est < 256) est = 256;
-    dim3 grid(ntiles, row_chunks(ntiles, est));
-    MmmCtx none{};
-    k_update<true><<<grid, kUpdateThreads, kSmemBytes, s>>>(c, none, j, tile0, 0);
+    const int nchunks = (c.n + kRestChunk - 1) / kRestChunk;
+    const int64_t items = (int64_t)ntiles * nchunks;
+    int grid = num_sms();
+    if (items < grid) grid = (int)items;
+    if (est_active_rows >= 4096) {
+        constexpr int bytes = (Tabs<8>::Words + 64 * kTileWords) * 8;
+        static bool set = false;
+        if (!set) {
+            cudaError_t e = allow_smem(k_rest<8, kRestU>, bytes);
+            if (e != cudaSuccess) return e;
+            set = true;
+        }
+        k_rest<8, kRestU><<<grid, kRestThreads, bytes, s>>>(c, j, tile_first, ntiles);
+    } else {
+        constexpr int bytes = (Tabs<4>::Words + 64 * kTileWords) * 8;
+        k_rest<4, kRestU><<<grid, kRestThreads, bytes, s>>>(c, j, tile_first, ntiles);
+    }
     return cudaGetLastError();
 }
 
@@ -276,11 +436,19 @@ cudaError_t launch_mmm_pass(const MmmCtx &c, int kb, int m_words, cudaStream_t s
 {
     const int ntiles = (m_words + kTileWords - 1) / kTileWords;
     if (ntiles <= 0 || c.n <= 0) return cudaSuccess;
-    cudaError_t e = set_smem_attr<false>();
-    if (e != cudaSuccess) return e;
-    dim3 grid(ntiles, row_chunks(ntiles, c.n));
-    DecompCtx none{};
-    k_update<false><<<grid, kUpdateThreads, kSmemBytes, s>>>(none, c, kb, 0, m_words);
+    static bool set = false;
+    if (!set) {
+        cudaError_t e = allow_smem(k_mmm_pass, kMmmSmemBytes);
+        if (e != cudaSuccess) return e;
+        set = true;
+    }
+    const int target = 2 * num_sms();
+    int chunks = (target + ntiles - 1) / ntiles;
+    const int maxc = c.n / 256 > 1 ? c.n / 256 : 1;
+    if (chunks > maxc) chunks = maxc;
+    if (chunks < 1) chunks = 1;
+    dim3 grid(ntiles, chunks);
+    k_mmm_pass<<<grid, kMmmThreads, kMmmSmemBytes, s>>>(c, kb, m_words);
     return cudaGetLastError();
 }
 
