@@ -116,6 +116,22 @@ size_t gf2_rank_workspace_bytes(int64_t n, int64_t m);
 int gf2_rank(const gf2_mat *A, int64_t *rank_host, unsigned flags,
              void *workspace, size_t ws_bytes, void *stream);
 
+/* Rank of A (n x m, n <= 4096 and m <= 4096) without allocating anything.
+ * No counterpart in the paper: this exists for callers that may not
+ * allocate device memory when they call in -- for instance a program that
+ * reserves a fixed device-memory budget at start-up and forbids allocations
+ * afterwards, or a framework that owns every device buffer.  The scratch is
+ * a static array of about 2.4 MiB inside the library (held by every GPU that
+ * loads the library, until the process exits).  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress), so make the
+ * first call before any stream capture.  Calls on one device share the
+ * array: calls that overlap on the GPU race.  rank_dev: device int64 that
+ * receives the rank (written asynchronously on `stream`, which the call
+ * synchronises once to check the padding bits).  Runs the same kernels as
+ * gf2_rank on the one stream given.  Errors: GF2_ERR_ARG, GF2_ERR_SHAPE,
+ * GF2_ERR_UNSUPPORTED (n or m > 4096), GF2_ERR_PADDING, GF2_ERR_CUDA. */
+int gf2_rank_noalloc(const gf2_mat *A, int64_t *rank_dev, void *stream);
+
 /* Same as gf2_decompose, end to end from HOST memory: A_host holds the
  * column blocks (word (i,q) at A_host[q*lda + i]); the factors are copied
  * back to the host buffers given (L_host/E_host may be NULL; their column
