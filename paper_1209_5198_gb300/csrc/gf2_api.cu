@@ -1,6 +1,8 @@
 // C ABI of the F2 library (declared in include/gf2.h): argument checks,
 // workspace carving and the host-side sequence of kernel launches.
 #include <atomic>
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -146,7 +148,9 @@ cudaError_t launch(int cls, cudaStream_t s, F &&f)
 // decomposition holds g_side_mutex, so the events are used by one call at a
 // time (a wait captures the event's state when it is enqueued).
 struct SideResources {
-    cudaStream_t stream = nullptr;
+    int device = 0;
+    cudaStream_t main = nullptr;    // wide updates and outputs
+    cudaStream_t stream = nullptr;  // the panel chain (high priority)
     std::vector<cudaEvent_t> events;
 };
 std::mutex g_side_mutex;
@@ -158,10 +162,14 @@ int side_resources(int nevents, SideResources **out)
     if (cudaGetDevice(&dev) != cudaSuccess) return GF2_ERR_CUDA;
     if ((int)g_side.size() <= dev) g_side.resize(dev + 1);
     SideResources &r = g_side[dev];
+    r.device = dev;
     if (!r.stream) {
         int lo = 0, hi = 0;
         if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) return GF2_ERR_CUDA;
         if (cudaStreamCreateWithPriority(&r.stream, cudaStreamNonBlocking, hi) != cudaSuccess) return GF2_ERR_CUDA;
+        if (cudaStreamCreateWithPriority(&r.main, cudaStreamNonBlocking, lo) != cudaSuccess) return GF2_ERR_CUDA;
+        if (prepare_update_kernels() != cudaSuccess) return GF2_ERR_CUDA;
+        if (prepare_panel_kernel() != cudaSuccess) return GF2_ERR_CUDA;
     }
     while ((int)r.events.size() < nevents) {
         cudaEvent_t e = nullptr;
@@ -172,7 +180,99 @@ int side_resources(int nevents, SideResources **out)
     return GF2_OK;
 }
 
+// ------------------------------------------------------------ graph cache
+// One captured graph per (device, shape, every pointer the kernels see).
+struct GraphKey {
+    int dev;
+    int64_t n, m, lda, ldl, lde;
+    const void *a, *perm, *piv, *rank, *L, *E, *ws;
+};
+struct GraphEntry {
+    GraphKey key;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    uint64_t stamp;
+};
+std::vector<GraphEntry> g_graphs;  // guarded by g_side_mutex
+uint64_t g_graph_clock = 0;
+constexpr size_t kMaxGraphs = 16;
+const bool g_use_graphs = [] {
+    const char *e = getenv("GF2_GRAPHS");
+    return !(e && e[0] == '0');
+}();
+
+cudaGraphExec_t find_graph(const GraphKey &k)
+{
+    for (auto &g : g_graphs)
+        if (memcmp(&g.key, &k, sizeof(GraphKey)) == 0) {
+            g.stamp = ++g_graph_clock;
+            return g.exec;
+        }
+    return nullptr;
+}
+
+void remember_graph(const GraphKey &k, cudaGraph_t graph, cudaGraphExec_t exec)
+{
+    if (g_graphs.size() >= kMaxGraphs) {
+        size_t old = 0;
+        for (size_t i = 1; i < g_graphs.size(); ++i)
+            if (g_graphs[i].stamp < g_graphs[old].stamp) old = i;
+        cudaGraphExecDestroy(g_graphs[old].exec);
+        cudaGraphDestroy(g_graphs[old].graph);
+        g_graphs.erase(g_graphs.begin() + old);
+    }
+    g_graphs.push_back(GraphEntry{k, graph, exec, ++g_graph_clock});
+}
+
+void drop_graphs()
+{
+    for (auto &g : g_graphs) {
+        cudaGraphExecDestroy(g.exec);
+        cudaGraphDestroy(g.graph);
+    }
+    g_graphs.clear();
+}
+
 // ------------------------------------------------------------ decompose
+// Enqueues the factorization of an ingested matrix on the library streams:
+// the panel chain (pivot selection, next column tile, Y and L) on P, the
+// wide trailing updates and the outputs on M:
+//   next(j) waits for rest(j-2) (it reuses Y[j % 2]) and, when column j+1
+//   opens a new tile, for rest(j-1) (which updated that tile);
+//   rest(j) waits for next(j) (its Y).
+int enqueue_factorization(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat *E, SideResources *side)
+{
+    cudaStream_t s = side->main, P = side->stream;
+    cudaEvent_t *evNext = side->events.data(), *evRest = evNext + c.mu;
+    cudaEvent_t evFork = evRest[c.mu], evJoin = evRest[c.mu + 1];
+    std::vector<char> rest_launched(c.mu, 0);
+    CK(cudaEventRecord(evFork, s));
+    CK(cudaStreamWaitEvent(P, evFork, 0));
+    for (int j = 0; j < c.mu; ++j) {
+        LAUNCH_ON(GF2_KCLASS_PANEL, P, launch_panel(c, j, P));
+        if (j >= 2 && rest_launched[j - 2]) CK(cudaStreamWaitEvent(P, evRest[j - 2], 0));
+        if (j >= 1 && (j + 1) % kTileWords == 0 && rest_launched[j - 1]) CK(cudaStreamWaitEvent(P, evRest[j - 1], 0));
+        LAUNCH_ON(GF2_KCLASS_NEXT, P, launch_next(c, j, P));
+        int tile_first = 0;
+        if (rest_tiles(c, j, &tile_first) > 0) {
+            CK(cudaEventRecord(evNext[j], P));
+            CK(cudaStreamWaitEvent(s, evNext[j], 0));
+            const int est = (int)(c.n - 64 * (int64_t)(j + 1));
+            LAUNCH(GF2_KCLASS_UPDATE, launch_rest(c, j, est, s));
+            CK(cudaEventRecord(evRest[j], s));
+            rest_launched[j] = 1;
+        }
+    }
+    CK(cudaEventRecord(evJoin, P));
+    CK(cudaStreamWaitEvent(s, evJoin, 0));
+    LAUNCH(GF2_KCLASS_LAYOUT, launch_finish_scalars(c, rank, s));
+    if (E) LAUNCH(GF2_KCLASS_LAYOUT, launch_finish_E(c, E->w, E->ld, s));
+    if (L)
+        LAUNCH(GF2_KCLASS_LAYOUT, launch_colblocks_from_rowmajor(c.Lint, c.ldl, c.perm, c.n, (int32_t)words_of(c.kmax),
+                                                                   L->w, L->ld, s));
+    return GF2_OK;
+}
+
 struct DecompLayout {
     int64_t mu, ldw, kmax, ldl;
     size_t oW, oY, oPP, oInfo, oLint, oEint, oFlag, total;
@@ -246,41 +346,49 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
     }
     if (c.Lint) CK(cudaMemsetAsync(c.Lint, 0, (size_t)n * d.ldl * 8, s));
 
-    // Panel chain (pivot selection, next column tile, Y and L) on a side
-    // stream P, the wide trailing updates on the caller's stream s:
-    //   next(j) waits for rest(j-2) (it reuses Y[j % 2]) and, when column
-    //   j+1 opens a new tile, for rest(j-1) (which updated that tile);
-    //   rest(j) waits for next(j) (its Y).
+    // The factorization runs on the library's two streams of this device
+    // (M: wide updates and outputs, P: the panel chain), joined to the
+    // caller's stream s by events; the whole sequence is captured once into
+    // a CUDA graph per (shape, pointers) and replayed on later calls.
     std::lock_guard<std::mutex> lock(g_side_mutex);
     SideResources *side = nullptr;
-    st = side_resources(2 * c.mu + 2, &side);
+    st = side_resources(2 * c.mu + 4, &side);
     if (st) return st;
-    cudaStream_t P = side->stream;
-    cudaEvent_t *evNext = side->events.data(), *evRest = evNext + c.mu;
-    cudaEvent_t evFork = evRest[c.mu], evJoin = evRest[c.mu + 1];
-    std::vector<char> rest_launched(c.mu, 0);
-    CK(cudaEventRecord(evFork, s));
-    CK(cudaStreamWaitEvent(P, evFork, 0));
-    for (int j = 0; j < c.mu; ++j) {
-        LAUNCH_ON(GF2_KCLASS_PANEL, P, launch_panel(c, j, P));
-        if (j >= 2 && rest_launched[j - 2]) CK(cudaStreamWaitEvent(P, evRest[j - 2], 0));
-        if (j >= 1 && (j + 1) % kTileWords == 0 && rest_launched[j - 1]) CK(cudaStreamWaitEvent(P, evRest[j - 1], 0));
-        LAUNCH_ON(GF2_KCLASS_NEXT, P, launch_next(c, j, P));
-        int tile_first = 0;
-        if (rest_tiles(c, j, &tile_first) > 0) {
-            CK(cudaEventRecord(evNext[j], P));
-            CK(cudaStreamWaitEvent(s, evNext[j], 0));
-            int est = (int)(n - 64 * (int64_t)(j + 1));
-            LAUNCH(GF2_KCLASS_UPDATE, launch_rest(c, j, est, s));
-            CK(cudaEventRecord(evRest[j], s));
-            rest_launched[j] = 1;
+    cudaEvent_t evIn = side->events[2 * c.mu + 2], evOut = side->events[2 * c.mu + 3];
+    CK(cudaEventRecord(evIn, s));
+    CK(cudaStreamWaitEvent(side->main, evIn, 0));
+    GraphKey key{};
+    key.dev = side->device;
+    key.n = n; key.m = m; key.a = A->w; key.lda = A->ld;
+    key.perm = perm; key.piv = pivcols; key.rank = rank;
+    key.L = L ? L->w : nullptr; key.ldl = L ? L->ld : 0;
+    key.E = E ? E->w : nullptr; key.lde = E ? E->ld : 0;
+    key.ws = ws;
+    if (g_timing.load() || !g_use_graphs) {
+        st = enqueue_factorization(c, rank, L, E, side);
+        if (st) return st;
+    } else {
+        cudaGraphExec_t exec = find_graph(key);
+        if (!exec) {
+            if (cudaStreamBeginCapture(side->main, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GF2_ERR_CUDA;
+            st = enqueue_factorization(c, rank, L, E, side);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(side->main, &graph);
+            if (st || ec != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                cudaGetLastError();
+                return st ? st : GF2_ERR_CUDA;
+            }
+            if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                return GF2_ERR_CUDA;
+            }
+            remember_graph(key, graph, exec);
         }
+        CK(cudaGraphLaunch(exec, side->main));
     }
-    CK(cudaEventRecord(evJoin, P));
-    CK(cudaStreamWaitEvent(s, evJoin, 0));
-    LAUNCH(GF2_KCLASS_LAYOUT, launch_finish_scalars(c, rank, s));
-    if (E) LAUNCH(GF2_KCLASS_LAYOUT, launch_finish_E(c, E->w, E->ld, s));
-    if (L) LAUNCH(GF2_KCLASS_LAYOUT, launch_colblocks_from_rowmajor(c.Lint, c.ldl, perm, (int32_t)n, (int32_t)words_of(kmax), L->w, L->ld, s));
+    CK(cudaEventRecord(evOut, side->main));
+    CK(cudaStreamWaitEvent(s, evOut, 0));
     return GF2_OK;
 }
 
@@ -312,6 +420,10 @@ int gf2_release_workspace(void)
     std::lock_guard<std::mutex> lock(g_ws_mutex);
     if ((int)g_ws.size() > dev && g_ws[dev].ptr) {
         if (cudaDeviceSynchronize() != cudaSuccess) return GF2_ERR_CUDA;
+        {
+            std::lock_guard<std::mutex> glock(g_side_mutex);
+            drop_graphs();  // graphs may point into the released workspace
+        }
         cudaFree(g_ws[dev].ptr);
         g_ws[dev] = OwnedWorkspace{};
     }

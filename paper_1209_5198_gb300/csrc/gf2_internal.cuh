@@ -75,6 +75,8 @@ cudaError_t launch_panel(const DecompCtx &c, int j, cudaStream_t s);
 cudaError_t launch_next(const DecompCtx &c, int j, cudaStream_t s);
 cudaError_t launch_rest(const DecompCtx &c, int j, int est_active_rows, cudaStream_t s);
 int rest_tiles(const DecompCtx &c, int j, int *tile_first);
+cudaError_t prepare_update_kernels();  // one-time kernel attributes (before any capture)
+cudaError_t prepare_panel_kernel();
 cudaError_t launch_mmm_pass(const MmmCtx &c, int kb, int m_words, cudaStream_t s);
 
 }  // namespace gf2

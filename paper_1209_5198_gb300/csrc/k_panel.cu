@@ -638,11 +638,31 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
     }
 }
 
+// Unused dynamic shared memory that keeps a panel CTA off any SM holding a
+// persistent k_rest CTA (about 133 KB): the panel runs on the SM k_rest
+// leaves free, without other warps competing for its scheduler.
+constexpr int kPanelReserveBytes = 110 * 1024;
+
 }  // namespace
+
+cudaError_t prepare_panel_kernel()
+{
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPanelReserveBytes);
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
 
 cudaError_t launch_panel(const DecompCtx &c, int j, cudaStream_t s)
 {
-    k_panel<<<1, kPanelThreads, 0, s>>>(c, j);
+    const cudaError_t e = prepare_panel_kernel();
+    if (e != cudaSuccess) return e;
+    k_panel<<<1, kPanelThreads, kPanelReserveBytes, s>>>(c, j);
     return cudaGetLastError();
 }
 

@@ -23,6 +23,8 @@
 // 128-bit shared-memory phase) read tables g and g^1, which live in opposite
 // 64-byte halves of the bank space, so lookups are conflict-free for any y.
 // The same tile code serves the standalone product C ^= A B.
+#include <mutex>
+
 #include "gf2_internal.cuh"
 
 namespace gf2 {
@@ -393,6 +395,24 @@ cudaError_t allow_smem(K kernel, int bytes)
 
 }  // namespace
 
+// Shared-memory limits of the kernels that need more than 48 KB, once per
+// device (must run before a stream capture records their launches).
+cudaError_t prepare_update_kernels()
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return cudaSuccess;
+    e = allow_smem(k_rest<8, kRestU>, (Tabs<8>::Words + 64 * kTileWords) * 8);
+    if (e == cudaSuccess) e = allow_smem(k_mmm_pass, kMmmSmemBytes);
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
+
 cudaError_t launch_next(const DecompCtx &c, int j, cudaStream_t s)
 {
     const int blocks = (c.n + kNextRows - 1) / kNextRows;
@@ -414,16 +434,15 @@ cudaError_t launch_rest(const DecompCtx &c, int j, int est_active_rows, cudaStre
     if (ntiles <= 0) return cudaSuccess;
     const int nchunks = (c.n + kRestChunk - 1) / kRestChunk;
     const int64_t items = (int64_t)ntiles * nchunks;
-    int grid = num_sms();
+    // one SM is left free for the panel kernel (whose shared-memory request
+    // keeps it off the SMs that hold a k_rest CTA): the panel is a serial,
+    // latency-bound chain that slows down when it shares a scheduler
+    int grid = num_sms() > 1 ? num_sms() - 1 : 1;
     if (items < grid) grid = (int)items;
+    cudaError_t e = prepare_update_kernels();
+    if (e != cudaSuccess) return e;
     if (est_active_rows >= 4096) {
         constexpr int bytes = (Tabs<8>::Words + 64 * kTileWords) * 8;
-        static bool set = false;
-        if (!set) {
-            cudaError_t e = allow_smem(k_rest<8, kRestU>, bytes);
-            if (e != cudaSuccess) return e;
-            set = true;
-        }
         k_rest<8, kRestU><<<grid, kRestThreads, bytes, s>>>(c, j, tile_first, ntiles);
     } else {
         constexpr int bytes = (Tabs<4>::Words + 64 * kTileWords) * 8;
@@ -436,12 +455,8 @@ cudaError_t launch_mmm_pass(const MmmCtx &c, int kb, int m_words, cudaStream_t s
 {
     const int ntiles = (m_words + kTileWords - 1) / kTileWords;
     if (ntiles <= 0 || c.n <= 0) return cudaSuccess;
-    static bool set = false;
-    if (!set) {
-        cudaError_t e = allow_smem(k_mmm_pass, kMmmSmemBytes);
-        if (e != cudaSuccess) return e;
-        set = true;
-    }
+    cudaError_t e = prepare_update_kernels();
+    if (e != cudaSuccess) return e;
     const int target = 2 * num_sms();
     int chunks = (target + ntiles - 1) / ntiles;
     const int maxc = c.n / 256 > 1 ? c.n / 256 : 1;
