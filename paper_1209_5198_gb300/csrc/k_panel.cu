@@ -9,17 +9,16 @@
 // such row gets no pivot (the paper inserts the virtual row (0,1,0) there,
 // Section 4.4); no column is ever exchanged.
 //
-// How (GB300 design, not the paper's CPU loop).  Warp 0 holds a window of up
-// to 64 consecutive rows (positions ib..ib+63, slot = position mod 64),
-// already reduced by the pivots found so far, TRANSPOSED: lane l owns the
-// columns (bits) l and l+32, each a 64-bit mask over the window slots.  For
-// bit k the owner broadcasts column k; the first qualifying row is a
-// find-first-set on it, circularly from the pivot slot; eliminating the
-// pivot row E_s from the rows that have bit k is one masked XOR per column;
-// each lane keeps bit s of its two columns of E_s, and the pivot's (bit,
-// offset) is recorded in a register.  The row exchanges themselves (perm,
-// slot tables) are replayed from those records before the window is
-// refilled and at the end, off the per-bit path.
+// How (GB300 design, not the paper's CPU loop).  Warp 0 holds rows reduced
+// by the pivots found so far TRANSPOSED: lane l owns the columns (bits) l and
+// l+32 as masks over row slots.  For bit k the owner broadcasts column k; the
+// first qualifying row is a find-first-set on it; eliminating the pivot row
+// E_s from the rows that have bit k is one masked XOR per column, and each
+// lane keeps bit s of its two columns of E_s.  The common case (the fast
+// path) holds the first 96 rows for the whole block with the exchanges
+// applied to the masks themselves; the general loop keeps a circular window
+// of 64 rows (slot = position mod 64), refilled as pivots consume it, and
+// replays the recorded exchanges on its slot tables off the per-bit path.
 // At the end the coordinate maps are derived from those bits and the raw
 // pivot words B_s:
 //   U    = E restricted to the pivot columns (unit upper triangular),
@@ -85,9 +84,8 @@ struct PanelShared {
     int32_t sidx[64];                // bit -> its pivot (or -1)
     int32_t slot_srow[kWin];
     uint64_t slot_raw[kWin];
-    uint32_t rec32[64];  // fast path: pivot t -> bit | offset << 8
-    uint64_t Lpr[64];    // fast path: probes that received E_t
-    uint64_t nrow[32];   // fast path: rows entering the window
+    uint64_t fraw[96];   // fast path: raw word and storage row of each register row
+    int32_t fsrow[96];
     uint64_t mask;
     unsigned long long orv;
     int req, from, found;
@@ -159,6 +157,110 @@ __device__ void scan_or(const DecompCtx &c, const uint64_t *Wj, PanelShared &sh)
     }
     acc = warp_or(acc);
     if ((tid & 31) == 0 && acc) atomicOr(&sh.orv, (unsigned long long)acc);
+}
+
+// Fast-path state of warp 0.  The 96 rows of positions R..R+95 are held
+// transposed: lane l owns the columns (bits) l (A) and l+32 (B) of the block,
+// each as three 32-bit masks over the slots (slot = position - R; word w
+// covers slots 32w..32w+31).  Lanes 0..6 also own the identity columns: bit b
+// of the original slot of the row now in each slot, moved with the rows so
+// that the exchanges need no other bookkeeping.  EA / EB bit s: entry of E_s
+// in column l / l+32.
+struct FastCols {
+    uint32_t A[3], B[3], ID[3];
+    uint64_t EA, EB;
+    int k, s;
+};
+
+// Word u of identity column b (lane b < 7): bit i is bit b of slot 32u + i.
+__device__ __forceinline__ uint32_t slot_index_bits(int u, int b)
+{
+    switch (b) {
+    case 0: return 0xAAAAAAAAu;
+    case 1: return 0xCCCCCCCCu;
+    case 2: return 0xF0F0F0F0u;
+    case 3: return 0xFF00FF00u;
+    case 4: return 0xFFFF0000u;
+    case 5: return (u & 1) ? ~0u : 0u;
+    case 6: return (u & 2) ? ~0u : 0u;
+    default: return 0u;
+    }
+}
+
+// Pivot s for bit k: its first qualifying row sits in the slot of the one-hot
+// mask fm0..fm2 (words 0..2; W2 = false when it is in word 0 or 1); the pivot
+// slot s is in word P.  Slots s and f exchange their rows, the pivot row
+// leaves the window (slot s is cleared) and its bits E_s are XORed into every
+// row with bit k: ck = column k without the pivot row (the row moved out of
+// slot s has bit k = 0 whenever f != s).
+template <int P, bool W2>
+__device__ __forceinline__ void fast_pivot(FastCols &st, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t fm0,
+                                           uint32_t fm1, uint32_t fm2)
+{
+    const uint32_t hsm = 1u << (st.s & 31);
+    const uint32_t ck0 = c0 ^ fm0, ck1 = c1 ^ fm1, ck2 = c2 ^ fm2;
+    auto at_f = [&](const uint32_t (&X)[3]) -> bool {
+        return (W2 ? ((X[0] & fm0) | (X[1] & fm1) | (X[2] & fm2)) : ((X[0] & fm0) | (X[1] & fm1))) != 0;
+    };
+    auto eliminate = [&](uint32_t (&X)[3]) -> bool {
+        const bool e = at_f(X);
+        const bool hb = (X[P] & hsm) != 0;
+        if (e != hb) {  // the head row's bit moves to slot f
+            X[0] ^= fm0;
+            X[1] ^= fm1;
+            if (W2) X[2] ^= fm2;
+        }
+        X[P] &= ~hsm;
+        if (e) {
+            X[0] ^= ck0;
+            X[1] ^= ck1;
+            X[2] ^= ck2;
+        }
+        return e;
+    };
+    const bool eA = eliminate(st.A), eB = eliminate(st.B);
+    {  // identity bits: exchange only
+        const bool e = at_f(st.ID);
+        const bool hb = (st.ID[P] & hsm) != 0;
+        if (e != hb) {
+            st.ID[0] ^= fm0;
+            st.ID[1] ^= fm1;
+            if (W2) st.ID[2] ^= fm2;
+            st.ID[P] ^= hsm;
+        }
+    }
+    const uint64_t sm = 1ull << st.s;
+    st.EA |= eA ? sm : 0ull;
+    st.EB |= eB ? sm : 0ull;
+    ++st.s;
+    ++st.k;
+}
+
+// Pivots with the pivot slot in word P (s < 32 for P = 0, s < 64 for P = 1),
+// up to smax pivots.  Returns true when bit k has no qualifying row among the
+// registers while more rows exist (the general loop takes over).
+template <int P>
+__device__ __forceinline__ bool fast_phase(FastCols &st, int nbits, int smax, bool more_rows)
+{
+    const int send = min(smax, 32 * (P + 1));
+    while (st.k < nbits && st.s < send) {
+        const int src = st.k & 31;
+        const bool lo = st.k < 32;
+        const uint32_t c0 = __shfl_sync(kFull, lo ? st.A[0] : st.B[0], src);
+        const uint32_t c1 = __shfl_sync(kFull, lo ? st.A[1] : st.B[1], src);
+        const uint32_t c2 = __shfl_sync(kFull, lo ? st.A[2] : st.B[2], src);
+        if (c0 | c1) {
+            const uint32_t fm0 = c0 & (0u - c0);
+            const uint32_t fm1 = c0 ? 0u : (c1 & (0u - c1));
+            fast_pivot<P, false>(st, c0, c1, c2, fm0, fm1, 0u);
+        } else if (c2) {
+            fast_pivot<P, true>(st, c0, c1, c2, 0u, 0u, c2 & (0u - c2));
+        } else {
+            if (more_rows) return true;
+            ++st.k;  // every remaining row is held and none has bit k
+        }
+    }
+    return false;
 }
 
 // <= 128 registers: 128 x 128 fits next to a 512 x 96 k_rest CTA on one SM
@@ -298,23 +400,18 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
     };
 
     // ------------------------------------------------------------ fast path
-    // The common case: the pivots of the block come from the first 96 rows.
-    // Those rows are loaded once into registers (lane l: positions
-    // R + l, R + 32 + l, R + 64 + l); the window has 32 slots (slot = position
-    // - R mod 32, the lane that holds the row), so every column is a 32-bit
-    // mask.  Each column also carries the 64 probe rows e_p (bit p of the
-    // column's probe word = entry of the reduced e_p): a row v entering the
-    // window is reduced by parity(v & probe word), with no serial chain, and
-    // the probe bits of the broadcast column are the probe part of the L
-    // column of the pivot, which gives Comp directly.  The exchanges are
-    // recorded as (bit, offset) and resolved at the end by tracking the
-    // position of every register row through them, one lane per row.  Any
-    // other situation leaves the fast path after resolving what it did, and
-    // the general loop below takes over.
+    // The common case: the pivots of the block come from the first 96 rows
+    // (positions R..R+95), held in registers for the whole block (see
+    // FastCols).  Every column is kept fully reduced by the pivots found so
+    // far and a row's bits move with the row when it is exchanged, so slots
+    // below the pivot slot are empty and the first qualifying row for bit k
+    // is the lowest set bit of column k.  When more than 96 rows would be
+    // needed the general loop below takes over.
     int k = 0;
     bool fast_complete = false;
     {
-        const int fend = min(R + 3 * 32, n);  // rows available in registers
+        const int fend = min(R + 3 * 32, n);  // rows held in registers: [R, fend)
+        const int nrows = fend - R;
         uint64_t raw[3];
         int srw[3];
 #pragma unroll
@@ -324,121 +421,65 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
         }
 #pragma unroll
         for (int u = 0; u < 3; ++u) raw[u] = srw[u] >= 0 ? Wj[(int64_t)srw[u] * c.ldw] : 0;
-        uint32_t fA = 0, fB = 0, fvalid = 0;
-        uint64_t Apr = 1ull << lane, Bpr = 1ull << (lane + 32);
-        int hs = 0;                      // slot of the pivot slot ib
-        uint32_t hsm = 1u, hmask = ~0u;  // its bit, and the slots at or after it
-        uint64_t smask = 1ull;           // bit s
-        auto fast_refill = [&]() {
-            const int end = min(ib + 32, fend);
-            if (fill >= end) return;
-            const int p = fill + ((R + lane - fill) & 31);
-            const bool isnew = p < end;
-            const int u = (p - R) >> 5;
-            const uint64_t v = isnew ? (u == 0 ? raw[0] : (u == 1 ? raw[1] : raw[2])) : 0;
-            sh.nrow[lane] = v;
-            const uint32_t newm = __ballot_sync(kFull, isnew);
-            __syncwarp();
-            uint32_t na = 0, nb = 0;
-#pragma unroll 8
-            for (int sl = 0; sl < 32; ++sl) {
-                const uint64_t w = sh.nrow[sl];
-                na |= (uint32_t)(__popcll(w & Apr) & 1) << sl;
-                nb |= (uint32_t)(__popcll(w & Bpr) & 1) << sl;
-            }
-            fA |= na & newm;
-            fB |= nb & newm;
-            fvalid |= newm;
-            fill = end;
-            __syncwarp();
-        };
-        fast_refill();
-        bool leave = false;
-        while (k < nbits && ib < n) {
-            if (fill < fend && fill - ib <= 16) fast_refill();
-            const uint32_t ckw = __shfl_sync(kFull, k < 32 ? fA : fB, k & 31);
-            const uint64_t ckp = __shfl_sync(kFull, k < 32 ? Apr : Bpr, k & 31);
-            const uint32_t h = ckw & fvalid;
-            const uint32_t after = h & hmask;
-            const uint32_t pick = after ? after : h;
-            if (!pick) {
-                if (fill < fend && fill < ib + 32) {
-                    fast_refill();
-                    continue;
-                }
-                if (fill >= n) {  // every remaining row is in the window, none has bit k
-                    const uint64_t worv = (uint64_t)__ballot_sync(kFull, (fA & fvalid) != 0) |
-                                          ((uint64_t)__ballot_sync(kFull, (fB & fvalid) != 0) << 32);
-                    const uint64_t above = k + 1 < 64 ? (worv & (~0ull << (k + 1))) : 0;
-                    k = above ? __ffsll((long long)above) - 1 : 64;
-                    continue;
-                }
-                leave = true;
-                break;
-            }
-            const uint32_t fm = pick & (0u - pick);
-            const bool moved = fm != hsm;
-            const bool eA = (fA & fm) != 0, eB = (fB & fm) != 0;
-            const uint32_t keep = ~(fm | hsm);
-            fA = (fA & keep) | ((moved && (fA & hsm)) ? fm : 0u);
-            fB = (fB & keep) | ((moved && (fB & hsm)) ? fm : 0u);
-            fvalid &= ~hsm;
-            const uint32_t ck1 = ckw & keep & fvalid;
-            if (eA) {
-                fA ^= ck1;
-                Apr ^= ckp;
-            }
-            if (eB) {
-                fB ^= ck1;
-                Bpr ^= ckp;
-            }
-            EA |= eA ? smask : 0ull;
-            EB |= eB ? smask : 0ull;
-            sh.rec32[s] = (uint32_t)k | ((uint32_t)((__ffs((int)fm) - 1 - hs) & 31) << 8);
-            sh.Lpr[s] = ckp;
-            hs = (hs + 1) & 31;
-            hsm = hs ? (hsm << 1) : 1u;
-            hmask = hs ? (hmask << 1) : ~0u;
-            smask <<= 1;
-            ++ib;
-            ++s;
-            ++k;
-        }
-        __syncwarp();
-        // resolve the recorded exchanges: final position of every register row
-        int pos[3];
-#pragma unroll
-        for (int u = 0; u < 3; ++u) pos[u] = R + 32 * u + lane;
-        for (int t = 0; t < s; ++t) {
-            const uint32_t rec = sh.rec32[t];
-            const int a = R + t, b = a + (int)(rec >> 8);
-#pragma unroll
-            for (int u = 0; u < 3; ++u) pos[u] = pos[u] == a ? b : (pos[u] == b ? a : pos[u]);
-        }
+        FastCols st;
 #pragma unroll
         for (int u = 0; u < 3; ++u) {
-            if (srw[u] < 0) continue;
-            if (pos[u] != R + 32 * u + lane) c.perm[pos[u]] = srw[u];
-            if (pos[u] < R + s) {
-                sh.B[pos[u] - R] = raw[u];
-                c.pivpanel[srw[u]] = j;
+            st.A[u] = transpose32((uint32_t)raw[u], lane);
+            st.B[u] = transpose32((uint32_t)(raw[u] >> 32), lane);
+            st.ID[u] = slot_index_bits(u, lane);
+            sh.fraw[32 * u + lane] = raw[u];
+            sh.fsrow[32 * u + lane] = srw[u];
+        }
+        st.EA = 0;
+        st.EB = 0;
+        st.k = 0;
+        st.s = 0;
+        const int smax = min(64, nrows);
+        const bool more_rows = fend < n;
+        bool leave = fast_phase<0>(st, nbits, smax, more_rows);
+        if (!leave) leave = fast_phase<1>(st, nbits, smax, more_rows);
+        __syncwarp();
+        s = st.s;
+        k = st.k;
+        EA = st.EA;
+        EB = st.EB;
+        // the row now at each position: its original slot from the
+        // identity bits, then its storage row and raw word
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            int q = 0;
+#pragma unroll
+            for (int b = 0; b < 7; ++b) q |= (int)((__shfl_sync(kFull, st.ID[u], b) >> lane) & 1) << b;
+            const int p = 32 * u + lane;
+            if (p < nrows) {
+                const int srow = sh.fsrow[q];
+                if (q != p) c.perm[R + p] = srow;
+                if (p < s) {
+                    sh.B[p] = sh.fraw[q];
+                    c.pivpanel[srow] = j;
+                }
             }
         }
-        for (int t = lane; t < s; t += 32) {
-            const int kt = (int)(sh.rec32[t] & 255);
-            sh.pb[t] = kt;
-            sh.sidx[kt] = t;
+        // the bit of pivot t is the lowest set bit of E_t: E_t is zero at the
+        // earlier pivot bits and at the bits that got no pivot before it
+        {
+            uint64_t e2[2] = {EA, EB};
+            transpose64(e2, lane);  // e2[h] = E_{lane + 32h}
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int t = lane + 32 * hh;
+                if (t < s) {
+                    const int kt = __ffsll((long long)e2[hh]) - 1;
+                    sh.pb[t] = kt;
+                    sh.sidx[kt] = t;
+                }
+            }
         }
         __syncwarp();
         s_done = s;
+        ib = R + s;
         fill = ib;  // the general loop starts from an empty window
-        if (!leave) {
-            fast_complete = true;
-            uint64_t l2[2] = {s > lane ? sh.Lpr[lane] : 0ull, s > lane + 32 ? sh.Lpr[lane + 32] : 0ull};
-            transpose64(l2, lane);  // Comp[p] bit t = probe p received E_t
-            sh.Comp[lane] = l2[0];
-            sh.Comp[lane + 32] = l2[1];
-        }
+        if (!leave) fast_complete = true;
     }
 
     if (!fast_complete) refill();
@@ -556,21 +597,29 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
     }
     __syncwarp();
     const int c0 = lane, c1 = lane + 32;
-    // rows c0, c1 of U^-1: U^T y = e_c, forward over t > c (fixed trip count);
-    // Comp at the pivot bits.  (The fast path already has Comp from its probes.)
-    if (!fast_complete) {
-        uint64_t y0 = c0 < s ? (1ull << c0) : 0, y1 = c1 < s ? (1ull << c1) : 0;
-#pragma unroll 8
-        for (int t = 1; t < 64; ++t) {
-            const uint64_t u = sh.Ucol[t];
-            const bool ok = t < s;
-            const uint64_t b0 = (uint64_t)(__popcll(u & y0) & 1) << t;
-            const uint64_t b1 = (uint64_t)(__popcll(u & y1) & 1) << t;
-            if (ok && t > c0) y0 |= b0;
-            if (ok && t > c1) y1 |= b1;
+    // Both triangular inverses by a backward column sweep over a unit upper
+    // triangular M (column t in Mcol[t], bits <= t): x = e_c; for t from the
+    // top down, x[t] is final once the columns above it have been removed,
+    // and column t leaves the right-hand side when x[t] = 1.  Two test-and-
+    // XOR steps per column, no parity chain.  U x = e_c gives column c of
+    // U^-1; T^T y = e_c (column t of T^T = row t of T) gives row c of T^-1.
+    auto sweep = [&](const uint64_t *Mcol, uint64_t x[2]) {
+        x[0] = c0 < s ? (1ull << c0) : 0;
+        x[1] = c1 < s ? (1ull << c1) : 0;
+#pragma unroll 4
+        for (int t = 63; t > 0; --t) {
+            const uint64_t u = Mcol[t] & ((1ull << t) - 1);
+            if ((x[0] >> t) & 1) x[0] ^= u;
+            if ((x[1] >> t) & 1) x[1] ^= u;
         }
-        sh.TI[c0] = y0;  // staging: rows of U^-1
-        sh.TI[c1] = y1;
+    };
+    // rows of U^-1 (staged in TI), then Comp at the pivot bits
+    {
+        uint64_t x[2];
+        sweep(sh.Ucol, x);
+        transpose64(x, lane);  // x[h] = row lane + 32h of U^-1
+        sh.TI[c0] = x[0];
+        sh.TI[c1] = x[1];
         __syncwarp();
         const int t0 = sh.sidx[c0], t1 = sh.sidx[c1];
         sh.Comp[c0] = t0 >= 0 ? sh.TI[t0] : 0;
@@ -591,25 +640,13 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
         sh.T[c1] = a1;
     }
     __syncwarp();
-    // T^-1 by columns: T x = e_c, x[t] = parity(T[t] & x) for t > c
-    uint64_t x2[2];
     {
-        uint64_t x0 = c0 < s ? (1ull << c0) : 0, x1 = c1 < s ? (1ull << c1) : 0;
-#pragma unroll 8
-        for (int t = 1; t < 64; ++t) {
-            const uint64_t tt = sh.T[t];
-            const bool ok = t < s;
-            const uint64_t b0 = (uint64_t)(__popcll(tt & x0) & 1) << t;
-            const uint64_t b1 = (uint64_t)(__popcll(tt & x1) & 1) << t;
-            if (ok && t > c0) x0 |= b0;
-            if (ok && t > c1) x1 |= b1;
-        }
-        x2[0] = x0;
-        x2[1] = x1;
+        uint64_t y[2];
+        sweep(sh.T, y);  // y[h] = row lane + 32h of T^-1
+        __syncwarp();
+        sh.TI[c0] = y[0];
+        sh.TI[c1] = y[1];
     }
-    transpose64(x2, lane);  // rows of T^-1
-    sh.TI[c0] = x2[0];
-    sh.TI[c1] = x2[1];
     __syncwarp();
     if (lane == 0) {
         pi->R = R;
