@@ -145,6 +145,36 @@ int gf2_decompose_host(int64_t n, int64_t m, const uint64_t *A_host, int64_t lda
                        void *workspace, size_t ws_bytes, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Linear systems A X = B over F2 from the factors of P*A = L*E (the use of
+ * the decomposition in Section 1 of the paper; forward and back
+ * substitution with the factors of Lemma 4.1).
+ *   L, E, perm, pivcols, rank   exactly as gf2_decompose wrote them for an
+ *           n x m matrix A (L is n x min(n,m), E is min(n,m) x m; device).
+ *   B       n x nrhs, 1 <= nrhs <= 64: one column block, so row i of B is the
+ *           word B->w[i] (bit c = right-hand side c).  Not modified.
+ *   X       m x nrhs (one column block), receives the solutions: for every
+ *           consistent right-hand side c, column c of X is the solution with
+ *           every free variable (non-pivot column) 0; the column of an
+ *           inconsistent right-hand side is 0.
+ *   consistent  device uint64: bit c set iff A x = column c of B has a
+ *           solution (bits >= nrhs are 0).
+ * Steps: v = P B; forward substitution with the unit lower triangle of L
+ * (rows < r); right-hand side c is consistent iff bit c of every residual
+ * row r..n-1 is 0; back substitution with E at the pivot columns.
+ * The call synchronises the stream once, to read the status of its bounded
+ * device-side waits and of the padding check.
+ * Errors: GF2_ERR_ARG (NULL, bad flag), GF2_ERR_SHAPE (nrhs outside 1..64,
+ * X not m x nrhs, L or E not the sizes above), GF2_ERR_PADDING (a bit of B
+ * at a column >= nrhs; checked unless GF2_NOCHECK), GF2_ERR_NOMEM,
+ * GF2_ERR_UNSUPPORTED (n or m >= 2^31), GF2_ERR_TIMEOUT (a grid-wide wait
+ * gave up; the outputs are then undefined), GF2_ERR_CUDA.
+ */
+size_t gf2_solve_workspace_bytes(int64_t n, int64_t m);
+int gf2_solve(const gf2_mat *L, const gf2_mat *E, const int32_t *perm, const int32_t *pivcols,
+              const int64_t *rank, const gf2_mat *B, gf2_mat *X, uint64_t *consistent,
+              unsigned flags, void *workspace, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
  * Diagnostics (no counterpart in the paper; used by the benchmark).
  * gf2_launch_count: kernels this library has launched since it was loaded.
  * gf2_timing_enable(1): from now on every launch is bracketed by CUDA events
@@ -158,7 +188,8 @@ int gf2_decompose_host(int64_t n, int64_t m, const uint64_t *A_host, int64_t lda
 #define GF2_KCLASS_NEXT 1    /* Y = D Z, L multipliers, next column tile     */
 #define GF2_KCLASS_UPDATE 2  /* wide trailing update / product pass (M4RM)   */
 #define GF2_KCLASS_LAYOUT 3  /* layout conversions and final outputs         */
-#define GF2_NUM_KCLASSES 4
+#define GF2_KCLASS_SOLVE 4   /* forward / back substitution (gf2_solve)      */
+#define GF2_NUM_KCLASSES 5
 int64_t gf2_launch_count(void);
 int gf2_timing_enable(int on);
 int gf2_timing_reset(void);

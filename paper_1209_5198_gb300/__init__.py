@@ -33,7 +33,7 @@ GF2_ERR_CUDA = 5
 GF2_ERR_TIMEOUT = 6
 GF2_ERR_UNSUPPORTED = 7
 GF2_NOCHECK = 1
-KCLASS = {"panel": 0, "next": 1, "update": 2, "layout": 3}
+KCLASS = {"panel": 0, "next": 1, "update": 2, "layout": 3, "solve": 4}
 
 
 class Gf2Error(RuntimeError):
@@ -81,6 +81,10 @@ def load() -> ctypes.CDLL:
     lib.gf2_decompose_host_workspace_bytes.argtypes = [I64, I64, ctypes.c_int]
     lib.gf2_decompose_host.restype = ctypes.c_int
     lib.gf2_decompose_host.argtypes = [I64, I64, P, I64, P, P, P, P, P, ctypes.c_uint, P, S, P]
+    lib.gf2_solve_workspace_bytes.restype = S
+    lib.gf2_solve_workspace_bytes.argtypes = [I64, I64]
+    lib.gf2_solve.restype = ctypes.c_int
+    lib.gf2_solve.argtypes = [M, M, P, P, P, M, M, P, ctypes.c_uint, P, S, P]
     lib.gf2_launch_count.restype = ctypes.c_int64
     lib.gf2_timing_enable.argtypes = [ctypes.c_int]
     lib.gf2_timing_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)]
@@ -208,6 +212,20 @@ def gf2_decompose_host(n: int, m: int, A_host: np.ndarray, perm_host: np.ndarray
                                   _stream(stream)), "gf2_decompose_host")
 
 
+def gf2_solve(L: Mat, E: Mat, perm: torch.Tensor, pivcols: torch.Tensor, rank: torch.Tensor, B: Mat, X: Mat,
+              consistent: torch.Tensor, flags: int = 0, workspace=None, stream=None) -> None:
+    """A X = B from the factors gf2_decompose wrote (B: n x nrhs, X: m x nrhs,
+    nrhs <= 64; consistent: int64 [1] on the device).  Synchronises the stream."""
+    lib = load()
+    n, m = B.rows, X.rows
+    if workspace is None:
+        workspace = _workspace(lib.gf2_solve_workspace_bytes(n, m), B.t.device)
+    l, e, b, x = L.c(), E.c(), B.c(), X.c()
+    _check(lib.gf2_solve(ctypes.byref(l), ctypes.byref(e), _ptr(perm), _ptr(pivcols), _ptr(rank), ctypes.byref(b),
+                         ctypes.byref(x), _ptr(consistent), flags, workspace.data_ptr(), workspace.numel(),
+                         _stream(stream)), "gf2_solve")
+
+
 # ----------------------------------------------------------------- helpers
 
 def decompose(A: Mat, factors: bool = True, flags: int = 0, stream=None) -> dict:
@@ -222,6 +240,16 @@ def decompose(A: Mat, factors: bool = True, flags: int = 0, stream=None) -> dict
     E = Mat.empty(k, m, dev) if factors else None
     gf2_decompose(A, perm, piv, rank, L, E, flags=flags, stream=stream)
     return dict(perm=perm[:n], pivcols=piv[:k], rank=rank, L=L, E=E)
+
+
+def solve(factors: dict, B: Mat, m: int, stream=None) -> dict:
+    """Solves A X = B with the output of decompose(); returns X (Mat, m x nrhs)
+    and the consistency mask (int)."""
+    X = Mat.empty(m, B.cols, B.t.device)
+    ok = torch.zeros(1, dtype=torch.int64, device=B.t.device)
+    gf2_solve(factors["L"], factors["E"], factors["perm"], factors["pivcols"], factors["rank"], B, X, ok,
+              stream=stream)
+    return dict(X=X, consistent=int(ok.cpu().numpy().view(np.uint64)[0]))
 
 
 def mmm(A: Mat, B: Mat, stream=None) -> Mat:

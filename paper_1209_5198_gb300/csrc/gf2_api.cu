@@ -411,7 +411,7 @@ const char *gf2_status_string(int status)
     }
 }
 
-int gf2_version(void) { return 1; }
+int gf2_version(void) { return 2; }
 
 int gf2_release_workspace(void)
 {
@@ -523,6 +523,69 @@ int gf2_decompose_host(int64_t n, int64_t m, const uint64_t *A_host, int64_t lda
     if (L_host && lw > 0) CK(cudaMemcpyAsync(L_host, Ld, (size_t)lw * n * 8, cudaMemcpyDeviceToHost, s));
     if (E_host && kmax > 0) CK(cudaMemcpyAsync(E_host, Ed, (size_t)mu * kmax * 8, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    return GF2_OK;
+}
+
+// ------------------------------------------------------------ solve
+size_t gf2_solve_workspace_bytes(int64_t n, int64_t m)
+{
+    if (n < 0 || m < 0) return 0;
+    const int64_t kmax = n < m ? n : m, mu = words_of(m), nbl = words_of(kmax);
+    return align_up((size_t)(n > 0 ? n : 1) * 8) + align_up((size_t)(kmax > 0 ? kmax : 1) * 8) +
+           align_up((size_t)(nbl > 0 ? nbl : 1) * 64 * 8) + align_up((size_t)(mu > 0 ? mu : 1) * 64 * 8) +
+           align_up((size_t)(mu + 1) * 4) + kAlign;
+}
+
+int gf2_solve(const gf2_mat *L, const gf2_mat *E, const int32_t *perm, const int32_t *pivcols, const int64_t *rank,
+              const gf2_mat *B, gf2_mat *X, uint64_t *consistent, unsigned flags, void *workspace, size_t ws_bytes,
+              void *stream)
+{
+    if (!mat_ok(L) || !mat_ok(E) || !mat_ok(B) || !mat_ok(X) || !rank || !consistent || (flags & ~GF2_NOCHECK))
+        return GF2_ERR_ARG;
+    const int64_t n = B->rows, m = X->rows, kmax = n < m ? n : m, nrhs = B->cols;
+    if (nrhs < 1 || nrhs > 64 || X->cols != nrhs) return GF2_ERR_SHAPE;
+    if (L->rows != n || L->cols != kmax || E->rows != kmax || E->cols != m) return GF2_ERR_SHAPE;
+    if (n >= (1ll << 31) || m >= (1ll << 31)) return GF2_ERR_UNSUPPORTED;
+    if ((n > 0 && (!perm || !B->w)) || (kmax > 0 && !pivcols) || (m > 0 && !X->w)) return GF2_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *ws = nullptr;
+    int st = get_workspace(workspace, ws_bytes, gf2_solve_workspace_bytes(n, m), &ws);
+    if (st) return st;
+    const int64_t mu = words_of(m), nbl = words_of(kmax);
+    char *p = static_cast<char *>(ws);
+    SolveCtx c{};
+    c.v = reinterpret_cast<uint64_t *>(p); p += align_up((size_t)(n > 0 ? n : 1) * 8);
+    c.y = reinterpret_cast<uint64_t *>(p); p += align_up((size_t)(kmax > 0 ? kmax : 1) * 8);
+    c.linv = reinterpret_cast<uint64_t *>(p); p += align_up((size_t)(nbl > 0 ? nbl : 1) * 64 * 8);
+    c.uinv = reinterpret_cast<uint64_t *>(p); p += align_up((size_t)(mu > 0 ? mu : 1) * 64 * 8);
+    c.qstart = reinterpret_cast<int32_t *>(p); p += align_up((size_t)(mu + 1) * 4);
+    c.sync = reinterpret_cast<uint32_t *>(p);
+    c.bad = reinterpret_cast<uint64_t *>(p + 64);
+    c.perm = perm;
+    c.pivcols = pivcols;
+    c.rank = rank;
+    c.L = L->w;
+    c.ldl = L->ld;
+    c.E = E->w;
+    c.lde = E->ld;
+    c.B = B->w;
+    c.X = X->w;
+    c.consistent = consistent;
+    c.rhs_mask = nrhs == 64 ? ~0ull : ((1ull << nrhs) - 1);
+    c.n = (int32_t)n;
+    c.m = (int32_t)m;
+    c.check = (flags & GF2_NOCHECK) ? 0 : 1;
+    CK(cudaMemsetAsync(p, 0, kAlign, s));
+    LAUNCH(GF2_KCLASS_SOLVE, launch_solve(c, s));
+    // the status of the bounded waits and of the padding check
+    std::lock_guard<std::mutex> lock(g_flag_mutex);
+    if (!g_flag_host) {
+        if (cudaHostAlloc(&g_flag_host, sizeof(uint32_t), cudaHostAllocDefault) != cudaSuccess) return GF2_ERR_CUDA;
+    }
+    CK(cudaMemcpyAsync(g_flag_host, c.sync + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (*g_flag_host & 1u) return GF2_ERR_TIMEOUT;
+    if (*g_flag_host & 2u) return GF2_ERR_PADDING;
     return GF2_OK;
 }
 

@@ -62,6 +62,27 @@ struct MmmCtx {
     int32_t n, k;
 };
 
+// Operands of a solve A X = B from the factors P*A = L*E (column blocks).
+struct SolveCtx {
+    const int32_t *perm, *pivcols;
+    const int64_t *rank;
+    const uint64_t *L; int64_t ldl;   // n x min(n,m)
+    const uint64_t *E; int64_t lde;   // min(n,m) x m
+    const uint64_t *B;                // [n] right-hand sides, bit c = column c
+    uint64_t *X;                      // [m] solutions
+    uint64_t *consistent;             // one word: bit c = right-hand side c is consistent
+    uint64_t rhs_mask;                // the nrhs low bits
+    uint64_t *v;                      // [n] P*B, then the residual rows
+    uint64_t *y;                      // [min(n,m)] forward result, then back-substitution state
+    uint64_t *linv;                   // [ceil(min(n,m)/64)][64] inverse diagonal blocks of L (rows)
+    uint64_t *uinv;                   // [ceil(m/64)][64] inverse diagonal blocks of E at its pivots
+    int32_t *qstart;                  // [ceil(m/64)+1] first pivot whose column is >= 64q
+    uint32_t *sync;                   // [2] barrier count, error bits (1 wait gave up, 2 padding)
+    uint64_t *bad;                    // one word: OR of the residual rows
+    int32_t n, m;
+    int32_t check;                    // report right-hand-side bits beyond nrhs
+};
+
 // ---- launchers (each returns the cudaError_t of its launch)
 cudaError_t launch_ingest(const uint64_t *A, int64_t lda, int32_t n, int32_t mu, uint64_t last_mask,
                           uint64_t *W, int64_t ldw, int32_t *perm_identity, int32_t *pivpanel_init,
@@ -78,5 +99,6 @@ int rest_tiles(const DecompCtx &c, int j, int *tile_first);
 cudaError_t prepare_update_kernels();  // one-time kernel attributes (before any capture)
 cudaError_t prepare_panel_kernel();
 cudaError_t launch_mmm_pass(const MmmCtx &c, int kb, int m_words, cudaStream_t s);
+cudaError_t launch_solve(const SolveCtx &c, cudaStream_t s);  // one cooperative launch
 
 }  // namespace gf2

@@ -59,3 +59,23 @@ def test_argument_errors_without_gpu(lib):
     # unknown flag
     assert lib.gf2_decompose(ctypes.byref(b), ctypes.c_void_p(8), ctypes.c_void_p(8), ctypes.c_void_p(8),
                              None, None, 0x80, None, 0, None) == g.GF2_ERR_ARG
+
+
+def test_solve_argument_errors_without_gpu(lib):
+    import paper_1209_5198_gb300 as g
+    P = ctypes.c_void_p(8)
+    L = g._CMat(1, 10, 10, 10)
+    E = g._CMat(2, 10, 10, 10)
+    B = g._CMat(3, 10, 64, 10)
+    X = g._CMat(4, 10, 64, 10)
+    args = lambda b, x: (ctypes.byref(L), ctypes.byref(E), P, P, P, ctypes.byref(b), ctypes.byref(x), P, 0, None, 0, None)
+    assert lib.gf2_solve(None, None, None, None, None, None, None, None, 0, None, 0, None) == g.GF2_ERR_ARG
+    B65 = g._CMat(3, 10, 65, 10)
+    X65 = g._CMat(4, 10, 65, 10)
+    assert lib.gf2_solve(*args(B65, X65)) == g.GF2_ERR_SHAPE       # more than 64 right-hand sides
+    X3 = g._CMat(4, 10, 3, 10)
+    assert lib.gf2_solve(*args(B, X3)) == g.GF2_ERR_SHAPE          # X has other columns than B
+    X12 = g._CMat(4, 12, 64, 12)
+    assert lib.gf2_solve(*args(B, X12)) == g.GF2_ERR_SHAPE         # E is not min(n,m) x m
+    assert lib.gf2_solve_workspace_bytes(-1, 5) == 0
+    assert lib.gf2_solve_workspace_bytes(32768, 32768) >= 8 * (32768 + 32768 + 2 * 512 * 64)
