@@ -316,7 +316,8 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
 
     DecompCtx c{};
     c.W = reinterpret_cast<uint64_t *>(base + d.oW);
-    c.ldw = d.ldw;
+    c.tstride = n * kTileWords;
+    c.lde = d.ldw;
     c.perm = perm;
     c.pivcols = pivcols;
     c.info = reinterpret_cast<PanelInfo *>(base + d.oInfo);
@@ -332,14 +333,14 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
     uint32_t *flag = reinterpret_cast<uint32_t *>(base + d.oFlag);
 
     if (n == 0 || m == 0) {
-        if (n > 0) LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest(A->w, A->ld > 0 ? A->ld : 1, (int32_t)n, 0, ~0ull, c.W, d.ldw, perm, nullptr, nullptr, s));
+        if (n > 0) LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest_tiled(A->w, A->ld > 0 ? A->ld : 1, (int32_t)n, 0, ~0ull, c.W, perm, nullptr, nullptr, s));
         CK(cudaMemsetAsync(rank, 0, sizeof(int64_t), s));
         if (L && n > 0 && L->cols > 0) CK(cudaMemsetAsync(L->w, 0, (size_t)L->ld * words_of(L->cols) * 8, s));
         return GF2_OK;
     }
 
     CK(cudaMemsetAsync(flag, 0, sizeof(uint32_t), s));
-    LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest(A->w, A->ld, (int32_t)n, (int32_t)d.mu, last_word_mask(m), c.W, d.ldw, perm, c.pivpanel, flag, s));
+    LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest_tiled(A->w, A->ld, (int32_t)n, (int32_t)d.mu, last_word_mask(m), c.W, perm, c.pivpanel, flag, s));
     if (!(flags & GF2_NOCHECK)) {
         st = check_flag(flag, s);
         if (st) return st;

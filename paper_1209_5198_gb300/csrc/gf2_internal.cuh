@@ -35,13 +35,19 @@ struct PanelInfo {
     uint64_t Erow[64];  // E_s restricted to the panel's 64 columns
 };
 
-// Device state of one decomposition.  W is a row-major copy of A: storage
+// Device state of one decomposition.  W is a working copy of A: storage
 // row i is row i of A and never moves; perm maps positions to storage rows
 // (row i of P*A is storage row perm[i]), so a row exchange is an exchange of
-// two perm entries and no data moves.
+// two perm entries and no data moves.  W is TILED by 8-word column tiles:
+// tile T holds words 8T..8T+7 of every storage row, row after row (64
+// contiguous bytes per row), so word q of row i is at
+//   W[(q / 8) * tstride + 8 * i + q % 8],   tstride = 8 * n.
+// A warp that updates 8 consecutive rows of a tile touches 512 contiguous
+// bytes.
 struct DecompCtx {
     uint64_t *W;
-    int64_t ldw;        // words per row of W, a multiple of kTileWords
+    int64_t tstride;    // words from one column tile of W to the next (8 * n)
+    int64_t lde;        // words per row of Eint, a multiple of kTileWords
     int32_t *perm;      // [n] position -> storage row (the output perm)
     int32_t *pivcols;   // [k]
     PanelInfo *info;    // [mu]
@@ -49,9 +55,15 @@ struct DecompCtx {
     int32_t *pivpanel;  // [n] per storage row: panel where it became a pivot (INT32_MAX: not yet)
     uint64_t *Lint;     // [n x ldl] per storage row, or null (rank only)
     int64_t ldl;
-    uint64_t *Eint;     // [k x ldw] per pivot index, or null
+    uint64_t *Eint;     // [k x lde] per pivot index (row-major), or null
     int32_t n, m, mu, kmax;
 };
+
+// Index of word q of storage row i in the tiled W.
+__device__ __forceinline__ int64_t widx(const DecompCtx &c, int64_t i, int q)
+{
+    return (int64_t)(q >> 3) * c.tstride + i * kTileWords + (q & 7);
+}
 
 // Row-major operands of a product C ^= A * B over F2 for one 64-row slice
 // of B (k-block kb): the multiplier of row i is word kb of A's row i.
@@ -86,7 +98,10 @@ struct SolveCtx {
 // ---- launchers (each returns the cudaError_t of its launch)
 cudaError_t launch_ingest(const uint64_t *A, int64_t lda, int32_t n, int32_t mu, uint64_t last_mask,
                           uint64_t *W, int64_t ldw, int32_t *perm_identity, int32_t *pivpanel_init,
-                          uint32_t *err, cudaStream_t s);
+                          uint32_t *err, cudaStream_t s);  // row-major W (ldw words per row)
+cudaError_t launch_ingest_tiled(const uint64_t *A, int64_t lda, int32_t n, int32_t mu, uint64_t last_mask,
+                                uint64_t *W, int32_t *perm_identity, int32_t *pivpanel_init, uint32_t *err,
+                                cudaStream_t s);  // tiled W (see DecompCtx), words up to a multiple of 8
 cudaError_t launch_colblocks_from_rowmajor(const uint64_t *R, int64_t ldr, const int32_t *row_of,
                                            int32_t rows, int32_t words, uint64_t *out, int64_t ldo,
                                            cudaStream_t s);

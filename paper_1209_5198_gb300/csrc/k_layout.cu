@@ -1,6 +1,7 @@
 // Layout kernels: the boundary's column-block layout (Section 3 of the
-// paper: word (i, q) at q*ld + i) to and from the row-major working layout
-// used inside the library, plus the final scalar outputs.
+// paper: word (i, q) at q*ld + i) to and from the working layouts used
+// inside the library (the tiled copy of A of the decomposition, row-major
+// operands of the product and the factors), plus the final scalar outputs.
 //
 // All of them are 32 x 32-word tile transposes through shared memory so that
 // both the column-block side (consecutive rows contiguous) and the row-major
@@ -14,9 +15,12 @@ namespace {
 constexpr int kT = 32;     // tile edge (words)
 constexpr int kTy = 8;     // threads in y; each thread moves kT / kTy words
 
-// A (column blocks, n rows, mu blocks) -> W (row-major, ldw words per row).
-// Words q >= mu of W are written as zero.  Bits beyond the last column of
-// the last block are checked against last_mask; any violation sets *err.
+// A (column blocks, n rows, mu blocks) -> W: row-major with ldw words per
+// row, or (TILED) in 8-word column tiles of 8*n words (word q of row i at
+// (q/8)*8n + 8i + q%8) with ldw = mu rounded up to 8.  Words q >= mu of W are
+// written as zero.  Bits beyond the last column of the last block are
+// checked against last_mask; any violation sets *err.
+template <bool TILED>
 __global__ void k_ingest(const uint64_t *__restrict__ A, int64_t lda, int32_t n, int32_t mu,
                          uint64_t last_mask, uint64_t *__restrict__ W, int64_t ldw,
                          int32_t *__restrict__ perm, int32_t *__restrict__ pivpanel,
@@ -41,7 +45,10 @@ __global__ void k_ingest(const uint64_t *__restrict__ A, int64_t lda, int32_t n,
 #pragma unroll
     for (int k = 0; k < kT / kTy; ++k) {
         const int i = i0 + ty + k * kTy, q = q0 + tx;
-        if (i < n && q < ldw) W[(int64_t)i * ldw + q] = tile[tx][ty + k * kTy];
+        if (i < n && q < ldw) {
+            const int64_t o = TILED ? (int64_t)(q >> 3) * 8 * n + (int64_t)i * 8 + (q & 7) : (int64_t)i * ldw + q;
+            W[o] = tile[tx][ty + k * kTy];
+        }
     }
     if (blockIdx.y == 0 && ty == 0 && i0 + tx < n) {
         if (perm) perm[i0 + tx] = i0 + tx;
@@ -118,7 +125,18 @@ cudaError_t launch_ingest(const uint64_t *A, int64_t lda, int32_t n, int32_t mu,
 {
     if (n <= 0) return cudaSuccess;
     dim3 grid((n + kT - 1) / kT, (unsigned)((ldw + kT - 1) / kT)), block(kT, kTy);
-    k_ingest<<<grid, block, 0, s>>>(A, lda, n, mu, last_mask, W, ldw, perm_identity, pivpanel_init, err);
+    k_ingest<false><<<grid, block, 0, s>>>(A, lda, n, mu, last_mask, W, ldw, perm_identity, pivpanel_init, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ingest_tiled(const uint64_t *A, int64_t lda, int32_t n, int32_t mu, uint64_t last_mask,
+                                uint64_t *W, int32_t *perm_identity, int32_t *pivpanel_init, uint32_t *err,
+                                cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t ldw = ((mu > 0 ? mu : 1) + kTileWords - 1) / kTileWords * kTileWords;
+    dim3 grid((n + kT - 1) / kT, (unsigned)((ldw + kT - 1) / kT)), block(kT, kTy);
+    k_ingest<true><<<grid, block, 0, s>>>(A, lda, n, mu, last_mask, W, ldw, perm_identity, pivpanel_init, err);
     return cudaGetLastError();
 }
 
@@ -136,7 +154,7 @@ cudaError_t launch_finish_E(const DecompCtx &c, uint64_t *E, int64_t lde, cudaSt
 {
     if (c.kmax <= 0 || c.mu <= 0) return cudaSuccess;
     dim3 grid((c.kmax + kT - 1) / kT, (c.mu + kT - 1) / kT), block(kT, kTy);
-    k_finish_E<<<grid, block, 0, s>>>(c.Eint, c.ldw, c.pivcols, c.info + (c.mu - 1), c.kmax, c.mu, E, lde);
+    k_finish_E<<<grid, block, 0, s>>>(c.Eint, c.lde, c.pivcols, c.info + (c.mu - 1), c.kmax, c.mu, E, lde);
     return cudaGetLastError();
 }
 

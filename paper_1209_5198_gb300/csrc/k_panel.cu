@@ -107,7 +107,7 @@ __device__ void scan_find(const DecompCtx &c, const uint64_t *Wj, PanelShared &s
         }
         uint64_t v[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) v[u] = srow[u] >= 0 ? Wj[(int64_t)srow[u] * c.ldw] : 0;
+        for (int u = 0; u < U; ++u) v[u] = srow[u] >= 0 ? Wj[(int64_t)srow[u] * kTileWords] : 0;
         int hit = 0;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -146,7 +146,7 @@ __device__ void scan_or(const DecompCtx &c, const uint64_t *Wj, PanelShared &sh)
         }
         uint64_t v[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) v[u] = srow[u] >= 0 ? Wj[(int64_t)srow[u] * c.ldw] : 0;
+        for (int u = 0; u < U; ++u) v[u] = srow[u] >= 0 ? Wj[(int64_t)srow[u] * kTileWords] : 0;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             uint64_t r = 0;
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
     const int n = c.n;
     const int nbits = min(64, c.m - 64 * j);
     PanelInfo *pi = c.info + j;
-    const uint64_t *Wj = c.W + j;
+    const uint64_t *Wj = c.W + (int64_t)(j >> 3) * c.tstride + (j & 7);  // word j of storage row i: Wj[8 i]
 
     if (R >= n || nbits <= 0) {
         if (tid == 0) {
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
             raw[u] = 0;
             if (isnew[u]) {
                 const int srow = c.perm[p];
-                raw[u] = Wj[(int64_t)srow * c.ldw];
+                raw[u] = Wj[(int64_t)srow * kTileWords];
                 sh.slot_srow[slot] = srow;
                 sh.slot_raw[slot] = raw[u];
             }
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
             srw[u] = p < fend ? c.perm[p] : -1;
         }
 #pragma unroll
-        for (int u = 0; u < 3; ++u) raw[u] = srw[u] >= 0 ? Wj[(int64_t)srw[u] * c.ldw] : 0;
+        for (int u = 0; u < 3; ++u) raw[u] = srw[u] >= 0 ? Wj[(int64_t)srw[u] * kTileWords] : 0;
         FastCols st;
 #pragma unroll
         for (int u = 0; u < 3; ++u) {
@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
                     // pivot outside the window; the row in the pivot slot
                     // moves there and leaves the window
                     const int psrow = c.perm[q];
-                    const uint64_t v = Wj[(int64_t)psrow * c.ldw];
+                    const uint64_t v = Wj[(int64_t)psrow * kTileWords];
                     uint64_t red = 0;
                     for (uint64_t b = v; b; b &= b - 1) red ^= sh.pred[__ffsll((long long)b) - 1];
                     const uint32_t eA = (red >> lane) & 1, eB = (red >> (lane + 32)) & 1;

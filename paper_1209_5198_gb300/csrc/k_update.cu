@@ -12,12 +12,14 @@
 //   k_rest  every column tile after that one; persistent (one CTA per SM),
 //           each CTA takes a contiguous range of (tile, row chunk) items and
 //           rebuilds its tables only when the tile changes.
-// Rows are visited in STORAGE order (row-major W, storage row = row of A):
+// Rows are visited in STORAGE order (tiled W, storage row = row of A):
 // the multiplier array is indexed by storage row and is zero for rows that
 // are already pivots, so no position->row indirection sits in the hot loop.
 //
-// GB300 layout choices: one row's 8-word tile is 64 contiguous bytes; a warp
-// covers 8 rows x 8 words with 128-bit accesses (lane = row slot (lane/4) x
+// GB300 layout choices: W is stored by 8-word column tiles, each tile
+// contiguous over the rows, so one row's tile is 64 contiguous bytes and 8
+// consecutive rows of a tile are 512; a warp covers 8 rows x 8 words with
+// 128-bit accesses (lane = row slot (lane/4) x
 // word pair (lane%4)); the tables sit in shared memory as
 // [table pair][x][half][8 words], and the two rows of a quarter-warp (one
 // 128-bit shared-memory phase) read tables g and g^1, which live in opposite
@@ -97,7 +99,7 @@ __device__ __forceinline__ void load_pivot_rows(const DecompCtx &c, int R, int r
     for (int idx = threadIdx.x; idx < 64 * kTileWords; idx += T) {
         const int t = idx / kTileWords, w = idx % kTileWords;
         uint64_t v = 0;
-        if (t < r) v = c.W[(int64_t)c.perm[R + t] * c.ldw + q0 + w];
+        if (t < r) v = c.W[widx(c, c.perm[R + t], q0 + w)];
         crow[idx] = v;
     }
 }
@@ -115,7 +117,7 @@ __device__ __forceinline__ void echelon_rows(const DecompCtx &c, const PanelInfo
         uint64_t acc = 0;
         for (int g = 0; g < ng; ++g)
             acc ^= tab[tab_entry<C>(g, (int)((ym >> (C * g)) & (Tabs<C>::X - 1))) * kTileWords + w];
-        c.Eint[(int64_t)(R + t) * c.ldw + q] = acc;
+        c.Eint[(int64_t)(R + t) * c.lde + q] = acc;
     }
 }
 
@@ -155,10 +157,10 @@ __global__ void __launch_bounds__(kNextThreads) k_next(DecompCtx c, int j)
     for (int u = 0; u < U; ++u) {
         row[u] = rb + (warp * U + u) * 8 + rs;
         const bool in = row[u] < re;
-        const uint64_t *Wr = c.W + (int64_t)(in ? row[u] : 0) * c.ldw;
+        const int64_t rr = in ? row[u] : 0;
         active[u] = in && c.pivpanel[row[u]] > j;
-        d[u] = in ? Wr[j] : 0;
-        a[u] = (in && live) ? *reinterpret_cast<const ulonglong2 *>(Wr + col) : make_ulonglong2(0, 0);
+        d[u] = in ? c.W[widx(c, rr, j)] : 0;
+        a[u] = (in && live) ? *reinterpret_cast<const ulonglong2 *>(c.W + widx(c, rr, col)) : make_ulonglong2(0, 0);
         l0[u] = l1[u] = 0;
         if (in && c.Lint && wp == 0) {
             const uint64_t *Lr = c.Lint + (int64_t)row[u] * c.ldl;
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(kNextThreads) k_next(DecompCtx c, int j)
         }
         if (live && y) {
             lookup<kNextC>(tab2, y, wp, swp, ng, a[u]);
-            *reinterpret_cast<ulonglong2 *>(c.W + (int64_t)row[u] * c.ldw + col) = a[u];
+            *reinterpret_cast<ulonglong2 *>(c.W + widx(c, row[u], col)) = a[u];
         }
     }
 
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(kNextThreads) k_next(DecompCtx c, int j)
                 Lr[wq] |= l << sh;
                 if (two) Lr[wq + 1] |= l >> (64 - sh);
             }
-            if (c.Eint) c.Eint[(int64_t)(R + t) * c.ldw + j] = pi->Erow[t];
+            if (c.Eint) c.Eint[(int64_t)(R + t) * c.lde + j] = pi->Erow[t];
         }
         if (c.Eint && has_tile) echelon_rows<kNextC, kNextThreads>(c, pi, R, r, q0, j + 1, ng, tab);
     }
@@ -252,7 +254,6 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
     const int64_t i0 = items * blockIdx.x / gridDim.x, i1 = items * (blockIdx.x + 1) / gridDim.x;
     const uint64_t *__restrict__ Yj = c.Y + (int64_t)(j & 1) * c.n;
     uint64_t *__restrict__ W = c.W;
-    const int64_t ldw = c.ldw;
     const int ng = ((r + C - 1) / C + 1) & ~1;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int rs = lane >> 2, wp = lane & 3, swp = rs & 1;
@@ -273,7 +274,7 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
         build_tables<C, kRestThreads>(tab, crow);
         __syncthreads();
         if (c.Eint && chunk == 0) echelon_rows<C, kRestThreads>(c, pi, R, r, q0, 0, ng, tab);
-        const int col = q0 + 2 * wp;
+        uint64_t *__restrict__ Wt = W + (int64_t)tile * c.tstride + 2 * wp;  // this lane's word pair of the tile
         const int rb = chunk * kRestChunk, re = min(c.n, chunk_end * kRestChunk);
         constexpr int STEP = 8 * U * NW;
         uint64_t yn[U];
@@ -295,7 +296,7 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
             for (int u = 0; u < U; ++u) {
                 const int row = base + u * 8 + rs;
                 a[u] = make_ulonglong2(0, 0);
-                if (y[u]) a[u] = *reinterpret_cast<const ulonglong2 *>(W + (int64_t)row * ldw + col);
+                if (y[u]) a[u] = *reinterpret_cast<const ulonglong2 *>(Wt + (int64_t)row * kTileWords);
             }
             for (int g = 0; g < ng; ++g) {
                 const int gg = g ^ swp;
@@ -310,7 +311,7 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int row = base + u * 8 + rs;
-                if (y[u]) *reinterpret_cast<ulonglong2 *>(W + (int64_t)row * ldw + col) = a[u];
+                if (y[u]) *reinterpret_cast<ulonglong2 *>(Wt + (int64_t)row * kTileWords) = a[u];
             }
         }
     }

@@ -81,7 +81,8 @@ extern "C" int gf2_rank_noalloc(const gf2_mat *A, int64_t *rank_dev, void *strea
     const int64_t mu = (m + 63) / 64;
     DecompCtx c{};
     c.W = reinterpret_cast<uint64_t *>(base + kOffW);
-    c.ldw = (mu + 7) / 8 * 8;
+    c.tstride = n * kTileWords;
+    c.lde = (mu + 7) / 8 * 8;
     c.perm = reinterpret_cast<int32_t *>(base + kOffPerm);
     c.pivcols = reinterpret_cast<int32_t *>(base + kOffPiv);
     c.info = reinterpret_cast<PanelInfo *>(base + kOffInfo);
@@ -99,7 +100,7 @@ extern "C" int gf2_rank_noalloc(const gf2_mat *A, int64_t *rank_dev, void *strea
     // the padding flag starts at zero; the scratch keeps the last call's contents
     if (cudaMemsetAsync(flag, 0, sizeof(uint32_t), s) != cudaSuccess) return GF2_ERR_CUDA;
     const uint64_t last = (m % 64) ? ((1ull << (m % 64)) - 1) : ~0ull;
-    if (launch_ingest(A->w, A->ld, (int32_t)n, (int32_t)mu, last, c.W, c.ldw, c.perm, c.pivpanel, flag, s) != cudaSuccess)
+    if (launch_ingest_tiled(A->w, A->ld, (int32_t)n, (int32_t)mu, last, c.W, c.perm, c.pivpanel, flag, s) != cudaSuccess)
         return GF2_ERR_CUDA;
     uint32_t flag_host = 0;  // a stack word: the copy allocates nothing
     if (cudaMemcpyAsync(&flag_host, flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return GF2_ERR_CUDA;
