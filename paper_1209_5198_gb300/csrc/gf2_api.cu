@@ -143,14 +143,16 @@ cudaError_t launch(int cls, cudaStream_t s, F &&f)
 #define LAUNCH_ON(cls, strm, expr) CK(launch((cls), (strm), [&]() { return (expr); }))
 
 // ------------------------------------------------------------ side stream
-// Per device: a high-priority non-blocking stream for the panel chain and a
-// pool of events for the cross-stream dependencies.  Enqueueing a
+// Per device: high-priority non-blocking streams for the panel chain and for
+// the look-ahead kernels, a low-priority one for the wide updates, and a pool
+// of events for the cross-stream dependencies.  Enqueueing a
 // decomposition holds g_side_mutex, so the events are used by one call at a
 // time (a wait captures the event's state when it is enqueued).
 struct SideResources {
     int device = 0;
     cudaStream_t main = nullptr;    // wide updates and outputs
     cudaStream_t stream = nullptr;  // the panel chain (high priority)
+    cudaStream_t next = nullptr;    // the look-ahead kernels (high priority)
     std::vector<cudaEvent_t> events;
 };
 std::mutex g_side_mutex;
@@ -167,6 +169,7 @@ int side_resources(int nevents, SideResources **out)
         int lo = 0, hi = 0;
         if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) return GF2_ERR_CUDA;
         if (cudaStreamCreateWithPriority(&r.stream, cudaStreamNonBlocking, hi) != cudaSuccess) return GF2_ERR_CUDA;
+        if (cudaStreamCreateWithPriority(&r.next, cudaStreamNonBlocking, hi) != cudaSuccess) return GF2_ERR_CUDA;
         if (cudaStreamCreateWithPriority(&r.main, cudaStreamNonBlocking, lo) != cudaSuccess) return GF2_ERR_CUDA;
         if (prepare_update_kernels() != cudaSuccess) return GF2_ERR_CUDA;
         if (prepare_panel_kernel() != cudaSuccess) return GF2_ERR_CUDA;
@@ -235,27 +238,35 @@ void drop_graphs()
 
 // ------------------------------------------------------------ decompose
 // Enqueues the factorization of an ingested matrix on the library streams:
-// the panel chain (pivot selection, next column tile, Y and L) on P, the
-// wide trailing updates and the outputs on M:
-//   next(j) waits for rest(j-2) (it reuses Y[j % 2]) and, when column j+1
-//   opens a new tile, for rest(j-1) (which updated that tile);
+// P runs the panels, N the look-ahead kernels, M the wide trailing updates
+// and the outputs:
+//   panel(j) waits for next(j-2), which wrote the F words it starts from and
+//     applied panel j-2 to word j;
+//   next(j) waits for panel(j), for rest(j-2) (it reuses Y[j % 2]) and, when
+//     word j+2 opens a new tile, for rest(j-1) (which updated that tile);
 //   rest(j) waits for next(j) (its Y).
+// So panel j+1 runs while next(j) and the updates of earlier panels run.
 int enqueue_factorization(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat *E, SideResources *side)
 {
-    cudaStream_t s = side->main, P = side->stream;
-    cudaEvent_t *evNext = side->events.data(), *evRest = evNext + c.mu;
-    cudaEvent_t evFork = evRest[c.mu], evJoin = evRest[c.mu + 1];
-    std::vector<char> rest_launched(c.mu, 0);
+    cudaStream_t s = side->main, P = side->stream, N = side->next;
+    const int mu = c.mu;
+    cudaEvent_t *evPanel = side->events.data(), *evNext = evPanel + mu, *evRest = evNext + mu;
+    cudaEvent_t evFork = evRest[mu], evJoinP = evRest[mu + 1], evJoinN = evRest[mu + 2];
+    std::vector<char> rest_launched(mu, 0);
     CK(cudaEventRecord(evFork, s));
     CK(cudaStreamWaitEvent(P, evFork, 0));
-    for (int j = 0; j < c.mu; ++j) {
+    CK(cudaStreamWaitEvent(N, evFork, 0));
+    for (int j = 0; j < mu; ++j) {
+        if (j >= 2) CK(cudaStreamWaitEvent(P, evNext[j - 2], 0));
         LAUNCH_ON(GF2_KCLASS_PANEL, P, launch_panel(c, j, P));
-        if (j >= 2 && rest_launched[j - 2]) CK(cudaStreamWaitEvent(P, evRest[j - 2], 0));
-        if (j >= 1 && (j + 1) % kTileWords == 0 && rest_launched[j - 1]) CK(cudaStreamWaitEvent(P, evRest[j - 1], 0));
-        LAUNCH_ON(GF2_KCLASS_NEXT, P, launch_next(c, j, P));
+        CK(cudaEventRecord(evPanel[j], P));
+        CK(cudaStreamWaitEvent(N, evPanel[j], 0));
+        if (j >= 2 && rest_launched[j - 2]) CK(cudaStreamWaitEvent(N, evRest[j - 2], 0));
+        if (j >= 1 && (j + 2) % kTileWords == 0 && rest_launched[j - 1]) CK(cudaStreamWaitEvent(N, evRest[j - 1], 0));
+        LAUNCH_ON(GF2_KCLASS_NEXT, N, launch_next(c, j, N));
+        CK(cudaEventRecord(evNext[j], N));
         int tile_first = 0;
         if (rest_tiles(c, j, &tile_first) > 0) {
-            CK(cudaEventRecord(evNext[j], P));
             CK(cudaStreamWaitEvent(s, evNext[j], 0));
             const int est = (int)(c.n - 64 * (int64_t)(j + 1));
             LAUNCH(GF2_KCLASS_UPDATE, launch_rest(c, j, est, s));
@@ -263,8 +274,10 @@ int enqueue_factorization(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat
             rest_launched[j] = 1;
         }
     }
-    CK(cudaEventRecord(evJoin, P));
-    CK(cudaStreamWaitEvent(s, evJoin, 0));
+    CK(cudaEventRecord(evJoinP, P));
+    CK(cudaStreamWaitEvent(s, evJoinP, 0));
+    CK(cudaEventRecord(evJoinN, N));
+    CK(cudaStreamWaitEvent(s, evJoinN, 0));
     LAUNCH(GF2_KCLASS_LAYOUT, launch_finish_scalars(c, rank, s));
     if (E) LAUNCH(GF2_KCLASS_LAYOUT, launch_finish_E(c, E->w, E->ld, s));
     if (L)
@@ -275,7 +288,7 @@ int enqueue_factorization(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat
 
 struct DecompLayout {
     int64_t mu, ldw, kmax, ldl;
-    size_t oW, oY, oPP, oInfo, oLint, oEint, oFlag, total;
+    size_t oW, oY, oF, oPP, oInfo, oLint, oEint, oFlag, total;
 };
 
 DecompLayout decomp_layout(int64_t n, int64_t m, bool factors)
@@ -288,6 +301,7 @@ DecompLayout decomp_layout(int64_t n, int64_t m, bool factors)
     size_t o = 0;
     d.oW = o; o += align_up((size_t)n * d.ldw * 8);
     d.oY = o; o += align_up((size_t)n * 2 * 8);
+    d.oF = o; o += align_up((size_t)n * 2 * 8);
     d.oPP = o; o += align_up((size_t)n * 4);
     d.oInfo = o; o += align_up((size_t)(d.mu > 0 ? d.mu : 1) * sizeof(PanelInfo));
     d.oLint = o; if (factors) o += align_up((size_t)n * d.ldl * 8);
@@ -322,6 +336,7 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
     c.pivcols = pivcols;
     c.info = reinterpret_cast<PanelInfo *>(base + d.oInfo);
     c.Y = reinterpret_cast<uint64_t *>(base + d.oY);
+    c.F = reinterpret_cast<uint64_t *>(base + d.oF);
     c.pivpanel = reinterpret_cast<int32_t *>(base + d.oPP);
     c.Lint = factors ? reinterpret_cast<uint64_t *>(base + d.oLint) : nullptr;
     c.ldl = d.ldl;
@@ -347,15 +362,16 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
     }
     if (c.Lint) CK(cudaMemsetAsync(c.Lint, 0, (size_t)n * d.ldl * 8, s));
 
-    // The factorization runs on the library's two streams of this device
-    // (M: wide updates and outputs, P: the panel chain), joined to the
-    // caller's stream s by events; the whole sequence is captured once into
-    // a CUDA graph per (shape, pointers) and replayed on later calls.
+    // The factorization runs on the library's three streams of this device
+    // (M: wide updates and outputs, P: the panel chain, N: the look-ahead
+    // kernels), joined to the caller's stream s by events; the whole
+    // sequence is captured once into a CUDA graph per (shape, pointers) and
+    // replayed on later calls.
     std::lock_guard<std::mutex> lock(g_side_mutex);
     SideResources *side = nullptr;
-    st = side_resources(2 * c.mu + 4, &side);
+    st = side_resources(3 * c.mu + 5, &side);
     if (st) return st;
-    cudaEvent_t evIn = side->events[2 * c.mu + 2], evOut = side->events[2 * c.mu + 3];
+    cudaEvent_t evIn = side->events[3 * c.mu + 3], evOut = side->events[3 * c.mu + 4];
     CK(cudaEventRecord(evIn, s));
     CK(cudaStreamWaitEvent(side->main, evIn, 0));
     GraphKey key{};

@@ -33,6 +33,7 @@ struct PanelInfo {
     uint64_t Tinv[64];
     uint64_t T[64];
     uint64_t Erow[64];  // E_s restricted to the panel's 64 columns
+    int32_t prow[64];   // storage row of pivot s
 };
 
 // Device state of one decomposition.  W is a working copy of A: storage
@@ -52,6 +53,9 @@ struct DecompCtx {
     int32_t *pivcols;   // [k]
     PanelInfo *info;    // [mu]
     uint64_t *Y;        // [2][n] per storage row: y of panel j in Y[j % 2]; 0 for pivot rows
+    uint64_t *F;        // [2][n] per storage row: its word j with every panel < j applied, in F[j % 2]
+                        // (j >= 1; written by the look-ahead kernel of panel j-1; word j of W
+                        // itself never receives panel j-1's update)
     int32_t *pivpanel;  // [n] per storage row: panel where it became a pivot (INT32_MAX: not yet)
     uint64_t *Lint;     // [n x ldl] per storage row, or null (rank only)
     int64_t ldl;

@@ -86,13 +86,44 @@ struct PanelShared {
     uint64_t slot_raw[kWin];
     uint64_t fraw[96];   // fast path: raw word and storage row of each register row
     int32_t fsrow[96];
+    int32_t prow[64];    // pivot s -> its storage row
+    uint64_t zt[256];    // 16 tables of 16: y = F * Zp of the previous panel
+    uint64_t ct[256];    // 16 tables of 16: y * C, C = word j of the previous panel's pivot rows
     uint64_t mask;
     unsigned long long orv;
     int req, from, found;
 };
 
+// Word j of storage row i with the updates of every panel < j.  W holds it
+// without the update of panel j-1, which is added here from the row's
+// finished word j-1 (Fp[i * fstride]: F, or W itself for j = 1): y = that
+// word * Zp, then word ^= y * C through the tables zt / ct (Fp = null when
+// panel j-1 left nothing to apply).
+struct PrevPanel {
+    const uint64_t *Fp;
+    int64_t fstride;
+};
+
+// The update of panel j-1 for a row whose finished word j-1 is f: (f Zp) C.
+__device__ __forceinline__ uint64_t prev_update(const PanelShared &sh, uint64_t f)
+{
+    uint64_t y = 0, u = 0;
+#pragma unroll
+    for (int g = 0; g < 16; ++g) y ^= sh.zt[g * 16 + (int)((f >> (4 * g)) & 15)];
+#pragma unroll
+    for (int g = 0; g < 16; ++g) u ^= sh.ct[g * 16 + (int)((y >> (4 * g)) & 15)];
+    return u;
+}
+
+__device__ __forceinline__ uint64_t panel_word(const uint64_t *Wj, const PrevPanel &pv, const PanelShared &sh, int i)
+{
+    uint64_t w = Wj[(int64_t)i * kTileWords];
+    if (pv.Fp) w ^= prev_update(sh, pv.Fp[(int64_t)i * pv.fstride]);
+    return w;
+}
+
 // Positions [from, n): first one whose panel word w has parity(w & mask) = 1.
-__device__ void scan_find(const DecompCtx &c, const uint64_t *Wj, PanelShared &sh)
+__device__ void scan_find(const DecompCtx &c, const uint64_t *Wj, const PrevPanel &pv, PanelShared &sh)
 {
     constexpr int U = 4;
     const int tid = threadIdx.x;
@@ -107,7 +138,7 @@ __device__ void scan_find(const DecompCtx &c, const uint64_t *Wj, PanelShared &s
         }
         uint64_t v[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) v[u] = srow[u] >= 0 ? Wj[(int64_t)srow[u] * kTileWords] : 0;
+        for (int u = 0; u < U; ++u) v[u] = srow[u] >= 0 ? panel_word(Wj, pv, sh, srow[u]) : 0;
         int hit = 0;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -122,7 +153,7 @@ __device__ void scan_find(const DecompCtx &c, const uint64_t *Wj, PanelShared &s
 
 // OR over positions [from, n) of the fully reduced panel words (reduction by
 // the current pivots: red(w) = XOR_{p in w} pred[p]).
-__device__ void scan_or(const DecompCtx &c, const uint64_t *Wj, PanelShared &sh)
+__device__ void scan_or(const DecompCtx &c, const uint64_t *Wj, const PrevPanel &pv, PanelShared &sh)
 {
     constexpr int U = 4;
     const int tid = threadIdx.x;
@@ -146,7 +177,7 @@ __device__ void scan_or(const DecompCtx &c, const uint64_t *Wj, PanelShared &sh)
         }
         uint64_t v[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) v[u] = srow[u] >= 0 ? Wj[(int64_t)srow[u] * kTileWords] : 0;
+        for (int u = 0; u < U; ++u) v[u] = srow[u] >= 0 ? panel_word(Wj, pv, sh, srow[u]) : 0;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             uint64_t r = 0;
@@ -282,13 +313,65 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
         return;
     }
 
+    // the update of panel j-1 that W does not hold yet (see panel_word)
+    PrevPanel pv{nullptr, 1};
+    const int rp = j > 0 ? c.info[j - 1].r : 0;
+    if (rp > 0) {
+        if (j == 1) {  // word 0 has no earlier update: W holds it
+            pv.Fp = c.W;
+            pv.fstride = kTileWords;
+        } else {
+            pv.Fp = c.F + (int64_t)((j - 1) & 1) * n;
+        }
+    }
+    // warp 0: the storage rows and words of the fast path's 96 rows, issued
+    // before anything waits (the fast path combines them once the tables
+    // of panel j-1 are built)
+    const int fend = min(R + 3 * 32, n);  // rows held in registers: [R, fend)
+    int srw[3];
+    uint64_t wv[3] = {0, 0, 0}, fv[3] = {0, 0, 0};
+    if (warp == 0) {
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            const int p = R + 32 * u + lane;
+            srw[u] = p < fend ? c.perm[p] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            if (srw[u] < 0) continue;
+            wv[u] = Wj[(int64_t)srw[u] * kTileWords];
+            if (pv.Fp) fv[u] = pv.Fp[(int64_t)srw[u] * pv.fstride];
+        }
+    }
+    if (pv.Fp) {
+        const PanelInfo *pp = c.info + (j - 1);
+        if (tid < 64) {
+            sh.T[tid] = pp->Zp[tid];
+            sh.TI[tid] = tid < rp ? Wj[(int64_t)pp->prow[tid] * kTileWords] : 0;
+        }
+        __syncthreads();
+        for (int e = tid; e < 256; e += kPanelThreads) {
+            const int g = e >> 4, x = e & 15;
+            uint64_t a = 0, b = 0;
+#pragma unroll
+            for (int bit = 0; bit < 4; ++bit)
+                if ((x >> bit) & 1) {
+                    a ^= sh.T[4 * g + bit];
+                    b ^= sh.TI[4 * g + bit];
+                }
+            sh.zt[e] = a;
+            sh.ct[e] = b;
+        }
+        __syncthreads();
+    }
+
     if (warp != 0) {  // helpers: serve scan requests of warp 0
         for (;;) {
             bar_sync(1, kPanelThreads);
             const int req = sh.req;
             if (req == kReqDone) return;
-            if (req == kReqFind) scan_find(c, Wj, sh);
-            else scan_or(c, Wj, sh);
+            if (req == kReqFind) scan_find(c, Wj, pv, sh);
+            else scan_or(c, Wj, pv, sh);
             bar_sync(2, kPanelThreads);
         }
     }
@@ -312,8 +395,8 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
         }
         __syncwarp();
         bar_sync(1, kPanelThreads);
-        if (req == kReqFind) scan_find(c, Wj, sh);
-        else scan_or(c, Wj, sh);
+        if (req == kReqFind) scan_find(c, Wj, pv, sh);
+        else scan_or(c, Wj, pv, sh);
         bar_sync(2, kPanelThreads);
     };
 
@@ -329,6 +412,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
                 const int pos = R + t, hs = pos & (kWin - 1), fs = (pos + f) & (kWin - 1);
                 const int psrow = sh.slot_srow[fs];
                 sh.B[t] = sh.slot_raw[fs];
+                sh.prow[t] = psrow;
                 sh.pb[t] = k;
                 sh.sidx[k] = t;
                 c.perm[pos] = psrow;
@@ -361,7 +445,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
             raw[u] = 0;
             if (isnew[u]) {
                 const int srow = c.perm[p];
-                raw[u] = Wj[(int64_t)srow * kTileWords];
+                raw[u] = panel_word(Wj, pv, sh, srow);
                 sh.slot_srow[slot] = srow;
                 sh.slot_raw[slot] = raw[u];
             }
@@ -410,17 +494,10 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
     int k = 0;
     bool fast_complete = false;
     {
-        const int fend = min(R + 3 * 32, n);  // rows held in registers: [R, fend)
         const int nrows = fend - R;
         uint64_t raw[3];
-        int srw[3];
 #pragma unroll
-        for (int u = 0; u < 3; ++u) {
-            const int p = R + 32 * u + lane;
-            srw[u] = p < fend ? c.perm[p] : -1;
-        }
-#pragma unroll
-        for (int u = 0; u < 3; ++u) raw[u] = srw[u] >= 0 ? Wj[(int64_t)srw[u] * kTileWords] : 0;
+        for (int u = 0; u < 3; ++u) raw[u] = (srw[u] >= 0 && pv.Fp) ? wv[u] ^ prev_update(sh, fv[u]) : wv[u];
         FastCols st;
 #pragma unroll
         for (int u = 0; u < 3; ++u) {
@@ -456,6 +533,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
                 if (q != p) c.perm[R + p] = srow;
                 if (p < s) {
                     sh.B[p] = sh.fraw[q];
+                    sh.prow[p] = srow;
                     c.pivpanel[srow] = j;
                 }
             }
@@ -509,7 +587,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
                     // pivot outside the window; the row in the pivot slot
                     // moves there and leaves the window
                     const int psrow = c.perm[q];
-                    const uint64_t v = Wj[(int64_t)psrow * kTileWords];
+                    const uint64_t v = panel_word(Wj, pv, sh, psrow);
                     uint64_t red = 0;
                     for (uint64_t b = v; b; b &= b - 1) red ^= sh.pred[__ffsll((long long)b) - 1];
                     const uint32_t eA = (red >> lane) & 1, eB = (red >> (lane + 32)) & 1;
@@ -526,6 +604,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
                         c.perm[q] = sh.slot_srow[hs];
                         c.pivpanel[psrow] = j;
                         sh.B[s] = v;
+                        sh.prow[s] = psrow;
                         sh.pb[s] = k;
                         sh.sidx[k] = s;
                     }
@@ -671,6 +750,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
         pi->T[t] = sh.T[t];
         pi->Erow[t] = sh.E[t];
         pi->pivbit[t] = sh.pb[t];
+        pi->prow[t] = sh.prow[t];
         c.pivcols[R + t] = 64 * j + sh.pb[t];
     }
 }

@@ -5,10 +5,11 @@
 // XORs per word, indexed by the c-bit chunks of its multiplier y.
 //
 // Two kernels per panel:
-//   k_next  the column tile holding column j+1 (the next panel), plus
-//           y = d Z and lambda = d Comp for every row (d = the row's word in
-//           column j; Y is kept per storage row for k_rest) and the L
-//           multipliers; small, on the critical path of the panel chain.
+//   k_next  y = d Z and lambda = d Comp for every row (d = the row's word in
+//           column j; Y is kept per storage row for k_rest), the L
+//           multipliers, word j+1 of every row with panel j applied (into a
+//           side buffer F, not into W) and the tile holding word j+2;
+//           it runs next to the panel kernel of block j+1.
 //   k_rest  every column tile after that one; persistent (one CTA per SM),
 //           each CTA takes a contiguous range of (tile, row chunk) items and
 //           rebuilds its tables only when the tile changes.
@@ -92,14 +93,15 @@ __device__ __forceinline__ void lookup(const ulonglong2 *tab2, uint64_t y, int w
     }
 }
 
-// Loads the C rows of panel j for the tile starting at word q0 (zero beyond r).
+// Loads the C rows of panel j (the pivot rows, by their storage rows prow)
+// for the tile starting at word q0 (zero beyond r).
 template <int T>
-__device__ __forceinline__ void load_pivot_rows(const DecompCtx &c, int R, int r, int q0, uint64_t *crow)
+__device__ __forceinline__ void load_pivot_rows(const DecompCtx &c, const int32_t *prow, int r, int q0, uint64_t *crow)
 {
     for (int idx = threadIdx.x; idx < 64 * kTileWords; idx += T) {
         const int t = idx / kTileWords, w = idx % kTileWords;
         uint64_t v = 0;
-        if (t < r) v = c.W[widx(c, c.perm[R + t], q0 + w)];
+        if (t < r) v = c.W[widx(c, prow[t], q0 + w)];
         crow[idx] = v;
     }
 }
@@ -122,68 +124,81 @@ __device__ __forceinline__ void echelon_rows(const DecompCtx &c, const PanelInfo
 }
 
 // -------------------------------------------------------------------- k_next
+// Look-ahead of panel j over every storage row (256 rows per CTA):
+//   d      = the row's word j with every panel < j applied (F[j%2]; W for j = 0)
+//   y      = d Zp (the paper's Y = D Z; 0 for the pivot rows of panels <= j) -> Y[j%2]
+//   lambda = d Comp -> the row's L multipliers of panel j
+//   F[(j+1)%2] = word j+1 with panel j applied (W keeps word j+1 without it:
+//            panel j+1 may be reading it meanwhile and adds the update itself)
+//   W ^= y C on the words >= j+2 of the tile holding word j+2
+// and, in block 0, the pivot rows' L rows (T) and their echelon words j,
+// j+1 and those of the tile.
 constexpr int kNextThreads = 256;
-constexpr int kNextRows = 256;  // storage rows per CTA
+constexpr int kNextRows = 256;  // storage rows per CTA (one wave next to the k_rest CTAs)
 constexpr int kNextC = 4;
-constexpr int kNextSmemWords = Tabs<kNextC>::Words + 64 * kTileWords + 16 * 16 * 2;
+constexpr int kNextSmemWords = Tabs<kNextC>::Words + 64 * kTileWords + 16 * 16 * 2 + 16 * 16;
 
-__global__ void __launch_bounds__(kNextThreads) k_next(DecompCtx c, int j)
+// <= 64 registers: a 256-thread CTA fits next to a persistent 512 x 96 k_rest CTA
+__global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
 {
     __shared__ __align__(16) uint64_t smem[kNextSmemWords];
     uint64_t *tab = smem;
     uint64_t *crow = smem + Tabs<kNextC>::Words;
     uint64_t *zc = crow + 64 * kTileWords;  // [g][x][y, lambda], 16 tables of 16 entries
+    uint64_t *c1 = zc + 16 * 16 * 2;        // [g][x]: y * (word j+1 of the pivot rows)
     const PanelInfo *pi = c.info + j;
     const int R = pi->R, r = pi->r;
-    if (r == 0) return;
     const int tid = threadIdx.x;
-    const bool has_tile = j + 1 < c.mu;
-    const int q0 = ((j + 1) / kTileWords) * kTileWords;
+    const bool has_f = j + 1 < c.mu;
+    const bool has_tile = j + 2 < c.mu;
+    const int q0 = ((j + 2) / kTileWords) * kTileWords;
     const int lane = tid & 31, warp = tid >> 5;
     const int rs = lane >> 2, wp = lane & 3, swp = rs & 1;
     const int col = q0 + 2 * wp;
-    const bool live = has_tile && (col + 1 >= j + 1);
+    const bool live_hi = has_tile && r > 0 && col + 1 >= j + 2;  // word col+1 takes the update
+    const bool live_lo = live_hi && col >= j + 2;                 // and word col too
     const int wq = R >> 6, sh = R & 63;
     const bool two = sh + r > 64;
     const int rb = blockIdx.x * kNextRows, re = min(c.n, rb + kNextRows);
+    const uint64_t *Fj = c.F + (int64_t)(j & 1) * c.n;
+    uint64_t *Fn = c.F + (int64_t)((j + 1) & 1) * c.n;
     constexpr int U = kNextRows / (8 * (kNextThreads / 32));  // row groups per warp
 
     // 1. every load of this thread's rows, issued before anything waits
-    int row[U];
-    bool active[U];
-    uint64_t d[U], l0[U], l1[U];
+    auto row_of = [&](int u) { return rb + (warp * U + u) * 8 + rs; };
+    uint32_t active = 0;  // bit u: row u is not a pivot of panels <= j
+    uint64_t d[U], w1[U];
     ulonglong2 a[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        row[u] = rb + (warp * U + u) * 8 + rs;
-        const bool in = row[u] < re;
-        const int64_t rr = in ? row[u] : 0;
-        active[u] = in && c.pivpanel[row[u]] > j;
-        d[u] = in ? c.W[widx(c, rr, j)] : 0;
-        a[u] = (in && live) ? *reinterpret_cast<const ulonglong2 *>(c.W + widx(c, rr, col)) : make_ulonglong2(0, 0);
-        l0[u] = l1[u] = 0;
-        if (in && c.Lint && wp == 0) {
-            const uint64_t *Lr = c.Lint + (int64_t)row[u] * c.ldl;
-            l0[u] = Lr[wq];
-            if (two) l1[u] = Lr[wq + 1];
-        }
+        const int row = row_of(u);
+        const bool in = row < re;
+        const int64_t rr = in ? row : 0;
+        if (in && r > 0 && c.pivpanel[row] > j) active |= 1u << u;
+        d[u] = !in ? 0 : (j == 0 ? c.W[widx(c, rr, 0)] : Fj[rr]);
+        w1[u] = (in && has_f && wp == 0) ? c.W[widx(c, rr, j + 1)] : 0;
+        a[u] = (in && live_hi) ? *reinterpret_cast<const ulonglong2 *>(c.W + widx(c, rr, col)) : make_ulonglong2(0, 0);
     }
-    // 2. tables of (Zp, Comp) for y and lambda, and of C for the tile
-    {
+    // 2. tables of (Zp, Comp) for y and lambda, of word j+1 of the pivot
+    // rows, and of C for the tile
+    if (r > 0) {
         const int g = tid >> 4, x = tid & 15;
-        uint64_t y = 0, l = 0;
+        uint64_t y = 0, l = 0, v = 0;
 #pragma unroll
         for (int b = 0; b < 4; ++b)
             if ((x >> b) & 1) {
-                y ^= pi->Zp[4 * g + b];
-                l ^= pi->Comp[4 * g + b];
+                const int s = 4 * g + b;
+                y ^= pi->Zp[s];
+                l ^= pi->Comp[s];
+                if (has_f && s < r) v ^= c.W[widx(c, pi->prow[s], j + 1)];
             }
         zc[2 * tid] = y;
         zc[2 * tid + 1] = l;
+        c1[tid] = v;
+        if (has_tile) load_pivot_rows<kNextThreads>(c, pi->prow, r, q0, crow);
     }
-    if (has_tile) load_pivot_rows<kNextThreads>(c, R, r, q0, crow);
     __syncthreads();
-    if (has_tile) build_tables<kNextC, kNextThreads>(tab, crow);
+    if (has_tile && r > 0) build_tables<kNextC, kNextThreads>(tab, crow);
     __syncthreads();
 
     // 3. compute and store
@@ -193,9 +208,10 @@ __global__ void __launch_bounds__(kNextThreads) k_next(DecompCtx c, int j)
     uint64_t *Ynext = c.Y + (int64_t)(j & 1) * c.n;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        if (row[u] >= re) continue;
+        const int row = row_of(u);
+        if (row >= re) continue;
         uint64_t y = 0, l = 0;
-        if (active[u]) {
+        if ((active >> u) & 1) {
 #pragma unroll
             for (int g = 0; g < 16; ++g) {
                 const ulonglong2 t = zc2[g * 16 + (int)((d[u] >> (4 * g)) & 15)];
@@ -204,32 +220,52 @@ __global__ void __launch_bounds__(kNextThreads) k_next(DecompCtx c, int j)
             }
         }
         if (wp == 0) {
-            Ynext[row[u]] = y;
-            if (c.Lint && l) {
-                uint64_t *Lr = c.Lint + (int64_t)row[u] * c.ldl;
-                Lr[wq] = l0[u] | (l << sh);
-                if (two) Lr[wq + 1] = l1[u] | (l >> (64 - sh));
+            Ynext[row] = y;
+            if (c.Lint && l) {  // this panel's bits of the L row: disjoint from every other panel's
+                unsigned long long *Lr = reinterpret_cast<unsigned long long *>(c.Lint + (int64_t)row * c.ldl);
+                atomicOr(Lr + wq, (unsigned long long)(l << sh));
+                if (two) atomicOr(Lr + wq + 1, (unsigned long long)(l >> (64 - sh)));
+            }
+            if (has_f) {
+                uint64_t f = w1[u];
+                if (y) {
+#pragma unroll
+                    for (int g = 0; g < 16; ++g) f ^= c1[g * 16 + (int)((y >> (4 * g)) & 15)];
+                }
+                Fn[row] = f;
             }
         }
-        if (live && y) {
+        if (live_hi && y) {
             lookup<kNextC>(tab2, y, wp, swp, ng, a[u]);
-            *reinterpret_cast<ulonglong2 *>(c.W + widx(c, row[u], col)) = a[u];
+            uint64_t *dst = c.W + widx(c, row, col);
+            if (live_lo) *reinterpret_cast<ulonglong2 *>(dst) = a[u];
+            else dst[1] = a[u].y;
         }
     }
 
-    if (blockIdx.x == 0) {
-        // the pivot rows: their L rows (T) and echelon words
+    if (blockIdx.x == 0 && r > 0) {
+        // the pivot rows: their L rows (T) and echelon words j and j+1
         for (int t = tid; t < r; t += kNextThreads) {
-            const int srow = c.perm[R + t];
+            const int srow = pi->prow[t];
             if (c.Lint) {
                 const uint64_t l = pi->T[t];
-                uint64_t *Lr = c.Lint + (int64_t)srow * c.ldl;
-                Lr[wq] |= l << sh;
-                if (two) Lr[wq + 1] |= l >> (64 - sh);
+                unsigned long long *Lr = reinterpret_cast<unsigned long long *>(c.Lint + (int64_t)srow * c.ldl);
+                atomicOr(Lr + wq, (unsigned long long)(l << sh));
+                if (two) atomicOr(Lr + wq + 1, (unsigned long long)(l >> (64 - sh)));
             }
-            if (c.Eint) c.Eint[(int64_t)(R + t) * c.lde + j] = pi->Erow[t];
+            if (c.Eint) {
+                uint64_t *Er = c.Eint + (int64_t)(R + t) * c.lde;
+                Er[j] = pi->Erow[t];
+                if (has_f) {
+                    const uint64_t ti = pi->Tinv[t];
+                    uint64_t e = 0;
+#pragma unroll
+                    for (int g = 0; g < 16; ++g) e ^= c1[g * 16 + (int)((ti >> (4 * g)) & 15)];
+                    Er[j + 1] = e;
+                }
+            }
         }
-        if (c.Eint && has_tile) echelon_rows<kNextC, kNextThreads>(c, pi, R, r, q0, j + 1, ng, tab);
+        if (c.Eint && has_tile) echelon_rows<kNextC, kNextThreads>(c, pi, R, r, q0, j + 2, ng, tab);
     }
 }
 
@@ -269,7 +305,7 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
         it = seg_end;
         const int q0 = tile * kTileWords;
         __syncthreads();
-        load_pivot_rows<kRestThreads>(c, R, r, q0, crow);
+        load_pivot_rows<kRestThreads>(c, pi->prow, r, q0, crow);
         __syncthreads();
         build_tables<C, kRestThreads>(tab, crow);
         __syncthreads();
@@ -423,7 +459,7 @@ cudaError_t launch_next(const DecompCtx &c, int j, cudaStream_t s)
 
 int rest_tiles(const DecompCtx &c, int j, int *tile_first)
 {
-    *tile_first = (j + 1) / kTileWords + 1;
+    *tile_first = (j + 2) / kTileWords + 1;
     const int tiles = (c.mu + kTileWords - 1) / kTileWords - *tile_first;
     return tiles > 0 ? tiles : 0;
 }

@@ -34,7 +34,8 @@ constexpr size_t align_na(size_t x) { return (x + kAlignNA - 1) / kAlignNA * kAl
 // layout of the static scratch (worst case n = m = 4096)
 constexpr size_t kOffW = 0;
 constexpr size_t kOffY = kOffW + align_na((size_t)kNoallocMaxDim * kNoallocMu * 8);
-constexpr size_t kOffPP = kOffY + align_na((size_t)kNoallocMaxDim * 2 * 8);
+constexpr size_t kOffF = kOffY + align_na((size_t)kNoallocMaxDim * 2 * 8);
+constexpr size_t kOffPP = kOffF + align_na((size_t)kNoallocMaxDim * 2 * 8);
 constexpr size_t kOffInfo = kOffPP + align_na((size_t)kNoallocMaxDim * 4);
 constexpr size_t kOffPerm = kOffInfo + align_na((size_t)kNoallocMu * sizeof(PanelInfo));
 constexpr size_t kOffPiv = kOffPerm + align_na((size_t)kNoallocMaxDim * 4);
@@ -87,6 +88,7 @@ extern "C" int gf2_rank_noalloc(const gf2_mat *A, int64_t *rank_dev, void *strea
     c.pivcols = reinterpret_cast<int32_t *>(base + kOffPiv);
     c.info = reinterpret_cast<PanelInfo *>(base + kOffInfo);
     c.Y = reinterpret_cast<uint64_t *>(base + kOffY);
+    c.F = reinterpret_cast<uint64_t *>(base + kOffF);
     c.pivpanel = reinterpret_cast<int32_t *>(base + kOffPP);
     c.Lint = nullptr;
     c.ldl = 1;
