@@ -195,6 +195,7 @@ struct GraphEntry {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     uint64_t stamp;
+    int64_t kernels;  // kernel nodes: the launches one replay makes
 };
 std::vector<GraphEntry> g_graphs;  // guarded by g_side_mutex
 uint64_t g_graph_clock = 0;
@@ -204,14 +205,29 @@ const bool g_use_graphs = [] {
     return !(e && e[0] == '0');
 }();
 
-cudaGraphExec_t find_graph(const GraphKey &k)
+cudaGraphExec_t find_graph(const GraphKey &k, int64_t *kernels)
 {
     for (auto &g : g_graphs)
         if (memcmp(&g.key, &k, sizeof(GraphKey)) == 0) {
             g.stamp = ++g_graph_clock;
+            *kernels = g.kernels;
             return g.exec;
         }
     return nullptr;
+}
+
+int64_t kernel_nodes(cudaGraph_t graph)
+{
+    size_t nn = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &nn) != cudaSuccess) return 0;
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn && cudaGraphGetNodes(graph, nodes.data(), &nn) != cudaSuccess) return 0;
+    int64_t k = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
 }
 
 void remember_graph(const GraphKey &k, cudaGraph_t graph, cudaGraphExec_t exec)
@@ -224,7 +240,7 @@ void remember_graph(const GraphKey &k, cudaGraph_t graph, cudaGraphExec_t exec)
         cudaGraphDestroy(g_graphs[old].graph);
         g_graphs.erase(g_graphs.begin() + old);
     }
-    g_graphs.push_back(GraphEntry{k, graph, exec, ++g_graph_clock});
+    g_graphs.push_back(GraphEntry{k, graph, exec, ++g_graph_clock, kernel_nodes(graph)});
 }
 
 void drop_graphs()
@@ -253,6 +269,7 @@ int enqueue_factorization(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat
     cudaEvent_t *evPanel = side->events.data(), *evNext = evPanel + mu, *evRest = evNext + mu;
     cudaEvent_t evFork = evRest[mu], evJoinP = evRest[mu + 1], evJoinN = evRest[mu + 2];
     std::vector<char> rest_launched(mu, 0);
+    CK(cudaMemsetAsync(c.nact, 0, (size_t)mu * sizeof(int32_t), s));
     CK(cudaEventRecord(evFork, s));
     CK(cudaStreamWaitEvent(P, evFork, 0));
     CK(cudaStreamWaitEvent(N, evFork, 0));
@@ -288,7 +305,7 @@ int enqueue_factorization(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat
 
 struct DecompLayout {
     int64_t mu, ldw, kmax, ldl;
-    size_t oW, oY, oF, oPP, oInfo, oLint, oEint, oFlag, total;
+    size_t oW, oY, oF, oAct, oNact, oPP, oInfo, oLint, oEint, oFlag, total;
 };
 
 DecompLayout decomp_layout(int64_t n, int64_t m, bool factors)
@@ -302,6 +319,8 @@ DecompLayout decomp_layout(int64_t n, int64_t m, bool factors)
     d.oW = o; o += align_up((size_t)n * d.ldw * 8);
     d.oY = o; o += align_up((size_t)n * 2 * 8);
     d.oF = o; o += align_up((size_t)n * 2 * 8);
+    d.oAct = o; o += align_up((size_t)n * 2 * 4);
+    d.oNact = o; o += align_up((size_t)(d.mu > 0 ? d.mu : 1) * 4);
     d.oPP = o; o += align_up((size_t)n * 4);
     d.oInfo = o; o += align_up((size_t)(d.mu > 0 ? d.mu : 1) * sizeof(PanelInfo));
     d.oLint = o; if (factors) o += align_up((size_t)n * d.ldl * 8);
@@ -337,6 +356,8 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
     c.info = reinterpret_cast<PanelInfo *>(base + d.oInfo);
     c.Y = reinterpret_cast<uint64_t *>(base + d.oY);
     c.F = reinterpret_cast<uint64_t *>(base + d.oF);
+    c.act = reinterpret_cast<int32_t *>(base + d.oAct);
+    c.nact = reinterpret_cast<int32_t *>(base + d.oNact);
     c.pivpanel = reinterpret_cast<int32_t *>(base + d.oPP);
     c.Lint = factors ? reinterpret_cast<uint64_t *>(base + d.oLint) : nullptr;
     c.ldl = d.ldl;
@@ -385,7 +406,8 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
         st = enqueue_factorization(c, rank, L, E, side);
         if (st) return st;
     } else {
-        cudaGraphExec_t exec = find_graph(key);
+        int64_t replayed = 0;  // kernels of a graph captured earlier (a capture counts its own)
+        cudaGraphExec_t exec = find_graph(key, &replayed);
         if (!exec) {
             if (cudaStreamBeginCapture(side->main, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GF2_ERR_CUDA;
             st = enqueue_factorization(c, rank, L, E, side);
@@ -403,6 +425,7 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
             remember_graph(key, graph, exec);
         }
         CK(cudaGraphLaunch(exec, side->main));
+        g_launches.fetch_add(replayed, std::memory_order_relaxed);
     }
     CK(cudaEventRecord(evOut, side->main));
     CK(cudaStreamWaitEvent(s, evOut, 0));

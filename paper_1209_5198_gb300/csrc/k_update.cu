@@ -13,9 +13,10 @@
 //   k_rest  every column tile after that one; persistent (one CTA per SM),
 //           each CTA takes a contiguous range of (tile, row chunk) items and
 //           rebuilds its tables only when the tile changes.
-// Rows are visited in STORAGE order (tiled W, storage row = row of A):
-// the multiplier array is indexed by storage row and is zero for rows that
-// are already pivots, so no position->row indirection sits in the hot loop.
+// Rows are visited in STORAGE order (tiled W, storage row = row of A), from
+// a list of the rows that are not pivots yet, which the look-ahead kernel
+// compacts panel by panel; the multiplier array is indexed by storage row,
+// so no position->row indirection sits in the hot loop.
 //
 // GB300 layout choices: W is stored by 8-word column tiles, each tile
 // contiguous over the rows, so one row's tile is 64 contiguous bytes and 8
@@ -159,22 +160,36 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
     const bool live_lo = live_hi && col >= j + 2;                 // and word col too
     const int wq = R >> 6, sh = R & 63;
     const bool two = sh + r > 64;
-    const int rb = blockIdx.x * kNextRows, re = min(c.n, rb + kNextRows);
+    // this CTA's rows: entries [rb, re) of the rows still active before
+    // panel j (every storage row for j = 0)
+    const int cnt = j == 0 ? c.n : c.nact[j - 1];
+    const int32_t *lst = j == 0 ? nullptr : c.act + (int64_t)((j - 1) & 1) * c.n;
+    const int rb = blockIdx.x * kNextRows, re = min(cnt, rb + kNextRows);
+    if (rb >= re && blockIdx.x != 0) return;
     const uint64_t *Fj = c.F + (int64_t)(j & 1) * c.n;
     uint64_t *Fn = c.F + (int64_t)((j + 1) & 1) * c.n;
     constexpr int U = kNextRows / (8 * (kNextThreads / 32));  // row groups per warp
 
     // 1. every load of this thread's rows, issued before anything waits
-    auto row_of = [&](int u) { return rb + (warp * U + u) * 8 + rs; };
+    __shared__ int keep_row[kNextRows];  // the rows that stay active, by list entry
+    __shared__ int keep_warp[kNextThreads / 32 + 1];
+    int rows[U];
     uint32_t active = 0;  // bit u: row u is not a pivot of panels <= j
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int k = rb + (warp * U + u) * 8 + rs;
+        rows[u] = k < re ? (lst ? lst[k] : k) : -1;
+    }
     uint64_t d[U], w1[U];
     ulonglong2 a[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        const int row = row_of(u);
-        const bool in = row < re;
+        const int row = rows[u];
+        const bool in = row >= 0;
         const int64_t rr = in ? row : 0;
-        if (in && r > 0 && c.pivpanel[row] > j) active |= 1u << u;
+        const bool keep = in && c.pivpanel[row] > j;
+        if (keep && r > 0) active |= 1u << u;
+        if (wp == 0) keep_row[(warp * U + u) * 8 + rs] = keep ? row : -1;
         d[u] = !in ? 0 : (j == 0 ? c.W[widx(c, rr, 0)] : Fj[rr]);
         w1[u] = (in && has_f && wp == 0) ? c.W[widx(c, rr, j + 1)] : 0;
         a[u] = (in && live_hi) ? *reinterpret_cast<const ulonglong2 *>(c.W + widx(c, rr, col)) : make_ulonglong2(0, 0);
@@ -199,7 +214,25 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
     }
     __syncthreads();
     if (has_tile && r > 0) build_tables<kNextC, kNextThreads>(tab, crow);
+    // the rows that stay active, appended to the list of panel j in list order
+    const int kept_row = keep_row[tid];
+    const unsigned kept_mask = __ballot_sync(0xffffffffu, kept_row >= 0);
+    if (lane == 0) keep_warp[warp] = __popc(kept_mask);
     __syncthreads();
+    if (tid == 0) {
+        int total = 0;
+        for (int w = 0; w < kNextThreads / 32; ++w) {
+            const int t = keep_warp[w];
+            keep_warp[w] = total;
+            total += t;
+        }
+        keep_warp[kNextThreads / 32] = total ? atomicAdd(c.nact + j, total) : 0;
+    }
+    __syncthreads();
+    if (kept_row >= 0) {
+        const int pos = keep_warp[kNextThreads / 32] + keep_warp[warp] + __popc(kept_mask & ((1u << lane) - 1));
+        c.act[(int64_t)(j & 1) * c.n + pos] = kept_row;
+    }
 
     // 3. compute and store
     const ulonglong2 *zc2 = reinterpret_cast<const ulonglong2 *>(zc);
@@ -208,8 +241,8 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
     uint64_t *Ynext = c.Y + (int64_t)(j & 1) * c.n;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        const int row = row_of(u);
-        if (row >= re) continue;
+        const int row = rows[u];
+        if (row < 0) continue;
         uint64_t y = 0, l = 0;
         if ((active >> u) & 1) {
 #pragma unroll
@@ -285,8 +318,15 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
     const PanelInfo *pi = c.info + j;
     const int R = pi->R, r = pi->r;
     if (r == 0) return;
-    const int nchunks = (c.n + kRestChunk - 1) / kRestChunk;
+    // the rows to update: the list of the rows that are not pivots of
+    // panels <= j (the rows that are have y = 0)
+    const int nact = c.nact[j];
+    const int32_t *__restrict__ act = c.act + (int64_t)(j & 1) * c.n;
+    // (with no row left the tiles are still visited when E is wanted: the
+    // pivot rows' echelon words come from the same tables)
+    const int nchunks = max((nact + kRestChunk - 1) / kRestChunk, c.Eint ? 1 : 0);
     const int64_t items = (int64_t)ntiles * nchunks;
+    if (items == 0) return;
     const int64_t i0 = items * blockIdx.x / gridDim.x, i1 = items * (blockIdx.x + 1) / gridDim.x;
     const uint64_t *__restrict__ Yj = c.Y + (int64_t)(j & 1) * c.n;
     uint64_t *__restrict__ W = c.W;
@@ -311,28 +351,34 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
         __syncthreads();
         if (c.Eint && chunk == 0) echelon_rows<C, kRestThreads>(c, pi, R, r, q0, 0, ng, tab);
         uint64_t *__restrict__ Wt = W + (int64_t)tile * c.tstride + 2 * wp;  // this lane's word pair of the tile
-        const int rb = chunk * kRestChunk, re = min(c.n, chunk_end * kRestChunk);
+        const int rb = chunk * kRestChunk, re = min(nact, chunk_end * kRestChunk);
         constexpr int STEP = 8 * U * NW;
         uint64_t yn[U];
+        int rown[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int row = rb + warp * 8 * U + u * 8 + rs;
-            yn[u] = row < re ? Yj[row] : 0;
+            const int k = rb + warp * 8 * U + u * 8 + rs;
+            rown[u] = k < re ? act[k] : -1;
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u) yn[u] = rown[u] >= 0 ? Yj[rown[u]] : 0;
         for (int base = rb + warp * 8 * U; base < re; base += STEP) {
             uint64_t y[U];
+            int row[U];
             ulonglong2 a[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 y[u] = yn[u];
-                const int nrow = base + STEP + u * 8 + rs;
-                yn[u] = nrow < re ? Yj[nrow] : 0;
+                row[u] = rown[u];
+                const int k = base + STEP + u * 8 + rs;
+                rown[u] = k < re ? act[k] : -1;
             }
 #pragma unroll
+            for (int u = 0; u < U; ++u) yn[u] = rown[u] >= 0 ? Yj[rown[u]] : 0;
+#pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int row = base + u * 8 + rs;
                 a[u] = make_ulonglong2(0, 0);
-                if (y[u]) a[u] = *reinterpret_cast<const ulonglong2 *>(Wt + (int64_t)row * kTileWords);
+                if (y[u]) a[u] = *reinterpret_cast<const ulonglong2 *>(Wt + (int64_t)row[u] * kTileWords);
             }
             for (int g = 0; g < ng; ++g) {
                 const int gg = g ^ swp;
@@ -345,10 +391,8 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
                 }
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int row = base + u * 8 + rs;
-                if (y[u]) *reinterpret_cast<ulonglong2 *>(Wt + (int64_t)row * kTileWords) = a[u];
-            }
+            for (int u = 0; u < U; ++u)
+                if (y[u]) *reinterpret_cast<ulonglong2 *>(Wt + (int64_t)row[u] * kTileWords) = a[u];
         }
     }
 }

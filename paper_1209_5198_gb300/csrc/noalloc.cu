@@ -35,7 +35,9 @@ constexpr size_t align_na(size_t x) { return (x + kAlignNA - 1) / kAlignNA * kAl
 constexpr size_t kOffW = 0;
 constexpr size_t kOffY = kOffW + align_na((size_t)kNoallocMaxDim * kNoallocMu * 8);
 constexpr size_t kOffF = kOffY + align_na((size_t)kNoallocMaxDim * 2 * 8);
-constexpr size_t kOffPP = kOffF + align_na((size_t)kNoallocMaxDim * 2 * 8);
+constexpr size_t kOffAct = kOffF + align_na((size_t)kNoallocMaxDim * 2 * 8);
+constexpr size_t kOffNact = kOffAct + align_na((size_t)kNoallocMaxDim * 2 * 4);
+constexpr size_t kOffPP = kOffNact + align_na((size_t)kNoallocMu * 4);
 constexpr size_t kOffInfo = kOffPP + align_na((size_t)kNoallocMaxDim * 4);
 constexpr size_t kOffPerm = kOffInfo + align_na((size_t)kNoallocMu * sizeof(PanelInfo));
 constexpr size_t kOffPiv = kOffPerm + align_na((size_t)kNoallocMaxDim * 4);
@@ -89,6 +91,8 @@ extern "C" int gf2_rank_noalloc(const gf2_mat *A, int64_t *rank_dev, void *strea
     c.info = reinterpret_cast<PanelInfo *>(base + kOffInfo);
     c.Y = reinterpret_cast<uint64_t *>(base + kOffY);
     c.F = reinterpret_cast<uint64_t *>(base + kOffF);
+    c.act = reinterpret_cast<int32_t *>(base + kOffAct);
+    c.nact = reinterpret_cast<int32_t *>(base + kOffNact);
     c.pivpanel = reinterpret_cast<int32_t *>(base + kOffPP);
     c.Lint = nullptr;
     c.ldl = 1;
@@ -109,6 +113,7 @@ extern "C" int gf2_rank_noalloc(const gf2_mat *A, int64_t *rank_dev, void *strea
     if (cudaStreamSynchronize(s) != cudaSuccess) return GF2_ERR_CUDA;
     if (flag_host) return GF2_ERR_PADDING;
     // the same kernels as gf2_rank, one stream, no look-ahead
+    if (cudaMemsetAsync(c.nact, 0, (size_t)c.mu * sizeof(int32_t), s) != cudaSuccess) return GF2_ERR_CUDA;
     for (int j = 0; j < c.mu; ++j) {
         if (launch_panel(c, j, s) != cudaSuccess) return GF2_ERR_CUDA;
         if (launch_next(c, j, s) != cudaSuccess) return GF2_ERR_CUDA;
