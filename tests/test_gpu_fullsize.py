@@ -1,0 +1,167 @@
+"""Parity at the benchmark's full sizes (n = m = 32768 and the 16384 fixed-rank
+and product configurations), in the launch configuration the benchmark times.
+
+The oracle cannot decompose a 32768 x 32768 matrix in seconds, so these tests
+check what it can compute and what holds at any size:
+  * the first 256 columns exactly: the oracle eliminates only those columns
+    (its column limit) and every decision it makes there is final -- the
+    first pivot columns, the rows at the first positions, the echelon rows of
+    those pivots and the L multipliers of every row for them;
+  * P*A = L*E by Freivalds' test with random vectors (a wrong bit anywhere in
+    L, E or P survives one vector with probability at most 1/2);
+  * the unit lower-triangular / row-echelon invariants of every row;
+  * the exact rank of products X*Y of known rank r (built on the CPU);
+  * solves and products checked against the definition A X = B, C = A B.
+Every input is built on the CPU from the seeded generators."""
+import numpy as np
+import pytest
+
+import f2gen
+import oracle
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("CUDA not available", allow_module_level=True)
+
+import paper_1209_5198_gb300 as gf2  # noqa: E402
+
+N = 32768
+NTHREADS = oracle.max_threads()
+
+
+def matvec_parity(M: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """Bits of M x over F2 (M row-major words, x packed words) as a 0/1 array."""
+    acc = np.zeros(M.shape[0], dtype=np.uint64)
+    for q in range(M.shape[1]):  # column by column keeps the temporaries small
+        acc += np.bitwise_count(M[:, q] & x[q]).astype(np.uint64)
+    return (acc & np.uint64(1)).astype(np.uint8)
+
+
+def pack(bits: np.ndarray, words: int) -> np.ndarray:
+    out = f2gen.pack_bits(bits.reshape(1, -1)).reshape(-1)
+    if out.size < words:
+        out = np.concatenate([out, np.zeros(words - out.size, dtype=np.uint64)])
+    return out[:words]
+
+
+def random_vectors(count: int, m: int, seed: int):
+    return [f2gen.uniform(1, m, seed, 900 + i).reshape(-1) for i in range(count)]
+
+
+def freivalds(A, perm, L, E, m, k, vectors):
+    """P A x == L (E x) for every vector x."""
+    for x in vectors:
+        ax = matvec_parity(A, x)[perm]
+        ex = matvec_parity(E, x)
+        lex = matvec_parity(L, pack(ex, L.shape[1]))
+        assert np.array_equal(ax, lex), "P*A*x != L*(E*x)"
+
+
+def check_shapes(perm, piv, r, L, E, n, m):
+    """perm a permutation; pivcols increasing; E row echelon with its leading
+    ones at pivcols and zero rows from r on; L unit lower trapezoidal with
+    zero columns from r on."""
+    assert np.array_equal(np.sort(perm), np.arange(n)), "perm is not a permutation"
+    p = piv[:r].astype(np.int64)
+    assert (np.diff(p) > 0).all() and (p >= 0).all() and (p < m).all()
+    assert (piv[r:] == -1).all()
+    rows = np.arange(r)
+    word, bit = p // 64, (p % 64).astype(np.uint64)
+    assert ((E[rows, word] >> bit) & np.uint64(1) == 1).all()
+    assert not (E[rows, word] & ((np.uint64(1) << bit) - np.uint64(1))).any()
+    for q in range(E.shape[1]):  # words before the leading word are zero
+        assert not E[:r][word > q, q].any()
+    assert not E[r:].any()
+    t = np.arange(r)
+    tw, tb = t // 64, (t % 64).astype(np.uint64)
+    assert ((L[t, tw] >> tb) & np.uint64(1) == 1).all()
+    above = ~((np.uint64(2) << tb) - np.uint64(1))
+    assert not (L[t, tw] & above).any()
+    for q in range(L.shape[1]):  # words after the diagonal word are zero
+        assert not L[:r][tw < q, q].any()
+    # columns >= r
+    if r < L.shape[1] * 64:
+        q0 = r // 64
+        if r % 64:
+            assert not (L[:, q0] & ~((np.uint64(1) << np.uint64(r % 64)) - np.uint64(1))).any()
+            q0 += 1
+        assert not L[:, q0:].any()
+
+
+def gpu_factors(A_rm, m):
+    n = A_rm.shape[0]
+    A = gf2.Mat.from_rowmajor(A_rm, m)
+    out = gf2.decompose(A, factors=True)
+    torch.cuda.synchronize()
+    r = int(out["rank"].item())
+    return (out["perm"].cpu().numpy(), out["pivcols"].cpu().numpy(), r,
+            out["L"].to_rowmajor(), out["E"].to_rowmajor(), out)
+
+
+def test_full_size_decomposition_32768():
+    A = f2gen.uniform(N, N, f2gen.BASE_SEED, 1, 0)  # the benchmark's input
+    perm, piv, r, L, E, _ = gpu_factors(A, N)
+    assert r >= N - 8  # a Bernoulli(1/2) square matrix has rank n - O(1)
+    check_shapes(perm, piv, r, L, E, N, N)
+    # the first 256 columns: the oracle's decisions there are final
+    c = 256
+    ref = oracle.ple(A, N, want_L=True, want_E=True, col_limit=c, nthreads=NTHREADS)
+    rc = ref["rank"]
+    assert np.array_equal(piv[:rc], ref["pivcols"])
+    assert rc == int((piv[:r] < c).sum())
+    assert np.array_equal(perm[:rc], ref["perm"][:rc])
+    assert np.array_equal(E[:rc], ref["E"][:rc])
+    inv_gpu = np.empty(N, dtype=np.int64)
+    inv_gpu[perm] = np.arange(N)
+    inv_ref = np.empty(N, dtype=np.int64)
+    inv_ref[ref["perm"]] = np.arange(N)
+    w = (rc + 63) // 64
+    mask = np.full(w, ~np.uint64(0), dtype=np.uint64)
+    if rc % 64:
+        mask[-1] = (np.uint64(1) << np.uint64(rc % 64)) - np.uint64(1)
+    assert np.array_equal(L[inv_gpu, :w] & mask, ref["L"][inv_ref, :w] & mask)
+    freivalds(A, perm, L, E, N, N, random_vectors(8, N, 77))
+
+
+@pytest.mark.parametrize("r", [8192, 16384 - 64])
+def test_full_size_fixed_rank_16384(r):
+    n = 16384
+    X, Y = f2gen.fixed_rank_factors(n, n, r, 500 + r)
+    A = oracle.mmm(X, Y, r, n, nthreads=NTHREADS)
+    perm, piv, rk, L, E, _ = gpu_factors(A, n)
+    assert rk == r
+    check_shapes(perm, piv, rk, L, E, n, n)
+    freivalds(A, perm, L, E, n, n, random_vectors(6, n, 78))
+
+
+def test_full_size_solve_32768():
+    A = f2gen.uniform(N, N, f2gen.BASE_SEED, 1, 0)
+    nrhs = 8
+    X0 = f2gen.rhs_from_solution(nrhs, N, 79)
+    # B = A X0 on the CPU, one right-hand side at a time
+    B = np.zeros(N, dtype=np.uint64)
+    for cidx in range(nrhs):
+        xc = pack(((X0[:, 0] >> np.uint64(cidx)) & np.uint64(1)).astype(np.uint8), A.shape[1])
+        B |= matvec_parity(A, xc).astype(np.uint64) << np.uint64(cidx)
+    Ad = gf2.Mat.from_rowmajor(A, N)
+    fac = gf2.decompose(Ad, factors=True)
+    Bd = gf2.Mat.from_rowmajor(B.reshape(-1, 1), nrhs)
+    out = gf2.solve(fac, Bd, N)
+    assert out["consistent"] == (1 << nrhs) - 1
+    X = out["X"].to_rowmajor().reshape(-1)
+    for cidx in range(nrhs):
+        xc = pack(((X >> np.uint64(cidx)) & np.uint64(1)).astype(np.uint8), A.shape[1])
+        bc = ((B >> np.uint64(cidx)) & np.uint64(1)).astype(np.uint8)
+        assert np.array_equal(matvec_parity(A, xc), bc)
+
+
+def test_full_size_product_16384():
+    n = 16384
+    Ah = f2gen.uniform(n, n, 80)
+    Bh = f2gen.uniform(n, n, 81)
+    C = gf2.mmm(gf2.Mat.from_rowmajor(Ah, n), gf2.Mat.from_rowmajor(Bh, n)).to_rowmajor()
+    for x in random_vectors(6, n, 82):
+        bx = matvec_parity(Bh, x)
+        assert np.array_equal(matvec_parity(C, x), matvec_parity(Ah, pack(bx, Ah.shape[1])))
