@@ -7,8 +7,12 @@
 
 namespace gf2 {
 
-// Column words handled by one CTA of the trailing update (64 bytes of a row).
-constexpr int kTileWords = 8;
+// Words of one column tile of the working copy (32 bytes of a row); a lane
+// of the trailing update owns one 128-bit word pair of a row's tile, so a
+// warp covers 16 rows of a tile.
+constexpr int kTileWords = 4;
+constexpr int kLanesPerRow = kTileWords / 2;
+constexpr int kRowsPerWarp = 32 / kLanesPerRow;
 // Four Russians table width c (Section 6 of the paper): a 64-bit multiplier
 // is split into 8 chunks of 8 bits, each looked up in a 256-entry table.
 constexpr int kTableBits = 8;
@@ -39,15 +43,15 @@ struct PanelInfo {
 // Device state of one decomposition.  W is a working copy of A: storage
 // row i is row i of A and never moves; perm maps positions to storage rows
 // (row i of P*A is storage row perm[i]), so a row exchange is an exchange of
-// two perm entries and no data moves.  W is TILED by 8-word column tiles:
-// tile T holds words 8T..8T+7 of every storage row, row after row (64
-// contiguous bytes per row), so word q of row i is at
-//   W[(q / 8) * tstride + 8 * i + q % 8],   tstride = 8 * n.
-// A warp that updates 8 consecutive rows of a tile touches 512 contiguous
+// two perm entries and no data moves.  W is TILED by column tiles of
+// kTileWords words: tile T holds words 4T..4T+3 of every storage row, row
+// after row (32 contiguous bytes per row), so word q of row i is at
+//   W[(q / 4) * tstride + 4 * i + q % 4],   tstride = 4 * n.
+// A warp that updates 16 consecutive rows of a tile touches 512 contiguous
 // bytes.
 struct DecompCtx {
     uint64_t *W;
-    int64_t tstride;    // words from one column tile of W to the next (8 * n)
+    int64_t tstride;    // words from one column tile of W to the next (kTileWords * n)
     int64_t lde;        // words per row of Eint, a multiple of kTileWords
     int32_t *perm;      // [n] position -> storage row (the output perm)
     int32_t *pivcols;   // [k]
@@ -69,7 +73,7 @@ struct DecompCtx {
 // Index of word q of storage row i in the tiled W.
 __device__ __forceinline__ int64_t widx(const DecompCtx &c, int64_t i, int q)
 {
-    return (int64_t)(q >> 3) * c.tstride + i * kTileWords + (q & 7);
+    return (int64_t)(q / kTileWords) * c.tstride + i * kTileWords + (q % kTileWords);
 }
 
 // Row-major operands of a product C ^= A * B over F2 for one 64-row slice

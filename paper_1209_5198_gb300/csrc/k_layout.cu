@@ -16,8 +16,8 @@ constexpr int kT = 32;     // tile edge (words)
 constexpr int kTy = 8;     // threads in y; each thread moves kT / kTy words
 
 // A (column blocks, n rows, mu blocks) -> W: row-major with ldw words per
-// row, or (TILED) in 8-word column tiles of 8*n words (word q of row i at
-// (q/8)*8n + 8i + q%8) with ldw = mu rounded up to 8.  Words q >= mu of W are
+// row, or (TILED) in column tiles of kTileWords words (word q of row i at
+// (q/T)*T*n + T*i + q%T, T = kTileWords) with ldw = mu rounded up to T.  Words q >= mu of W are
 // written as zero.  Bits beyond the last column of the last block are
 // checked against last_mask; any violation sets *err.
 template <bool TILED>
@@ -46,7 +46,8 @@ __global__ void k_ingest(const uint64_t *__restrict__ A, int64_t lda, int32_t n,
     for (int k = 0; k < kT / kTy; ++k) {
         const int i = i0 + ty + k * kTy, q = q0 + tx;
         if (i < n && q < ldw) {
-            const int64_t o = TILED ? (int64_t)(q >> 3) * 8 * n + (int64_t)i * 8 + (q & 7) : (int64_t)i * ldw + q;
+            const int64_t o = TILED ? (int64_t)(q / kTileWords) * kTileWords * n + (int64_t)i * kTileWords + (q % kTileWords)
+                                    : (int64_t)i * ldw + q;
             W[o] = tile[tx][ty + k * kTy];
         }
     }

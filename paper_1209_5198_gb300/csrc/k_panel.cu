@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
     const int n = c.n;
     const int nbits = min(64, c.m - 64 * j);
     PanelInfo *pi = c.info + j;
-    const uint64_t *Wj = c.W + (int64_t)(j >> 3) * c.tstride + (j & 7);  // word j of storage row i: Wj[8 i]
+    const uint64_t *Wj = c.W + (int64_t)(j / kTileWords) * c.tstride + (j % kTileWords);  // word j of row i: Wj[T i]
 
     if (R >= n || nbits <= 0) {
         if (tid == 0) {
@@ -756,9 +756,10 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
 }
 
 // Unused dynamic shared memory that keeps a panel CTA off any SM holding a
-// persistent k_rest CTA (about 133 KB): the panel runs on the SM k_rest
-// leaves free, without other warps competing for its scheduler.
-constexpr int kPanelReserveBytes = 110 * 1024;
+// persistent k_rest CTA (about 67 KB; with this reserve the two need more
+// than the 228 KB of an SM): the panel runs on the SM k_rest leaves free,
+// without other warps competing for its scheduler.
+constexpr int kPanelReserveBytes = 160 * 1024;
 
 }  // namespace
 

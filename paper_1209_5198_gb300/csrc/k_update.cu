@@ -1,6 +1,6 @@
 // Trailing update A(j+1) = E xor Y C (eq. (Aj) of the paper) by the Method
 // of Four Russians (M4RM, Section 6): the r <= 64 pivot rows C of panel j
-// are combined, per 8-word column tile, into 64/c tables of 2^c entries (one
+// are combined, per 4-word column tile, into 64/c tables of 2^c entries (one
 // XOR per entry), and every other row then takes 64/c table lookups and
 // XORs per word, indexed by the c-bit chunks of its multiplier y.
 //
@@ -18,14 +18,14 @@
 // compacts panel by panel; the multiplier array is indexed by storage row,
 // so no position->row indirection sits in the hot loop.
 //
-// GB300 layout choices: W is stored by 8-word column tiles, each tile
-// contiguous over the rows, so one row's tile is 64 contiguous bytes and 8
-// consecutive rows of a tile are 512; a warp covers 8 rows x 8 words with
-// 128-bit accesses (lane = row slot (lane/4) x
-// word pair (lane%4)); the tables sit in shared memory as
-// [table pair][x][half][8 words], and the two rows of a quarter-warp (one
-// 128-bit shared-memory phase) read tables g and g^1, which live in opposite
-// 64-byte halves of the bank space, so lookups are conflict-free for any y.
+// GB300 layout choices: W is stored by 4-word column tiles, each tile
+// contiguous over the rows, so one row's tile is 32 contiguous bytes and 16
+// consecutive rows of a tile are 512; a warp covers 16 rows x 4 words with
+// 128-bit accesses (lane = row slot (lane/2) x word pair (lane%2)); the
+// tables sit in shared memory as [table quad][x][quarter][4 words], and the
+// four rows of a quarter-warp (one 128-bit shared-memory phase) read tables
+// g, g^1, g^2, g^3, which live in the four 32-byte quarters of the bank
+// space, so lookups are conflict-free for any y.
 // The same tile code serves the standalone product C ^= A B.
 #include <mutex>
 
@@ -41,11 +41,18 @@ struct Tabs {
     static constexpr int Words = K * X * kTileWords; // shared-memory words
 };
 
-// index (in 8-word entries) of entry x of table g
+// index (in tile-word entries) of entry x of table g
 template <int C>
 __device__ __forceinline__ int tab_entry(int g, int x)
 {
-    return ((((g >> 1) << C) + x) << 1) | (g & 1);
+    return ((((g >> 2) << C) + x) << 2) | (g & 3);
+}
+
+// tables in use for r pivot rows: a multiple of 4 (whole quads; unused ones are zero)
+template <int C>
+__device__ __forceinline__ int tables_used(int r)
+{
+    return ((r + C - 1) / C + 3) & ~3;
 }
 
 // Tables of the 64 x 8-word rows in crow (rows beyond r are zero).
@@ -154,7 +161,7 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
     const bool has_tile = j + 2 < c.mu;
     const int q0 = ((j + 2) / kTileWords) * kTileWords;
     const int lane = tid & 31, warp = tid >> 5;
-    const int rs = lane >> 2, wp = lane & 3, swp = rs & 1;
+    const int rs = lane / kLanesPerRow, wp = lane % kLanesPerRow, swp = rs & 3;
     const int col = q0 + 2 * wp;
     const bool live_hi = has_tile && r > 0 && col + 1 >= j + 2;  // word col+1 takes the update
     const bool live_lo = live_hi && col >= j + 2;                 // and word col too
@@ -168,7 +175,7 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
     if (rb >= re && blockIdx.x != 0) return;
     const uint64_t *Fj = c.F + (int64_t)(j & 1) * c.n;
     uint64_t *Fn = c.F + (int64_t)((j + 1) & 1) * c.n;
-    constexpr int U = kNextRows / (8 * (kNextThreads / 32));  // row groups per warp
+    constexpr int U = kNextRows / (kRowsPerWarp * (kNextThreads / 32));  // row groups per warp
 
     // 1. every load of this thread's rows, issued before anything waits
     __shared__ int keep_row[kNextRows];  // the rows that stay active, by list entry
@@ -177,7 +184,7 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
     uint32_t active = 0;  // bit u: row u is not a pivot of panels <= j
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        const int k = rb + (warp * U + u) * 8 + rs;
+        const int k = rb + (warp * U + u) * kRowsPerWarp + rs;
         rows[u] = k < re ? (lst ? lst[k] : k) : -1;
     }
     uint64_t d[U], w1[U];
@@ -189,7 +196,7 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
         const int64_t rr = in ? row : 0;
         const bool keep = in && c.pivpanel[row] > j;
         if (keep && r > 0) active |= 1u << u;
-        if (wp == 0) keep_row[(warp * U + u) * 8 + rs] = keep ? row : -1;
+        if (wp == 0) keep_row[(warp * U + u) * kRowsPerWarp + rs] = keep ? row : -1;
         d[u] = !in ? 0 : (j == 0 ? c.W[widx(c, rr, 0)] : Fj[rr]);
         w1[u] = (in && has_f && wp == 0) ? c.W[widx(c, rr, j + 1)] : 0;
         a[u] = (in && live_hi) ? *reinterpret_cast<const ulonglong2 *>(c.W + widx(c, rr, col)) : make_ulonglong2(0, 0);
@@ -237,7 +244,7 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
     // 3. compute and store
     const ulonglong2 *zc2 = reinterpret_cast<const ulonglong2 *>(zc);
     const ulonglong2 *tab2 = reinterpret_cast<const ulonglong2 *>(tab);
-    const int ng = ((r + kNextC - 1) / kNextC + 1) & ~1;
+    const int ng = tables_used<kNextC>(r);
     uint64_t *Ynext = c.Y + (int64_t)(j & 1) * c.n;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -330,9 +337,9 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
     const int64_t i0 = items * blockIdx.x / gridDim.x, i1 = items * (blockIdx.x + 1) / gridDim.x;
     const uint64_t *__restrict__ Yj = c.Y + (int64_t)(j & 1) * c.n;
     uint64_t *__restrict__ W = c.W;
-    const int ng = ((r + C - 1) / C + 1) & ~1;
+    const int ng = tables_used<C>(r);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int rs = lane >> 2, wp = lane & 3, swp = rs & 1;
+    const int rs = lane / kLanesPerRow, wp = lane % kLanesPerRow, swp = rs & 3;
     constexpr int NW = kRestThreads / 32;
     const ulonglong2 *tab2 = reinterpret_cast<const ulonglong2 *>(tab);
     // The item range is split into segments of one tile each: one table
@@ -352,17 +359,17 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
         if (c.Eint && chunk == 0) echelon_rows<C, kRestThreads>(c, pi, R, r, q0, 0, ng, tab);
         uint64_t *__restrict__ Wt = W + (int64_t)tile * c.tstride + 2 * wp;  // this lane's word pair of the tile
         const int rb = chunk * kRestChunk, re = min(nact, chunk_end * kRestChunk);
-        constexpr int STEP = 8 * U * NW;
+        constexpr int STEP = kRowsPerWarp * U * NW;
         uint64_t yn[U];
         int rown[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int k = rb + warp * 8 * U + u * 8 + rs;
+            const int k = rb + warp * kRowsPerWarp * U + u * kRowsPerWarp + rs;
             rown[u] = k < re ? act[k] : -1;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) yn[u] = rown[u] >= 0 ? Yj[rown[u]] : 0;
-        for (int base = rb + warp * 8 * U; base < re; base += STEP) {
+        for (int base = rb + warp * kRowsPerWarp * U; base < re; base += STEP) {
             uint64_t y[U];
             int row[U];
             ulonglong2 a[U];
@@ -370,7 +377,7 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
             for (int u = 0; u < U; ++u) {
                 y[u] = yn[u];
                 row[u] = rown[u];
-                const int k = base + STEP + u * 8 + rs;
+                const int k = base + STEP + u * kRowsPerWarp + rs;
                 rown[u] = k < re ? act[k] : -1;
             }
 #pragma unroll
@@ -418,21 +425,21 @@ __global__ void __launch_bounds__(kMmmThreads, 1) k_mmm_pass(MmmCtx mc, int kb, 
     build_tables<kMmmC, kMmmThreads>(tab, crow);
     __syncthreads();
     const ulonglong2 *tab2 = reinterpret_cast<const ulonglong2 *>(tab);
-    const int ng = ((r + kMmmC - 1) / kMmmC + 1) & ~1;
+    const int ng = tables_used<kMmmC>(r);
     const int lane = tid & 31, warp = tid >> 5;
-    const int rs = lane >> 2, wp = lane & 3, swp = rs & 1;
+    const int rs = lane / kLanesPerRow, wp = lane % kLanesPerRow, swp = rs & 3;
     const int col = q0 + 2 * wp;
     const bool live = col < m_words;
     const int rows = mc.n;
     const int chunk = (rows + gridDim.y - 1) / gridDim.y;
     const int rb = blockIdx.y * chunk, re = min(rows, rb + chunk);
     constexpr int U = 4;
-    for (int base = rb + warp * 8 * U; base < re; base += 8 * U * (kMmmThreads / 32)) {
+    for (int base = rb + warp * kRowsPerWarp * U; base < re; base += kRowsPerWarp * U * (kMmmThreads / 32)) {
         uint64_t y[U];
         ulonglong2 a[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int i = base + u * 8 + rs;
+            const int i = base + u * kRowsPerWarp + rs;
             y[u] = i < re ? mc.A[(int64_t)i * mc.lda + kb] : 0;
             a[u] = make_ulonglong2(0, 0);
             if (i < re && live) a[u] = *reinterpret_cast<const ulonglong2 *>(mc.C + (int64_t)i * mc.ldc + col);
@@ -449,7 +456,7 @@ __global__ void __launch_bounds__(kMmmThreads, 1) k_mmm_pass(MmmCtx mc, int kb, 
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int i = base + u * 8 + rs;
+            const int i = base + u * kRowsPerWarp + rs;
             if (i < re && live) *reinterpret_cast<ulonglong2 *>(mc.C + (int64_t)i * mc.ldc + col) = a[u];
         }
     }
