@@ -204,6 +204,11 @@ const bool g_use_graphs = [] {
     const char *e = getenv("GF2_GRAPHS");
     return !(e && e[0] == '0');
 }();
+// wide updates by pairs of panels (GF2_PAIRS=0: one update per panel)
+const bool g_use_pairs = [] {
+    const char *e = getenv("GF2_PAIRS");
+    return !(e && e[0] == '0');
+}();
 
 cudaGraphExec_t find_graph(const GraphKey &k, int64_t *kernels)
 {
@@ -258,9 +263,13 @@ void drop_graphs()
 // and the outputs:
 //   panel(j) waits for next(j-2), which wrote the F words it starts from and
 //     applied panel j-2 to word j;
-//   next(j) waits for panel(j), for rest(j-2) (it reuses Y[j % 2]) and, when
-//     word j+2 opens a new tile, for rest(j-1) (which updated that tile);
-//   rest(j) waits for next(j) (its Y).
+//   one panel at a time: next(j) waits for panel(j), for rest(j-2) (it reuses
+//     Y and the active list of j-2) and, when word j+2 opens a new tile, for
+//     rest(j-1) (which updated that tile); rest(j) waits for next(j);
+//   by pairs (j even, j+1): next(j) waits for panel(j) and for the previous
+//     pair's update, which covered the tiles it rewrites and last read the
+//     buffers it reuses; next(j+1) follows next(j); rest(j, j+1) waits for
+//     next(j+1); a lone last panel is updated alone.
 // So panel j+1 runs while next(j) and the updates of earlier panels run.
 int enqueue_factorization(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat *E, SideResources *side)
 {
@@ -278,15 +287,23 @@ int enqueue_factorization(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat
         LAUNCH_ON(GF2_KCLASS_PANEL, P, launch_panel(c, j, P));
         CK(cudaEventRecord(evPanel[j], P));
         CK(cudaStreamWaitEvent(N, evPanel[j], 0));
-        if (j >= 2 && rest_launched[j - 2]) CK(cudaStreamWaitEvent(N, evRest[j - 2], 0));
-        if (j >= 1 && (j + 2) % kTileWords == 0 && rest_launched[j - 1]) CK(cudaStreamWaitEvent(N, evRest[j - 1], 0));
+        if (c.pair) {
+            if (!(j & 1) && j >= 1 && rest_launched[j - 1]) CK(cudaStreamWaitEvent(N, evRest[j - 1], 0));
+        } else {
+            if (j >= 2 && rest_launched[j - 2]) CK(cudaStreamWaitEvent(N, evRest[j - 2], 0));
+            if (j >= 1 && (j + 2) % kTileWords == 0 && rest_launched[j - 1]) CK(cudaStreamWaitEvent(N, evRest[j - 1], 0));
+        }
         LAUNCH_ON(GF2_KCLASS_NEXT, N, launch_next(c, j, N));
         CK(cudaEventRecord(evNext[j], N));
+        // the wide update: of this panel, of the pair ending here, or none
+        // (first panel of a pair)
+        const int np = !c.pair ? 1 : ((j & 1) ? 2 : (j == mu - 1 ? 1 : 0));
+        const int jf = j - np + 1;
         int tile_first = 0;
-        if (rest_tiles(c, j, &tile_first) > 0) {
+        if (np > 0 && rest_tiles(c, jf, np, &tile_first) > 0) {
             CK(cudaStreamWaitEvent(s, evNext[j], 0));
             const int est = (int)(c.n - 64 * (int64_t)(j + 1));
-            LAUNCH(GF2_KCLASS_UPDATE, launch_rest(c, j, est, s));
+            LAUNCH(GF2_KCLASS_UPDATE, launch_rest(c, jf, np, est, s));
             CK(cudaEventRecord(evRest[j], s));
             rest_launched[j] = 1;
         }
@@ -317,7 +334,7 @@ DecompLayout decomp_layout(int64_t n, int64_t m, bool factors)
     d.ldl = words_of(d.kmax) > 0 ? words_of(d.kmax) : 1;
     size_t o = 0;
     d.oW = o; o += align_up((size_t)n * d.ldw * 8);
-    d.oY = o; o += align_up((size_t)n * 2 * 8);
+    d.oY = o; o += align_up((size_t)n * 4 * 8);
     d.oF = o; o += align_up((size_t)n * 2 * 8);
     d.oAct = o; o += align_up((size_t)n * 2 * 4);
     d.oNact = o; o += align_up((size_t)(d.mu > 0 ? d.mu : 1) * 4);
@@ -366,6 +383,7 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
     c.m = (int32_t)m;
     c.mu = (int32_t)d.mu;
     c.kmax = (int32_t)kmax;
+    c.pair = g_use_pairs ? 1 : 0;
     uint32_t *flag = reinterpret_cast<uint32_t *>(base + d.oFlag);
 
     if (n == 0 || m == 0) {

@@ -56,7 +56,7 @@ struct DecompCtx {
     int32_t *perm;      // [n] position -> storage row (the output perm)
     int32_t *pivcols;   // [k]
     PanelInfo *info;    // [mu]
-    uint64_t *Y;        // [2][n] per storage row: y of panel j in Y[j % 2]; 0 for pivot rows
+    uint64_t *Y;        // [4][n] per storage row: y of panel j in Y[j % 4]; 0 for pivot rows
     uint64_t *F;        // [2][n] per storage row: its word j with every panel < j applied, in F[j % 2]
                         // (j >= 1; written by the look-ahead kernel of panel j-1; word j of W
                         // itself never receives panel j-1's update)
@@ -68,6 +68,7 @@ struct DecompCtx {
     int64_t ldl;
     uint64_t *Eint;     // [k x lde] per pivot index (row-major), or null
     int32_t n, m, mu, kmax;
+    int32_t pair;       // wide updates by pairs of panels (j even, j+1)
 };
 
 // Index of word q of storage row i in the tiled W.
@@ -120,8 +121,9 @@ cudaError_t launch_finish_E(const DecompCtx &c, uint64_t *E, int64_t lde, cudaSt
 cudaError_t launch_finish_scalars(const DecompCtx &c, int64_t *rank, cudaStream_t s);
 cudaError_t launch_panel(const DecompCtx &c, int j, cudaStream_t s);
 cudaError_t launch_next(const DecompCtx &c, int j, cudaStream_t s);
-cudaError_t launch_rest(const DecompCtx &c, int j, int est_active_rows, cudaStream_t s);
-int rest_tiles(const DecompCtx &c, int j, int *tile_first);
+// the wide update of panel j (np = 1) or of the pair j, j+1 (np = 2)
+cudaError_t launch_rest(const DecompCtx &c, int j, int np, int est_active_rows, cudaStream_t s);
+int rest_tiles(const DecompCtx &c, int j, int np, int *tile_first);
 cudaError_t prepare_update_kernels();  // one-time kernel attributes (before any capture)
 cudaError_t prepare_panel_kernel();
 cudaError_t launch_mmm_pass(const MmmCtx &c, int kb, int m_words, cudaStream_t s);

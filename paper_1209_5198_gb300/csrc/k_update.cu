@@ -55,11 +55,11 @@ __device__ __forceinline__ int tables_used(int r)
     return ((r + C - 1) / C + 3) & ~3;
 }
 
-// Tables of the 64 x 8-word rows in crow (rows beyond r are zero).
+// Tables g0.. of the 64 tile rows in crow (rows beyond r are zero).
 // Thread -> (word w, table g, sub-range of x); each sub-range walks its low
 // bits in Gray order, one XOR per entry.
 template <int C, int T>
-__device__ __forceinline__ void build_tables(uint64_t *tab, const uint64_t *crow)
+__device__ __forceinline__ void build_tables(uint64_t *tab, const uint64_t *crow, int g0 = 0)
 {
     constexpr int K = Tabs<C>::K, X = Tabs<C>::X;
     constexpr int PAIRS = K * kTileWords;
@@ -78,12 +78,12 @@ __device__ __forceinline__ void build_tables(uint64_t *tab, const uint64_t *crow
 #pragma unroll
     for (int b = LQ; b < C; ++b)
         if ((x0 >> b) & 1) v ^= cb[b];
-    tab[tab_entry<C>(g, x0) * kTileWords + w] = v;
+    tab[tab_entry<C>(g0 + g, x0) * kTileWords + w] = v;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const int b = (i & 1) ? 0 : (i & 2) ? 1 : (i & 4) ? 2 : (i & 8) ? 3 : (i & 16) ? 4 : (i & 32) ? 5 : (i & 64) ? 6 : 7;
         v ^= cb[b];
-        tab[tab_entry<C>(g, x0 + (i ^ (i >> 1))) * kTileWords + w] = v;
+        tab[tab_entry<C>(g0 + g, x0 + (i ^ (i >> 1))) * kTileWords + w] = v;
     }
 }
 
@@ -114,10 +114,11 @@ __device__ __forceinline__ void load_pivot_rows(const DecompCtx &c, const int32_
     }
 }
 
-// Echelon rows of the panel's pivots on one tile: E_s = Tinv[s] * C.
+// Echelon rows of the panel's pivots on one tile: E_s = Tinv[s] * C (the
+// panel's tables are g0..g0+ng-1).
 template <int C, int T>
 __device__ __forceinline__ void echelon_rows(const DecompCtx &c, const PanelInfo *pi, int R, int r, int q0,
-                                             int live_from, int ng, const uint64_t *tab)
+                                             int live_from, int ng, const uint64_t *tab, int g0 = 0)
 {
     for (int idx = threadIdx.x; idx < r * kTileWords; idx += T) {
         const int t = idx / kTileWords, w = idx % kTileWords;
@@ -126,45 +127,55 @@ __device__ __forceinline__ void echelon_rows(const DecompCtx &c, const PanelInfo
         const uint64_t ym = pi->Tinv[t];
         uint64_t acc = 0;
         for (int g = 0; g < ng; ++g)
-            acc ^= tab[tab_entry<C>(g, (int)((ym >> (C * g)) & (Tabs<C>::X - 1))) * kTileWords + w];
+            acc ^= tab[tab_entry<C>(g0 + g, (int)((ym >> (C * g)) & (Tabs<C>::X - 1))) * kTileWords + w];
         c.Eint[(int64_t)(R + t) * c.lde + q] = acc;
     }
 }
 
 // -------------------------------------------------------------------- k_next
-// Look-ahead of panel j over every storage row (256 rows per CTA):
+// Look-ahead of panel j over the rows still active before it (256 per CTA):
 //   d      = the row's word j with every panel < j applied (F[j%2]; W for j = 0)
-//   y      = d Zp (the paper's Y = D Z; 0 for the pivot rows of panels <= j) -> Y[j%2]
+//   y      = d Zp (the paper's Y = D Z; 0 for the pivot rows of panels <= j) -> Y[j%4]
 //   lambda = d Comp -> the row's L multipliers of panel j
 //   F[(j+1)%2] = word j+1 with panel j applied (W keeps word j+1 without it:
 //            panel j+1 may be reading it meanwhile and adds the update itself)
-//   W ^= y C on the words >= j+2 of the tile holding word j+2
-// and, in block 0, the pivot rows' L rows (T) and their echelon words j,
-// j+1 and those of the tile.
+//   W ^= y C on the words >= j+2 of the tile holding word j+2 and, when
+//            panel j opens a pair of panels (whose wide update starts after
+//            the tile holding word j+3), of that tile too
+//   the compacted list of the rows that stay active
+// and, in block 0, the pivot rows' L rows (T) and their echelon words on
+// the same columns.  For the second panel of a pair it also applies the first
+// panel's update to its own pivot rows on every tile of the wide update,
+// which reads them as table rows.
 constexpr int kNextThreads = 256;
 constexpr int kNextRows = 256;  // storage rows per CTA (one wave next to the k_rest CTAs)
 constexpr int kNextC = 4;
-constexpr int kNextSmemWords = Tabs<kNextC>::Words + 64 * kTileWords + 16 * 16 * 2 + 16 * 16;
+constexpr int kNextTiles = 2;   // tiles of W the look-ahead updates (at most)
+constexpr int kNextSmemWords = kNextTiles * (Tabs<kNextC>::Words + 64 * kTileWords) + 16 * 16 * 2 + 16 * 16;
 
 // <= 64 registers: a 256-thread CTA fits next to a persistent 512 x 96 k_rest CTA
 __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
 {
     __shared__ __align__(16) uint64_t smem[kNextSmemWords];
-    uint64_t *tab = smem;
-    uint64_t *crow = smem + Tabs<kNextC>::Words;
-    uint64_t *zc = crow + 64 * kTileWords;  // [g][x][y, lambda], 16 tables of 16 entries
-    uint64_t *c1 = zc + 16 * 16 * 2;        // [g][x]: y * (word j+1 of the pivot rows)
+    uint64_t *tab = smem;                                      // [tile][Tabs<4>::Words]
+    uint64_t *crow = tab + kNextTiles * Tabs<kNextC>::Words;   // [tile][64 x kTileWords]
+    uint64_t *zc = crow + kNextTiles * 64 * kTileWords;        // [g][x][y, lambda], 16 tables of 16 entries
+    uint64_t *c1 = zc + 16 * 16 * 2;                           // [g][x]: y * (word j+1 of the pivot rows)
     const PanelInfo *pi = c.info + j;
     const int R = pi->R, r = pi->r;
     const int tid = threadIdx.x;
     const bool has_f = j + 1 < c.mu;
-    const bool has_tile = j + 2 < c.mu;
-    const int q0 = ((j + 2) / kTileWords) * kTileWords;
+    const bool pair_first = c.pair && !(j & 1) && j + 1 < c.mu;
+    const bool pair_second = c.pair && (j & 1);
+    const int ntiles_w = (c.mu + kTileWords - 1) / kTileWords;
+    const int t0 = (j + 2) / kTileWords;  // first tile of the range
+    const int nt = j + 2 >= c.mu ? 0 : min((j + 2 + (pair_first ? 1 : 0)) / kTileWords, ntiles_w - 1) - t0 + 1;
+    const int q0 = t0 * kTileWords;
     const int lane = tid & 31, warp = tid >> 5;
     const int rs = lane / kLanesPerRow, wp = lane % kLanesPerRow, swp = rs & 3;
     const int col = q0 + 2 * wp;
-    const bool live_hi = has_tile && r > 0 && col + 1 >= j + 2;  // word col+1 takes the update
-    const bool live_lo = live_hi && col >= j + 2;                 // and word col too
+    const bool live_hi = nt > 0 && r > 0 && col + 1 >= j + 2;  // word col+1 takes the update
+    const bool live_lo = live_hi && col >= j + 2;                // and word col too
     const int wq = R >> 6, sh = R & 63;
     const bool two = sh + r > 64;
     // this CTA's rows: entries [rb, re) of the rows still active before
@@ -172,7 +183,8 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
     const int cnt = j == 0 ? c.n : c.nact[j - 1];
     const int32_t *lst = j == 0 ? nullptr : c.act + (int64_t)((j - 1) & 1) * c.n;
     const int rb = blockIdx.x * kNextRows, re = min(cnt, rb + kNextRows);
-    if (rb >= re && blockIdx.x != 0) return;
+    const bool rows_here = rb < re;
+    if (!rows_here && blockIdx.x != 0 && !pair_second) return;
     const uint64_t *Fj = c.F + (int64_t)(j & 1) * c.n;
     uint64_t *Fn = c.F + (int64_t)((j + 1) & 1) * c.n;
     constexpr int U = kNextRows / (kRowsPerWarp * (kNextThreads / 32));  // row groups per warp
@@ -202,25 +214,28 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
         a[u] = (in && live_hi) ? *reinterpret_cast<const ulonglong2 *>(c.W + widx(c, rr, col)) : make_ulonglong2(0, 0);
     }
     // 2. tables of (Zp, Comp) for y and lambda, of word j+1 of the pivot
-    // rows, and of C for the tile
+    // rows, and of C for the tiles
     if (r > 0) {
         const int g = tid >> 4, x = tid & 15;
         uint64_t y = 0, l = 0, v = 0;
 #pragma unroll
         for (int b = 0; b < 4; ++b)
             if ((x >> b) & 1) {
-                const int s = 4 * g + b;
-                y ^= pi->Zp[s];
-                l ^= pi->Comp[s];
-                if (has_f && s < r) v ^= c.W[widx(c, pi->prow[s], j + 1)];
+                const int s2 = 4 * g + b;
+                y ^= pi->Zp[s2];
+                l ^= pi->Comp[s2];
+                if (has_f && s2 < r) v ^= c.W[widx(c, pi->prow[s2], j + 1)];
             }
         zc[2 * tid] = y;
         zc[2 * tid + 1] = l;
         c1[tid] = v;
-        if (has_tile) load_pivot_rows<kNextThreads>(c, pi->prow, r, q0, crow);
+        for (int tt = 0; tt < nt; ++tt)
+            load_pivot_rows<kNextThreads>(c, pi->prow, r, q0 + tt * kTileWords, crow + tt * 64 * kTileWords);
     }
     __syncthreads();
-    if (has_tile && r > 0) build_tables<kNextC, kNextThreads>(tab, crow);
+    if (r > 0)
+        for (int tt = 0; tt < nt; ++tt)
+            build_tables<kNextC, kNextThreads>(tab + tt * Tabs<kNextC>::Words, crow + tt * 64 * kTileWords);
     // the rows that stay active, appended to the list of panel j in list order
     const int kept_row = keep_row[tid];
     const unsigned kept_mask = __ballot_sync(0xffffffffu, kept_row >= 0);
@@ -245,10 +260,12 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
     const ulonglong2 *zc2 = reinterpret_cast<const ulonglong2 *>(zc);
     const ulonglong2 *tab2 = reinterpret_cast<const ulonglong2 *>(tab);
     const int ng = tables_used<kNextC>(r);
-    uint64_t *Ynext = c.Y + (int64_t)(j & 1) * c.n;
+    uint64_t *Ynext = c.Y + (int64_t)(j & 3) * c.n;
+    uint64_t yv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int row = rows[u];
+        yv[u] = 0;
         if (row < 0) continue;
         uint64_t y = 0, l = 0;
         if ((active >> u) & 1) {
@@ -259,6 +276,7 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
                 l ^= t.y;
             }
         }
+        yv[u] = y;
         if (wp == 0) {
             Ynext[row] = y;
             if (c.Lint && l) {  // this panel's bits of the L row: disjoint from every other panel's
@@ -280,6 +298,22 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
             uint64_t *dst = c.W + widx(c, row, col);
             if (live_lo) *reinterpret_cast<ulonglong2 *>(dst) = a[u];
             else dst[1] = a[u].y;
+        }
+    }
+    // the second tile of a pair's range: every word of it
+    if (nt > 1 && r > 0) {
+        const int col2 = q0 + kTileWords + 2 * wp;
+        const ulonglong2 *tab2b = reinterpret_cast<const ulonglong2 *>(tab + Tabs<kNextC>::Words);
+        ulonglong2 b2[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            b2[u] = (rows[u] >= 0 && yv[u]) ? *reinterpret_cast<const ulonglong2 *>(c.W + widx(c, rows[u], col2))
+                                            : make_ulonglong2(0, 0);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (rows[u] < 0 || !yv[u]) continue;
+            lookup<kNextC>(tab2b, yv[u], wp, swp, ng, b2[u]);
+            *reinterpret_cast<ulonglong2 *>(c.W + widx(c, rows[u], col2)) = b2[u];
         }
     }
 
@@ -305,45 +339,93 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
                 }
             }
         }
-        if (c.Eint && has_tile) echelon_rows<kNextC, kNextThreads>(c, pi, R, r, q0, j + 2, ng, tab);
+        if (c.Eint)
+            for (int tt = 0; tt < nt; ++tt)
+                echelon_rows<kNextC, kNextThreads>(c, pi, R, r, q0 + tt * kTileWords, j + 2, ng,
+                                                   tab + tt * Tabs<kNextC>::Words);
+    }
+
+    // 4. second panel of a pair: the first panel's update of this panel's
+    // pivot rows on the tiles of the wide update (tiles after t0)
+    if (pair_second && r > 0) {
+        const PanelInfo *pp = c.info + (j - 1);
+        const int rp = pp->r;
+        if (rp > 0) {
+            const uint64_t *Yp = c.Y + (int64_t)((j - 1) & 3) * c.n;
+            const int s2 = tid / kTileWords, w = tid % kTileWords;  // pivot row s2 of panel j, word w
+            const bool mine = s2 < r;
+            const int srow = mine ? pi->prow[s2] : 0;
+            const uint64_t yp = mine ? Yp[srow] : 0;
+            uint64_t *cprev = crow;  // the first panel's pivot rows on one tile
+            for (int tile = t0 + 1 + blockIdx.x; tile < ntiles_w; tile += gridDim.x) {
+                __syncthreads();
+                load_pivot_rows<kNextThreads>(c, pp->prow, rp, tile * kTileWords, cprev);
+                __syncthreads();
+                if (mine && yp) {
+                    uint64_t *dst = c.W + widx(c, srow, tile * kTileWords + w);
+                    uint64_t acc = *dst;
+                    for (uint64_t b = yp; b; b &= b - 1) acc ^= cprev[(__ffsll((long long)b) - 1) * kTileWords + w];
+                    *dst = acc;
+                }
+            }
+        }
     }
 }
 
 // -------------------------------------------------------------------- k_rest
+// The wide update of panel j (NP = 1), or of the pair of panels j, j+1 at
+// once (NP = 2, the wide-panel form of Section 5: w = 128 columns, one read
+// and one write of every trailing word per pair): W ^= y_j C_j (+ y_j+1 C_j+1)
+// on the tiles after the look-ahead range, over the rows that are not pivots
+// of panels <= j + NP - 1.  For a pair the tables of C_j+1 are built from the
+// second panel's pivot rows AFTER the first panel's update (the look-ahead
+// kernel of panel j+1 applied it), so the two products simply add.
 constexpr int kRestThreads = 512;
-constexpr int kRestChunk = 256;  // storage rows per work item
-constexpr int kRestU = 6;        // row groups of 8 rows per warp and iteration
+constexpr int kRestChunk = 256;  // list entries per work item
+constexpr int kRestU = 6;        // row groups of 16 rows per warp and iteration (one panel)
+constexpr int kRest2U = 4;       // the same for a pair
 
-template <int C, int U>
-// at most 96 registers: 512 x 96 leaves room on the SM for a k_next or k_panel CTA
-// (128 threads) next to this persistent CTA
+template <int C, int NP>
+constexpr int rest_smem_bytes()
+{
+    return (NP * Tabs<C>::Words + NP * 64 * kTileWords) * 8;
+}
+
+template <int C, int U, int NP>
+// at most 96 registers: 512 x 96 leaves room on the SM for a k_next CTA
+// (256 x 64) next to this persistent CTA
 __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int ntiles)
 {
+    static_assert(NP == 1 || NP == 2, "one panel or a pair");
     extern __shared__ __align__(16) uint64_t smem[];
-    uint64_t *tab = smem;
-    uint64_t *crow = smem + Tabs<C>::Words;
-    const PanelInfo *pi = c.info + j;
-    const int R = pi->R, r = pi->r;
-    if (r == 0) return;
+    uint64_t *tab = smem;                          // [NP * K tables][X][kTileWords]
+    uint64_t *crow = smem + NP * Tabs<C>::Words;   // [NP][64 x kTileWords]
+    constexpr int K = Tabs<C>::K;
+    const PanelInfo *pi0 = c.info + j;
+    const PanelInfo *pi1 = c.info + j + NP - 1;
+    const int r0 = pi0->r, r1 = NP == 2 ? pi1->r : 0;
+    if (r0 == 0 && r1 == 0) return;
     // the rows to update: the list of the rows that are not pivots of
-    // panels <= j (the rows that are have y = 0)
-    const int nact = c.nact[j];
-    const int32_t *__restrict__ act = c.act + (int64_t)(j & 1) * c.n;
+    // panels <= j + NP - 1 (the rows that are have y = 0)
+    const int jl = j + NP - 1;
+    const int nact = c.nact[jl];
+    const int32_t *__restrict__ act = c.act + (int64_t)(jl & 1) * c.n;
     // (with no row left the tiles are still visited when E is wanted: the
     // pivot rows' echelon words come from the same tables)
     const int nchunks = max((nact + kRestChunk - 1) / kRestChunk, c.Eint ? 1 : 0);
     const int64_t items = (int64_t)ntiles * nchunks;
     if (items == 0) return;
     const int64_t i0 = items * blockIdx.x / gridDim.x, i1 = items * (blockIdx.x + 1) / gridDim.x;
-    const uint64_t *__restrict__ Yj = c.Y + (int64_t)(j & 1) * c.n;
+    const uint64_t *__restrict__ Y0 = c.Y + (int64_t)(j & 3) * c.n;
+    const uint64_t *__restrict__ Y1 = c.Y + (int64_t)((j + 1) & 3) * c.n;
     uint64_t *__restrict__ W = c.W;
-    const int ng = tables_used<C>(r);
+    const int ng0 = tables_used<C>(r0), ng1 = NP == 2 ? tables_used<C>(r1) : 0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int rs = lane / kLanesPerRow, wp = lane % kLanesPerRow, swp = rs & 3;
     constexpr int NW = kRestThreads / 32;
     const ulonglong2 *tab2 = reinterpret_cast<const ulonglong2 *>(tab);
     // The item range is split into segments of one tile each: one table
-    // build per segment, then one pipelined pass over its contiguous rows.
+    // build per segment, then one pipelined pass over its rows.
     for (int64_t it = i0; it < i1;) {
         const int tile = tile_first + (int)(it / nchunks);
         const int chunk = (int)(it % nchunks);
@@ -352,15 +434,20 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
         it = seg_end;
         const int q0 = tile * kTileWords;
         __syncthreads();
-        load_pivot_rows<kRestThreads>(c, pi->prow, r, q0, crow);
+        load_pivot_rows<kRestThreads>(c, pi0->prow, r0, q0, crow);
+        if (NP == 2) load_pivot_rows<kRestThreads>(c, pi1->prow, r1, q0, crow + 64 * kTileWords);
         __syncthreads();
         build_tables<C, kRestThreads>(tab, crow);
+        if (NP == 2) build_tables<C, kRestThreads>(tab, crow + 64 * kTileWords, K);
         __syncthreads();
-        if (c.Eint && chunk == 0) echelon_rows<C, kRestThreads>(c, pi, R, r, q0, 0, ng, tab);
+        if (c.Eint && chunk == 0) {
+            echelon_rows<C, kRestThreads>(c, pi0, pi0->R, r0, q0, 0, ng0, tab);
+            if (NP == 2) echelon_rows<C, kRestThreads>(c, pi1, pi1->R, r1, q0, 0, ng1, tab, K);
+        }
         uint64_t *__restrict__ Wt = W + (int64_t)tile * c.tstride + 2 * wp;  // this lane's word pair of the tile
         const int rb = chunk * kRestChunk, re = min(nact, chunk_end * kRestChunk);
         constexpr int STEP = kRowsPerWarp * U * NW;
-        uint64_t yn[U];
+        uint64_t yn0[U], yn1[U];
         int rown[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -368,38 +455,57 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
             rown[u] = k < re ? act[k] : -1;
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) yn[u] = rown[u] >= 0 ? Yj[rown[u]] : 0;
+        for (int u = 0; u < U; ++u) {
+            yn0[u] = rown[u] >= 0 ? Y0[rown[u]] : 0;
+            yn1[u] = (NP == 2 && rown[u] >= 0) ? Y1[rown[u]] : 0;
+        }
         for (int base = rb + warp * kRowsPerWarp * U; base < re; base += STEP) {
-            uint64_t y[U];
+            uint64_t y0[U], y1[U];
             int row[U];
             ulonglong2 a[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                y[u] = yn[u];
+                y0[u] = yn0[u];
+                y1[u] = yn1[u];
                 row[u] = rown[u];
                 const int k = base + STEP + u * kRowsPerWarp + rs;
                 rown[u] = k < re ? act[k] : -1;
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u) yn[u] = rown[u] >= 0 ? Yj[rown[u]] : 0;
+            for (int u = 0; u < U; ++u) {
+                yn0[u] = rown[u] >= 0 ? Y0[rown[u]] : 0;
+                yn1[u] = (NP == 2 && rown[u] >= 0) ? Y1[rown[u]] : 0;
+            }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 a[u] = make_ulonglong2(0, 0);
-                if (y[u]) a[u] = *reinterpret_cast<const ulonglong2 *>(Wt + (int64_t)row[u] * kTileWords);
+                if (y0[u] | y1[u]) a[u] = *reinterpret_cast<const ulonglong2 *>(Wt + (int64_t)row[u] * kTileWords);
             }
-            for (int g = 0; g < ng; ++g) {
+            for (int g = 0; g < ng0; ++g) {
                 const int gg = g ^ swp;
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const int x = (int)((y[u] >> (C * gg)) & (Tabs<C>::X - 1));
+                    const int x = (int)((y0[u] >> (C * gg)) & (Tabs<C>::X - 1));
                     const ulonglong2 t = tab2[tab_entry<C>(gg, x) * (kTileWords / 2) + wp];
                     a[u].x ^= t.x;
                     a[u].y ^= t.y;
                 }
             }
+            if (NP == 2) {
+                for (int g = 0; g < ng1; ++g) {
+                    const int gg = g ^ swp;
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int x = (int)((y1[u] >> (C * gg)) & (Tabs<C>::X - 1));
+                        const ulonglong2 t = tab2[tab_entry<C>(K + gg, x) * (kTileWords / 2) + wp];
+                        a[u].x ^= t.x;
+                        a[u].y ^= t.y;
+                    }
+                }
+            }
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (y[u]) *reinterpret_cast<ulonglong2 *>(Wt + (int64_t)row[u] * kTileWords) = a[u];
+                if (y0[u] | y1[u]) *reinterpret_cast<ulonglong2 *>(Wt + (int64_t)row[u] * kTileWords) = a[u];
         }
     }
 }
@@ -495,7 +601,8 @@ cudaError_t prepare_update_kernels()
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(mu);
     if (done[dev]) return cudaSuccess;
-    e = allow_smem(k_rest<8, kRestU>, (Tabs<8>::Words + 64 * kTileWords) * 8);
+    e = allow_smem(k_rest<8, kRestU, 1>, rest_smem_bytes<8, 1>());
+    if (e == cudaSuccess) e = allow_smem(k_rest<8, kRest2U, 2>, rest_smem_bytes<8, 2>());
     if (e == cudaSuccess) e = allow_smem(k_mmm_pass, kMmmSmemBytes);
     if (e == cudaSuccess) done[dev] = true;
     return e;
@@ -508,17 +615,17 @@ cudaError_t launch_next(const DecompCtx &c, int j, cudaStream_t s)
     return cudaGetLastError();
 }
 
-int rest_tiles(const DecompCtx &c, int j, int *tile_first)
+int rest_tiles(const DecompCtx &c, int j, int np, int *tile_first)
 {
-    *tile_first = (j + 2) / kTileWords + 1;
+    *tile_first = (j + 1 + np) / kTileWords + 1;
     const int tiles = (c.mu + kTileWords - 1) / kTileWords - *tile_first;
     return tiles > 0 ? tiles : 0;
 }
 
-cudaError_t launch_rest(const DecompCtx &c, int j, int est_active_rows, cudaStream_t s)
+cudaError_t launch_rest(const DecompCtx &c, int j, int np, int est_active_rows, cudaStream_t s)
 {
     int tile_first = 0;
-    const int ntiles = rest_tiles(c, j, &tile_first);
+    const int ntiles = rest_tiles(c, j, np, &tile_first);
     if (ntiles <= 0) return cudaSuccess;
     const int nchunks = (c.n + kRestChunk - 1) / kRestChunk;
     const int64_t items = (int64_t)ntiles * nchunks;
@@ -529,13 +636,12 @@ cudaError_t launch_rest(const DecompCtx &c, int j, int est_active_rows, cudaStre
     if (items < grid) grid = (int)items;
     cudaError_t e = prepare_update_kernels();
     if (e != cudaSuccess) return e;
-    if (est_active_rows >= 4096) {
-        constexpr int bytes = (Tabs<8>::Words + 64 * kTileWords) * 8;
-        k_rest<8, kRestU><<<grid, kRestThreads, bytes, s>>>(c, j, tile_first, ntiles);
-    } else {
-        constexpr int bytes = (Tabs<4>::Words + 64 * kTileWords) * 8;
-        k_rest<4, kRestU><<<grid, kRestThreads, bytes, s>>>(c, j, tile_first, ntiles);
-    }
+    if (np == 2)
+        k_rest<8, kRest2U, 2><<<grid, kRestThreads, rest_smem_bytes<8, 2>(), s>>>(c, j, tile_first, ntiles);
+    else if (est_active_rows >= 4096)
+        k_rest<8, kRestU, 1><<<grid, kRestThreads, rest_smem_bytes<8, 1>(), s>>>(c, j, tile_first, ntiles);
+    else
+        k_rest<4, kRestU, 1><<<grid, kRestThreads, rest_smem_bytes<4, 1>(), s>>>(c, j, tile_first, ntiles);
     return cudaGetLastError();
 }
 

@@ -34,7 +34,7 @@ constexpr size_t align_na(size_t x) { return (x + kAlignNA - 1) / kAlignNA * kAl
 // layout of the static scratch (worst case n = m = 4096)
 constexpr size_t kOffW = 0;
 constexpr size_t kOffY = kOffW + align_na((size_t)kNoallocMaxDim * kNoallocMu * 8);
-constexpr size_t kOffF = kOffY + align_na((size_t)kNoallocMaxDim * 2 * 8);
+constexpr size_t kOffF = kOffY + align_na((size_t)kNoallocMaxDim * 4 * 8);
 constexpr size_t kOffAct = kOffF + align_na((size_t)kNoallocMaxDim * 2 * 8);
 constexpr size_t kOffNact = kOffAct + align_na((size_t)kNoallocMaxDim * 2 * 4);
 constexpr size_t kOffPP = kOffNact + align_na((size_t)kNoallocMu * 4);
@@ -118,7 +118,7 @@ extern "C" int gf2_rank_noalloc(const gf2_mat *A, int64_t *rank_dev, void *strea
         if (launch_panel(c, j, s) != cudaSuccess) return GF2_ERR_CUDA;
         if (launch_next(c, j, s) != cudaSuccess) return GF2_ERR_CUDA;
         int tile_first = 0;
-        if (rest_tiles(c, j, &tile_first) > 0 && launch_rest(c, j, (int)(n - 64 * (int64_t)(j + 1)), s) != cudaSuccess)
+        if (rest_tiles(c, j, 1, &tile_first) > 0 && launch_rest(c, j, 1, (int)(n - 64 * (int64_t)(j + 1)), s) != cudaSuccess)
             return GF2_ERR_CUDA;
     }
     if (launch_finish_scalars(c, rank_dev, s) != cudaSuccess) return GF2_ERR_CUDA;
