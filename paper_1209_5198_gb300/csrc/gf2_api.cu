@@ -278,7 +278,6 @@ int enqueue_factorization(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat
     cudaEvent_t *evPanel = side->events.data(), *evNext = evPanel + mu, *evRest = evNext + mu;
     cudaEvent_t evFork = evRest[mu], evJoinP = evRest[mu + 1], evJoinN = evRest[mu + 2];
     std::vector<char> rest_launched(mu, 0);
-    CK(cudaMemsetAsync(c.nact, 0, (size_t)mu * sizeof(int32_t), s));
     CK(cudaEventRecord(evFork, s));
     CK(cudaStreamWaitEvent(P, evFork, 0));
     CK(cudaStreamWaitEvent(N, evFork, 0));
@@ -400,6 +399,7 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
         if (st) return st;
     }
     if (c.Lint) CK(cudaMemsetAsync(c.Lint, 0, (size_t)n * d.ldl * 8, s));
+    CK(cudaMemsetAsync(c.nact, 0, (size_t)c.mu * sizeof(int32_t), s));  // the active-list counts
 
     // The factorization runs on the library's three streams of this device
     // (M: wide updates and outputs, P: the panel chain, N: the look-ahead
