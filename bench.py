@@ -45,6 +45,48 @@ def bitops(n: int, m: int, pivcols: np.ndarray) -> float:
     return float(np.sum(2.0 * (n - t - 1) * (m - q - 1)))
 
 
+TILE_WORDS = 4  # words per column tile of the library's working copy
+
+
+def rest_launch_bytes(n: int, mu: int, rj: np.ndarray, pairs: bool, lookups: bool = False) -> list:
+    """Algorithmic bytes of every k_rest launch of one decomposition: one
+    read and one write (16 B) of every word the launch updates.  Panel j's
+    wide update (or that of the pair j, j+1, j even) covers the rows that are
+    not pivots of the panels it applies and the column tiles after the one
+    holding word j+2 (j+3 for a pair); a launch happens when its panels have
+    pivots and such tiles exist."""
+    Rj = np.concatenate([[0], np.cumsum(rj)])
+    out = []
+    j = 0
+    while j < mu:
+        np_ = 2 if (pairs and j + 1 < mu) else 1
+        rows = n - Rj[j + np_]
+        words = mu - TILE_WORDS * ((j + 1 + np_) // TILE_WORDS + 1)
+        if rj[j:j + np_].sum() > 0 and words > 0:
+            per_word = 64.0 * np_ if lookups else 16.0
+            out.append(per_word * max(rows, 0) * words)
+        j += np_
+    return out
+
+
+def smem_roofline(lookup_bytes: float, upd_ms: float, clocks: dict):
+    """The update's co-bound: table-lookup bytes per second against the shared
+    memory bandwidth of the SMs it runs on (128 B/clk each, all SMs but the
+    one kept for the panel kernel, at the SM clock sampled under load)."""
+    try:
+        import torch
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count - 1
+    except Exception:
+        return None
+    mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz")
+    if not mhz or upd_ms <= 0:
+        return None
+    peak = 128.0 * sms * mhz * 1e6 / 1e9
+    achieved = lookup_bytes / (upd_ms / 1000.0) / 1e9
+    return {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "per_word_bytes": "64 per panel (8 lookups of 8 B, c = 8)"}
+
+
 def rest_traffic(n: int, m: int):
     """DRAM bytes per k_rest launch from the committed ncu capture of this
     workload, or None when the kernel source changed since the capture (or
@@ -264,14 +306,11 @@ def run_ours(args):
     mu = (m + 63) // 64
     blk = pivh // 64
     rj = np.bincount(blk, minlength=mu)
-    Rj = np.concatenate([[0], np.cumsum(rj)[:-1]])
-    j = np.arange(mu)
-    rows_below = np.maximum(n - Rj - rj, 0)
-    # k_rest(j) updates the column tiles after the one holding word j+2 (the
-    # look-ahead kernel takes words j+1.. of that tile): read + write 8 bytes
-    # per word of every row below the pivots
-    live_words = np.maximum(mu - 8 * ((j + 2) // 8 + 1), 0)
-    alg_bytes = float(np.sum(np.where(rj > 0, 16.0 * rows_below * live_words, 0.0))) * prof_steps
+    pairs = os.environ.get("GF2_PAIRS", "1") != "0"
+    alg_bytes = float(np.sum(rest_launch_bytes(n, mu, rj, pairs))) * prof_steps
+    # the co-bound: shared-memory table lookups, 8 of 8 bytes per updated word
+    # and panel (c = 8), against 128 B/clk on each SM the update runs on
+    lookup_bytes = float(np.sum(rest_launch_bytes(n, mu, rj, pairs, lookups=True))) * prof_steps
     upd_ms, upd_n = per_class["update"]
     peaks = {}
     try:
@@ -345,6 +384,7 @@ def run_ours(args):
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                          "peak_source": peak_src,
                          "alg_bytes_per_launch": alg_bytes / max(1, upd_n),
+                         "smem_lookups": smem_roofline(lookup_bytes, upd_ms, clocks),
                          "avg_launch_ms": upd_ms / max(1, upd_n), "launches": upd_n,
                          "time_share": shares},
             "kernel_ms_per_step": {c: v[0] / prof_steps for c, v in per_class.items()},
