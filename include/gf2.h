@@ -145,6 +145,28 @@ int gf2_decompose_host(int64_t n, int64_t m, const uint64_t *A_host, int64_t lda
                        void *workspace, size_t ws_bytes, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Batched decomposition: `count` independent matrices, each decomposed as
+ * gf2_decompose would (same pivot rule, same outputs, bit for bit), in one
+ * persistent launch: one CTA factors one matrix at a time (Lemma 4.1 block by
+ * block) and takes the next from a shared queue, largest work first.  Meant
+ * for many small and medium systems (each n, m <= 4096).
+ *   A[i]        n_i x m_i (column blocks, device; not modified)
+ *   perm[i]     device int32[n_i]; pivcols[i] device int32[min(n_i, m_i)]
+ *   rank        device int64[count]
+ *   L, E        arrays of count descriptors as gf2_decompose (both or neither;
+ *               NULL: rank, perm and pivcols only)
+ * The descriptor arrays are read on the host during the call.  The call
+ * synchronises the stream once (it reads the padding status back).
+ * Errors: GF2_ERR_ARG, GF2_ERR_SHAPE, GF2_ERR_PADDING, GF2_ERR_NOMEM,
+ * GF2_ERR_UNSUPPORTED (a matrix with more than 4096 rows or columns),
+ * GF2_ERR_CUDA.
+ */
+size_t gf2_decompose_batched_workspace_bytes(int count, const int64_t *n, const int64_t *m, int want_factors);
+int gf2_decompose_batched(int count, const gf2_mat *A, int32_t *const *perm, int32_t *const *pivcols,
+                          int64_t *rank, const gf2_mat *L, const gf2_mat *E, unsigned flags,
+                          void *workspace, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
  * Linear systems A X = B over F2 from the factors of P*A = L*E (the use of
  * the decomposition in Section 1 of the paper; forward and back
  * substitution with the factors of Lemma 4.1).

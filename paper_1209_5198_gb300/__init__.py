@@ -81,6 +81,10 @@ def load() -> ctypes.CDLL:
     lib.gf2_decompose_host_workspace_bytes.argtypes = [I64, I64, ctypes.c_int]
     lib.gf2_decompose_host.restype = ctypes.c_int
     lib.gf2_decompose_host.argtypes = [I64, I64, P, I64, P, P, P, P, P, ctypes.c_uint, P, S, P]
+    lib.gf2_decompose_batched_workspace_bytes.restype = S
+    lib.gf2_decompose_batched_workspace_bytes.argtypes = [ctypes.c_int, P, P, ctypes.c_int]
+    lib.gf2_decompose_batched.restype = ctypes.c_int
+    lib.gf2_decompose_batched.argtypes = [ctypes.c_int, P, P, P, P, P, P, ctypes.c_uint, P, S, P]
     lib.gf2_solve_workspace_bytes.restype = S
     lib.gf2_solve_workspace_bytes.argtypes = [I64, I64]
     lib.gf2_solve.restype = ctypes.c_int
@@ -212,6 +216,30 @@ def gf2_decompose_host(n: int, m: int, A_host: np.ndarray, perm_host: np.ndarray
                                   _stream(stream)), "gf2_decompose_host")
 
 
+def gf2_decompose_batched(As: list, perms: list, pivcols: list, ranks: torch.Tensor,
+                          Ls: list | None = None, Es: list | None = None, flags: int = 0, workspace=None,
+                          stream=None) -> None:
+    """Decomposes every matrix of As in one launch (outputs as gf2_decompose;
+    ranks: int64 [len(As)] on the device).  Synchronises the stream."""
+    lib = load()
+    count = len(As)
+    if count == 0:
+        return
+    ns = (ctypes.c_int64 * count)(*[a.rows for a in As])
+    ms = (ctypes.c_int64 * count)(*[a.cols for a in As])
+    want = Ls is not None
+    if workspace is None:
+        workspace = _workspace(lib.gf2_decompose_batched_workspace_bytes(count, ns, ms, int(want)), ranks.device)
+    A_arr = (_CMat * count)(*[a.c() for a in As])
+    P_arr = (ctypes.c_void_p * count)(*[_ptr(p) for p in perms])
+    V_arr = (ctypes.c_void_p * count)(*[_ptr(p) for p in pivcols])
+    L_arr = (_CMat * count)(*[x.c() for x in Ls]) if want else None
+    E_arr = (_CMat * count)(*[x.c() for x in Es]) if want else None
+    _check(lib.gf2_decompose_batched(count, A_arr, P_arr, V_arr, _ptr(ranks), L_arr, E_arr, flags,
+                                     workspace.data_ptr(), workspace.numel(), _stream(stream)),
+           "gf2_decompose_batched")
+
+
 def gf2_solve(L: Mat, E: Mat, perm: torch.Tensor, pivcols: torch.Tensor, rank: torch.Tensor, B: Mat, X: Mat,
               consistent: torch.Tensor, flags: int = 0, workspace=None, stream=None) -> None:
     """A X = B from the factors gf2_decompose wrote (B: n x nrhs, X: m x nrhs,
@@ -240,6 +268,26 @@ def decompose(A: Mat, factors: bool = True, flags: int = 0, stream=None) -> dict
     E = Mat.empty(k, m, dev) if factors else None
     gf2_decompose(A, perm, piv, rank, L, E, flags=flags, stream=stream)
     return dict(perm=perm[:n], pivcols=piv[:k], rank=rank, L=L, E=E)
+
+
+def decompose_batched(As: list, factors: bool = True, flags: int = 0, stream=None) -> list:
+    """Allocates the outputs and runs gf2_decompose_batched; returns one dict
+    per matrix as decompose() does (rank as an int64 tensor view)."""
+    if not As:
+        return []
+    dev = As[0].t.device
+    perms = [torch.empty(max(a.rows, 1), dtype=torch.int32, device=dev) for a in As]
+    pivs = [torch.empty(max(min(a.rows, a.cols), 1), dtype=torch.int32, device=dev) for a in As]
+    ranks = torch.zeros(len(As), dtype=torch.int64, device=dev)
+    Ls = [Mat.empty(a.rows, min(a.rows, a.cols), dev) for a in As] if factors else None
+    Es = [Mat.empty(min(a.rows, a.cols), a.cols, dev) for a in As] if factors else None
+    gf2_decompose_batched(As, perms, pivs, ranks, Ls, Es, flags=flags, stream=stream)
+    out = []
+    for i, a in enumerate(As):
+        k = min(a.rows, a.cols)
+        out.append(dict(perm=perms[i][:a.rows], pivcols=pivs[i][:k], rank=ranks[i:i + 1],
+                        L=Ls[i] if factors else None, E=Es[i] if factors else None))
+    return out
 
 
 def solve(factors: dict, B: Mat, m: int, stream=None) -> dict:

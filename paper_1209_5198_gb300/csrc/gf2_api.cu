@@ -1,5 +1,6 @@
 // C ABI of the F2 library (declared in include/gf2.h): argument checks,
 // workspace carving and the host-side sequence of kernel launches.
+#include <algorithm>
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
@@ -19,6 +20,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 int64_t words_of(int64_t cols) { return (cols + 63) / 64; }
 int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
+int64_t round_up_tiles(int64_t words) { return (words + kTileWords - 1) / kTileWords * kTileWords; }
 
 uint64_t last_word_mask(int64_t cols)
 {
@@ -645,6 +647,132 @@ int gf2_solve(const gf2_mat *L, const gf2_mat *E, const int32_t *perm, const int
     if (*g_flag_host & 1u) return GF2_ERR_TIMEOUT;
     if (*g_flag_host & 2u) return GF2_ERR_PADDING;
     return GF2_OK;
+}
+
+// ------------------------------------------------------------ batched
+}  // extern "C"
+
+namespace {
+
+constexpr int64_t kBatchMaxDim = 4096;
+
+struct BatchLayout {
+    int grid;
+    int64_t nmax, mumax, kmax_max;
+    int64_t off_y, off_info, off_pivpanel, off_lint, off_eint, slice_words;
+    size_t off_items, off_order, off_sync, off_scratch, total;
+};
+
+int64_t round_words(int64_t w) { return (w + 31) / 32 * 32; }  // 256-byte slices
+
+int batch_layout(int count, const int64_t *n, const int64_t *m, bool factors, BatchLayout *L)
+{
+    BatchLayout d{};
+    for (int i = 0; i < count; ++i) {
+        d.nmax = n[i] > d.nmax ? n[i] : d.nmax;
+        d.mumax = words_of(m[i]) > d.mumax ? words_of(m[i]) : d.mumax;
+        const int64_t k = n[i] < m[i] ? n[i] : m[i];
+        d.kmax_max = k > d.kmax_max ? k : d.kmax_max;
+    }
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return GF2_ERR_CUDA;
+    const int want = sms * batch_ctas_per_sm();
+    d.grid = count < want ? (count > 0 ? count : 1) : want;
+    const int64_t nm = d.nmax > 0 ? d.nmax : 1;
+    const int64_t ldw = round_up_tiles(d.mumax > 0 ? d.mumax : 1);
+    const int64_t ldl = words_of(d.kmax_max) > 0 ? words_of(d.kmax_max) : 1;
+    int64_t o = round_words(nm * ldw);                       // W (tiled)
+    d.off_y = o; o += round_words(nm);                        // Y
+    d.off_info = o; o += round_words(2 * (int64_t)((sizeof(PanelInfo) + 7) / 8));
+    d.off_pivpanel = o; o += round_words((nm + 1) / 2);
+    d.off_lint = o; if (factors) o += round_words(nm * ldl);
+    d.off_eint = o; if (factors) o += round_words((d.kmax_max > 0 ? d.kmax_max : 1) * ldw);
+    d.slice_words = o;
+    size_t b = 0;
+    d.off_items = b; b += align_up((size_t)(count > 0 ? count : 1) * sizeof(BatchItem));
+    d.off_order = b; b += align_up((size_t)(count > 0 ? count : 1) * 4);
+    d.off_sync = b; b += kAlign;
+    d.off_scratch = b; b += (size_t)d.grid * (size_t)d.slice_words * 8;
+    d.total = b;
+    *L = d;
+    return GF2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gf2_decompose_batched_workspace_bytes(int count, const int64_t *n, const int64_t *m, int want_factors)
+{
+    if (count < 0 || (count > 0 && (!n || !m))) return 0;
+    BatchLayout d{};
+    if (batch_layout(count, n, m, want_factors != 0, &d) != GF2_OK) return 0;
+    return d.total;
+}
+
+int gf2_decompose_batched(int count, const gf2_mat *A, int32_t *const *perm, int32_t *const *pivcols, int64_t *rank,
+                          const gf2_mat *L, const gf2_mat *E, unsigned flags, void *workspace, size_t ws_bytes,
+                          void *stream)
+{
+    if (count < 0 || (flags & ~GF2_NOCHECK)) return GF2_ERR_ARG;
+    if (count == 0) return GF2_OK;
+    if (!A || !perm || !rank || (count > 0 && !pivcols)) return GF2_ERR_ARG;
+    const bool factors = L || E;
+    if (factors && (!L || !E)) return GF2_ERR_ARG;
+    std::vector<int64_t> ns(count), ms(count);
+    std::vector<BatchItem> items(count);
+    for (int i = 0; i < count; ++i) {
+        if (!mat_ok(&A[i]) || !perm[i]) return GF2_ERR_ARG;
+        const int64_t n = A[i].rows, m = A[i].cols, k = n < m ? n : m;
+        if (n > kBatchMaxDim || m > kBatchMaxDim) return GF2_ERR_UNSUPPORTED;
+        if (k > 0 && !pivcols[i]) return GF2_ERR_ARG;
+        if (factors && (!mat_ok(&L[i]) || !mat_ok(&E[i]) || L[i].rows != n || L[i].cols != k || E[i].rows != k ||
+                        E[i].cols != m))
+            return GF2_ERR_SHAPE;
+        ns[i] = n;
+        ms[i] = m;
+        items[i] = BatchItem{A[i].w, A[i].ld, (int32_t)n, (int32_t)m, perm[i], pivcols[i], rank + i,
+                             factors ? L[i].w : nullptr, factors ? L[i].ld : 0,
+                             factors ? E[i].w : nullptr, factors ? E[i].ld : 0};
+    }
+    BatchLayout d{};
+    int st = batch_layout(count, ns.data(), ms.data(), factors, &d);
+    if (st) return st;
+    void *ws = nullptr;
+    st = get_workspace(workspace, ws_bytes, d.total, &ws);
+    if (st) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *p = static_cast<char *>(ws);
+    // largest work first, so that the CTAs finish together
+    std::vector<int32_t> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const double wa = (double)ns[a] * words_of(ms[a]) * (ns[a] < ms[a] ? ns[a] : ms[a]);
+        const double wb = (double)ns[b] * words_of(ms[b]) * (ns[b] < ms[b] ? ns[b] : ms[b]);
+        return wa > wb;
+    });
+    CK(cudaMemcpyAsync(p + d.off_items, items.data(), sizeof(BatchItem) * count, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(p + d.off_order, order.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(p + d.off_sync, 0, kAlign, s));
+    BatchCtx b{};
+    b.items = reinterpret_cast<const BatchItem *>(p + d.off_items);
+    b.order = reinterpret_cast<const int32_t *>(p + d.off_order);
+    b.next_item = reinterpret_cast<int32_t *>(p + d.off_sync);
+    b.err = reinterpret_cast<uint32_t *>(p + d.off_sync + 64);
+    b.scratch = reinterpret_cast<uint64_t *>(p + d.off_scratch);
+    b.scratch_words = d.slice_words;
+    b.off_y = d.off_y;
+    b.off_info = d.off_info;
+    b.off_pivpanel = d.off_pivpanel;
+    b.off_lint = d.off_lint;
+    b.off_eint = d.off_eint;
+    b.count = count;
+    b.factors = factors ? 1 : 0;
+    b.check = (flags & GF2_NOCHECK) ? 0 : 1;
+    LAUNCH(GF2_KCLASS_PANEL, launch_batch(b, d.grid, s));
+    // the padding status (and the host arrays above stay alive until here)
+    return check_flag(b.err, s);
 }
 
 // ------------------------------------------------------------ product

@@ -69,7 +69,14 @@ struct DecompCtx {
     uint64_t *Eint;     // [k x lde] per pivot index (row-major), or null
     int32_t n, m, mu, kmax;
     int32_t pair;       // wide updates by pairs of panels (j even, j+1)
+    int32_t info_ring;  // info holds only panels j-1 and j (info[j % 2]): the batched form
 };
+
+// The PanelInfo of panel j.
+__device__ __forceinline__ PanelInfo *panel_info(const DecompCtx &c, int j)
+{
+    return c.info + (c.info_ring ? (j & 1) : j);
+}
 
 // Index of word q of storage row i in the tiled W.
 __device__ __forceinline__ int64_t widx(const DecompCtx &c, int64_t i, int q)
@@ -84,6 +91,29 @@ struct MmmCtx {
     const uint64_t *B; int64_t ldb;   // row-major, k x ceil(m/64)
     uint64_t *C; int64_t ldc;         // row-major, n x ldc (multiple of 8)
     int32_t n, k;
+};
+
+// One matrix of a batched decomposition (the caller's buffers; column blocks).
+struct BatchItem {
+    const uint64_t *A; int64_t lda;
+    int32_t n, m;
+    int32_t *perm, *pivcols;
+    int64_t *rank;
+    uint64_t *L; int64_t ldl;   // null: rank only
+    uint64_t *E; int64_t lde;
+};
+
+// A batched decomposition: the items, the order in which CTAs take them, and
+// one scratch slice per CTA (offsets in words within a slice).
+struct BatchCtx {
+    const BatchItem *items;
+    const int32_t *order;       // items by decreasing work
+    int32_t *next_item;         // shared counter (zero before the launch)
+    uint32_t *err;              // padding flag
+    uint64_t *scratch;
+    int64_t scratch_words;      // per CTA
+    int64_t off_y, off_info, off_pivpanel, off_lint, off_eint;
+    int32_t count, factors, check;
 };
 
 // Operands of a solve A X = B from the factors P*A = L*E (column blocks).
@@ -128,5 +158,7 @@ cudaError_t prepare_update_kernels();  // one-time kernel attributes (before any
 cudaError_t prepare_panel_kernel();
 cudaError_t launch_mmm_pass(const MmmCtx &c, int kb, int m_words, cudaStream_t s);
 cudaError_t launch_solve(const SolveCtx &c, cudaStream_t s);  // one cooperative launch
+int batch_ctas_per_sm();
+cudaError_t launch_batch(const BatchCtx &b, int grid, cudaStream_t s);
 
 }  // namespace gf2
