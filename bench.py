@@ -212,6 +212,104 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ batched
+
+BATCH_METRIC = "batched decomposition matrices/s (P*A = L*E each)"
+
+
+def batch_matrices(count: int, p: float, seed: int, dev):
+    """The batched workload: count matrices, rows and columns uniform in
+    [64, 2048], entries Bernoulli(p); every second matrix made rank-deficient
+    (its rows after a random r are XORs of two of its first r rows).  Made on
+    the GPU with torch's seeded generator (inputs only); returns row-major
+    int64 word tensors and their column counts."""
+    import torch
+    g = torch.Generator(device=dev).manual_seed(seed)
+    sizes = torch.randint(64, 2049, (count, 2), generator=g, device=dev).cpu().tolist()
+    mats = []
+    for i, (n, m) in enumerate(sizes):
+        mu = (m + 63) // 64
+        bits = torch.rand((n, mu * 64), generator=g, device=dev) < p
+        bits[:, m:] = False
+        w = (bits.view(n, mu, 64).to(torch.int64) << torch.arange(64, device=dev)).sum(-1)
+        if i % 2 == 1:
+            r = int(torch.randint(1, min(n, m) + 1, (1,), generator=g, device=dev).item())
+            if r < n:
+                a = torch.randint(0, r, (n - r,), generator=g, device=dev)
+                b = torch.randint(0, r, (n - r,), generator=g, device=dev)
+                w[r:] = w[a] ^ w[b]
+        mats.append((w, n, m))
+    return mats
+
+
+def run_batched(args):
+    import torch
+
+    import paper_1209_5198_gb300 as gf2
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    count = args.batch
+    lib = gf2.load()
+    stream = torch.cuda.current_stream()
+    results = {}
+    for p, seed in ((0.5, 0x1209), (0.1, 0x5198)):
+        mats = batch_matrices(count, p, seed, dev)
+        As = [gf2.Mat(w.t().contiguous(), n, m) for w, n, m in mats]
+        perms = [torch.empty(n, dtype=torch.int32, device=dev) for _, n, _ in mats]
+        pivs = [torch.empty(min(n, m), dtype=torch.int32, device=dev) for _, n, m in mats]
+        ranks = torch.zeros(count, dtype=torch.int64, device=dev)
+        Ls = [gf2.Mat.empty(n, min(n, m), dev) for _, n, m in mats]
+        Es = [gf2.Mat.empty(min(n, m), m, dev) for _, n, m in mats]
+        ns = [n for _, n, _ in mats]
+        ms = [m for _, _, m in mats]
+        import ctypes
+        wsb = lib.gf2_decompose_batched_workspace_bytes(count, (ctypes.c_int64 * count)(*ns),
+                                                        (ctypes.c_int64 * count)(*ms), 1)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+
+        def step():
+            gf2.gf2_decompose_batched(As, perms, pivs, ranks, Ls, Es, workspace=ws, stream=stream)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_batch = e0.elapsed_time(e1) / args.steps
+        rk = ranks.cpu().numpy()
+        ops = sum(bitops(n, m, pv.cpu().numpy()[: int(r)]) for (_, n, m), pv, r in zip(mats, pivs, rk))
+        # the same matrices one plain gf2_decompose call after another
+        wsp = torch.empty(lib.gf2_decompose_workspace_bytes(2048, 2048, 1), dtype=torch.uint8, device=dev)
+        rk1 = torch.zeros(1, dtype=torch.int64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(count):
+            gf2.gf2_decompose(As[i], perms[i], pivs[i], rk1, Ls[i], Es[i], workspace=wsp, stream=stream)
+        torch.cuda.synchronize()
+        ms_loop = (time.perf_counter() - t0) * 1000
+        results[p] = dict(ms=ms_batch, ops=ops, ms_loop=ms_loop, deficient=int(sum(1 for (w, n, m), r in zip(mats, rk) if r < min(n, m))))
+    total_ms = sum(r["ms"] for r in results.values())
+    total_loop = sum(r["ms_loop"] for r in results.values())
+    line = {
+        "metric": BATCH_METRIC, "value": 2 * count / (total_ms / 1000), "unit": "matrices/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"batched: 2 batches (p = 0.5, 0.1) of {count} matrices, rows and cols uniform "
+                               f"in [64, 2048], every second one rank-deficient; one step = both batches",
+                   "per_batch_ms": {str(p): r["ms"] for p, r in results.items()},
+                   "rank_deficient": {str(p): r["deficient"] for p, r in results.items()}},
+        "bitops_per_s": sum(r["ops"] for r in results.values()) / (total_ms / 1000),
+        "plain_loop": {"value": 2 * count / (total_loop / 1000), "unit": "matrices/s",
+                       "how": "one gf2_decompose call per matrix on the same stream, host clock, one pass"},
+        "speedup_vs_plain_loop": total_loop / total_ms,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ ours
 
 def run_ours(args):
@@ -406,10 +504,15 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="decompose", choices=["decompose", "batched"],
+                    help="decompose: the headline 32768^2 decomposition; batched: many small matrices in one launch")
+    ap.add_argument("--batch", type=int, default=4096, help="matrices per batch (batched workload)")
     args = ap.parse_args()
     args.m = args.m or args.n
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -237,6 +237,18 @@ int64_t kernel_nodes(cudaGraph_t graph)
     return k;
 }
 
+// Keys of recent calls that ran without a graph (a second call captures one).
+std::vector<GraphKey> g_seen;  // guarded by g_side_mutex
+
+bool seen_before(const GraphKey &k)
+{
+    for (auto &s : g_seen)
+        if (memcmp(&s, &k, sizeof(GraphKey)) == 0) return true;
+    if (g_seen.size() >= 4 * kMaxGraphs) g_seen.erase(g_seen.begin());
+    g_seen.push_back(k);
+    return false;
+}
+
 void remember_graph(const GraphKey &k, cudaGraph_t graph, cudaGraphExec_t exec)
 {
     if (g_graphs.size() >= kMaxGraphs) {
@@ -252,6 +264,7 @@ void remember_graph(const GraphKey &k, cudaGraph_t graph, cudaGraphExec_t exec)
 
 void drop_graphs()
 {
+    g_seen.clear();
     for (auto &g : g_graphs) {
         cudaGraphExecDestroy(g.exec);
         cudaGraphDestroy(g.graph);
@@ -428,6 +441,16 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
     } else {
         int64_t replayed = 0;  // kernels of a graph captured earlier (a capture counts its own)
         cudaGraphExec_t exec = find_graph(key, &replayed);
+        if (!exec && !seen_before(key)) {
+            // first call with this shape and these buffers: enqueue directly
+            // (a capture and instantiation cost more than one run; a repeat
+            // call is captured and every later one replays the graph)
+            st = enqueue_factorization(c, rank, L, E, side);
+            if (st) return st;
+            CK(cudaEventRecord(evOut, side->main));
+            CK(cudaStreamWaitEvent(s, evOut, 0));
+            return GF2_OK;
+        }
         if (!exec) {
             if (cudaStreamBeginCapture(side->main, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GF2_ERR_CUDA;
             st = enqueue_factorization(c, rank, L, E, side);
