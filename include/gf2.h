@@ -47,7 +47,9 @@ extern "C" {
 #define GF2_ERR_UNSUPPORTED 7 /* size beyond what this build handles        */
 
 /* flags */
-#define GF2_NOCHECK 1u /* skip the padding check of the inputs */
+#define GF2_NOCHECK 1u    /* skip the padding check of the inputs */
+#define GF2_MMM_TABLES 2u /* gf2_mmm: Four Russians passes (M4RM) */
+#define GF2_MMM_TENSOR 4u /* gf2_mmm: tensor cores (e4m3 products, exact mod 2; k < 2^24) */
 
 typedef struct gf2_mat {
     uint64_t *w;          /* device pointer, column blocks (see above) */
@@ -66,8 +68,12 @@ int gf2_version(void);
 int gf2_release_workspace(void);
 
 /* ------------------------------------------------------------------------
- * Product over F2 (Section 1 and Section 6 of the paper; the Four Russians
- * method M4RM of Section 6 with tables in shared memory).
+ * Product over F2 (Section 1 and Section 6 of the paper).  Two backends:
+ * the Four Russians method M4RM of Section 6 with tables in shared memory,
+ * and the tensor cores (every entry an e4m3 0 or 1, exact integer sums in
+ * fp32, entry = lowest bit), chosen by the flags GF2_MMM_TABLES /
+ * GF2_MMM_TENSOR; with neither, M4RM (the faster of the two on the GB300).
+ * GF2_MMM_TENSOR with k >= 2^24 also runs M4RM.  Both give the same bits.
  *   C = A*B        (accumulate == 0)
  *   C = C xor A*B  (accumulate != 0)
  * A is n x k, B is k x m, C is n x m (all column blocks, device memory,
@@ -76,7 +82,7 @@ int gf2_release_workspace(void);
  * Errors: GF2_ERR_ARG (NULL), GF2_ERR_SHAPE (A.cols != B.rows, C not n x m,
  * ld < rows), GF2_ERR_PADDING, GF2_ERR_NOMEM, GF2_ERR_CUDA.
  */
-size_t gf2_mmm_workspace_bytes(int64_t n, int64_t k, int64_t m);
+size_t gf2_mmm_workspace_bytes(int64_t n, int64_t k, int64_t m, unsigned flags);
 int gf2_mmm(const gf2_mat *A, const gf2_mat *B, gf2_mat *C, int accumulate, unsigned flags,
             void *workspace, size_t ws_bytes, void *stream);
 

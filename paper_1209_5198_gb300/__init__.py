@@ -25,6 +25,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgf2.so")
 
 GF2_OK = 0
+GF2_MMM_TABLES = 2
+GF2_MMM_TENSOR = 4
 GF2_ERR_ARG = 1
 GF2_ERR_SHAPE = 2
 GF2_ERR_PADDING = 3
@@ -66,7 +68,7 @@ def load() -> ctypes.CDLL:
     lib.gf2_version.restype = ctypes.c_int
     lib.gf2_release_workspace.restype = ctypes.c_int
     lib.gf2_mmm_workspace_bytes.restype = S
-    lib.gf2_mmm_workspace_bytes.argtypes = [I64, I64, I64]
+    lib.gf2_mmm_workspace_bytes.argtypes = [I64, I64, I64, ctypes.c_uint]
     lib.gf2_mmm.restype = ctypes.c_int
     lib.gf2_mmm.argtypes = [M, M, M, ctypes.c_int, ctypes.c_uint, P, S, P]
     lib.gf2_decompose_workspace_bytes.restype = S
@@ -167,7 +169,7 @@ def gf2_mmm(A: Mat, B: Mat, C: Mat, accumulate: bool = False, flags: int = 0, wo
     """C = A*B (or C ^= A*B) over F2.  Asynchronous on ``stream``."""
     lib = load()
     if workspace is None:
-        workspace = _workspace(lib.gf2_mmm_workspace_bytes(A.rows, A.cols, B.cols), C.t.device)
+        workspace = _workspace(lib.gf2_mmm_workspace_bytes(A.rows, A.cols, B.cols, flags), C.t.device)
     a, b, c = A.c(), B.c(), C.c()
     _check(lib.gf2_mmm(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), int(bool(accumulate)), flags,
                        workspace.data_ptr(), workspace.numel(), _stream(stream)), "gf2_mmm")

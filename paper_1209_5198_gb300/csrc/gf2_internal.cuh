@@ -159,6 +159,13 @@ cudaError_t prepare_panel_kernel();
 cudaError_t launch_mmm_pass(const MmmCtx &c, int kb, int m_words, cudaStream_t s);
 cudaError_t launch_solve(const SolveCtx &c, cudaStream_t s);  // one cooperative launch
 int batch_ctas_per_sm();
+// the product on the tensor cores (k < 2^24): A8, B8 are n_pad x k_pad and
+// m_pad x k_pad bytes (dimensions rounded up to mma_pad)
+int64_t mma_pad(int64_t x);
+cudaError_t launch_mma_product(const uint64_t *A, int64_t lda, const uint64_t *B, int64_t ldb, uint64_t *C,
+                               int64_t ldc, int n, int k, int m, int accumulate, uint8_t *A8, uint8_t *B8,
+                               cudaStream_t s);
+cudaError_t launch_check_last_block(const uint64_t *last, int rows, uint64_t mask, uint32_t *err, cudaStream_t s);
 cudaError_t launch_batch(const BatchCtx &b, int grid, cudaStream_t s);
 
 }  // namespace gf2

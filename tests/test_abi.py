@@ -40,7 +40,7 @@ def test_host_only_entry_points(lib):
     assert ws >= 3 * n * (m // 64) * 8  # working copy + L + E, row-major
     assert lib.gf2_decompose_workspace_bytes(n, m, 0) < ws
     assert lib.gf2_rank_workspace_bytes(n, m) >= lib.gf2_decompose_workspace_bytes(n, m, 0)
-    assert lib.gf2_mmm_workspace_bytes(1000, 2000, 3000) >= 8 * (1000 * 32 + 2000 * 47 + 1000 * 47)
+    assert lib.gf2_mmm_workspace_bytes(1000, 2000, 3000, 0) >= 8 * (1000 * 32 + 2000 * 47 + 1000 * 47)
     assert lib.gf2_decompose_workspace_bytes(-1, 5, 0) == 0
 
 

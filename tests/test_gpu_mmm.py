@@ -14,24 +14,57 @@ if not torch.cuda.is_available():
 import paper_1209_5198_gb300 as gf2  # noqa: E402
 
 
+BACKENDS = {"auto": 0, "tables": gf2.GF2_MMM_TABLES, "tensor": gf2.GF2_MMM_TENSOR}
+
+
+@pytest.mark.parametrize("backend", sorted(BACKENDS))
 @pytest.mark.parametrize("n,k,m", [(1, 1, 1), (5, 70, 3), (64, 64, 64), (300, 130, 650), (1024, 1024, 1024),
-                                   (1000, 1300, 777), (2048, 64, 4100), (129, 2000, 65)])
-def test_product_matches_oracle(n, k, m):
+                                   (1000, 1300, 777), (2048, 64, 4100), (129, 2000, 65), (257, 4099, 191)])
+def test_product_matches_oracle(n, k, m, backend):
+    flags = BACKENDS[backend]
     A = f2gen.uniform(n, k, 41, n, k)
     B = f2gen.uniform(k, m, 42, k, m)
     ref = oracle.mmm(A, B, k, m, nthreads=oracle.max_threads())
     Ad = gf2.Mat.from_rowmajor(A, k, ld=n + 1)
     Bd = gf2.Mat.from_rowmajor(B, m)
     Cd = gf2.Mat.empty(n, m, ld=n + 7)
-    gf2.gf2_mmm(Ad, Bd, Cd)
+    gf2.gf2_mmm(Ad, Bd, Cd, flags=flags)
     assert np.array_equal(Cd.to_rowmajor(), ref)
     # accumulate: C ^= A*B twice gives back the original C
     C0 = f2gen.uniform(n, m, 43, n, m)
     Cd = gf2.Mat.from_rowmajor(C0, m)
-    gf2.gf2_mmm(Ad, Bd, Cd, accumulate=True)
+    gf2.gf2_mmm(Ad, Bd, Cd, accumulate=True, flags=flags)
     assert np.array_equal(Cd.to_rowmajor(), ref ^ C0)
-    gf2.gf2_mmm(Ad, Bd, Cd, accumulate=True)
+    gf2.gf2_mmm(Ad, Bd, Cd, accumulate=True, flags=flags)
     assert np.array_equal(Cd.to_rowmajor(), C0)
+
+
+def test_product_dense_ones_exact():
+    """All-ones operands: every sum is k, the largest the accumulator holds
+    here; entry parity = k mod 2 for both backends."""
+    for k in (4095, 4096):
+        n = m = 200
+        A = np.full((n, (k + 63) // 64), ~np.uint64(0), dtype=np.uint64)
+        if k % 64:
+            A[:, -1] = (np.uint64(1) << np.uint64(k % 64)) - np.uint64(1)
+        B = np.full((k, (m + 63) // 64), ~np.uint64(0), dtype=np.uint64)
+        B[:, -1] = (np.uint64(1) << np.uint64(m % 64)) - np.uint64(1)
+        ref = oracle.mmm(A, B, k, m)
+        for flags in (gf2.GF2_MMM_TABLES, gf2.GF2_MMM_TENSOR):
+            Cd = gf2.Mat.empty(n, m)
+            gf2.gf2_mmm(gf2.Mat.from_rowmajor(A, k), gf2.Mat.from_rowmajor(B, m), Cd, flags=flags)
+            assert np.array_equal(Cd.to_rowmajor(), ref)
+
+
+def test_product_padding_error_both_backends():
+    A = f2gen.uniform(100, 300, 45)
+    A[7, 4] |= np.uint64(1) << np.uint64(50)  # column 306 >= 300
+    B = f2gen.uniform(300, 100, 46)
+    for flags in (gf2.GF2_MMM_TABLES, gf2.GF2_MMM_TENSOR):
+        with pytest.raises(gf2.Gf2Error) as e:
+            gf2.gf2_mmm(gf2.Mat.from_rowmajor(A, 300), gf2.Mat.from_rowmajor(B, 100), gf2.Mat.empty(100, 100),
+                        flags=flags)
+        assert e.value.status == gf2.GF2_ERR_PADDING
 
 
 def test_product_of_fixed_rank_factors_has_that_rank():
