@@ -203,6 +203,84 @@ int gf2_solve(const gf2_mat *L, const gf2_mat *E, const int32_t *perm, const int
               unsigned flags, void *workspace, size_t ws_bytes, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Serving: a request engine for rank and solve requests on many matrices
+ * (the paper's use of the decomposition, Section 1: many systems over F2,
+ * each factored once and then solved as right-hand sides arrive).  No
+ * counterpart in the paper's code; the arithmetic is gf2_decompose's and
+ * gf2_solve's, bit for bit.
+ *
+ * The engine runs on its own host thread.  Requests carry a matrix key; the
+ * factors of a key stay resident in device memory (an arena of
+ * `device_bytes`, least recently used factors evicted first when room is
+ * needed) so that later requests on the same key only solve.  Continuous
+ * batching: a request is admitted once it has arrived and its memory fits;
+ * misses are decomposed (several small matrices, up to 512 x 512, together
+ * in one batched launch, the others by the plain decomposition on the whole
+ * GPU); every solve whose factors
+ * are ready joins the next solve launch, one CTA per request, while up to
+ * four earlier launches are still on the GPU.  Each CTA writes its results
+ * to mapped host memory and raises a per-request flag, so a request is
+ * complete as soon as its own CTA is done.
+ * GF2_SERVE_SERIAL: one request at a time through gf2_decompose and
+ * gf2_solve, waiting for each (the one-at-a-time baseline), same residency.
+ */
+#define GF2_SERVE_SERIAL 1u
+
+typedef struct gf2_server gf2_server;
+
+typedef struct gf2_request {
+    uint64_t id;          /* caller's tag, returned in the completion                     */
+    uint64_t matrix;      /* key: requests with the same key share resident factors and
+                             must give the same n, m (and the same A)                     */
+    int64_t n, m;         /* size of A, 1 <= n, m <= the server's limits                  */
+    const uint64_t *A;    /* HOST column blocks of A (word (i,q) at A[q*lda + i], padding
+                             bits 0); read only when the key's factors are not resident   */
+    int64_t lda;          /* >= n                                                         */
+    int32_t nrhs;         /* 0: rank only; 1..64: solve A X = B                            */
+    const uint64_t *B;    /* HOST, n words, bit c = right-hand side c (bits >= nrhs 0)     */
+    uint64_t *X;          /* HOST, m words out: the solutions as gf2_solve gives them      */
+    double arrival_us;    /* earliest admission on the server clock (0: on submission)     */
+} gf2_request;
+
+typedef struct gf2_completion {
+    uint64_t id;
+    int32_t status;       /* GF2_OK or the error of this request                          */
+    int32_t hit;          /* 1: the factors were resident (or being built) on admission   */
+    int64_t rank;
+    uint64_t consistent;  /* bit c: right-hand side c has a solution                      */
+    double arrival_us;    /* max(arrival_us, submission time)                              */
+    double admit_us, done_us;
+} gf2_completion;
+
+typedef struct gf2_server_stats {
+    int64_t completed, hits, misses, evictions;
+    int64_t solve_launches, batched_decompositions, plain_decompositions;
+    int64_t max_batch, resident_bytes, arena_bytes;
+} gf2_server_stats;
+
+/* Creates an engine on the current device.  device_bytes: the device memory
+ * for factors, staging and solve scratch (one eighth of it, at most 1 GiB,
+ * is kept for the solve launches); max_n, max_m: the largest matrix
+ * accepted (a plain-decomposition workspace of that size is kept outside the
+ * arena); max_batch: solves per launch (<= 4096).
+ * Errors: GF2_ERR_ARG, GF2_ERR_NOMEM, GF2_ERR_CUDA. */
+int gf2_server_create(int64_t device_bytes, int64_t max_n, int64_t max_m, int max_batch, unsigned flags,
+                      gf2_server **out);
+/* Queues `count` requests (descriptors copied; the host buffers A, B, X must
+ * stay valid until the request completes).  A request that is malformed
+ * (sizes, nrhs, padding bits of A or B, a key reused with another size)
+ * completes at once with its error.  Thread-safe.  Errors: GF2_ERR_ARG. */
+int gf2_server_submit(gf2_server *server, const gf2_request *requests, int count);
+/* Moves up to `max` completions to `out` (*count of them), waiting up to
+ * wait_us microseconds for the first one (0: no wait).  Thread-safe. */
+int gf2_server_poll(gf2_server *server, gf2_completion *out, int max, int64_t wait_us, int *count);
+/* The server clock: microseconds since gf2_server_create. */
+double gf2_server_clock_us(const gf2_server *server);
+int gf2_server_stats_read(const gf2_server *server, gf2_server_stats *stats);
+/* Finishes every request already submitted, then frees the engine. */
+int gf2_server_destroy(gf2_server *server);
+
+/* ------------------------------------------------------------------------
  * Diagnostics (no counterpart in the paper; used by the benchmark).
  * gf2_launch_count: kernels this library has launched since it was loaded.
  * gf2_timing_enable(1): from now on every launch is bracketed by CUDA events

@@ -35,6 +35,7 @@ GF2_ERR_CUDA = 5
 GF2_ERR_TIMEOUT = 6
 GF2_ERR_UNSUPPORTED = 7
 GF2_NOCHECK = 1
+GF2_SERVE_SERIAL = 1
 KCLASS = {"panel": 0, "next": 1, "update": 2, "layout": 3, "solve": 4}
 
 
@@ -91,6 +92,18 @@ def load() -> ctypes.CDLL:
     lib.gf2_solve_workspace_bytes.argtypes = [I64, I64]
     lib.gf2_solve.restype = ctypes.c_int
     lib.gf2_solve.argtypes = [M, M, P, P, P, M, M, P, ctypes.c_uint, P, S, P]
+    lib.gf2_server_create.restype = ctypes.c_int
+    lib.gf2_server_create.argtypes = [I64, I64, I64, ctypes.c_int, ctypes.c_uint, ctypes.POINTER(P)]
+    lib.gf2_server_submit.restype = ctypes.c_int
+    lib.gf2_server_submit.argtypes = [P, P, ctypes.c_int]
+    lib.gf2_server_poll.restype = ctypes.c_int
+    lib.gf2_server_poll.argtypes = [P, P, ctypes.c_int, I64, ctypes.POINTER(ctypes.c_int)]
+    lib.gf2_server_clock_us.restype = ctypes.c_double
+    lib.gf2_server_clock_us.argtypes = [P]
+    lib.gf2_server_stats_read.restype = ctypes.c_int
+    lib.gf2_server_stats_read.argtypes = [P, P]
+    lib.gf2_server_destroy.restype = ctypes.c_int
+    lib.gf2_server_destroy.argtypes = [P]
     lib.gf2_launch_count.restype = ctypes.c_int64
     lib.gf2_timing_enable.argtypes = [ctypes.c_int]
     lib.gf2_timing_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)]
@@ -332,3 +345,88 @@ def timing_read() -> dict:
         _check(lib.gf2_timing_read(cls, ctypes.byref(ms), ctypes.byref(cnt)), "gf2_timing_read")
         out[name] = (ms.value, cnt.value)
     return out
+
+
+# ------------------------------------------------------------- serving
+
+# gf2_request / gf2_completion / gf2_server_stats of include/gf2.h, as numpy
+# record types (C layout: align=True)
+REQUEST_DTYPE = np.dtype([("id", "<u8"), ("matrix", "<u8"), ("n", "<i8"), ("m", "<i8"), ("A", "<u8"),
+                          ("lda", "<i8"), ("nrhs", "<i4"), ("B", "<u8"), ("X", "<u8"), ("arrival_us", "<f8")],
+                         align=True)
+COMPLETION_DTYPE = np.dtype([("id", "<u8"), ("status", "<i4"), ("hit", "<i4"), ("rank", "<i8"),
+                             ("consistent", "<u8"), ("arrival_us", "<f8"), ("admit_us", "<f8"),
+                             ("done_us", "<f8")], align=True)
+STATS_FIELDS = ("completed", "hits", "misses", "evictions", "solve_launches", "batched_decompositions",
+                "plain_decompositions", "max_batch", "resident_bytes", "arena_bytes")
+
+
+class Server:
+    """The serving engine (gf2_server_*): rank / solve requests on resident
+    factors, continuous batching on the GPU (or, with ``serial=True``, one
+    request at a time through gf2_decompose and gf2_solve).
+
+    Requests are REQUEST_DTYPE records whose A, B, X fields are HOST
+    addresses; those buffers must stay alive until the request completes.
+    """
+
+    def __init__(self, device_bytes: int, max_n: int, max_m: int, max_batch: int = 1024, serial: bool = False):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.gf2_server_create(int(device_bytes), int(max_n), int(max_m), int(max_batch),
+                                     GF2_SERVE_SERIAL if serial else 0, ctypes.byref(h)), "gf2_server_create")
+        self._h = h
+        self._lib = lib
+
+    def submit(self, requests: np.ndarray) -> None:
+        requests = np.ascontiguousarray(requests, dtype=REQUEST_DTYPE)
+        _check(self._lib.gf2_server_submit(self._h, requests.ctypes.data, len(requests)), "gf2_server_submit")
+
+    def poll(self, max_count: int = 4096, wait_us: int = 0) -> np.ndarray:
+        out = np.zeros(max_count, dtype=COMPLETION_DTYPE)
+        got = ctypes.c_int(0)
+        _check(self._lib.gf2_server_poll(self._h, out.ctypes.data, max_count, int(wait_us), ctypes.byref(got)),
+               "gf2_server_poll")
+        return out[: got.value]
+
+    def wait_all(self, count: int, timeout_s: float = 600.0) -> np.ndarray:
+        """Completions until `count` have arrived (raises after timeout_s)."""
+        import time
+        parts, have = [], 0
+        t_end = time.monotonic() + timeout_s
+        while have < count:
+            if time.monotonic() > t_end:
+                raise TimeoutError(f"{have} of {count} requests completed")
+            c = self.poll(4096, 20000)
+            parts.append(c)
+            have += len(c)
+        return np.concatenate(parts) if parts else np.zeros(0, dtype=COMPLETION_DTYPE)
+
+    def clock_us(self) -> float:
+        return float(self._lib.gf2_server_clock_us(self._h))
+
+    def stats(self) -> dict:
+        raw = (ctypes.c_int64 * len(STATS_FIELDS))()
+        _check(self._lib.gf2_server_stats_read(self._h, ctypes.byref(raw)), "gf2_server_stats_read")
+        return dict(zip(STATS_FIELDS, list(raw)))
+
+    def close(self) -> None:
+        if self._h:
+            _check(self._lib.gf2_server_destroy(self._h), "gf2_server_destroy")
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def host_colblocks(rowmajor: np.ndarray, cols: int, pinned: bool = True) -> torch.Tensor:
+    """Row-major words -> column blocks (ceil(cols/64), rows) in a host int64
+    tensor (pinned by default), for the serving requests' A."""
+    words = np.ascontiguousarray(np.asarray(rowmajor, dtype=np.uint64))
+    mu = (cols + 63) // 64
+    t = torch.empty((mu, words.shape[0]), dtype=torch.int64, pin_memory=pinned)
+    t.numpy().view(np.uint64)[:] = words[:, :mu].T
+    return t

@@ -743,7 +743,6 @@ int gf2_decompose_batched(int count, const gf2_mat *A, int32_t *const *perm, int
     if (!A || !perm || !rank || (count > 0 && !pivcols)) return GF2_ERR_ARG;
     const bool factors = L || E;
     if (factors && (!L || !E)) return GF2_ERR_ARG;
-    std::vector<int64_t> ns(count), ms(count);
     std::vector<BatchItem> items(count);
     for (int i = 0; i < count; ++i) {
         if (!mat_ok(&A[i]) || !perm[i]) return GF2_ERR_ARG;
@@ -753,11 +752,39 @@ int gf2_decompose_batched(int count, const gf2_mat *A, int32_t *const *perm, int
         if (factors && (!mat_ok(&L[i]) || !mat_ok(&E[i]) || L[i].rows != n || L[i].cols != k || E[i].rows != k ||
                         E[i].cols != m))
             return GF2_ERR_SHAPE;
-        ns[i] = n;
-        ms[i] = m;
         items[i] = BatchItem{A[i].w, A[i].ld, (int32_t)n, (int32_t)m, perm[i], pivcols[i], rank + i,
                              factors ? L[i].w : nullptr, factors ? L[i].ld : 0,
                              factors ? E[i].w : nullptr, factors ? E[i].ld : 0};
+    }
+    return gf2::decompose_batched_items(count, items.data(), factors, flags, workspace, ws_bytes, stream);
+}
+
+}  // extern "C"
+
+namespace gf2 {
+
+size_t decompose_batched_items_bytes(int count, const BatchItem *items, bool factors)
+{
+    std::vector<int64_t> ns(count), ms(count);
+    for (int i = 0; i < count; ++i) {
+        ns[i] = items[i].n;
+        ms[i] = items[i].m;
+    }
+    BatchLayout d{};
+    if (batch_layout(count, ns.data(), ms.data(), factors, &d) != GF2_OK) return 0;
+    return d.total;
+}
+
+// The batched decomposition of items already checked (each n, m <= 4096).
+// With GF2_NOCHECK the call does not synchronise the stream.
+int decompose_batched_items(int count, const BatchItem *items, bool factors, unsigned flags, void *workspace,
+                            size_t ws_bytes, void *stream)
+{
+    if (count <= 0) return GF2_OK;
+    std::vector<int64_t> ns(count), ms(count);
+    for (int i = 0; i < count; ++i) {
+        ns[i] = items[i].n;
+        ms[i] = items[i].m;
     }
     BatchLayout d{};
     int st = batch_layout(count, ns.data(), ms.data(), factors, &d);
@@ -775,7 +802,9 @@ int gf2_decompose_batched(int count, const gf2_mat *A, int32_t *const *perm, int
         const double wb = (double)ns[b] * words_of(ms[b]) * (ns[b] < ms[b] ? ns[b] : ms[b]);
         return wa > wb;
     });
-    CK(cudaMemcpyAsync(p + d.off_items, items.data(), sizeof(BatchItem) * count, cudaMemcpyHostToDevice, s));
+    // (copies from pageable memory: the calls return once the host arrays
+    // have been staged)
+    CK(cudaMemcpyAsync(p + d.off_items, items, sizeof(BatchItem) * count, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(p + d.off_order, order.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(p + d.off_sync, 0, kAlign, s));
     BatchCtx b{};
@@ -794,9 +823,15 @@ int gf2_decompose_batched(int count, const gf2_mat *A, int32_t *const *perm, int
     b.factors = factors ? 1 : 0;
     b.check = (flags & GF2_NOCHECK) ? 0 : 1;
     LAUNCH(GF2_KCLASS_PANEL, launch_batch(b, d.grid, s));
-    // the padding status (and the host arrays above stay alive until here)
-    return check_flag(b.err, s);
+    if (flags & GF2_NOCHECK) return GF2_OK;
+    return check_flag(b.err, s);  // the padding status
 }
+
+void add_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+}  // namespace gf2
+
+extern "C" {
 
 // ------------------------------------------------------------ product
 size_t mmm_tables_bytes(int64_t n, int64_t k, int64_t m)

@@ -137,6 +137,16 @@ struct SolveCtx {
     int32_t check;                    // report right-hand-side bits beyond nrhs
 };
 
+// One solve of a serving batch: the operands, where its rank goes and the
+// word that is set once its outputs are written (both may be mapped host
+// memory).  nrhs == 0: the rank alone.
+struct ServeItem {
+    SolveCtx c;
+    int64_t *rank_out;
+    uint32_t *done;
+    int32_t nrhs;
+};
+
 // ---- launchers (each returns the cudaError_t of its launch)
 cudaError_t launch_ingest(const uint64_t *A, int64_t lda, int32_t n, int32_t mu, uint64_t last_mask,
                           uint64_t *W, int64_t ldw, int32_t *perm_identity, int32_t *pivpanel_init,
@@ -158,6 +168,8 @@ cudaError_t prepare_update_kernels();  // one-time kernel attributes (before any
 cudaError_t prepare_panel_kernel();
 cudaError_t launch_mmm_pass(const MmmCtx &c, int kb, int m_words, cudaStream_t s);
 cudaError_t launch_solve(const SolveCtx &c, cudaStream_t s);  // one cooperative launch
+int serve_ctas_per_sm();
+cudaError_t launch_serve_solve(const ServeItem *items, int count, int32_t *next, int grid, cudaStream_t s);
 int batch_ctas_per_sm();
 // the product on the tensor cores (k < 2^24): A8, B8 are n_pad x k_pad and
 // m_pad x k_pad bytes (dimensions rounded up to mma_pad)
@@ -167,5 +179,13 @@ cudaError_t launch_mma_product(const uint64_t *A, int64_t lda, const uint64_t *B
                                cudaStream_t s);
 cudaError_t launch_check_last_block(const uint64_t *last, int rows, uint64_t mask, uint32_t *err, cudaStream_t s);
 cudaError_t launch_batch(const BatchCtx &b, int grid, cudaStream_t s);
+
+// ---- host helpers shared by the entry points (gf2_api.cu)
+// the batched decomposition of checked items (each n, m <= 4096); with
+// GF2_NOCHECK it does not synchronise the stream
+size_t decompose_batched_items_bytes(int count, const BatchItem *items, bool factors);
+int decompose_batched_items(int count, const BatchItem *items, bool factors, unsigned flags, void *workspace,
+                            size_t ws_bytes, void *stream);
+void add_launches(int64_t k);  // kernels launched outside the entry points' own counting
 
 }  // namespace gf2

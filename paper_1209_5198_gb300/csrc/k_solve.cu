@@ -148,20 +148,40 @@ __device__ void upper_block_inverse(const SolveCtx &c, int q, int r, uint64_t *w
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(kSolveThreads) k_solve(SolveCtx c)
+// The barrier between the steps of one solve: grid-wide for the cooperative
+// launch, the CTA's own for a solve that one CTA runs alone.
+struct GridSync {
+    uint32_t *count, *err;
+    uint32_t epoch;
+    int *s_ok;
+    __device__ bool operator()() { return grid_barrier(count, err, epoch, s_ok); }
+};
+struct CtaSync {
+    __device__ bool operator()()
+    {
+        __syncthreads();
+        return true;
+    }
+};
+
+struct SolveShared {
+    uint64_t tab[8 * 256];
+    uint64_t vec[64];  // the right-hand side of the current diagonal block
+    uint64_t res[64];  // its solution (spread over the block's columns)
+    uint64_t wrow[kSolveWarps][64];
+    int s_ok;
+};
+
+// One solve, run by G CTAs (this is CTA b) that meet at `bar` between steps.
+template <class Sync>
+__device__ void solve_body(const SolveCtx &c, int b, int G, Sync &bar, SolveShared &sh)
 {
-    __shared__ uint64_t tab[8 * 256];
-    __shared__ uint64_t vec[64];  // the right-hand side of the current diagonal block
-    __shared__ uint64_t res[64];  // its solution (spread over the block's columns)
-    __shared__ uint64_t wrow[kSolveWarps][64];
-    __shared__ int s_ok;
+    uint64_t *tab = sh.tab, *vec = sh.vec, *res = sh.res;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int G = gridDim.x, b = blockIdx.x;
     const int n = c.n, m = c.m, kmax = min(n, m);
     const int r = (int)min(max(*c.rank, (int64_t)0), (int64_t)kmax);
     const int mu = (m + 63) / 64, nbl = (r + 63) / 64;
-    uint32_t *count = c.sync, *err = c.sync + 1;
-    uint32_t epoch = 0;
+    uint32_t *err = c.sync + 1;
     const int gthreads = G * kSolveThreads, gtid = b * kSolveThreads + tid;
     const int gw = b * kSolveWarps + warp, GW = G * kSolveWarps;
 
@@ -186,10 +206,10 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveCtx c)
         const int qlast = r > 0 ? min(max(c.pivcols[r - 1] >> 6, -1), mu - 1) : -1;
         for (int qq = qlast + 1 + gtid; qq <= mu; qq += gthreads) c.qstart[qq] = r;
     }
-    for (int J = gw; J < nbl; J += GW) lower_block_inverse(c, J, r, wrow[warp], lane);
-    if (!grid_barrier(count, err, epoch, &s_ok)) return;
+    for (int J = gw; J < nbl; J += GW) lower_block_inverse(c, J, r, sh.wrow[warp], lane);
+    if (!bar()) return;
     // needed only by the back substitution; the barriers below order them
-    for (int q = gw; q < mu; q += GW) upper_block_inverse(c, q, r, wrow[warp], lane);
+    for (int q = gw; q < mu; q += GW) upper_block_inverse(c, q, r, sh.wrow[warp], lane);
 
     // ---- forward substitution, 64 rows at a time
     const int rb = (int)((int64_t)n * b / G), re = (int)((int64_t)n * (b + 1) / G);
@@ -214,7 +234,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveCtx c)
             const uint64_t w = LJ[i];
             if (w) c.v[i] = __ldcg(c.v + i) ^ lookup(tab, w);
         }
-        if (!grid_barrier(count, err, epoch, &s_ok)) return;
+        if (!bar()) return;
     }
 
     // ---- consistency: OR of the residual rows
@@ -225,7 +245,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveCtx c)
         for (int off = 16; off; off >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, off);
         if (lane == 0 && bad) atomicOr(reinterpret_cast<unsigned long long *>(c.bad), (unsigned long long)bad);
     }
-    if (!grid_barrier(count, err, epoch, &s_ok)) return;
+    if (!bar()) return;
     const uint64_t ok = c.rhs_mask & ~__ldcg(c.bad);
     if (b == 0 && tid == 0) *c.consistent = ok;
 
@@ -257,7 +277,47 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveCtx c)
             const uint64_t w = Eq[t];
             if (w) c.y[t] = __ldcg(c.y + t) ^ lookup(tab, w);
         }
-        if (!grid_barrier(count, err, epoch, &s_ok)) return;
+        if (!bar()) return;
+    }
+}
+
+__global__ void __launch_bounds__(kSolveThreads) k_solve(SolveCtx c)
+{
+    __shared__ SolveShared sh;
+    GridSync bar{c.sync, c.sync + 1, 0, &sh.s_ok};
+    solve_body(c, blockIdx.x, gridDim.x, bar, sh);
+}
+
+// Many independent solves in one launch (the serving form): every CTA takes
+// the next item from a shared counter (items in decreasing size) and solves
+// it alone.  Its outputs may live in mapped host memory: once they are
+// written and fenced at system scope, the item's done word is set, so the
+// host can hand each result back without waiting for the whole launch.
+__global__ void __launch_bounds__(kSolveThreads) k_serve_solve(const ServeItem *items, int count, int32_t *next)
+{
+    __shared__ SolveShared sh;
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(next, 1);
+        __syncthreads();
+        const int k = s_item;
+        __syncthreads();
+        if (k >= count) return;
+        const ServeItem &it = items[k];
+        if (it.nrhs > 0) {
+            if (tid == 0) *it.c.bad = 0;
+            __syncthreads();
+            CtaSync bar;
+            solve_body(it.c, 0, 1, bar, sh);
+        }
+        if (tid == 0) {
+            const int64_t kmax = min(it.c.n, it.c.m);
+            *it.rank_out = min(max(*it.c.rank, (int64_t)0), kmax);
+        }
+        __threadfence_system();
+        __syncthreads();
+        if (tid == 0) asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(it.done), "r"(1u) : "memory");
     }
 }
 
@@ -280,6 +340,20 @@ cudaError_t launch_solve(const SolveCtx &c, cudaStream_t s)
     void *args[] = {&arg};
     return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_solve), dim3(grid), dim3(kSolveThreads), args,
                                        0, s);
+}
+
+int serve_ctas_per_sm()
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve_solve, kSolveThreads, 0) != cudaSuccess) return 1;
+    return per_sm > 0 ? per_sm : 1;
+}
+
+cudaError_t launch_serve_solve(const ServeItem *items, int count, int32_t *next, int grid, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    k_serve_solve<<<grid, kSolveThreads, 0, s>>>(items, count, next);
+    return cudaGetLastError();
 }
 
 }  // namespace gf2

@@ -79,3 +79,51 @@ def test_solve_argument_errors_without_gpu(lib):
     assert lib.gf2_solve(*args(B, X12)) == g.GF2_ERR_SHAPE         # E is not min(n,m) x m
     assert lib.gf2_solve_workspace_bytes(-1, 5) == 0
     assert lib.gf2_solve_workspace_bytes(32768, 32768) >= 8 * (32768 + 32768 + 2 * 512 * 64)
+
+
+def test_serving_records_match_the_c_layout(tmp_path):
+    """The numpy record types of the binding have the C structs' sizes and
+    field offsets (a C program built against include/gf2.h prints them)."""
+    import shutil
+    import subprocess
+
+    import paper_1209_5198_gb300 as g
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    fields_req = [f for f in g.REQUEST_DTYPE.names]
+    fields_done = [f for f in g.COMPLETION_DTYPE.names]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gf2.h"', "int main(void) {",
+             '  printf("req %zu\\n", sizeof(gf2_request));',
+             '  printf("done %zu\\n", sizeof(gf2_completion));',
+             '  printf("stats %zu\\n", sizeof(gf2_server_stats));']
+    lines += [f'  printf("req.{f} %zu\\n", offsetof(gf2_request, {f}));' for f in fields_req]
+    lines += [f'  printf("done.{f} %zu\\n", offsetof(gf2_completion, {f}));' for f in fields_done]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    assert int(got["req"]) == g.REQUEST_DTYPE.itemsize
+    assert int(got["done"]) == g.COMPLETION_DTYPE.itemsize
+    assert int(got["stats"]) == 8 * len(g.STATS_FIELDS)
+    for f in fields_req:
+        assert int(got[f"req.{f}"]) == g.REQUEST_DTYPE.fields[f][1], f
+    for f in fields_done:
+        assert int(got[f"done.{f}"]) == g.COMPLETION_DTYPE.fields[f][1], f
+
+
+def test_server_argument_errors_without_gpu(lib):
+    import paper_1209_5198_gb300 as g
+    h = ctypes.c_void_p()
+    assert lib.gf2_server_create(0, 16, 16, 8, 0, ctypes.byref(h)) == g.GF2_ERR_ARG
+    assert lib.gf2_server_create(1 << 20, 0, 16, 8, 0, ctypes.byref(h)) == g.GF2_ERR_ARG
+    assert lib.gf2_server_create(1 << 20, 16, 16, 0, 0, ctypes.byref(h)) == g.GF2_ERR_ARG
+    assert lib.gf2_server_create(1 << 20, 16, 16, 8, 0x10, ctypes.byref(h)) == g.GF2_ERR_ARG
+    assert lib.gf2_server_create(1 << 20, 16, 16, 8, 0, None) == g.GF2_ERR_ARG
+    assert lib.gf2_server_submit(None, None, 0) == g.GF2_ERR_ARG
+    cnt = ctypes.c_int(0)
+    assert lib.gf2_server_poll(None, None, 0, 0, ctypes.byref(cnt)) == g.GF2_ERR_ARG
+    assert lib.gf2_server_destroy(None) == g.GF2_ERR_ARG
