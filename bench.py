@@ -310,6 +310,162 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ serving
+
+SERVE_METRIC = "served solves/s (rank + solve requests on resident factors, continuous batching)"
+
+
+class ServeWorkload:
+    """Config 5: `ids` square matrices, n = 2^U with U uniform in [8, 14],
+    rounded up to a multiple of 64, entries Bernoulli(1/2) (random words made
+    on the GPU with torch's seeded generator, inputs only); `nreq` requests,
+    matrix ids Zipf(s = 1.1) over the ids, k uniform in 1..64 right-hand
+    sides, B = A X0 (so every right-hand side is consistent; B is formed on
+    the GPU with the library's product).  Host buffers (A pinned column
+    blocks, B and X per request) stay alive with the object."""
+
+    def __init__(self, nreq: int, ids: int, seed: int):
+        import torch
+
+        import paper_1209_5198_gb300 as gf2
+        dev = torch.device("cuda", 0)
+        rng = np.random.default_rng(seed)
+        g = torch.Generator(device=dev).manual_seed(seed)
+        self.n = [int(-(-int(round(2.0 ** u)) // 64) * 64) for u in rng.uniform(8, 14, size=ids)]
+        self.A, B64 = [], []
+        for n in self.n:
+            mu = n // 64
+            Ad = torch.randint(-(2 ** 63), 2 ** 63 - 1, (mu, n), dtype=torch.int64, generator=g, device=dev)
+            X0 = torch.randint(-(2 ** 63), 2 ** 63 - 1, (1, n), dtype=torch.int64, generator=g, device=dev)
+            C = gf2.Mat.empty(n, 64, dev)
+            gf2.gf2_mmm(gf2.Mat(Ad, n, n), gf2.Mat(X0, n, 64), C)
+            Ah = torch.empty((mu, n), dtype=torch.int64, pin_memory=True)
+            Ah.copy_(Ad)
+            self.A.append(Ah)
+            B64.append(C.t[0].cpu().numpy().view(np.uint64).copy())
+        zipf = 1.0 / np.arange(1, ids + 1) ** 1.1
+        self.key = rng.choice(ids, size=nreq, p=zipf / zipf.sum())
+        self.k = rng.integers(1, 65, size=nreq)
+        nn = np.array(self.n)[self.key]
+        off = np.concatenate([[0], np.cumsum(nn)])
+        self.Bpool = np.empty(int(off[-1]), dtype=np.uint64)
+        self.Xpool = np.zeros(int(off[-1]), dtype=np.uint64)
+        self.req = np.zeros(nreq, dtype=gf2.REQUEST_DTYPE)
+        for i in range(nreq):
+            kk, n, o = int(self.key[i]), int(nn[i]), int(off[i])
+            mask = np.uint64((1 << int(self.k[i])) - 1) if self.k[i] < 64 else ~np.uint64(0)
+            np.bitwise_and(B64[kk], mask, out=self.Bpool[o:o + n])
+            self.req[i] = (i, kk, n, n, self.A[kk].data_ptr(), n, int(self.k[i]),
+                           self.Bpool.ctypes.data + 8 * o, self.Xpool.ctypes.data + 8 * o, 0.0)
+        self.nn = nn
+
+    def bytes_per_request(self):
+        # right-hand sides in, solutions out; A once per distinct key (a miss)
+        h2d = float(np.mean(self.nn) * 8) + sum(self.n[k] ** 2 / 8 for k in set(self.key.tolist())) / len(self.key)
+        return h2d, float(np.mean(self.nn) * 8)
+
+
+def serve_run(w: ServeWorkload, serial: bool, arrivals_us=None, device_bytes: int = 16 << 30):
+    """One pass of the request trace through a fresh engine (cold factors).
+    Returns (completions, makespan_s, launches, stats)."""
+    import paper_1209_5198_gb300 as gf2
+    req = w.req.copy()
+    w.Xpool[:] = 0
+    with gf2.Server(device_bytes, 16384, 16384, max_batch=1024, serial=serial) as s:
+        t_first = s.clock_us() + 20000.0  # the engine has the whole trace before the first arrival
+        req["arrival_us"] = t_first + (0.0 if arrivals_us is None else np.asarray(arrivals_us))
+        l0 = gf2.launch_count()
+        s.submit(req)
+        done = s.wait_all(len(req), timeout_s=1800)
+        launches = gf2.launch_count() - l0
+        st = s.stats()
+    bad = done[done["status"] != gf2.GF2_OK]
+    if len(bad):
+        raise RuntimeError(f"{len(bad)} requests failed, first status {int(bad[0]['status'])}")
+    makespan = (float(done["done_us"].max()) - t_first) / 1e6
+    return done, makespan, launches, st
+
+
+def latency_ms(done):
+    lat = (done["done_us"] - done["arrival_us"]) / 1000.0
+    return float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
+
+
+def run_serving(args):
+    import torch
+
+    torch.cuda.set_device(0)
+    w = ServeWorkload(args.requests, 256, 0x5198)
+    rates = [0.25, 0.5, 0.75, 0.9]
+    done_sat_serial, span_serial, _, _ = serve_run(w, serial=True)
+    cap_serial = len(w.req) / span_serial
+    for _ in range(max(0, args.warmup - 1)):
+        serve_run(w, serial=False)
+    clk = ClockSampler(0)
+    clk.start()
+    done_sat, span, launches, st = serve_run(w, serial=False)
+    clocks = clk.stop()
+    verify_serving(w, done_sat, 16)
+    cap = len(w.req) / span
+    rng = np.random.default_rng(7)
+    per_rate = []
+    for f in rates:
+        lam = f * cap_serial  # requests per second
+        arr = np.cumsum(rng.exponential(1e6 / lam, size=len(w.req)))
+        d_ours, span_o, _, _ = serve_run(w, serial=False, arrivals_us=arr)
+        d_ser, span_s, _, _ = serve_run(w, serial=True, arrivals_us=arr)
+        p50, p99 = latency_ms(d_ours)
+        s50, s99 = latency_ms(d_ser)
+        per_rate.append({"load": f, "offered_per_s": lam, "served_per_s": len(w.req) / span_o,
+                         "p50_ms": p50, "p99_ms": p99, "serial_p50_ms": s50, "serial_p99_ms": s99})
+    sat_p50, sat_p99 = latency_ms(done_sat)
+    h2d, d2h = w.bytes_per_request()
+    line = {
+        "metric": SERVE_METRIC, "value": cap, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+        "ms_per_step": span * 1000, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"serving: {len(w.req)} requests, 256 square matrices n = 2^U(8,14) rounded up "
+                               "to 64, ids Zipf(1.1), k = 1..64 right-hand sides, B = A X0, cold factors; "
+                               "one step = the whole trace, all requests at t = 0 (saturated)",
+                   "requests": len(w.req), "distinct_matrices": int(len(set(w.key.tolist()))),
+                   "mean_n": float(np.mean(w.nn))},
+        "latency_saturated": {"p50_ms": sat_p50, "p99_ms": sat_p99},
+        "serial": {"value": cap_serial, "unit": "solves/s",
+                   "how": "the same engine with GF2_SERVE_SERIAL: gf2_decompose / gf2_solve one request at a time"},
+        "speedup_vs_serial": cap / cap_serial,
+        "poisson": per_rate,
+        "stats": st,
+        "e2e": {"value": cap, "unit": "solves/s", "h2d_bytes_per_step": h2d * len(w.req),
+                "d2h_bytes_per_step": d2h * len(w.req)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def verify_serving(w: ServeWorkload, done, count: int):
+    """A X = B for `count` sampled requests (host arithmetic: parity of A's
+    rows against X, column block by column block)."""
+    rng = np.random.default_rng(3)
+    small = np.flatnonzero(w.nn <= 4096)  # keeps the host check to a few seconds
+    ids = rng.choice(small, size=min(count, len(small)), replace=False)
+    for i in ids:
+        c = done[done["id"] == i][0]
+        kk, n, k = int(w.key[i]), int(w.nn[i]), int(w.k[i])
+        assert int(c["consistent"]) == ((1 << k) - 1 if k < 64 else (1 << 64) - 1), i
+        A = w.A[kk].numpy().view(np.uint64)  # column blocks (n/64, n)
+        o = int(w.req[i]["X"] - w.Xpool.ctypes.data) // 8
+        X = w.Xpool[o:o + n]
+        B = w.Bpool[o:o + n]
+        acc = np.zeros(n, dtype=np.uint64)
+        for q in range(n // 64):  # acc[row] ^= XOR of X[64q + t] over the set bits t of A(row, q)
+            blk = A[q]
+            for t in range(64):
+                sel = ((blk >> np.uint64(t)) & np.uint64(1)).astype(bool)
+                acc[sel] ^= X[64 * q + t]
+        assert np.array_equal(acc, B), f"request {i}: A X != B"
+
+
 # ------------------------------------------------------------------ ours
 
 def run_ours(args):
@@ -504,8 +660,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="decompose", choices=["decompose", "batched"],
-                    help="decompose: the headline 32768^2 decomposition; batched: many small matrices in one launch")
+    ap.add_argument("--workload", default="decompose", choices=["decompose", "batched", "serving"],
+                    help="decompose: the headline 32768^2 decomposition; batched: many small matrices in one "
+                         "launch; serving: a request stream on resident factors")
+    ap.add_argument("--requests", type=int, default=20000, help="requests in the serving trace")
     ap.add_argument("--batch", type=int, default=4096, help="matrices per batch (batched workload)")
     args = ap.parse_args()
     args.m = args.m or args.n
@@ -513,6 +671,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -215,8 +215,8 @@ int gf2_solve(const gf2_mat *L, const gf2_mat *E, const int32_t *perm, const int
  * needed) so that later requests on the same key only solve.  Continuous
  * batching: a request is admitted once it has arrived and its memory fits;
  * misses are decomposed (several small matrices, up to 512 x 512, together
- * in one batched launch, the others by the plain decomposition on the whole
- * GPU); every solve whose factors
+ * in one batched launch, the others by the plain decomposition, up to four
+ * side by side); every solve whose factors
  * are ready joins the next solve launch, one CTA per request, while up to
  * four earlier launches are still on the GPU.  Each CTA writes its results
  * to mapped host memory and raises a per-request flag, so a request is

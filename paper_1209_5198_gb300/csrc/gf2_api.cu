@@ -4,6 +4,7 @@
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -145,27 +146,43 @@ cudaError_t launch(int cls, cudaStream_t s, F &&f)
 #define LAUNCH_ON(cls, strm, expr) CK(launch((cls), (strm), [&]() { return (expr); }))
 
 // ------------------------------------------------------------ side stream
-// Per device: high-priority non-blocking streams for the panel chain and for
-// the look-ahead kernels, a low-priority one for the wide updates, and a pool
-// of events for the cross-stream dependencies.  Enqueueing a
-// decomposition holds g_side_mutex, so the events are used by one call at a
-// time (a wait captures the event's state when it is enqueued).
+// Per device, kLanes sets of: high-priority non-blocking streams for the
+// panel chain and for the look-ahead kernels, a low-priority one for the
+// wide updates, and a pool of events for the cross-stream dependencies.
+// Each decomposition takes the next lane in turn and holds that lane's mutex
+// while it enqueues, so a lane's events are used by one call at a time (a
+// wait captures the event's state when it is enqueued), and decompositions
+// issued on different caller streams run side by side on the GPU.
+constexpr int kLanes = 4;
 struct SideResources {
     int device = 0;
     cudaStream_t main = nullptr;    // wide updates and outputs
     cudaStream_t stream = nullptr;  // the panel chain (high priority)
     cudaStream_t next = nullptr;    // the look-ahead kernels (high priority)
     std::vector<cudaEvent_t> events;
+    std::mutex mu;                  // held while a decomposition is enqueued
 };
-std::mutex g_side_mutex;
-std::vector<SideResources> g_side;
+struct DeviceLanes {
+    SideResources lane[kLanes];
+};
+std::mutex g_lanes_mutex;  // guards the table below
+std::vector<std::unique_ptr<DeviceLanes>> g_lanes;
+std::atomic<unsigned> g_next_lane{0};
 
-int side_resources(int nevents, SideResources **out)
+// The next lane of the current device, locked (lock owns its mutex).
+int side_resources(int nevents, SideResources **out, std::unique_lock<std::mutex> &lock)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return GF2_ERR_CUDA;
-    if ((int)g_side.size() <= dev) g_side.resize(dev + 1);
-    SideResources &r = g_side[dev];
+    DeviceLanes *dl = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_lanes_mutex);
+        if ((int)g_lanes.size() <= dev) g_lanes.resize(dev + 1);
+        if (!g_lanes[dev]) g_lanes[dev].reset(new DeviceLanes);
+        dl = g_lanes[dev].get();
+    }
+    SideResources &r = dl->lane[g_next_lane.fetch_add(1, std::memory_order_relaxed) % kLanes];
+    lock = std::unique_lock<std::mutex>(r.mu);
     r.device = dev;
     if (!r.stream) {
         int lo = 0, hi = 0;
@@ -199,7 +216,8 @@ struct GraphEntry {
     uint64_t stamp;
     int64_t kernels;  // kernel nodes: the launches one replay makes
 };
-std::vector<GraphEntry> g_graphs;  // guarded by g_side_mutex
+std::mutex g_graph_mutex;          // guards the graph cache
+std::vector<GraphEntry> g_graphs;  // guarded by g_graph_mutex
 uint64_t g_graph_clock = 0;
 constexpr size_t kMaxGraphs = 16;
 const bool g_use_graphs = [] {
@@ -238,7 +256,7 @@ int64_t kernel_nodes(cudaGraph_t graph)
 }
 
 // Keys of recent calls that ran without a graph (a second call captures one).
-std::vector<GraphKey> g_seen;  // guarded by g_side_mutex
+std::vector<GraphKey> g_seen;  // guarded by g_graph_mutex
 
 bool seen_before(const GraphKey &k)
 {
@@ -249,8 +267,17 @@ bool seen_before(const GraphKey &k)
     return false;
 }
 
-void remember_graph(const GraphKey &k, cudaGraph_t graph, cudaGraphExec_t exec)
+// Caches a captured graph and returns the one to launch: the cached one if
+// another call captured the same key meanwhile (the new one is dropped).
+cudaGraphExec_t remember_graph(const GraphKey &k, cudaGraph_t graph, cudaGraphExec_t exec)
 {
+    for (auto &g : g_graphs)
+        if (memcmp(&g.key, &k, sizeof(GraphKey)) == 0) {
+            cudaGraphExecDestroy(exec);
+            cudaGraphDestroy(graph);
+            g.stamp = ++g_graph_clock;
+            return g.exec;
+        }
     if (g_graphs.size() >= kMaxGraphs) {
         size_t old = 0;
         for (size_t i = 1; i < g_graphs.size(); ++i)
@@ -260,6 +287,7 @@ void remember_graph(const GraphKey &k, cudaGraph_t graph, cudaGraphExec_t exec)
         g_graphs.erase(g_graphs.begin() + old);
     }
     g_graphs.push_back(GraphEntry{k, graph, exec, ++g_graph_clock, kernel_nodes(graph)});
+    return exec;
 }
 
 void drop_graphs()
@@ -421,9 +449,9 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
     // kernels), joined to the caller's stream s by events; the whole
     // sequence is captured once into a CUDA graph per (shape, pointers) and
     // replayed on later calls.
-    std::lock_guard<std::mutex> lock(g_side_mutex);
+    std::unique_lock<std::mutex> lane_lock;
     SideResources *side = nullptr;
-    st = side_resources(3 * c.mu + 5, &side);
+    st = side_resources(3 * c.mu + 5, &side, lane_lock);
     if (st) return st;
     cudaEvent_t evIn = side->events[3 * c.mu + 3], evOut = side->events[3 * c.mu + 4];
     CK(cudaEventRecord(evIn, s));
@@ -439,19 +467,30 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
         st = enqueue_factorization(c, rank, L, E, side);
         if (st) return st;
     } else {
-        int64_t replayed = 0;  // kernels of a graph captured earlier (a capture counts its own)
-        cudaGraphExec_t exec = find_graph(key, &replayed);
-        if (!exec && !seen_before(key)) {
+        bool replayed = false, seen = false;
+        {
+            // a cached graph is launched under the cache's lock, so that no
+            // other call evicts (destroys) it in between
+            std::lock_guard<std::mutex> glock(g_graph_mutex);
+            int64_t kernels = 0;  // kernels of a graph captured earlier (a capture counts its own)
+            cudaGraphExec_t exec = find_graph(key, &kernels);
+            if (exec) {
+                CK(cudaGraphLaunch(exec, side->main));
+                g_launches.fetch_add(kernels, std::memory_order_relaxed);
+                replayed = true;
+            } else {
+                seen = seen_before(key);
+            }
+        }
+        if (replayed) {
+            // done
+        } else if (!seen) {
             // first call with this shape and these buffers: enqueue directly
             // (a capture and instantiation cost more than one run; a repeat
             // call is captured and every later one replays the graph)
             st = enqueue_factorization(c, rank, L, E, side);
             if (st) return st;
-            CK(cudaEventRecord(evOut, side->main));
-            CK(cudaStreamWaitEvent(s, evOut, 0));
-            return GF2_OK;
-        }
-        if (!exec) {
+        } else {
             if (cudaStreamBeginCapture(side->main, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GF2_ERR_CUDA;
             st = enqueue_factorization(c, rank, L, E, side);
             cudaGraph_t graph = nullptr;
@@ -461,14 +500,15 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
                 cudaGetLastError();
                 return st ? st : GF2_ERR_CUDA;
             }
+            cudaGraphExec_t exec = nullptr;
             if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
                 cudaGraphDestroy(graph);
                 return GF2_ERR_CUDA;
             }
-            remember_graph(key, graph, exec);
+            std::lock_guard<std::mutex> glock(g_graph_mutex);
+            exec = remember_graph(key, graph, exec);
+            CK(cudaGraphLaunch(exec, side->main));
         }
-        CK(cudaGraphLaunch(exec, side->main));
-        g_launches.fetch_add(replayed, std::memory_order_relaxed);
     }
     CK(cudaEventRecord(evOut, side->main));
     CK(cudaStreamWaitEvent(s, evOut, 0));
@@ -504,7 +544,7 @@ int gf2_release_workspace(void)
     if ((int)g_ws.size() > dev && g_ws[dev].ptr) {
         if (cudaDeviceSynchronize() != cudaSuccess) return GF2_ERR_CUDA;
         {
-            std::lock_guard<std::mutex> glock(g_side_mutex);
+            std::lock_guard<std::mutex> glock(g_graph_mutex);
             drop_graphs();  // graphs may point into the released workspace
         }
         cudaFree(g_ws[dev].ptr);

@@ -168,8 +168,8 @@ cudaError_t prepare_update_kernels();  // one-time kernel attributes (before any
 cudaError_t prepare_panel_kernel();
 cudaError_t launch_mmm_pass(const MmmCtx &c, int kb, int m_words, cudaStream_t s);
 cudaError_t launch_solve(const SolveCtx &c, cudaStream_t s);  // one cooperative launch
-int serve_ctas_per_sm();
-cudaError_t launch_serve_solve(const ServeItem *items, int count, int32_t *next, int grid, cudaStream_t s);
+// one CTA per item, items[0] first; max_n: the largest n among the items
+cudaError_t launch_serve_solve(const ServeItem *items, int count, int32_t *next, int64_t max_n, cudaStream_t s);
 int batch_ctas_per_sm();
 // the product on the tensor cores (k < 2^24): A8, B8 are n_pad x k_pad and
 // m_pad x k_pad bytes (dimensions rounded up to mma_pad)

@@ -24,7 +24,7 @@
 // L is used in its own column blocks (diagonal block J = rows 64J.. of
 // column block J); E likewise, the diagonal block of column block q being
 // the pivots whose columns fall in q.
-#include "gf2_internal.cuh"
+#include "solve_core.cuh"
 
 namespace gf2 {
 namespace {
@@ -63,89 +63,6 @@ __device__ bool grid_barrier(uint32_t *count, uint32_t *err, uint32_t &epoch, in
     }
     __syncthreads();
     return *s_ok != 0;
-}
-
-// 8 tables of 256 entries: entry (g, x) = XOR of vals[8g + b] over the bits b of x.
-__device__ __forceinline__ void build_tables(uint64_t *tab, const uint64_t *vals)
-{
-    for (int e = threadIdx.x; e < 8 * 256; e += kSolveThreads) {
-        const int g = e >> 8, x = e & 255;
-        uint64_t acc = 0;
-#pragma unroll
-        for (int b = 0; b < 8; ++b)
-            if ((x >> b) & 1) acc ^= vals[8 * g + b];
-        tab[e] = acc;
-    }
-}
-
-__device__ __forceinline__ uint64_t lookup(const uint64_t *tab, uint64_t w)
-{
-    uint64_t a = 0;
-#pragma unroll
-    for (int g = 0; g < 8; ++g) a ^= tab[g * 256 + (int)((w >> (8 * g)) & 255)];
-    return a;
-}
-
-// Rows of the inverse of diagonal block J of L (one warp).  Row i of L^-1
-// solves y L = e_i: from the last column down, once y_t is final, row t of L
-// (below the diagonal) leaves the right-hand side when y_t = 1.
-__device__ void lower_block_inverse(const SolveCtx &c, int J, int r, uint64_t *wrow, int lane)
-{
-    const int base = 64 * J, cnt = min(64, r - base);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int t = lane + 32 * h;
-        wrow[t] = t < cnt ? c.L[(int64_t)J * c.ldl + base + t] : 0;
-    }
-    __syncwarp();
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int i = lane + 32 * h;
-        uint64_t y = i < cnt ? (1ull << i) : 0;
-#pragma unroll 4
-        for (int t = 63; t > 0; --t)
-            if ((y >> t) & 1) y ^= wrow[t] & ((1ull << t) - 1);
-        c.linv[(int64_t)J * 64 + i] = y;
-    }
-    __syncwarp();
-}
-
-// Rows of the inverse of the diagonal block of column block q of E (one
-// warp): U[s][s'] = E[t0+s][p_{t0+s'}] for the cnt pivots t0.. whose columns
-// lie in block q (unit upper triangular).  Row i of U^-1 solves y U = e_i,
-// swept from the first column up.
-__device__ void upper_block_inverse(const SolveCtx &c, int q, int r, uint64_t *wrow, int lane)
-{
-    const int t0 = min(max(__ldcg(c.qstart + q), 0), r);
-    const int cnt = min(max(__ldcg(c.qstart + q + 1) - t0, 0), min(64, r - t0));
-    if (cnt == 0) return;
-    int pb[2];
-    uint64_t w[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int s = lane + 32 * h;
-        pb[h] = s < cnt ? ((c.pivcols[t0 + s] - 64 * q) & 63) : 0;
-        w[h] = s < cnt ? c.E[(int64_t)q * c.lde + t0 + s] : 0;
-    }
-    uint64_t u[2] = {0, 0};
-    for (int s2 = 0; s2 < cnt; ++s2) {  // compress the rows to the pivot columns
-        const int b = __shfl_sync(0xffffffffu, s2 < 32 ? pb[0] : pb[1], s2 & 31);
-        u[0] |= ((w[0] >> b) & 1) << s2;
-        u[1] |= ((w[1] >> b) & 1) << s2;
-    }
-    wrow[lane] = u[0];
-    wrow[lane + 32] = u[1];
-    __syncwarp();
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int i = lane + 32 * h;
-        uint64_t y = i < cnt ? (1ull << i) : 0;
-#pragma unroll 4
-        for (int t = 0; t < 63; ++t)
-            if ((y >> t) & 1) y ^= wrow[t] & ~((2ull << t) - 1);
-        c.uinv[(int64_t)q * 64 + i] = y;
-    }
-    __syncwarp();
 }
 
 // The barrier between the steps of one solve: grid-wide for the cooperative
@@ -226,13 +143,13 @@ __device__ void solve_body(const SolveCtx &c, int b, int G, Sync &bar, SolveShar
             if (b == 0 && tid < cnt) c.y[base + tid] = acc;
         }
         __syncthreads();
-        build_tables(tab, res);
+        solve_tables<kSolveThreads>(tab, res);
         __syncthreads();
         // every row below the block (the residual rows i >= r included)
         const uint64_t *LJ = c.L + (int64_t)J * c.ldl;
         for (int i = max(rb, min(base + 64, r)) + tid; i < re; i += kSolveThreads) {
             const uint64_t w = LJ[i];
-            if (w) c.v[i] = __ldcg(c.v + i) ^ lookup(tab, w);
+            if (w) c.v[i] = __ldcg(c.v + i) ^ solve_lookup(tab, w);
         }
         if (!bar()) return;
     }
@@ -270,12 +187,12 @@ __device__ void solve_body(const SolveCtx &c, int b, int G, Sync &bar, SolveShar
             if (b == 0 && (unsigned)col < (unsigned)m) c.X[col] = acc & ok;
         }
         __syncthreads();
-        build_tables(tab, res);
+        solve_tables<kSolveThreads>(tab, res);
         __syncthreads();
         const uint64_t *Eq = c.E + (int64_t)q * c.lde;
         for (int t = tb + tid; t < min(te, t0); t += kSolveThreads) {
             const uint64_t w = Eq[t];
-            if (w) c.y[t] = __ldcg(c.y + t) ^ lookup(tab, w);
+            if (w) c.y[t] = __ldcg(c.y + t) ^ solve_lookup(tab, w);
         }
         if (!bar()) return;
     }
@@ -286,39 +203,6 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveCtx c)
     __shared__ SolveShared sh;
     GridSync bar{c.sync, c.sync + 1, 0, &sh.s_ok};
     solve_body(c, blockIdx.x, gridDim.x, bar, sh);
-}
-
-// Many independent solves in one launch (the serving form): every CTA takes
-// the next item from a shared counter (items in decreasing size) and solves
-// it alone.  Its outputs may live in mapped host memory: once they are
-// written and fenced at system scope, the item's done word is set, so the
-// host can hand each result back without waiting for the whole launch.
-__global__ void __launch_bounds__(kSolveThreads) k_serve_solve(const ServeItem *items, int count, int32_t *next)
-{
-    __shared__ SolveShared sh;
-    __shared__ int s_item;
-    const int tid = threadIdx.x;
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(next, 1);
-        __syncthreads();
-        const int k = s_item;
-        __syncthreads();
-        if (k >= count) return;
-        const ServeItem &it = items[k];
-        if (it.nrhs > 0) {
-            if (tid == 0) *it.c.bad = 0;
-            __syncthreads();
-            CtaSync bar;
-            solve_body(it.c, 0, 1, bar, sh);
-        }
-        if (tid == 0) {
-            const int64_t kmax = min(it.c.n, it.c.m);
-            *it.rank_out = min(max(*it.c.rank, (int64_t)0), kmax);
-        }
-        __threadfence_system();
-        __syncthreads();
-        if (tid == 0) asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(it.done), "r"(1u) : "memory");
-    }
 }
 
 }  // namespace
@@ -340,20 +224,6 @@ cudaError_t launch_solve(const SolveCtx &c, cudaStream_t s)
     void *args[] = {&arg};
     return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_solve), dim3(grid), dim3(kSolveThreads), args,
                                        0, s);
-}
-
-int serve_ctas_per_sm()
-{
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve_solve, kSolveThreads, 0) != cudaSuccess) return 1;
-    return per_sm > 0 ? per_sm : 1;
-}
-
-cudaError_t launch_serve_solve(const ServeItem *items, int count, int32_t *next, int grid, cudaStream_t s)
-{
-    if (count <= 0) return cudaSuccess;
-    k_serve_solve<<<grid, kSolveThreads, 0, s>>>(items, count, next);
-    return cudaGetLastError();
 }
 
 }  // namespace gf2

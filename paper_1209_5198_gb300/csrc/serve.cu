@@ -15,9 +15,11 @@
 //      A in the device arena (evicting the least recently used factors that
 //      no request holds) -- when that does not fit, later misses wait too,
 //      so misses are admitted in order as memory frees up;
-//   4. new misses are decomposed on the decomposition stream: several small
-//      ones (up to 512 x 512) together in one batched launch, the others one
-//      by one by the plain decomposition;
+//   4. new misses are decomposed on four decomposition lanes in turn (a
+//      stream and a workspace each; the library runs each plain
+//      decomposition on its own set of streams, so lanes overlap on the
+//      GPU): several small misses (up to 512 x 512) together in one batched
+//      launch, every other one by the plain decomposition;
 //   5. every admitted request whose factors are ready joins one solve
 //      launch on a free slot (four slots: up to four launches in flight),
 //      one CTA per request, largest first.
@@ -48,6 +50,7 @@ using Clock = std::chrono::steady_clock;
 
 constexpr size_t kAl = 256;
 constexpr int kSlots = 4;
+constexpr int kDecLanes = 4;
 // misses up to this size go to one batched decomposition (one CTA per
 // matrix) when at least kBatchedDecompMin of them are new in the same turn;
 // larger ones take the plain decomposition, which uses the whole GPU
@@ -199,13 +202,15 @@ struct gf2_server {
     unsigned flags = 0;
     int64_t max_n = 0, max_m = 0;
     int max_batch = 1;
-    int grid_cap = 1;
     Clock::time_point t0;
     Arena arena;        // factors, staging of A, batched-decomposition workspaces
     Arena solve_arena;  // right-hand sides and scratch of the solve launches in flight
-    void *dec_ws = nullptr;
+    // decomposition lanes: a stream and a plain-decomposition workspace each,
+    // so that up to kDecLanes misses are decomposed side by side
+    void *dec_ws[kDecLanes] = {};
     size_t dec_ws_bytes = 0;
-    cudaStream_t dec_stream = nullptr;
+    cudaStream_t dec_stream[kDecLanes] = {};
+    unsigned next_lane = 0;
     Slot slots[kSlots];
     std::unordered_map<uint64_t, Entry *> cache;
     uint64_t lru_clock = 0;
@@ -330,27 +335,27 @@ Entry *new_entry(gf2_server *S, Req *q, bool *never)
     return e;
 }
 
-int copy_a_in(gf2_server *S, Entry *e)
+int copy_a_in(gf2_server *S, Entry *e, int lane)
 {
     const int64_t mu = wordsof(e->m);
     char *dst = S->arena.at(e->a_off);
     cudaError_t ce;
     if (e->lda == e->n)
-        ce = cudaMemcpyAsync(dst, e->A_host, (size_t)mu * e->n * 8, cudaMemcpyHostToDevice, S->dec_stream);
+        ce = cudaMemcpyAsync(dst, e->A_host, (size_t)mu * e->n * 8, cudaMemcpyHostToDevice, S->dec_stream[lane]);
     else
         ce = cudaMemcpy2DAsync(dst, (size_t)e->n * 8, e->A_host, (size_t)e->lda * 8, (size_t)e->n * 8, (size_t)mu,
-                               cudaMemcpyHostToDevice, S->dec_stream);
+                               cudaMemcpyHostToDevice, S->dec_stream[lane]);
     return ce == cudaSuccess ? GF2_OK : GF2_ERR_CUDA;
 }
 
-int plain_decompose(gf2_server *S, Entry *e)
+int plain_decompose(gf2_server *S, Entry *e, int lane)
 {
     const int64_t k = e->kmax;
     gf2_mat A{reinterpret_cast<uint64_t *>(S->arena.at(e->a_off)), e->n, e->m, e->n};
     gf2_mat L{e->L, e->n, k, e->n};
     gf2_mat E{e->E, k, e->m, k > 0 ? k : 1};
-    return gf2_decompose(&A, e->perm, e->piv, e->rank, &L, &E, GF2_NOCHECK, S->dec_ws, S->dec_ws_bytes,
-                         S->dec_stream);
+    return gf2_decompose(&A, e->perm, e->piv, e->rank, &L, &E, GF2_NOCHECK, S->dec_ws[lane], S->dec_ws_bytes,
+                         S->dec_stream[lane]);
 }
 
 void fail_entry(Entry *e, int status)
@@ -486,21 +491,27 @@ bool admit(gf2_server *S)
 }
 
 // ---- step 4: decompositions of the new misses
+// Records the end of a decomposition job on its lane and queues the job.
+void queue_job(gf2_server *S, DecompJob &&job, int lane)
+{
+    if (cudaEventCreateWithFlags(&job.ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(job.ev, S->dec_stream[lane]) != cudaSuccess) {
+        cudaGetLastError();
+        S->sticky = GF2_ERR_CUDA;
+        cudaStreamSynchronize(S->dec_stream[lane]);
+        if (!job.ev) cudaEventCreateWithFlags(&job.ev, cudaEventDisableTiming);
+    }
+    S->jobs.push_back(std::move(job));
+}
+
 bool launch_builds(gf2_server *S)
 {
     if (S->to_build.empty()) return false;
     std::vector<Entry *> small, large;
-    for (Entry *e : S->to_build) {
-        if (copy_a_in(S, e) != GF2_OK) {
-            S->sticky = GF2_ERR_CUDA;
-            fail_entry(e, GF2_ERR_CUDA);
-            continue;
-        }
-        (e->n <= kBatchedDecompMax && e->m <= kBatchedDecompMax ? small : large).push_back(e);
-    }
+    for (Entry *e : S->to_build) (e->n <= kBatchedDecompMax && e->m <= kBatchedDecompMax ? small : large).push_back(e);
     S->to_build.clear();
-    DecompJob job;
     if (small.size() >= kBatchedDecompMin) {
+        // one batched launch for the small misses of this turn
         std::vector<BatchItem> items(small.size());
         for (size_t i = 0; i < small.size(); ++i) {
             Entry *e = small[i];
@@ -511,8 +522,14 @@ bool launch_builds(gf2_server *S)
         const size_t wb = decompose_batched_items_bytes((int)items.size(), items.data(), true);
         size_t off = 0;
         if (wb && alloc_evicting(S, wb, &off)) {
-            const int st = decompose_batched_items((int)items.size(), items.data(), true, GF2_NOCHECK,
-                                                   S->arena.at(off), wb, S->dec_stream);
+            const int lane = (int)(S->next_lane++ % kDecLanes);
+            int st = GF2_OK;
+            for (Entry *e : small)
+                if (st == GF2_OK) st = copy_a_in(S, e, lane);
+            if (st == GF2_OK)
+                st = decompose_batched_items((int)items.size(), items.data(), true, GF2_NOCHECK, S->arena.at(off), wb,
+                                             S->dec_stream[lane]);
+            DecompJob job;
             job.has_ws = true;
             job.ws_off = off;
             job.ws_bytes = wb;
@@ -520,6 +537,7 @@ bool launch_builds(gf2_server *S)
                 if (st != GF2_OK) fail_entry(e, st);
                 job.entries.push_back(e);
             }
+            queue_job(S, std::move(job), lane);
             std::lock_guard<std::mutex> lock(S->mu);
             ++S->stats.batched_decompositions;
             small.clear();
@@ -527,21 +545,18 @@ bool launch_builds(gf2_server *S)
         // no room for the batched workspace: the plain path below, one by one
     }
     for (Entry *e : small) large.push_back(e);
+    // the larger misses, one plain decomposition each, lanes in turn
     for (Entry *e : large) {
-        const int st = plain_decompose(S, e);
+        const int lane = (int)(S->next_lane++ % kDecLanes);
+        int st = copy_a_in(S, e, lane);
+        if (st == GF2_OK) st = plain_decompose(S, e, lane);
         if (st != GF2_OK) fail_entry(e, st);
+        DecompJob job;
         job.entries.push_back(e);
+        queue_job(S, std::move(job), lane);
         std::lock_guard<std::mutex> lock(S->mu);
         ++S->stats.plain_decompositions;
     }
-    if (job.entries.empty()) return true;
-    if (cudaEventCreateWithFlags(&job.ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventRecord(job.ev, S->dec_stream) != cudaSuccess) {
-        S->sticky = GF2_ERR_CUDA;
-        cudaStreamSynchronize(S->dec_stream);
-        if (!job.ev) cudaEventCreateWithFlags(&job.ev, cudaEventDisableTiming);
-    }
-    S->jobs.push_back(std::move(job));
     return true;
 }
 
@@ -663,11 +678,12 @@ bool launch_solves(gf2_server *S)
             }
             // (the host wrote the done words before the launch is enqueued)
             std::atomic_thread_fence(std::memory_order_seq_cst);
-            const int grid = (int)std::min<size_t>(cnt, (size_t)S->grid_cap);
+            int64_t max_n = 0;
+            for (Req *q : take) max_n = std::max(max_n, q->r.n);
             cudaError_t ce = cudaMemcpyAsync(dev, hin, in_bytes, cudaMemcpyHostToDevice, sl->stream);
             if (ce == cudaSuccess)
                 ce = launch_serve_solve(reinterpret_cast<const ServeItem *>(dev + kAl), (int)cnt,
-                                        reinterpret_cast<int32_t *>(dev), grid, sl->stream);
+                                        reinterpret_cast<int32_t *>(dev), max_n, sl->stream);
             if (ce == cudaSuccess) ce = cudaEventRecord(sl->ev, sl->stream);
             if (ce != cudaSuccess) {
                 cudaGetLastError();
@@ -720,9 +736,9 @@ bool serial_step(gf2_server *S)
             complete(S, q, GF2_ERR_NOMEM, 0, 0);
             return true;
         }
-        int st = copy_a_in(S, e);
-        if (st == GF2_OK) st = plain_decompose(S, e);
-        if (st == GF2_OK && cudaStreamSynchronize(S->dec_stream) != cudaSuccess) st = GF2_ERR_CUDA;
+        int st = copy_a_in(S, e, 0);
+        if (st == GF2_OK) st = plain_decompose(S, e, 0);
+        if (st == GF2_OK && cudaStreamSynchronize(S->dec_stream[0]) != cudaSuccess) st = GF2_ERR_CUDA;
         S->arena.release(e->a_off, e->a_bytes);
         e->a_bytes = 0;
         if (st != GF2_OK) {
@@ -761,21 +777,22 @@ bool serial_step(gf2_server *S)
         uint64_t *Xd = reinterpret_cast<uint64_t *>(p + up(wb) + up((size_t)n * 8));
         uint64_t *cd = reinterpret_cast<uint64_t *>(p + up(wb) + up((size_t)n * 8) + up((size_t)m * 8));
         gf2_mat L{e->L, n, k, n}, E{e->E, k, m, k > 0 ? k : 1}, B{Bd, n, q->r.nrhs, n}, X{Xd, m, q->r.nrhs, m};
-        if (cudaMemcpyAsync(Bd, q->r.B, (size_t)n * 8, cudaMemcpyHostToDevice, S->dec_stream) != cudaSuccess)
+        cudaStream_t ds = S->dec_stream[0];
+        if (cudaMemcpyAsync(Bd, q->r.B, (size_t)n * 8, cudaMemcpyHostToDevice, ds) != cudaSuccess)
             st = GF2_ERR_CUDA;
         if (st == GF2_OK)
-            st = gf2_solve(&L, &E, e->perm, e->piv, e->rank, &B, &X, cd, GF2_NOCHECK, p, wb, S->dec_stream);
+            st = gf2_solve(&L, &E, e->perm, e->piv, e->rank, &B, &X, cd, GF2_NOCHECK, p, wb, ds);
         if (st == GF2_OK &&
-            (cudaMemcpyAsync(q->r.X, Xd, (size_t)m * 8, cudaMemcpyDeviceToHost, S->dec_stream) != cudaSuccess ||
-             cudaMemcpyAsync(&cons, cd, 8, cudaMemcpyDeviceToHost, S->dec_stream) != cudaSuccess))
+            (cudaMemcpyAsync(q->r.X, Xd, (size_t)m * 8, cudaMemcpyDeviceToHost, ds) != cudaSuccess ||
+             cudaMemcpyAsync(&cons, cd, 8, cudaMemcpyDeviceToHost, ds) != cudaSuccess))
             st = GF2_ERR_CUDA;
         if (st == GF2_OK &&
-            (cudaMemcpyAsync(&rank, e->rank, 8, cudaMemcpyDeviceToHost, S->dec_stream) != cudaSuccess ||
-             cudaStreamSynchronize(S->dec_stream) != cudaSuccess))
+            (cudaMemcpyAsync(&rank, e->rank, 8, cudaMemcpyDeviceToHost, ds) != cudaSuccess ||
+             cudaStreamSynchronize(ds) != cudaSuccess))
             st = GF2_ERR_CUDA;
         S->arena.release(off, need);
-    } else if (cudaMemcpyAsync(&rank, e->rank, 8, cudaMemcpyDeviceToHost, S->dec_stream) != cudaSuccess ||
-               cudaStreamSynchronize(S->dec_stream) != cudaSuccess) {
+    } else if (cudaMemcpyAsync(&rank, e->rank, 8, cudaMemcpyDeviceToHost, S->dec_stream[0]) != cudaSuccess ||
+               cudaStreamSynchronize(S->dec_stream[0]) != cudaSuccess) {
         st = GF2_ERR_CUDA;
     }
     if (st == GF2_ERR_CUDA) S->sticky = st;
@@ -855,7 +872,8 @@ void engine_main(gf2_server *S)
     // every request is complete; wait for the GPU before the memory goes
     for (Slot &s : S->slots)
         if (s.stream) cudaStreamSynchronize(s.stream);
-    if (S->dec_stream) cudaStreamSynchronize(S->dec_stream);
+    for (cudaStream_t d : S->dec_stream)
+        if (d) cudaStreamSynchronize(d);
 }
 
 // host-side checks of one request; GF2_OK or its error
@@ -889,8 +907,10 @@ void destroy_resources(gf2_server *S)
         if (s.in_host) cudaFreeHost(s.in_host);
         if (s.out_host) cudaFreeHost(s.out_host);
     }
-    if (S->dec_stream) cudaStreamDestroy(S->dec_stream);
-    if (S->dec_ws) cudaFree(S->dec_ws);
+    for (int l = 0; l < kDecLanes; ++l) {
+        if (S->dec_stream[l]) cudaStreamDestroy(S->dec_stream[l]);
+        if (S->dec_ws[l]) cudaFree(S->dec_ws[l]);
+    }
     for (auto &kv : S->cache) delete kv.second;
     S->cache.clear();
 }
@@ -919,7 +939,6 @@ int gf2_server_create(int64_t device_bytes, int64_t max_n, int64_t max_m, int ma
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S->device) != cudaSuccess ||
         cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess)
         st = GF2_ERR_CUDA;
-    S->grid_cap = sms * serve_ctas_per_sm();
     // the solve launches get their own arena, so that resident factors can
     // never crowd out the solves that release them
     const size_t one = solve_scratch_bytes(max_n, max_m) + up((size_t)max_n * 8) + 2 * kAl + up(sizeof(ServeItem));
@@ -930,14 +949,17 @@ int gf2_server_create(int64_t device_bytes, int64_t max_n, int64_t max_m, int ma
     if (st == GF2_OK) st = S->arena.init((size_t)device_bytes - solve_bytes);
     if (st == GF2_OK) {
         S->dec_ws_bytes = gf2_decompose_workspace_bytes(max_n, max_m, 1);
-        if (cudaMalloc(&S->dec_ws, S->dec_ws_bytes) != cudaSuccess) {
-            cudaGetLastError();
-            S->dec_ws = nullptr;
-            st = GF2_ERR_NOMEM;
+        const int lanes = (flags & GF2_SERVE_SERIAL) ? 1 : kDecLanes;
+        for (int l = 0; l < lanes && st == GF2_OK; ++l) {
+            if (cudaMalloc(&S->dec_ws[l], S->dec_ws_bytes) != cudaSuccess) {
+                cudaGetLastError();
+                S->dec_ws[l] = nullptr;
+                st = GF2_ERR_NOMEM;
+            } else if (cudaStreamCreateWithFlags(&S->dec_stream[l], cudaStreamNonBlocking) != cudaSuccess) {
+                st = GF2_ERR_CUDA;
+            }
         }
     }
-    if (st == GF2_OK && cudaStreamCreateWithFlags(&S->dec_stream, cudaStreamNonBlocking) != cudaSuccess)
-        st = GF2_ERR_CUDA;
     for (Slot &s : S->slots) {
         if (st != GF2_OK) break;
         if (cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, hi) != cudaSuccess ||
