@@ -94,7 +94,7 @@ def rest_traffic(n: int, m: int):
     import hashlib
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "k_rest_32768_traffic.json")))
-        src = open(os.path.join(ROOT, t["source"]), "rb").read()
+        src = b"".join(open(os.path.join(ROOT, f), "rb").read() for f in t["sources"])
     except Exception:
         return None
     if t.get("n") != n or t.get("m") != m or hashlib.sha256(src).hexdigest() != t.get("source_sha256"):
