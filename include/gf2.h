@@ -68,23 +68,47 @@ int gf2_version(void);
 int gf2_release_workspace(void);
 
 /* ------------------------------------------------------------------------
- * Product over F2 (Section 1 and Section 6 of the paper).  Two backends:
- * the Four Russians method M4RM of Section 6 with tables in shared memory,
- * and the tensor cores (every entry an e4m3 0 or 1, exact integer sums in
- * fp32, entry = lowest bit), chosen by the flags GF2_MMM_TABLES /
- * GF2_MMM_TENSOR; with neither, M4RM (the faster of the two on the GB300).
- * GF2_MMM_TENSOR with k >= 2^24 also runs M4RM.  Both give the same bits.
+ * Product over F2 (Section 1 and Section 6 of the paper).
  *   C = A*B        (accumulate == 0)
  *   C = C xor A*B  (accumulate != 0)
  * A is n x k, B is k x m, C is n x m (all column blocks, device memory,
  * owned by the caller).  C must not alias A or B.  Exact: every result bit
- * is the parity of the AND of a row of A and a column of B.
- * Errors: GF2_ERR_ARG (NULL), GF2_ERR_SHAPE (A.cols != B.rows, C not n x m,
- * ld < rows), GF2_ERR_PADDING, GF2_ERR_NOMEM, GF2_ERR_CUDA.
+ * is the parity of the AND of a row of A and a column of B, whatever the
+ * backend:
+ *   default / no backend flag: the Four Russians method (M4RM, Section 6),
+ *       one kernel on the column blocks (tables of 8 rows of B in shared
+ *       memory, C kept in registers over the inner dimension), under
+ *       Strassen-Winograd recursion (7 products, 15 additions per level;
+ *       the recursion of Section 5) while n, k and m are all at least the
+ *       Strassen cutoff, n is even, k a whole even number of words and m an
+ *       even number of words.  The cutoff is off until gf2_mmm_autotune or
+ *       gf2_mmm_set_strassen_cutoff sets it.
+ *   GF2_MMM_TABLES: M4RM alone (no recursion).
+ *   GF2_MMM_TENSOR: the tensor cores (every entry an e4m3 0 or 1, exact
+ *       integer sums in fp32, entry = lowest bit; k < 2^24, else M4RM).
+ * The workspace depends on the backend and the recursion depth: size it
+ * with the same flags (and after the same cutoff setting).
+ * Errors: GF2_ERR_ARG (NULL, both backend flags), GF2_ERR_SHAPE (A.cols !=
+ * B.rows, C not n x m, ld < rows), GF2_ERR_PADDING, GF2_ERR_NOMEM,
+ * GF2_ERR_UNSUPPORTED (a dimension >= 2^31), GF2_ERR_CUDA.
  */
 size_t gf2_mmm_workspace_bytes(int64_t n, int64_t k, int64_t m, unsigned flags);
 int gf2_mmm(const gf2_mat *A, const gf2_mat *B, gf2_mat *C, int accumulate, unsigned flags,
             void *workspace, size_t ws_bytes, void *stream);
+
+/* The Strassen cutoff of the default product (a process-wide setting).
+ * gf2_mmm_autotune times, on the current device, square products of size d
+ * = 2048, 4096, ... up to max_dim (at most 32768) with M4RM alone and with
+ * one Strassen-Winograd level, and sets the cutoff to the smallest d from
+ * which one level is faster at d and at every larger size tried (off when
+ * it never is); *cutoff receives it.  It allocates about 3 d^2/8 bytes plus
+ * one level's temporaries, synchronises the stream and leaves the device
+ * memory as it found it.  gf2_mmm_set_strassen_cutoff sets it directly
+ * (>= 128; 2^62 turns the recursion off).  Errors: GF2_ERR_ARG,
+ * GF2_ERR_NOMEM, GF2_ERR_CUDA. */
+int gf2_mmm_autotune(int64_t max_dim, int64_t *cutoff, void *stream);
+int gf2_mmm_set_strassen_cutoff(int64_t cutoff);
+int64_t gf2_mmm_strassen_cutoff(void);
 
 /* ------------------------------------------------------------------------
  * Decomposition P*A = L*E (Section 4, Lemma 4.1 of the paper: block

@@ -72,6 +72,11 @@ def load() -> ctypes.CDLL:
     lib.gf2_mmm_workspace_bytes.argtypes = [I64, I64, I64, ctypes.c_uint]
     lib.gf2_mmm.restype = ctypes.c_int
     lib.gf2_mmm.argtypes = [M, M, M, ctypes.c_int, ctypes.c_uint, P, S, P]
+    lib.gf2_mmm_autotune.restype = ctypes.c_int
+    lib.gf2_mmm_autotune.argtypes = [I64, ctypes.POINTER(I64), P]
+    lib.gf2_mmm_set_strassen_cutoff.restype = ctypes.c_int
+    lib.gf2_mmm_set_strassen_cutoff.argtypes = [I64]
+    lib.gf2_mmm_strassen_cutoff.restype = I64
     lib.gf2_decompose_workspace_bytes.restype = S
     lib.gf2_decompose_workspace_bytes.argtypes = [I64, I64, ctypes.c_int]
     lib.gf2_decompose.restype = ctypes.c_int
@@ -315,10 +320,29 @@ def solve(factors: dict, B: Mat, m: int, stream=None) -> dict:
     return dict(X=X, consistent=int(ok.cpu().numpy().view(np.uint64)[0]))
 
 
-def mmm(A: Mat, B: Mat, stream=None) -> Mat:
+def mmm(A: Mat, B: Mat, flags: int = 0, stream=None) -> Mat:
     C = Mat.empty(A.rows, B.cols, A.t.device)
-    gf2_mmm(A, B, C, stream=stream)
+    gf2_mmm(A, B, C, flags=flags, stream=stream)
     return C
+
+
+STRASSEN_OFF = 1 << 62
+
+
+def mmm_autotune(max_dim: int = 32768, stream=None) -> int:
+    """Times M4RM against one Strassen-Winograd level on this device and sets
+    the product's Strassen cutoff (returned; STRASSEN_OFF when never faster)."""
+    out = ctypes.c_int64(0)
+    _check(load().gf2_mmm_autotune(int(max_dim), ctypes.byref(out), _stream(stream)), "gf2_mmm_autotune")
+    return int(out.value)
+
+
+def set_strassen_cutoff(cutoff: int) -> None:
+    _check(load().gf2_mmm_set_strassen_cutoff(int(cutoff)), "gf2_mmm_set_strassen_cutoff")
+
+
+def strassen_cutoff() -> int:
+    return int(load().gf2_mmm_strassen_cutoff())
 
 
 # ------------------------------------------------------------- diagnostics

@@ -874,11 +874,111 @@ void add_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed
 extern "C" {
 
 // ------------------------------------------------------------ product
-size_t mmm_tables_bytes(int64_t n, int64_t k, int64_t m)
+}  // extern "C"
+
+namespace {
+
+// Strassen-Winograd over the Four Russians product (the recursion of the
+// paper's Section 5 for C = A B): a level applies while n, k and m are at
+// least the cutoff, n is even, k is a whole even number of words and m an
+// even number of words.
+std::atomic<int64_t> g_strassen_cutoff{int64_t(1) << 62};  // off until tuned or set
+
+struct CBView {
+    uint64_t *w;
+    int64_t ld;
+};
+
+int strassen_levels(int64_t n, int64_t k, int64_t mw, int64_t cutoff)
 {
-    const int64_t kw = words_of(k), mw = words_of(m);
-    return align_up((size_t)n * (kw > 0 ? kw : 1) * 8) + align_up((size_t)k * (mw > 0 ? mw : 1) * 8) +
-           align_up((size_t)n * round8(mw > 0 ? mw : 1) * 8) + kAlign;
+    int levels = 0;
+    while (levels < 8) {
+        const int64_t kw = words_of(k), m = 64 * mw;
+        if (n < cutoff || k < cutoff || m < cutoff) break;
+        if ((n & 1) || (kw & 1) || (mw & 1) || k != 64 * kw) break;
+        n /= 2;
+        k /= 2;
+        mw /= 2;
+        ++levels;
+    }
+    return levels;
+}
+
+// temporaries of the levels: S1..S4 (n/2 x k/2), T1..T4 (k/2 x m/2), X (n/2 x m/2)
+size_t strassen_level_words(int64_t n, int64_t k, int64_t mw)
+{
+    const int64_t n2 = n / 2, kw2 = words_of(k) / 2, k2 = 64 * kw2, mw2 = mw / 2;
+    return (size_t)(4 * n2 * kw2 + 4 * k2 * mw2 + n2 * mw2);
+}
+
+size_t strassen_bytes(int64_t n, int64_t k, int64_t mw, int levels)
+{
+    size_t words = 0;
+    for (int l = 0; l < levels; ++l) {
+        words += strassen_level_words(n, k, mw);
+        n /= 2;
+        k /= 2;
+        mw /= 2;
+    }
+    return words * 8;
+}
+
+int mmm_rec(CBView C, CBView A, CBView B, int64_t n, int64_t k, int64_t mw, bool acc, int levels, uint64_t *tmp,
+            cudaStream_t s)
+{
+    if (levels == 0) {
+        MmmCtx c{A.w, A.ld, B.w, B.ld, C.w, C.ld, (int32_t)n, (int32_t)k, (int32_t)mw, acc ? kMmmXor : kMmmStore};
+        LAUNCH(GF2_KCLASS_UPDATE, launch_mmm(c, s));
+        return GF2_OK;
+    }
+    const int64_t n2 = n / 2, kw2 = words_of(k) / 2, k2 = 64 * kw2, mw2 = mw / 2;
+    if (!acc) CK(cudaMemset2DAsync(C.w, (size_t)C.ld * 8, 0, (size_t)n * 8, (size_t)mw, s));
+    const CBView A11{A.w, A.ld}, A12{A.w + kw2 * A.ld, A.ld}, A21{A.w + n2, A.ld}, A22{A.w + kw2 * A.ld + n2, A.ld};
+    const CBView B11{B.w, B.ld}, B12{B.w + mw2 * B.ld, B.ld}, B21{B.w + k2, B.ld}, B22{B.w + mw2 * B.ld + k2, B.ld};
+    const CBView C11{C.w, C.ld}, C12{C.w + mw2 * C.ld, C.ld}, C21{C.w + n2, C.ld}, C22{C.w + mw2 * C.ld + n2, C.ld};
+    uint64_t *p = tmp;
+    auto take = [&](int64_t ld, int64_t words) {
+        CBView v{p, ld};
+        p += ld * words;
+        return v;
+    };
+    const CBView S1 = take(n2, kw2), S2 = take(n2, kw2), S3 = take(n2, kw2), S4 = take(n2, kw2);
+    const CBView T1 = take(k2, mw2), T2 = take(k2, mw2), T3 = take(k2, mw2), T4 = take(k2, mw2);
+    const CBView X = take(n2, mw2);
+    uint64_t *next = p;  // the sub-products' own temporaries
+    auto add = [&](CBView D, CBView P, CBView Q, int64_t rows, int64_t words) {
+        return launch_xor(D.w, D.ld, P.w, P.ld, Q.w, Q.ld, rows, words, s);
+    };
+    LAUNCH(GF2_KCLASS_LAYOUT, add(S1, A21, A22, n2, kw2));
+    LAUNCH(GF2_KCLASS_LAYOUT, add(S2, S1, A11, n2, kw2));
+    LAUNCH(GF2_KCLASS_LAYOUT, add(S3, A11, A21, n2, kw2));
+    LAUNCH(GF2_KCLASS_LAYOUT, add(S4, A12, S2, n2, kw2));
+    LAUNCH(GF2_KCLASS_LAYOUT, add(T1, B12, B11, k2, mw2));
+    LAUNCH(GF2_KCLASS_LAYOUT, add(T2, B22, T1, k2, mw2));
+    LAUNCH(GF2_KCLASS_LAYOUT, add(T3, B22, B12, k2, mw2));
+    LAUNCH(GF2_KCLASS_LAYOUT, add(T4, T2, B21, k2, mw2));
+    int st;
+    // C11 = P1 + P2
+    if ((st = mmm_rec(X, A11, B11, n2, k2, mw2, false, levels - 1, next, s))) return st;  // X = P1
+    LAUNCH(GF2_KCLASS_LAYOUT, add(C11, C11, X, n2, mw2));
+    if ((st = mmm_rec(C11, A12, B21, n2, k2, mw2, true, levels - 1, next, s))) return st;  // + P2
+    // U2 = P1 + P6 into C12, C21, C22
+    if ((st = mmm_rec(X, S2, T2, n2, k2, mw2, true, levels - 1, next, s))) return st;
+    LAUNCH(GF2_KCLASS_LAYOUT, add(C12, C12, X, n2, mw2));
+    LAUNCH(GF2_KCLASS_LAYOUT, add(C21, C21, X, n2, mw2));
+    LAUNCH(GF2_KCLASS_LAYOUT, add(C22, C22, X, n2, mw2));
+    // P7 into C21, C22
+    if ((st = mmm_rec(X, S3, T3, n2, k2, mw2, false, levels - 1, next, s))) return st;
+    LAUNCH(GF2_KCLASS_LAYOUT, add(C21, C21, X, n2, mw2));
+    LAUNCH(GF2_KCLASS_LAYOUT, add(C22, C22, X, n2, mw2));
+    // P5 into C12, C22
+    if ((st = mmm_rec(X, S1, T1, n2, k2, mw2, false, levels - 1, next, s))) return st;
+    LAUNCH(GF2_KCLASS_LAYOUT, add(C12, C12, X, n2, mw2));
+    LAUNCH(GF2_KCLASS_LAYOUT, add(C22, C22, X, n2, mw2));
+    // P3 into C12, P4 into C21
+    if ((st = mmm_rec(C12, S4, B22, n2, k2, mw2, true, levels - 1, next, s))) return st;
+    if ((st = mmm_rec(C21, A22, T4, n2, k2, mw2, true, levels - 1, next, s))) return st;
+    return GF2_OK;
 }
 
 size_t mmm_tensor_bytes(int64_t n, int64_t k, int64_t m)
@@ -888,17 +988,27 @@ size_t mmm_tensor_bytes(int64_t n, int64_t k, int64_t m)
 }
 
 // the tensor-core product only when the flags ask for it: measured on the
-// GB300 the Four Russians passes are as fast at n = 4096 and 2.4x / 3x
-// faster at n = 16384 / 32768
+// GB300 the Four Russians product is faster at every size
 bool mmm_use_tensor(int64_t k, unsigned flags)
 {
     return (flags & GF2_MMM_TENSOR) && !(flags & GF2_MMM_TABLES) && k < (1ll << 24);
 }
 
+int mmm_levels(int64_t n, int64_t k, int64_t m, unsigned flags)
+{
+    if (flags & (GF2_MMM_TABLES | GF2_MMM_TENSOR)) return 0;
+    return strassen_levels(n, k, words_of(m), g_strassen_cutoff.load());
+}
+
+}  // namespace
+
+extern "C" {
+
 size_t gf2_mmm_workspace_bytes(int64_t n, int64_t k, int64_t m, unsigned flags)
 {
     if (n < 0 || k < 0 || m < 0) return 0;
-    return mmm_use_tensor(k, flags) ? mmm_tensor_bytes(n, k, m) : mmm_tables_bytes(n, k, m);
+    if (mmm_use_tensor(k, flags)) return mmm_tensor_bytes(n, k, m);
+    return align_up(strassen_bytes(n, k, words_of(m), mmm_levels(n, k, m, flags))) + kAlign;
 }
 
 int gf2_mmm(const gf2_mat *A, const gf2_mat *B, gf2_mat *C, int accumulate, unsigned flags, void *workspace,
@@ -912,49 +1022,123 @@ int gf2_mmm(const gf2_mat *A, const gf2_mat *B, gf2_mat *C, int accumulate, unsi
     const int64_t n = A->rows, k = A->cols, m = B->cols;
     if (n >= (1ll << 31) || k >= (1ll << 31) || m >= (1ll << 31)) return GF2_ERR_UNSUPPORTED;
     if (n == 0 || m == 0) return GF2_OK;
-    const int64_t kw = words_of(k), mw = words_of(m), ldc = round8(mw);
+    const int64_t kw = words_of(k), mw = words_of(m);
     if (k == 0) {
-        if (!accumulate) CK(cudaMemsetAsync(C->w, 0, (size_t)C->ld * mw * 8, s));
+        if (!accumulate) CK(cudaMemset2DAsync(C->w, (size_t)C->ld * 8, 0, (size_t)n * 8, (size_t)mw, s));
         return GF2_OK;
     }
     void *ws = nullptr;
     int st = get_workspace(workspace, ws_bytes, gf2_mmm_workspace_bytes(n, k, m, flags), &ws);
     if (st) return st;
     char *p = static_cast<char *>(ws);
-    if (mmm_use_tensor(k, flags)) {
+    const bool tensor = mmm_use_tensor(k, flags);
+    const int levels = tensor ? 0 : mmm_levels(n, k, m, flags);
+    uint32_t *flag = reinterpret_cast<uint32_t *>(
+        p + (tensor ? mmm_tensor_bytes(n, k, m) - kAlign : align_up(strassen_bytes(n, k, mw, levels))));
+    if (!(flags & GF2_NOCHECK)) {
+        CK(cudaMemsetAsync(flag, 0, sizeof(uint32_t), s));
+        LAUNCH(GF2_KCLASS_LAYOUT, launch_check_last_block(A->w + (kw - 1) * A->ld, (int)n, last_word_mask(k), flag, s));
+        LAUNCH(GF2_KCLASS_LAYOUT, launch_check_last_block(B->w + (mw - 1) * B->ld, (int)k, last_word_mask(m), flag, s));
+        if (accumulate)
+            LAUNCH(GF2_KCLASS_LAYOUT, launch_check_last_block(C->w + (mw - 1) * C->ld, (int)n, last_word_mask(m), flag, s));
+        st = check_flag(flag, s);
+        if (st) return st;
+    }
+    if (tensor) {
         const size_t kp = (size_t)mma_pad(k);
         uint8_t *A8 = reinterpret_cast<uint8_t *>(p);
         uint8_t *B8 = A8 + align_up((size_t)mma_pad(n) * kp);
-        uint32_t *flag = reinterpret_cast<uint32_t *>(B8 + align_up((size_t)mma_pad(m) * kp));
-        if (!(flags & GF2_NOCHECK)) {
-            CK(cudaMemsetAsync(flag, 0, sizeof(uint32_t), s));
-            LAUNCH(GF2_KCLASS_LAYOUT, launch_check_last_block(A->w + (kw - 1) * A->ld, (int)n, last_word_mask(k), flag, s));
-            LAUNCH(GF2_KCLASS_LAYOUT, launch_check_last_block(B->w + (mw - 1) * B->ld, (int)k, last_word_mask(m), flag, s));
-            if (accumulate)
-                LAUNCH(GF2_KCLASS_LAYOUT, launch_check_last_block(C->w + (mw - 1) * C->ld, (int)n, last_word_mask(m), flag, s));
-            st = check_flag(flag, s);
-            if (st) return st;
-        }
         LAUNCH(GF2_KCLASS_UPDATE, launch_mma_product(A->w, A->ld, B->w, B->ld, C->w, C->ld, (int)n, (int)k, (int)m,
                                                      accumulate, A8, B8, s));
         return GF2_OK;
     }
-    uint64_t *Ar = reinterpret_cast<uint64_t *>(p); p += align_up((size_t)n * kw * 8);
-    uint64_t *Br = reinterpret_cast<uint64_t *>(p); p += align_up((size_t)k * mw * 8);
-    uint64_t *Cr = reinterpret_cast<uint64_t *>(p); p += align_up((size_t)n * ldc * 8);
-    uint32_t *flag = reinterpret_cast<uint32_t *>(p);
-    CK(cudaMemsetAsync(flag, 0, sizeof(uint32_t), s));
-    LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest(A->w, A->ld, (int32_t)n, (int32_t)kw, last_word_mask(k), Ar, kw, nullptr, nullptr, flag, s));
-    LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest(B->w, B->ld, (int32_t)k, (int32_t)mw, last_word_mask(m), Br, mw, nullptr, nullptr, flag, s));
-    if (accumulate) LAUNCH(GF2_KCLASS_LAYOUT, launch_ingest(C->w, C->ld, (int32_t)n, (int32_t)mw, last_word_mask(m), Cr, ldc, nullptr, nullptr, flag, s));
-    else CK(cudaMemsetAsync(Cr, 0, (size_t)n * ldc * 8, s));
-    if (!(flags & GF2_NOCHECK)) {
-        st = check_flag(flag, s);
-        if (st) return st;
+    return mmm_rec(CBView{C->w, C->ld}, CBView{A->w, A->ld}, CBView{B->w, B->ld}, n, k, mw, accumulate != 0, levels,
+                   reinterpret_cast<uint64_t *>(p), s);
+}
+
+int gf2_mmm_set_strassen_cutoff(int64_t cutoff)
+{
+    if (cutoff < 128) return GF2_ERR_ARG;
+    g_strassen_cutoff.store(cutoff);
+    return GF2_OK;
+}
+
+int64_t gf2_mmm_strassen_cutoff(void) { return g_strassen_cutoff.load(); }
+
+}  // extern "C"
+
+namespace {
+
+__global__ void k_fill_words(uint64_t *w, int64_t count, uint64_t seed)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed + 0x9e3779b97f4a7c15ull * (uint64_t)(i + 1);  // SplitMix64 finaliser
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        w[i] = z ^ (z >> 31);
     }
-    MmmCtx c{Ar, kw, Br, mw, Cr, ldc, (int32_t)n, (int32_t)k};
-    for (int kb = 0; kb < kw; ++kb) LAUNCH(GF2_KCLASS_UPDATE, launch_mmm_pass(c, kb, (int)mw, s));
-    LAUNCH(GF2_KCLASS_LAYOUT, launch_colblocks_from_rowmajor(Cr, ldc, nullptr, (int32_t)n, (int32_t)mw, C->w, C->ld, s));
+}
+
+// best of `reps` timings (ms) of one square product of size d, at `levels`
+int time_product(uint64_t *A, uint64_t *B, uint64_t *C, uint64_t *tmp, int64_t d, int levels, int reps, cudaStream_t s,
+                 float *best)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return GF2_ERR_CUDA;
+    *best = 1e30f;
+    int st = GF2_OK;
+    for (int r = 0; r < reps + 1 && st == GF2_OK; ++r) {  // the first run warms up
+        if (cudaEventRecord(e0, s) != cudaSuccess) st = GF2_ERR_CUDA;
+        if (st == GF2_OK)
+            st = mmm_rec(CBView{C, d}, CBView{A, d}, CBView{B, d}, d, d, d / 64, false, levels, tmp, s);
+        if (st == GF2_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+            st = GF2_ERR_CUDA;
+        float ms = 0;
+        if (st == GF2_OK && r > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < *best) *best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gf2_mmm_autotune(int64_t max_dim, int64_t *cutoff, void *stream)
+{
+    if (!cutoff || max_dim < 1024) return GF2_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int64_t top = 1024;
+    while (top * 2 <= max_dim && top < 32768) top *= 2;
+    const size_t mat = (size_t)top * (top / 64) * 8;
+    const size_t tmp = strassen_bytes(top, top, top / 64, 1);
+    char *buf = nullptr;
+    if (cudaMalloc(&buf, 3 * mat + tmp) != cudaSuccess) {
+        cudaGetLastError();
+        return GF2_ERR_NOMEM;
+    }
+    uint64_t *A = reinterpret_cast<uint64_t *>(buf), *B = A + mat / 8, *C = B + mat / 8, *T = C + mat / 8;
+    int st = GF2_OK;
+    k_fill_words<<<1024, 256, 0, s>>>(A, (int64_t)(2 * mat / 8), 0x1209519812095198ull);
+    if (cudaGetLastError() != cudaSuccess) st = GF2_ERR_CUDA;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    // the smallest size from which one level is faster at that size and at
+    // every larger size tried
+    int64_t chosen = int64_t(1) << 62;
+    for (int64_t d = top; d >= 2048 && st == GF2_OK; d /= 2) {
+        float direct = 0, one = 0;
+        const int reps = d >= 16384 ? 2 : 4;
+        st = time_product(A, B, C, T, d, 0, reps, s, &direct);
+        if (st == GF2_OK) st = time_product(A, B, C, T, d, 1, reps, s, &one);
+        if (st != GF2_OK || one >= direct) break;
+        chosen = d;
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(buf);
+    if (st != GF2_OK) return st;
+    g_strassen_cutoff.store(chosen);
+    *cutoff = chosen;
     return GF2_OK;
 }
 

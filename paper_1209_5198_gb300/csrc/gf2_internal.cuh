@@ -86,12 +86,18 @@ __device__ __forceinline__ int64_t widx(const DecompCtx &c, int64_t i, int q)
 
 // Row-major operands of a product C ^= A * B over F2 for one 64-row slice
 // of B (k-block kb): the multiplier of row i is word kb of A's row i.
+// Operands of a product C (+)= A B over F2, all in column blocks (word (i, q)
+// at X[q*ld + i]): A is n x k, B is k x (64 mw), C is n x (64 mw).
 struct MmmCtx {
-    const uint64_t *A; int64_t lda;   // row-major, n x ceil(k/64)
-    const uint64_t *B; int64_t ldb;   // row-major, k x ceil(m/64)
-    uint64_t *C; int64_t ldc;         // row-major, n x ldc (multiple of 8)
-    int32_t n, k;
+    const uint64_t *A; int64_t lda;
+    const uint64_t *B; int64_t ldb;
+    uint64_t *C; int64_t ldc;
+    int32_t n, k, mw;
+    int32_t mode;                     // kMmmStore, kMmmXor or kMmmAtomicXor
 };
+constexpr int kMmmStore = 0;      // C = A B
+constexpr int kMmmXor = 1;        // C ^= A B
+constexpr int kMmmAtomicXor = 2;  // C ^= A B by atomics (the inner dimension split over CTAs)
 
 // One matrix of a batched decomposition (the caller's buffers; column blocks).
 struct BatchItem {
@@ -166,7 +172,13 @@ cudaError_t launch_rest(const DecompCtx &c, int j, int np, int est_active_rows, 
 int rest_tiles(const DecompCtx &c, int j, int np, int *tile_first);
 cudaError_t prepare_update_kernels();  // one-time kernel attributes (before any capture)
 cudaError_t prepare_panel_kernel();
-cudaError_t launch_mmm_pass(const MmmCtx &c, int kb, int m_words, cudaStream_t s);
+// the Four Russians product (csrc/k_mmm.cu); with mode kMmmStore or kMmmXor
+// the launch may split the inner dimension (then C is zeroed first for
+// kMmmStore and updated by atomics)
+cudaError_t launch_mmm(MmmCtx c, cudaStream_t s);
+// D = X ^ Y over rows x words (column blocks; D may be X)
+cudaError_t launch_xor(uint64_t *D, int64_t ldd, const uint64_t *X, int64_t ldx, const uint64_t *Y, int64_t ldy,
+                       int64_t rows, int64_t words, cudaStream_t s);
 cudaError_t launch_solve(const SolveCtx &c, cudaStream_t s);  // one cooperative launch
 // one CTA per item, items[0] first; max_n: the largest n among the items
 cudaError_t launch_serve_solve(const ServeItem *items, int count, int32_t *next, int64_t max_n, cudaStream_t s);

@@ -412,64 +412,6 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
     }
 }
 
-// ------------------------------------------------------------------ product
-constexpr int kMmmThreads = 256;
-constexpr int kMmmC = 8;
-constexpr int kMmmSmemBytes = (Tabs<kMmmC>::Words + 64 * kTileWords) * 8;
-
-__global__ void __launch_bounds__(kMmmThreads, 1) k_mmm_pass(MmmCtx mc, int kb, int m_words)
-{
-    extern __shared__ __align__(16) uint64_t smem[];
-    uint64_t *tab = smem;
-    uint64_t *crow = smem + Tabs<kMmmC>::Words;
-    const int tid = threadIdx.x;
-    const int q0 = blockIdx.x * kTileWords;
-    const int r = min(64, mc.k - 64 * kb);
-    for (int idx = tid; idx < 64 * kTileWords; idx += kMmmThreads) {
-        const int t = idx / kTileWords, w = idx % kTileWords;
-        crow[idx] = (t < r && q0 + w < m_words) ? mc.B[(int64_t)(64 * kb + t) * mc.ldb + q0 + w] : 0;
-    }
-    __syncthreads();
-    build_tables<kMmmC, kMmmThreads>(tab, crow);
-    __syncthreads();
-    const ulonglong2 *tab2 = reinterpret_cast<const ulonglong2 *>(tab);
-    const int ng = tables_used<kMmmC>(r);
-    const int lane = tid & 31, warp = tid >> 5;
-    const int rs = lane / kLanesPerRow, wp = lane % kLanesPerRow, swp = rs & 3;
-    const int col = q0 + 2 * wp;
-    const bool live = col < m_words;
-    const int rows = mc.n;
-    const int chunk = (rows + gridDim.y - 1) / gridDim.y;
-    const int rb = blockIdx.y * chunk, re = min(rows, rb + chunk);
-    constexpr int U = 4;
-    for (int base = rb + warp * kRowsPerWarp * U; base < re; base += kRowsPerWarp * U * (kMmmThreads / 32)) {
-        uint64_t y[U];
-        ulonglong2 a[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int i = base + u * kRowsPerWarp + rs;
-            y[u] = i < re ? mc.A[(int64_t)i * mc.lda + kb] : 0;
-            a[u] = make_ulonglong2(0, 0);
-            if (i < re && live) a[u] = *reinterpret_cast<const ulonglong2 *>(mc.C + (int64_t)i * mc.ldc + col);
-        }
-        for (int g = 0; g < ng; ++g) {
-            const int gg = g ^ swp;
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int x = (int)((y[u] >> (kMmmC * gg)) & 255);
-                const ulonglong2 t = tab2[tab_entry<kMmmC>(gg, x) * (kTileWords / 2) + wp];
-                a[u].x ^= t.x;
-                a[u].y ^= t.y;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int i = base + u * kRowsPerWarp + rs;
-            if (i < re && live) *reinterpret_cast<ulonglong2 *>(mc.C + (int64_t)i * mc.ldc + col) = a[u];
-        }
-    }
-}
-
 int g_num_sms = 0;
 
 int num_sms()
@@ -505,7 +447,6 @@ cudaError_t prepare_update_kernels()
     if (done[dev]) return cudaSuccess;
     e = allow_smem(k_rest<8, kRestU, 1>, rest_smem_bytes<8, 1>());
     if (e == cudaSuccess) e = allow_smem(k_rest<8, kRest2U, 2>, rest_smem_bytes<8, 2>());
-    if (e == cudaSuccess) e = allow_smem(k_mmm_pass, kMmmSmemBytes);
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }
@@ -544,22 +485,6 @@ cudaError_t launch_rest(const DecompCtx &c, int j, int np, int est_active_rows, 
         k_rest<8, kRestU, 1><<<grid, kRestThreads, rest_smem_bytes<8, 1>(), s>>>(c, j, tile_first, ntiles);
     else
         k_rest<4, kRestU, 1><<<grid, kRestThreads, rest_smem_bytes<4, 1>(), s>>>(c, j, tile_first, ntiles);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_mmm_pass(const MmmCtx &c, int kb, int m_words, cudaStream_t s)
-{
-    const int ntiles = (m_words + kTileWords - 1) / kTileWords;
-    if (ntiles <= 0 || c.n <= 0) return cudaSuccess;
-    cudaError_t e = prepare_update_kernels();
-    if (e != cudaSuccess) return e;
-    const int target = 2 * num_sms();
-    int chunks = (target + ntiles - 1) / ntiles;
-    const int maxc = c.n / 256 > 1 ? c.n / 256 : 1;
-    if (chunks > maxc) chunks = maxc;
-    if (chunks < 1) chunks = 1;
-    dim3 grid(ntiles, chunks);
-    k_mmm_pass<<<grid, kMmmThreads, kMmmSmemBytes, s>>>(c, kb, m_words);
     return cudaGetLastError();
 }
 

@@ -40,7 +40,20 @@ def test_host_only_entry_points(lib):
     assert ws >= 3 * n * (m // 64) * 8  # working copy + L + E, row-major
     assert lib.gf2_decompose_workspace_bytes(n, m, 0) < ws
     assert lib.gf2_rank_workspace_bytes(n, m) >= lib.gf2_decompose_workspace_bytes(n, m, 0)
-    assert lib.gf2_mmm_workspace_bytes(1000, 2000, 3000, 0) >= 8 * (1000 * 32 + 2000 * 47 + 1000 * 47)
+    # the product: M4RM needs only a status word; the tensor path the byte
+    # expansions of A and B; the recursion one level's temporaries per level
+    assert 0 < lib.gf2_mmm_workspace_bytes(1000, 2000, 3000, 0) <= 4096
+    assert lib.gf2_mmm_workspace_bytes(1000, 2000, 3000, 4) >= 1024 * 2048 + 3072 * 2048
+    import paper_1209_5198_gb300 as g
+    old = g.strassen_cutoff()
+    try:
+        g.set_strassen_cutoff(2048)
+        d = 4096  # one level: S1..S4 (2048 x 32 words), T1..T4 (2048 x 32), X (2048 x 32)
+        assert lib.gf2_mmm_workspace_bytes(d, d, d, 0) >= 8 * 9 * 2048 * 32
+        assert lib.gf2_mmm_workspace_bytes(d, d, d, 2) <= 4096      # GF2_MMM_TABLES: no recursion
+        assert lib.gf2_mmm_workspace_bytes(d, d + 64, d, 0) <= 4096  # odd number of words in k
+    finally:
+        g.set_strassen_cutoff(old)
     assert lib.gf2_decompose_workspace_bytes(-1, 5, 0) == 0
 
 

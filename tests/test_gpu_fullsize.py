@@ -157,11 +157,19 @@ def test_full_size_solve_32768():
         assert np.array_equal(matvec_parity(A, xc), bc)
 
 
-def test_full_size_product_16384():
+@pytest.mark.parametrize("strassen", [False, True])
+def test_full_size_product_16384(strassen):
+    """C = A B at 16384 by Freivalds (C x = A (B x) for random x), with M4RM
+    alone and with two Strassen-Winograd levels (cutoff 8192 -> 4096)."""
     n = 16384
     Ah = f2gen.uniform(n, n, 80)
     Bh = f2gen.uniform(n, n, 81)
-    C = gf2.mmm(gf2.Mat.from_rowmajor(Ah, n), gf2.Mat.from_rowmajor(Bh, n)).to_rowmajor()
+    old = gf2.strassen_cutoff()
+    try:
+        gf2.set_strassen_cutoff(8192 if strassen else gf2.STRASSEN_OFF)
+        C = gf2.mmm(gf2.Mat.from_rowmajor(Ah, n), gf2.Mat.from_rowmajor(Bh, n)).to_rowmajor()
+    finally:
+        gf2.set_strassen_cutoff(old)
     for x in random_vectors(6, n, 82):
         bx = matvec_parity(Bh, x)
         assert np.array_equal(matvec_parity(C, x), matvec_parity(Ah, pack(bx, Ah.shape[1])))

@@ -14,14 +14,24 @@ if not torch.cuda.is_available():
 import paper_1209_5198_gb300 as gf2  # noqa: E402
 
 
-BACKENDS = {"auto": 0, "tables": gf2.GF2_MMM_TABLES, "tensor": gf2.GF2_MMM_TENSOR}
+BACKENDS = {"auto": 0, "tables": gf2.GF2_MMM_TABLES, "tensor": gf2.GF2_MMM_TENSOR, "strassen": 0}
+
+
+@pytest.fixture
+def cutoff():
+    """Runs the test with a given Strassen cutoff, restoring the old one."""
+    old = gf2.strassen_cutoff()
+    yield gf2.set_strassen_cutoff
+    gf2.set_strassen_cutoff(old)
 
 
 @pytest.mark.parametrize("backend", sorted(BACKENDS))
 @pytest.mark.parametrize("n,k,m", [(1, 1, 1), (5, 70, 3), (64, 64, 64), (300, 130, 650), (1024, 1024, 1024),
-                                   (1000, 1300, 777), (2048, 64, 4100), (129, 2000, 65), (257, 4099, 191)])
-def test_product_matches_oracle(n, k, m, backend):
+                                   (1000, 1300, 777), (2048, 64, 4100), (129, 2000, 65), (257, 4099, 191),
+                                   (1024, 2048, 1000), (4000, 512, 768), (2048, 2048, 2048)])
+def test_product_matches_oracle(n, k, m, backend, cutoff):
     flags = BACKENDS[backend]
+    cutoff(128 if backend == "strassen" else gf2.STRASSEN_OFF)
     A = f2gen.uniform(n, k, 41, n, k)
     B = f2gen.uniform(k, m, 42, k, m)
     ref = oracle.mmm(A, B, k, m, nthreads=oracle.max_threads())
@@ -65,6 +75,24 @@ def test_product_padding_error_both_backends():
             gf2.gf2_mmm(gf2.Mat.from_rowmajor(A, 300), gf2.Mat.from_rowmajor(B, 100), gf2.Mat.empty(100, 100),
                         flags=flags)
         assert e.value.status == gf2.GF2_ERR_PADDING
+
+
+def test_strassen_levels_and_ragged_edges(cutoff):
+    """Recursion depths 1..3 (cutoff 256: 2048 -> 1024 -> 512 -> 256), a ragged
+    m (padding bits stay zero through the additions), and accumulate."""
+    cutoff(256)
+    for n, k, m in ((2048, 2048, 2048), (512, 1024, 1000), (1536, 768, 1280)):
+        A = f2gen.uniform(n, k, 47, n)
+        B = f2gen.uniform(k, m, 48, k)
+        C0 = f2gen.uniform(n, m, 49, n)
+        ref = oracle.mmm(A, B, k, m, nthreads=oracle.max_threads())
+        Cd = gf2.Mat.from_rowmajor(C0, m, ld=n + 3)
+        gf2.gf2_mmm(gf2.Mat.from_rowmajor(A, k, ld=n + 1), gf2.Mat.from_rowmajor(B, m, ld=k + 2), Cd,
+                    accumulate=True)
+        assert np.array_equal(Cd.to_rowmajor(), ref ^ C0)
+        Cd = gf2.Mat.empty(n, m)
+        gf2.gf2_mmm(gf2.Mat.from_rowmajor(A, k), gf2.Mat.from_rowmajor(B, m), Cd)
+        assert np.array_equal(Cd.to_rowmajor(), ref)
 
 
 def test_product_of_fixed_rank_factors_has_that_rank():
