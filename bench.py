@@ -310,6 +310,218 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ product
+
+PRODUCT_METRIC = "GF(2) product bit-op/s (C = A B, square Bernoulli(1/2))"
+
+
+def rand_words(rows: int, cols: int, g, dev):
+    """A rows x cols Bernoulli(1/2) matrix as column blocks of random words
+    (cols a multiple of 64), made on the GPU with torch's seeded generator."""
+    import torch
+    return torch.randint(-(2 ** 63), 2 ** 63 - 1, (cols // 64, rows), dtype=torch.int64, generator=g, device=dev)
+
+
+def time_calls(fn, steps: int, stream) -> float:
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_product(args):
+    import torch
+
+    import paper_1209_5198_gb300 as gf2
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    lib = gf2.load()
+    cutoff = gf2.mmm_autotune(32768)
+    g = torch.Generator(device=dev).manual_seed(0x1209)
+    backends = {"m4rm": gf2.GF2_MMM_TABLES, "strassen": 0, "tensor": gf2.GF2_MMM_TENSOR}
+    table, main = [], None
+    props = torch.cuda.get_device_properties(0)
+    sms = props.multi_processor_count
+    for n in args.product_sizes:
+        A = gf2.Mat(rand_words(n, n, g, dev), n, n)
+        B = gf2.Mat(rand_words(n, n, g, dev), n, n)
+        outs = {}
+        row = {"n": n, "strassen_levels": 0}
+        for name, fl in backends.items():
+            if name == "tensor" and n > args.tensor_max:
+                continue
+            C = gf2.Mat.empty(n, n, dev)
+            ws = torch.empty(max(1, lib.gf2_mmm_workspace_bytes(n, n, n, fl)), dtype=torch.uint8, device=dev)
+            fn = lambda: gf2.gf2_mmm(A, B, C, flags=fl, workspace=ws, stream=stream)
+            for _ in range(args.warmup):
+                fn()
+            steps = args.steps if n <= 32768 else max(1, args.steps // 2)
+            if name == "tensor":
+                steps = 1
+            sampler = None
+            if n == 32768 and name == "strassen":
+                sampler = ClockSampler(0)
+                sampler.start()
+                l0 = gf2.launch_count()
+            ms = time_calls(fn, steps, stream)
+            if sampler:
+                row["clocks"] = sampler.stop()
+                row["launches_per_step"] = (gf2.launch_count() - l0) / steps
+            row[name + "_ms"] = ms
+            row[name + "_bitops_per_s"] = 2.0 * n ** 3 / (ms / 1000)
+            outs[name] = C.t
+        ref = outs["m4rm"]
+        row["backends_agree"] = all(bool(torch.equal(ref, t)) for t in outs.values())
+        levels, d = 0, n
+        while d >= cutoff and levels < 8:
+            levels, d = levels + 1, d // 2
+        row["strassen_levels"] = levels
+        table.append(row)
+        if n == 32768:
+            main = row
+        del A, B, outs
+        torch.cuda.empty_cache()
+    if main is None:
+        main = table[-1]
+    n = main["n"]
+    # roofline of the M4RM kernel: its shared-memory lookups, n*m*k/64 bytes
+    # (8 B per row, output word and 8 bits of the inner dimension)
+    clk = (main.get("clocks") or {}).get("sm_mhz") or 2070.0
+    lookup_bytes = n ** 3 / 64.0
+    achieved = lookup_bytes / (main["m4rm_ms"] / 1000) / 1e9
+    peak = 128.0 * sms * clk * 1e6 / 1e9
+    # end to end: A and B from pinned host memory, C back, inside the timed region
+    Ah = torch.empty((n // 64, n), dtype=torch.int64, pin_memory=True)
+    Bh = torch.empty((n // 64, n), dtype=torch.int64, pin_memory=True)
+    Ch = torch.empty((n // 64, n), dtype=torch.int64, pin_memory=True)
+    Ah.copy_(rand_words(n, n, g, dev))
+    Bh.copy_(rand_words(n, n, g, dev))
+    Ad, Bd, Cd = torch.empty_like(Ah, device=dev), torch.empty_like(Bh, device=dev), torch.empty_like(Ch, device=dev)
+    ws = torch.empty(max(1, lib.gf2_mmm_workspace_bytes(n, n, n, 0)), dtype=torch.uint8, device=dev)
+
+    def e2e_step():
+        Ad.copy_(Ah, non_blocking=True)
+        Bd.copy_(Bh, non_blocking=True)
+        gf2.gf2_mmm(gf2.Mat(Ad, n, n), gf2.Mat(Bd, n, n), gf2.Mat(Cd, n, n), workspace=ws, stream=stream)
+        Ch.copy_(Cd, non_blocking=True)
+
+    e2e_step()
+    e2e_ms = time_calls(e2e_step, max(1, args.steps // 2), stream)
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = product_cpu_sample(n, args.cpu_seconds)
+    line = {
+        "metric": PRODUCT_METRIC, "value": 2.0 * n ** 3 / (main["strassen_ms"] / 1000), "unit": "bit-op/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": main["strassen_ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"product C = A B, n = k = m = {n}, Bernoulli(1/2) words from torch's seeded "
+                               "generator; default backend = M4RM under Strassen-Winograd at the cutoff the "
+                               "library's autotuner picked on this GPU", "n": n, "strassen_cutoff": cutoff,
+                   "l2": "no flush: A, B and C (3 x n^2/8 bytes) exceed the 129 MB L2 from n = 32768; smaller "
+                         "sizes run L2-warm"},
+        "sizes": table,
+        "roofline": {"kernel": "k_mmm (M4RM product, no recursion)", "bound": "smem", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "alg_bytes_per_launch": lookup_bytes,
+                     "peak_source": f"128 B/clk/SM x {sms} SMs x {clk:.0f} MHz (shared-memory bandwidth)"},
+        "e2e": {"value": 2.0 * n ** 3 / (e2e_ms / 1000), "unit": "bit-op/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(2 * Ah.numel() * 8), "d2h_bytes_per_step": int(Ch.numel() * 8)},
+        "cpu_baseline": cpu,
+        "gpu_launches": main.get("launches_per_step"),
+        "clocks": main.get("clocks"),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def product_cpu_sample(n: int, seconds: float):
+    """The oracle's product on the first rows of A (all of B), sized to about
+    `seconds`, scaled to bit-op/s."""
+    import oracle
+    oracle.build()
+    cores = oracle.max_threads()
+    B = f2gen.uniform(n, n, 0x1209, 1)
+    rows = 64
+    A = f2gen.uniform(rows, n, 0x1209, 2)
+    t0 = time.perf_counter()
+    oracle.mmm(A, B, n, n, nthreads=cores)
+    dt = time.perf_counter() - t0
+    if dt < seconds / 4:
+        rows = int(min(n, rows * seconds / max(dt, 1e-3) * 0.8))
+        A = f2gen.uniform(rows, n, 0x1209, 2)
+        t0 = time.perf_counter()
+        oracle.mmm(A, B, n, n, nthreads=cores)
+        dt = time.perf_counter() - t0
+    return {"value": 2.0 * rows * n * n / dt, "unit": "bit-op/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle product of the first {rows} rows of A with all of B (n = {n}), {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------ sizes
+
+SIZES_METRIC = "decomposition time and GF(2) bit-op/s across the scale configurations"
+
+
+def run_sizes(args):
+    """The scale configurations of the plain decomposition: square 16384,
+    32768, 65536 Bernoulli(1/2); rectangular 16384 x 65536 and 65536 x 16384;
+    fixed rank r = n/2 and n - 64 (A = X Y, X n x r and Y r x n Bernoulli(1/2),
+    full rank with overwhelming probability, formed with the library's
+    product).  Inputs made on the GPU with torch's seeded generator."""
+    import torch
+
+    import paper_1209_5198_gb300 as gf2
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    lib = gf2.load()
+    g = torch.Generator(device=dev).manual_seed(0x5198)
+    cfgs = [(16384, 16384, None), (32768, 32768, None), (65536, 65536, None), (16384, 65536, None),
+            (65536, 16384, None), (16384, 16384, 8192), (16384, 16384, 16320), (32768, 32768, 16384),
+            (32768, 32768, 32704)]
+    rows = []
+    for n, m, r in cfgs:
+        if r is None:
+            A = gf2.Mat(rand_words(n, m, g, dev), n, m)
+        else:
+            X = gf2.Mat(rand_words(n, r, g, dev), n, r)  # r is a multiple of 64 here
+            Y = gf2.Mat(rand_words(r, m, g, dev), r, m)
+            A = gf2.Mat.empty(n, m, dev)
+            gf2.gf2_mmm(X, Y, A, flags=gf2.GF2_MMM_TABLES, stream=stream)
+            del X, Y
+        k = min(n, m)
+        perm = torch.empty(n, dtype=torch.int32, device=dev)
+        piv = torch.empty(k, dtype=torch.int32, device=dev)
+        rk = torch.zeros(1, dtype=torch.int64, device=dev)
+        L = gf2.Mat.empty(n, k, dev)
+        E = gf2.Mat.empty(k, m, dev)
+        ws = torch.empty(lib.gf2_decompose_workspace_bytes(n, m, 1), dtype=torch.uint8, device=dev)
+        fn = lambda: gf2.gf2_decompose(A, perm, piv, rk, L, E, workspace=ws, stream=stream)
+        for _ in range(max(2, args.warmup)):  # the second call captures the graph
+            fn()
+        ms = time_calls(fn, 2, stream)
+        rank = int(rk.item())
+        ops = bitops(n, m, piv.cpu().numpy()[:rank])
+        rows.append({"n": n, "m": m, "kind": "fixed rank" if r else "Bernoulli(1/2)", "r_built": r,
+                     "rank": rank, "ms": ms, "bitops_per_s": ops / (ms / 1000)})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        del A, L, E, ws
+        torch.cuda.empty_cache()
+    main = next(x for x in rows if x["n"] == 32768 and x["m"] == 32768 and x["r_built"] is None)
+    line = {
+        "metric": SIZES_METRIC, "value": main["bitops_per_s"], "unit": "bit-op/s", "n_gpus": 1, "steps": 2,
+        "warmup": max(2, args.warmup), "ms_per_step": main["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "plain decomposition (L and E) over the scale configurations; value = the "
+                               "32768 x 32768 Bernoulli(1/2) case", "configs": rows},
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ serving
 
 SERVE_METRIC = "served solves/s (rank + solve requests on resident factors, continuous batching)"
@@ -660,10 +872,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="decompose", choices=["decompose", "batched", "serving"],
+    ap.add_argument("--workload", default="decompose", choices=["decompose", "batched", "serving", "product", "sizes"],
                     help="decompose: the headline 32768^2 decomposition; batched: many small matrices in one "
                          "launch; serving: a request stream on resident factors")
     ap.add_argument("--requests", type=int, default=20000, help="requests in the serving trace")
+    ap.add_argument("--product-sizes", type=int, nargs="+", default=[8192, 16384, 32768, 65536])
+    ap.add_argument("--tensor-max", type=int, default=32768, help="largest n timed on the tensor-core backend")
     ap.add_argument("--batch", type=int, default=4096, help="matrices per batch (batched workload)")
     args = ap.parse_args()
     args.m = args.m or args.n
@@ -673,6 +887,10 @@ def main():
         run_batched(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "product":
+        run_product(args)
+    elif args.workload == "sizes":
+        run_sizes(args)
     else:
         run_ours(args)
 
