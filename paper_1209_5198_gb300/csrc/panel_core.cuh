@@ -40,7 +40,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWin = 64;  // window slots
-enum { kReqDone = 0, kReqFind = 1, kReqOr = 2 };
+enum { kReqDone = 0, kReqFind = 1 };
 
 __device__ __forceinline__ void bar_sync(int id, int nthreads)
 {
@@ -126,13 +126,41 @@ __device__ __forceinline__ uint64_t panel_word(const uint64_t *Wj, const PrevPan
     return w;
 }
 
+// Tables of the reduction by the current pivots (red(w) = XOR_{p in w}
+// pred[p]), 8 bits at a time.
+__device__ __forceinline__ void build_reduction_tables(PanelShared &sh)
+{
+    for (int e = threadIdx.x; e < kNumTables * 256; e += kPanelThreads) {
+        const int g = e >> 8, x = e & 255;
+        uint64_t acc = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+            if ((x >> b) & 1) acc ^= sh.pred[8 * g + b];
+        sh.tab[e] = acc;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ uint64_t reduce_word(const PanelShared &sh, uint64_t v)
+{
+    uint64_t r = 0;
+#pragma unroll
+    for (int g = 0; g < kNumTables; ++g) r ^= sh.tab[g * 256 + ((v >> (8 * g)) & 255)];
+    return r;
+}
+
 // Positions [from, n): first one whose panel word w has parity(w & mask) = 1.
+// The same pass ORs the fully reduced words into sh.orv, so that when no
+// position qualifies sh.orv holds the OR over all of them (a block whose
+// remaining rows are zero, as once the rank is used up, costs one pass).
 __device__ void scan_find(const DecompCtx &c, const uint64_t *Wj, const PrevPanel &pv, PanelShared &sh)
 {
     constexpr int U = 4;
     const int tid = threadIdx.x;
+    build_reduction_tables(sh);
     const int from = sh.from, n = c.n;
     const uint64_t mask = sh.mask;
+    uint64_t acc = 0;
     for (int base = from; base < n; base += kPanelThreads * U) {
         int srow[U];
 #pragma unroll
@@ -146,49 +174,13 @@ __device__ void scan_find(const DecompCtx &c, const uint64_t *Wj, const PrevPane
         int hit = 0;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
+            acc |= reduce_word(sh, v[u]);
             if (!hit && (__popcll(v[u] & mask) & 1)) {
                 atomicMin(&sh.found, base + u * kPanelThreads + tid);
                 hit = 1;
             }
         }
         if (__syncthreads_or(hit)) break;
-    }
-}
-
-// OR over positions [from, n) of the fully reduced panel words (reduction by
-// the current pivots: red(w) = XOR_{p in w} pred[p]).
-__device__ void scan_or(const DecompCtx &c, const uint64_t *Wj, const PrevPanel &pv, PanelShared &sh)
-{
-    constexpr int U = 4;
-    const int tid = threadIdx.x;
-    for (int e = tid; e < kNumTables * 256; e += kPanelThreads) {
-        const int g = e >> 8, x = e & 255;
-        uint64_t acc = 0;
-#pragma unroll
-        for (int b = 0; b < 8; ++b)
-            if ((x >> b) & 1) acc ^= sh.pred[8 * g + b];
-        sh.tab[e] = acc;
-    }
-    __syncthreads();
-    const int from = sh.from, n = c.n;
-    uint64_t acc = 0;
-    for (int base = from; base < n; base += kPanelThreads * U) {
-        int srow[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int q = base + u * kPanelThreads + tid;
-            srow[u] = q < n ? c.perm[q] : -1;
-        }
-        uint64_t v[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) v[u] = srow[u] >= 0 ? panel_word(Wj, pv, sh, srow[u]) : 0;
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            uint64_t r = 0;
-#pragma unroll
-            for (int g = 0; g < kNumTables; ++g) r ^= sh.tab[g * 256 + ((v[u] >> (8 * g)) & 255)];
-            acc |= r;
-        }
     }
     acc = warp_or(acc);
     if ((tid & 31) == 0 && acc) atomicOr(&sh.orv, (unsigned long long)acc);
@@ -374,8 +366,7 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
             bar_sync(1, kPanelThreads);
             const int req = sh.req;
             if (req == kReqDone) return;
-            if (req == kReqFind) scan_find(c, Wj, pv, sh);
-            else scan_or(c, Wj, pv, sh);
+            scan_find(c, Wj, pv, sh);
             bar_sync(2, kPanelThreads);
         }
     }
@@ -399,8 +390,7 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
         }
         __syncwarp();
         bar_sync(1, kPanelThreads);
-        if (req == kReqFind) scan_find(c, Wj, pv, sh);
-        else scan_or(c, Wj, pv, sh);
+        scan_find(c, Wj, pv, sh);
         bar_sync(2, kPanelThreads);
     };
 
@@ -585,7 +575,10 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
                 publish_reduced_units();
                 uint64_t ck = 0;  // bit p: entry k of red(e_p)
                 for (int p = 0; p < 64; ++p) ck |= ((sh.pred[p] >> k) & 1) << p;
-                request(kReqFind, fill, ck, 0);
+                // (the OR of the window's reduced rows seeds the scan's OR)
+                const uint64_t wor = (uint64_t)__ballot_sync(kFull, (A & valid) != 0) |
+                                     ((uint64_t)__ballot_sync(kFull, (B & valid) != 0) << 32);
+                request(kReqFind, fill, ck, wor);
                 const int q = sh.found;
                 if (q != INT_MAX) {
                     // pivot outside the window; the row in the pivot slot
@@ -621,10 +614,9 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
                     continue;
                 }
                 // Bit k has no pivot.  The next bit that can have one is the
-                // lowest bit above k set in some reduced remaining row.
-                const uint64_t worv = (uint64_t)__ballot_sync(kFull, (A & valid) != 0) |
-                                      ((uint64_t)__ballot_sync(kFull, (B & valid) != 0) << 32);
-                request(kReqOr, fill, 0, worv);
+                // lowest bit above k set in some reduced remaining row: the
+                // find scan went over every row behind the window and left
+                // their OR (with the window's) in sh.orv.
                 const uint64_t above = k + 1 < 64 ? (sh.orv & (~0ull << (k + 1))) : 0;
                 k = above ? __ffsll((long long)above) - 1 : 64;
                 continue;
