@@ -309,10 +309,10 @@ void drop_graphs()
 //   one panel at a time: next(j) waits for panel(j), for rest(j-2) (it reuses
 //     Y and the active list of j-2) and, when word j+2 opens a new tile, for
 //     rest(j-1) (which updated that tile); rest(j) waits for next(j);
-//   by pairs (j even, j+1): next(j) waits for panel(j) and for the previous
-//     pair's update, which covered the tiles it rewrites and last read the
-//     buffers it reuses; next(j+1) follows next(j); rest(j, j+1) waits for
-//     next(j+1); a lone last panel is updated alone.
+//   by pairs (j even, j+1): next(j) waits for panel(j) and for the update
+//     that last covered the tile it rewrites (the previous pair's for
+//     j = 4k+2, the one before for j = 4k); next(j+1) follows next(j);
+//     rest(j, j+1) waits for next(j+1); a lone last panel is updated alone.
 // So panel j+1 runs while next(j) and the updates of earlier panels run.
 int enqueue_factorization(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat *E, SideResources *side)
 {
@@ -330,7 +330,19 @@ int enqueue_factorization(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat
         CK(cudaEventRecord(evPanel[j], P));
         CK(cudaStreamWaitEvent(N, evPanel[j], 0));
         if (c.pair) {
-            if (!(j & 1) && j >= 1 && rest_launched[j - 1]) CK(cudaStreamWaitEvent(N, evRest[j - 1], 0));
+            // next(j), j even, rewrites the tile of word j+2.  For j = 4k that
+            // is tile k, which the update of pair (j-4, j-3) covers and the
+            // previous pair's update (tiles from k+1 on) does not: it waits
+            // for the former only and runs beside the latter.  For j = 4k+2
+            // the tile is k+1: it waits for the previous pair's update.
+            // next(j+1) follows next(j) on N; its tile (of word j+3) is that
+            // of next(j), its active list one of four, and the first panel's
+            // update of its pivot rows happens inside the pair's own update.
+            if (!(j & 1) && (j & 3) == 0) {
+                if (j >= 3 && rest_launched[j - 3]) CK(cudaStreamWaitEvent(N, evRest[j - 3], 0));
+            } else if (!(j & 1)) {
+                if (j >= 1 && rest_launched[j - 1]) CK(cudaStreamWaitEvent(N, evRest[j - 1], 0));
+            }
         } else {
             if (j >= 2 && rest_launched[j - 2]) CK(cudaStreamWaitEvent(N, evRest[j - 2], 0));
             if (j >= 1 && (j + 2) % kTileWords == 0 && rest_launched[j - 1]) CK(cudaStreamWaitEvent(N, evRest[j - 1], 0));
@@ -378,7 +390,7 @@ DecompLayout decomp_layout(int64_t n, int64_t m, bool factors)
     d.oW = o; o += align_up((size_t)n * d.ldw * 8);
     d.oY = o; o += align_up((size_t)n * 4 * 8);
     d.oF = o; o += align_up((size_t)n * 2 * 8);
-    d.oAct = o; o += align_up((size_t)n * 2 * 4);
+    d.oAct = o; o += align_up((size_t)n * 4 * 4);
     d.oNact = o; o += align_up((size_t)(d.mu > 0 ? d.mu : 1) * 4);
     d.oPP = o; o += align_up((size_t)n * 4);
     d.oInfo = o; o += align_up((size_t)(d.mu > 0 ? d.mu : 1) * sizeof(PanelInfo));

@@ -61,7 +61,7 @@ struct DecompCtx {
                         // (j >= 1; written by the look-ahead kernel of panel j-1; word j of W
                         // itself never receives panel j-1's update)
     int32_t *pivpanel;  // [n] per storage row: panel where it became a pivot (INT32_MAX: not yet)
-    int32_t *act;       // [2][n] act[j % 2]: the storage rows that are not pivots of panels <= j
+    int32_t *act;       // [4][n] act[j % 4]: the storage rows that are not pivots of panels <= j
                         // (ascending within each 256-entry piece), written by the look-ahead of panel j
     int32_t *nact;      // [mu] number of entries of act after panel j (zero before the run)
     uint64_t *Lint;     // [n x ldl] per storage row, or null (rank only)

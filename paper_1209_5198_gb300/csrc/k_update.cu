@@ -26,7 +26,6 @@
 // four rows of a quarter-warp (one 128-bit shared-memory phase) read tables
 // g, g^1, g^2, g^3, which live in the four 32-byte quarters of the bank
 // space, so lookups are conflict-free for any y.
-// The same tile code serves the standalone product C ^= A B.
 #include <mutex>
 
 #include "m4rm_core.cuh"
@@ -44,11 +43,12 @@ namespace {
 //   W ^= y C on the words >= j+2 of the tile holding word j+2 and, when
 //            panel j opens a pair of panels (whose wide update starts after
 //            the tile holding word j+3), of that tile too
-//   the compacted list of the rows that stay active
+//   the compacted list of the rows that stay active (act[j%4]: four lists, so
+//            that no list is rewritten while an update that reads it may run)
 // and, in block 0, the pivot rows' L rows (T) and their echelon words on
-// the same columns.  For the second panel of a pair it also applies the first
-// panel's update to its own pivot rows on every tile of the wide update,
-// which reads them as table rows.
+// the same columns.  (The second panel of a pair gets the first panel's
+// update on the tiles of the wide update inside that update, where its
+// pivot rows are table rows.)
 constexpr int kNextThreads = 256;
 constexpr int kNextRows = 256;  // storage rows per CTA (one wave next to the k_rest CTAs)
 constexpr int kNextC = 4;
@@ -68,7 +68,6 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
     const int tid = threadIdx.x;
     const bool has_f = j + 1 < c.mu;
     const bool pair_first = c.pair && !(j & 1) && j + 1 < c.mu;
-    const bool pair_second = c.pair && (j & 1);
     const int ntiles_w = (c.mu + kTileWords - 1) / kTileWords;
     const int t0 = (j + 2) / kTileWords;  // first tile of the range
     const int nt = j + 2 >= c.mu ? 0 : min((j + 2 + (pair_first ? 1 : 0)) / kTileWords, ntiles_w - 1) - t0 + 1;
@@ -83,10 +82,10 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
     // this CTA's rows: entries [rb, re) of the rows still active before
     // panel j (every storage row for j = 0)
     const int cnt = j == 0 ? c.n : c.nact[j - 1];
-    const int32_t *lst = j == 0 ? nullptr : c.act + (int64_t)((j - 1) & 1) * c.n;
+    const int32_t *lst = j == 0 ? nullptr : c.act + (int64_t)((j - 1) & 3) * c.n;
     const int rb = blockIdx.x * kNextRows, re = min(cnt, rb + kNextRows);
     const bool rows_here = rb < re;
-    if (!rows_here && blockIdx.x != 0 && !pair_second) return;
+    if (!rows_here && blockIdx.x != 0) return;
     const uint64_t *Fj = c.F + (int64_t)(j & 1) * c.n;
     uint64_t *Fn = c.F + (int64_t)((j + 1) & 1) * c.n;
     constexpr int U = kNextRows / (kRowsPerWarp * (kNextThreads / 32));  // row groups per warp
@@ -155,7 +154,7 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
     __syncthreads();
     if (kept_row >= 0) {
         const int pos = keep_warp[kNextThreads / 32] + keep_warp[warp] + __popc(kept_mask & ((1u << lane) - 1));
-        c.act[(int64_t)(j & 1) * c.n + pos] = kept_row;
+        c.act[(int64_t)(j & 3) * c.n + pos] = kept_row;
     }
 
     // 3. compute and store
@@ -246,32 +245,6 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
                 echelon_rows<kNextC, kNextThreads>(c, pi, R, r, q0 + tt * kTileWords, j + 2, ng,
                                                    tab + tt * Tabs<kNextC>::Words);
     }
-
-    // 4. second panel of a pair: the first panel's update of this panel's
-    // pivot rows on the tiles of the wide update (tiles after t0)
-    if (pair_second && r > 0) {
-        const PanelInfo *pp = c.info + (j - 1);
-        const int rp = pp->r;
-        if (rp > 0) {
-            const uint64_t *Yp = c.Y + (int64_t)((j - 1) & 3) * c.n;
-            const int s2 = tid / kTileWords, w = tid % kTileWords;  // pivot row s2 of panel j, word w
-            const bool mine = s2 < r;
-            const int srow = mine ? pi->prow[s2] : 0;
-            const uint64_t yp = mine ? Yp[srow] : 0;
-            uint64_t *cprev = crow;  // the first panel's pivot rows on one tile
-            for (int tile = t0 + 1 + blockIdx.x; tile < ntiles_w; tile += gridDim.x) {
-                __syncthreads();
-                load_pivot_rows<kNextThreads>(c, pp->prow, rp, tile * kTileWords, cprev);
-                __syncthreads();
-                if (mine && yp) {
-                    uint64_t *dst = c.W + widx(c, srow, tile * kTileWords + w);
-                    uint64_t acc = *dst;
-                    for (uint64_t b = yp; b; b &= b - 1) acc ^= cprev[(__ffsll((long long)b) - 1) * kTileWords + w];
-                    *dst = acc;
-                }
-            }
-        }
-    }
 }
 
 // -------------------------------------------------------------------- k_rest
@@ -311,7 +284,7 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
     // panels <= j + NP - 1 (the rows that are have y = 0)
     const int jl = j + NP - 1;
     const int nact = c.nact[jl];
-    const int32_t *__restrict__ act = c.act + (int64_t)(jl & 1) * c.n;
+    const int32_t *__restrict__ act = c.act + (int64_t)(jl & 3) * c.n;
     // (with no row left the tiles are still visited when E is wanted: the
     // pivot rows' echelon words come from the same tables)
     const int nchunks = max((nact + kRestChunk - 1) / kRestChunk, c.Eint ? 1 : 0);
@@ -340,7 +313,23 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
         if (NP == 2) load_pivot_rows<kRestThreads>(c, pi1->prow, r1, q0, crow + 64 * kTileWords);
         __syncthreads();
         build_tables<C, kRestThreads>(tab, crow);
-        if (NP == 2) build_tables<C, kRestThreads>(tab, crow + 64 * kTileWords, K);
+        if (NP == 2) {
+            // Panel j+1's pivot rows are not on the active list: give them
+            // panel j's update on this tile here (with panel j's tables),
+            // then build panel j+1's tables from them.  (Their words in W are
+            // not read again: the echelon rows come from these tables.)
+            __syncthreads();
+            for (int idx = tid; idx < r1 * kTileWords; idx += kRestThreads) {
+                const uint64_t y = Y0[pi1->prow[idx / kTileWords]];
+                if (!y) continue;
+                uint64_t acc = 0;
+                for (int g = 0; g < ng0; ++g)
+                    acc ^= tab[tab_entry<C>(g, (int)((y >> (C * g)) & (Tabs<C>::X - 1))) * kTileWords + idx % kTileWords];
+                crow[64 * kTileWords + idx] ^= acc;
+            }
+            __syncthreads();
+            build_tables<C, kRestThreads>(tab, crow + 64 * kTileWords, K);
+        }
         __syncthreads();
         if (c.Eint && chunk == 0) {
             echelon_rows<C, kRestThreads>(c, pi0, pi0->R, r0, q0, 0, ng0, tab);

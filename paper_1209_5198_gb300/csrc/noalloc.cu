@@ -36,7 +36,7 @@ constexpr size_t kOffW = 0;
 constexpr size_t kOffY = kOffW + align_na((size_t)kNoallocMaxDim * kNoallocMu * 8);
 constexpr size_t kOffF = kOffY + align_na((size_t)kNoallocMaxDim * 4 * 8);
 constexpr size_t kOffAct = kOffF + align_na((size_t)kNoallocMaxDim * 2 * 8);
-constexpr size_t kOffNact = kOffAct + align_na((size_t)kNoallocMaxDim * 2 * 4);
+constexpr size_t kOffNact = kOffAct + align_na((size_t)kNoallocMaxDim * 4 * 4);
 constexpr size_t kOffPP = kOffNact + align_na((size_t)kNoallocMu * 4);
 constexpr size_t kOffInfo = kOffPP + align_na((size_t)kNoallocMaxDim * 4);
 constexpr size_t kOffPerm = kOffInfo + align_na((size_t)kNoallocMu * sizeof(PanelInfo));
