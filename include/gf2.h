@@ -151,7 +151,7 @@ int gf2_rank(const gf2_mat *A, int64_t *rank_host, unsigned flags,
  * allocate device memory when they call in -- for instance a program that
  * reserves a fixed device-memory budget at start-up and forbids allocations
  * afterwards, or a framework that owns every device buffer.  The scratch is
- * a static array of about 2.4 MiB inside the library (held by every GPU that
+ * a static array of about 2.7 MiB inside the library (held by every GPU that
  * loads the library, until the process exits).  The first call on a device
  * looks up that array's device address (cudaGetSymbolAddress), so make the
  * first call before any stream capture.  Calls on one device share the

@@ -320,7 +320,13 @@ int enqueue_factorization(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat
     const int mu = c.mu;
     cudaEvent_t *evPanel = side->events.data(), *evNext = evPanel + mu, *evRest = evNext + mu;
     cudaEvent_t evFork = evRest[mu], evJoinP = evRest[mu + 1], evJoinN = evRest[mu + 2];
-    std::vector<char> rest_launched(mu, 0);
+    cudaEvent_t *evHead = evRest + mu + 5;  // after evIn / evOut of the caller
+    std::vector<char> rest_launched(mu, 0), head_launched(mu, 0);
+    // the event after which the tile a pair's update starts with is done
+    auto first_tile_done = [&](int jr) -> cudaEvent_t {
+        if (jr < 0 || jr >= mu || !rest_launched[jr]) return nullptr;
+        return head_launched[jr] ? evHead[jr] : evRest[jr];
+    };
     CK(cudaEventRecord(evFork, s));
     CK(cudaStreamWaitEvent(P, evFork, 0));
     CK(cudaStreamWaitEvent(N, evFork, 0));
@@ -330,18 +336,19 @@ int enqueue_factorization(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat
         CK(cudaEventRecord(evPanel[j], P));
         CK(cudaStreamWaitEvent(N, evPanel[j], 0));
         if (c.pair) {
-            // next(j), j even, rewrites the tile of word j+2.  For j = 4k that
-            // is tile k, which the update of pair (j-4, j-3) covers and the
-            // previous pair's update (tiles from k+1 on) does not: it waits
-            // for the former only and runs beside the latter.  For j = 4k+2
-            // the tile is k+1: it waits for the previous pair's update.
-            // next(j+1) follows next(j) on N; its tile (of word j+3) is that
+            // next(j), j even, rewrites the tile of word j+2: tile k for
+            // j = 4k, the first tile of the update of pair (j-4, j-3); tile
+            // k+1 for j = 4k+2, the first tile of the previous pair's update.
+            // Those updates run that tile in a launch of its own (the head),
+            // so next(j) waits for the head only and runs beside the rest of
+            // the update.  next(j+1) follows next(j) on N; its tile is that
             // of next(j), its active list one of four, and the first panel's
             // update of its pivot rows happens inside the pair's own update.
-            if (!(j & 1) && (j & 3) == 0) {
-                if (j >= 3 && rest_launched[j - 3]) CK(cudaStreamWaitEvent(N, evRest[j - 3], 0));
-            } else if (!(j & 1)) {
-                if (j >= 1 && rest_launched[j - 1]) CK(cudaStreamWaitEvent(N, evRest[j - 1], 0));
+            // (The Y buffers and active lists form a ring of kRing, so those
+            // of the update still running are not rewritten meanwhile.)
+            if (!(j & 1)) {
+                const cudaEvent_t ev = first_tile_done((j & 3) == 0 ? j - 3 : j - 1);
+                if (ev) CK(cudaStreamWaitEvent(N, ev, 0));
             }
         } else {
             if (j >= 2 && rest_launched[j - 2]) CK(cudaStreamWaitEvent(N, evRest[j - 2], 0));
@@ -354,10 +361,19 @@ int enqueue_factorization(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat
         const int np = !c.pair ? 1 : ((j & 1) ? 2 : (j == mu - 1 ? 1 : 0));
         const int jf = j - np + 1;
         int tile_first = 0;
-        if (np > 0 && rest_tiles(c, jf, np, &tile_first) > 0) {
+        const int ntiles = np > 0 ? rest_tiles(c, jf, np, &tile_first) : 0;
+        if (ntiles > 0) {
             CK(cudaStreamWaitEvent(s, evNext[j], 0));
             const int est = (int)(c.n - 64 * (int64_t)(j + 1));
-            LAUNCH(GF2_KCLASS_UPDATE, launch_rest(c, jf, np, est, s));
+            if (np == 2 && (jf & 3) == 0) {
+                // pair (4k, 4k+1): its first tile (k+1) alone, then the others
+                LAUNCH(GF2_KCLASS_UPDATE, launch_rest(c, jf, np, est, s, 0, 1));
+                CK(cudaEventRecord(evHead[j], s));
+                head_launched[j] = 1;
+                if (ntiles > 1) LAUNCH(GF2_KCLASS_UPDATE, launch_rest(c, jf, np, est, s, 1));
+            } else {
+                LAUNCH(GF2_KCLASS_UPDATE, launch_rest(c, jf, np, est, s));
+            }
             CK(cudaEventRecord(evRest[j], s));
             rest_launched[j] = 1;
         }
@@ -388,9 +404,9 @@ DecompLayout decomp_layout(int64_t n, int64_t m, bool factors)
     d.ldl = words_of(d.kmax) > 0 ? words_of(d.kmax) : 1;
     size_t o = 0;
     d.oW = o; o += align_up((size_t)n * d.ldw * 8);
-    d.oY = o; o += align_up((size_t)n * 4 * 8);
+    d.oY = o; o += align_up((size_t)n * kRing * 8);
     d.oF = o; o += align_up((size_t)n * 2 * 8);
-    d.oAct = o; o += align_up((size_t)n * 4 * 4);
+    d.oAct = o; o += align_up((size_t)n * kRing * 4);
     d.oNact = o; o += align_up((size_t)(d.mu > 0 ? d.mu : 1) * 4);
     d.oPP = o; o += align_up((size_t)n * 4);
     d.oInfo = o; o += align_up((size_t)(d.mu > 0 ? d.mu : 1) * sizeof(PanelInfo));
@@ -463,7 +479,7 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
     // replayed on later calls.
     std::unique_lock<std::mutex> lane_lock;
     SideResources *side = nullptr;
-    st = side_resources(3 * c.mu + 5, &side, lane_lock);
+    st = side_resources(4 * c.mu + 5, &side, lane_lock);
     if (st) return st;
     cudaEvent_t evIn = side->events[3 * c.mu + 3], evOut = side->events[3 * c.mu + 4];
     CK(cudaEventRecord(evIn, s));

@@ -11,6 +11,10 @@ namespace gf2 {
 // of the trailing update owns one 128-bit word pair of a row's tile, so a
 // warp covers 16 rows of a tile.
 constexpr int kTileWords = 4;
+// Y buffers and active lists kept per panel, cyclically: an update may still
+// read those of panel j while the look-ahead kernels of panels up to j + 5
+// write theirs
+constexpr int kRing = 8;
 constexpr int kLanesPerRow = kTileWords / 2;
 constexpr int kRowsPerWarp = 32 / kLanesPerRow;
 // Four Russians table width c (Section 6 of the paper): a 64-bit multiplier
@@ -56,12 +60,12 @@ struct DecompCtx {
     int32_t *perm;      // [n] position -> storage row (the output perm)
     int32_t *pivcols;   // [k]
     PanelInfo *info;    // [mu]
-    uint64_t *Y;        // [4][n] per storage row: y of panel j in Y[j % 4]; 0 for pivot rows
+    uint64_t *Y;        // [kRing][n] per storage row: y of panel j in Y[j % kRing]; 0 for pivot rows
     uint64_t *F;        // [2][n] per storage row: its word j with every panel < j applied, in F[j % 2]
                         // (j >= 1; written by the look-ahead kernel of panel j-1; word j of W
                         // itself never receives panel j-1's update)
     int32_t *pivpanel;  // [n] per storage row: panel where it became a pivot (INT32_MAX: not yet)
-    int32_t *act;       // [4][n] act[j % 4]: the storage rows that are not pivots of panels <= j
+    int32_t *act;       // [kRing][n] act[j % kRing]: the storage rows that are not pivots of panels <= j
                         // (ascending within each 256-entry piece), written by the look-ahead of panel j
     int32_t *nact;      // [mu] number of entries of act after panel j (zero before the run)
     uint64_t *Lint;     // [n x ldl] per storage row, or null (rank only)
@@ -168,7 +172,10 @@ cudaError_t launch_finish_scalars(const DecompCtx &c, int64_t *rank, cudaStream_
 cudaError_t launch_panel(const DecompCtx &c, int j, cudaStream_t s);
 cudaError_t launch_next(const DecompCtx &c, int j, cudaStream_t s);
 // the wide update of panel j (np = 1) or of the pair j, j+1 (np = 2)
-cudaError_t launch_rest(const DecompCtx &c, int j, int np, int est_active_rows, cudaStream_t s);
+// the wide update of panel j (np = 1) or of panels j, j+1 (np = 2) on its
+// tiles from the skip-th on, at most limit of them
+cudaError_t launch_rest(const DecompCtx &c, int j, int np, int est_active_rows, cudaStream_t s, int skip = 0,
+                        int limit = 1 << 30);
 int rest_tiles(const DecompCtx &c, int j, int np, int *tile_first);
 cudaError_t prepare_update_kernels();  // one-time kernel attributes (before any capture)
 cudaError_t prepare_panel_kernel();

@@ -36,15 +36,16 @@ namespace {
 // -------------------------------------------------------------------- k_next
 // Look-ahead of panel j over the rows still active before it (256 per CTA):
 //   d      = the row's word j with every panel < j applied (F[j%2]; W for j = 0)
-//   y      = d Zp (the paper's Y = D Z; 0 for the pivot rows of panels <= j) -> Y[j%4]
+//   y      = d Zp (the paper's Y = D Z; 0 for the pivot rows of panels <= j) -> Y[j % kRing]
 //   lambda = d Comp -> the row's L multipliers of panel j
 //   F[(j+1)%2] = word j+1 with panel j applied (W keeps word j+1 without it:
 //            panel j+1 may be reading it meanwhile and adds the update itself)
 //   W ^= y C on the words >= j+2 of the tile holding word j+2 and, when
 //            panel j opens a pair of panels (whose wide update starts after
 //            the tile holding word j+3), of that tile too
-//   the compacted list of the rows that stay active (act[j%4]: four lists, so
-//            that no list is rewritten while an update that reads it may run)
+//   the compacted list of the rows that stay active (act[j % kRing]: a ring
+//            of lists, so that no list is rewritten while an update that
+//            reads it may run)
 // and, in block 0, the pivot rows' L rows (T) and their echelon words on
 // the same columns.  (The second panel of a pair gets the first panel's
 // update on the tiles of the wide update inside that update, where its
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
     // this CTA's rows: entries [rb, re) of the rows still active before
     // panel j (every storage row for j = 0)
     const int cnt = j == 0 ? c.n : c.nact[j - 1];
-    const int32_t *lst = j == 0 ? nullptr : c.act + (int64_t)((j - 1) & 3) * c.n;
+    const int32_t *lst = j == 0 ? nullptr : c.act + (int64_t)((j - 1) % kRing) * c.n;
     const int rb = blockIdx.x * kNextRows, re = min(cnt, rb + kNextRows);
     const bool rows_here = rb < re;
     if (!rows_here && blockIdx.x != 0) return;
@@ -154,14 +155,14 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
     __syncthreads();
     if (kept_row >= 0) {
         const int pos = keep_warp[kNextThreads / 32] + keep_warp[warp] + __popc(kept_mask & ((1u << lane) - 1));
-        c.act[(int64_t)(j & 3) * c.n + pos] = kept_row;
+        c.act[(int64_t)(j % kRing) * c.n + pos] = kept_row;
     }
 
     // 3. compute and store
     const ulonglong2 *zc2 = reinterpret_cast<const ulonglong2 *>(zc);
     const ulonglong2 *tab2 = reinterpret_cast<const ulonglong2 *>(tab);
     const int ng = tables_used<kNextC>(r);
-    uint64_t *Ynext = c.Y + (int64_t)(j & 3) * c.n;
+    uint64_t *Ynext = c.Y + (int64_t)(j % kRing) * c.n;
     uint64_t yv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -284,15 +285,15 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
     // panels <= j + NP - 1 (the rows that are have y = 0)
     const int jl = j + NP - 1;
     const int nact = c.nact[jl];
-    const int32_t *__restrict__ act = c.act + (int64_t)(jl & 3) * c.n;
+    const int32_t *__restrict__ act = c.act + (int64_t)(jl % kRing) * c.n;
     // (with no row left the tiles are still visited when E is wanted: the
     // pivot rows' echelon words come from the same tables)
     const int nchunks = max((nact + kRestChunk - 1) / kRestChunk, c.Eint ? 1 : 0);
     const int64_t items = (int64_t)ntiles * nchunks;
     if (items == 0) return;
     const int64_t i0 = items * blockIdx.x / gridDim.x, i1 = items * (blockIdx.x + 1) / gridDim.x;
-    const uint64_t *__restrict__ Y0 = c.Y + (int64_t)(j & 3) * c.n;
-    const uint64_t *__restrict__ Y1 = c.Y + (int64_t)((j + 1) & 3) * c.n;
+    const uint64_t *__restrict__ Y0 = c.Y + (int64_t)(j % kRing) * c.n;
+    const uint64_t *__restrict__ Y1 = c.Y + (int64_t)((j + 1) % kRing) * c.n;
     uint64_t *__restrict__ W = c.W;
     const int ng0 = tables_used<C>(r0), ng1 = NP == 2 ? tables_used<C>(r1) : 0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -454,10 +455,12 @@ int rest_tiles(const DecompCtx &c, int j, int np, int *tile_first)
     return tiles > 0 ? tiles : 0;
 }
 
-cudaError_t launch_rest(const DecompCtx &c, int j, int np, int est_active_rows, cudaStream_t s)
+cudaError_t launch_rest(const DecompCtx &c, int j, int np, int est_active_rows, cudaStream_t s, int skip, int limit)
 {
     int tile_first = 0;
-    const int ntiles = rest_tiles(c, j, np, &tile_first);
+    int ntiles = rest_tiles(c, j, np, &tile_first) - skip;
+    tile_first += skip;
+    if (ntiles > limit) ntiles = limit;
     if (ntiles <= 0) return cudaSuccess;
     const int nchunks = (c.n + kRestChunk - 1) / kRestChunk;
     const int64_t items = (int64_t)ntiles * nchunks;

@@ -9,7 +9,7 @@
 // entry point needs nothing but the input matrix and the output word.
 //
 // The scratch is one file-scope __device__ array (kNoallocBytes, about
-// 2.4 MiB).  Every GPU that loads the library holds it until the process
+// 2.7 MiB).  Every GPU that loads the library holds it until the process
 // exits.  Host code must not use the array's name as a device address:
 // the first call on each device, with that device current, asks the runtime
 // for the array's device address (cudaGetSymbolAddress) and keeps it.  Do
@@ -34,9 +34,9 @@ constexpr size_t align_na(size_t x) { return (x + kAlignNA - 1) / kAlignNA * kAl
 // layout of the static scratch (worst case n = m = 4096)
 constexpr size_t kOffW = 0;
 constexpr size_t kOffY = kOffW + align_na((size_t)kNoallocMaxDim * kNoallocMu * 8);
-constexpr size_t kOffF = kOffY + align_na((size_t)kNoallocMaxDim * 4 * 8);
+constexpr size_t kOffF = kOffY + align_na((size_t)kNoallocMaxDim * kRing * 8);
 constexpr size_t kOffAct = kOffF + align_na((size_t)kNoallocMaxDim * 2 * 8);
-constexpr size_t kOffNact = kOffAct + align_na((size_t)kNoallocMaxDim * 4 * 4);
+constexpr size_t kOffNact = kOffAct + align_na((size_t)kNoallocMaxDim * kRing * 4);
 constexpr size_t kOffPP = kOffNact + align_na((size_t)kNoallocMu * 4);
 constexpr size_t kOffInfo = kOffPP + align_na((size_t)kNoallocMaxDim * 4);
 constexpr size_t kOffPerm = kOffInfo + align_na((size_t)kNoallocMu * sizeof(PanelInfo));
