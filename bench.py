@@ -49,8 +49,9 @@ TILE_WORDS = 4  # words per column tile of the library's working copy
 
 
 def rest_launch_bytes(n: int, mu: int, rj: np.ndarray, pairs: bool, lookups: bool = False) -> list:
-    """Algorithmic bytes of every k_rest launch of one decomposition: one
-    read and one write (16 B) of every word the launch updates.  Panel j's
+    """Algorithmic bytes of every wide update of one decomposition (a pair's
+    head and body launches together): one read and one write (16 B) of every
+    word the update touches.  Panel j's
     wide update (or that of the pair j, j+1, j even) covers the rows that are
     not pivots of the panels it applies and the column tiles after the one
     holding word j+2 (j+3 for a pair); a launch happens when its panels have

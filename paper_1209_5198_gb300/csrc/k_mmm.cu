@@ -173,26 +173,28 @@ cudaError_t launch_mmm(MmmCtx c, cudaStream_t s)
         return cudaMemset2DAsync(c.C, (size_t)c.ldc * 8, 0, (size_t)c.n * 8, (size_t)c.mw, s);
     }
     // Cost model: whole waves of CTAs, each CTA's time proportional to its
-    // slices of B times (its row groups + the per-slice overhead); an
-    // inner-dimension split costs a few percent (zeroing C, atomics).  Pick
-    // the cheapest shape and split.
+    // slices of B times (its row groups + the per-slice overhead of table
+    // build, barriers and loads: about four row groups); two resident CTAs
+    // share an SM, each at half rate.  Splitting the inner dimension evens
+    // out the last wave (it zeroes C first and combines the parts by atomics
+    // in L2: more DRAM traffic, but the kernel is bound by shared memory); a
+    // split keeps at least min(32, max(8, kw/8)) slices per CTA.  Fitted to
+    // measured times of every shape and of 1..32 splits at n = 8192..32768.
     const int kw = (c.k + 63) / 64;
     const int64_t tiles = (c.mw + kTileWords - 1) / kTileWords;
+    const int minper = kw / 8 < 8 ? 8 : (kw / 8 > 32 ? 32 : kw / 8);
     double best = 1e300;
     int bi = 0, bsplit = 1;
     for (int i = 0; i < (int)(sizeof(kShapes) / sizeof(kShapes[0])); ++i) {
         const int64_t rows_per_cta = (int64_t)kRowsPerWarp * kPWarps * kShapes[i].u;
         const int64_t blocks = (c.n + rows_per_cta - 1) / rows_per_cta;
         const int64_t slots = (int64_t)kShapes[i].minb * sm_count();
-        for (int splits = 1; splits <= 64 && (splits == 1 || kw / splits >= 8); ++splits) {
+        for (int splits = 1; splits <= 64 && (splits == 1 || kw / splits >= minper); ++splits) {
             const int per = (kw + splits - 1) / splits;
             const int64_t ctas = tiles * blocks * ((kw + per - 1) / per);
             const int64_t waves = (ctas + slots - 1) / slots;
-            // two resident CTAs share an SM (each at half rate); a slice's
-            // table build, barriers and loads cost about four row groups
-            // (fitted to the measured times of the four shapes)
             const double share = kShapes[i].minb == 2 ? 2.0 : 1.0;
-            const double cost = (double)waves * per * (kShapes[i].u + 4.0) * share * (splits > 1 ? 1.05 : 1.0);
+            const double cost = (double)waves * per * (kShapes[i].u + 4.0) * share * (splits > 1 ? 1.02 : 1.0);
             if (cost < best) {
                 best = cost;
                 bi = i;
