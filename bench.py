@@ -252,6 +252,9 @@ def run_batched(args):
     count = args.batch
     lib = gf2.load()
     stream = torch.cuda.current_stream()
+    # the table size per matrix size, measured by the library's autotuner
+    tune = {}
+    c8_from = gf2.batched_autotune(2048, times=tune)
     results = {}
     for p, seed in ((0.5, 0x1209), (0.1, 0x5198)):
         mats = batch_matrices(count, p, seed, dev)
@@ -281,6 +284,15 @@ def run_batched(args):
         e1.record(stream)
         torch.cuda.synchronize()
         ms_batch = e0.elapsed_time(e1) / args.steps
+        # the same batch with 4-bit tables for every matrix (no autotuned split)
+        gf2.set_batched_c8_from(1 << 62)
+        ws4 = torch.empty(lib.gf2_decompose_batched_workspace_bytes(count, (ctypes.c_int64 * count)(*ns),
+                                                                    (ctypes.c_int64 * count)(*ms), 1),
+                          dtype=torch.uint8, device=dev)
+        step4 = lambda: gf2.gf2_decompose_batched(As, perms, pivs, ranks, Ls, Es, workspace=ws4, stream=stream)
+        step4()
+        ms_c4 = time_calls(step4, args.steps, stream)
+        gf2.set_batched_c8_from(c8_from)
         rk = ranks.cpu().numpy()
         ops = sum(bitops(n, m, pv.cpu().numpy()[: int(r)]) for (_, n, m), pv, r in zip(mats, pivs, rk))
         # the same matrices one plain gf2_decompose call after another
@@ -292,7 +304,8 @@ def run_batched(args):
             gf2.gf2_decompose(As[i], perms[i], pivs[i], rk1, Ls[i], Es[i], workspace=wsp, stream=stream)
         torch.cuda.synchronize()
         ms_loop = (time.perf_counter() - t0) * 1000
-        results[p] = dict(ms=ms_batch, ops=ops, ms_loop=ms_loop, deficient=int(sum(1 for (w, n, m), r in zip(mats, rk) if r < min(n, m))))
+        results[p] = dict(ms=ms_batch, ms_c4=ms_c4, ops=ops, ms_loop=ms_loop,
+                          deficient=int(sum(1 for (w, n, m), r in zip(mats, rk) if r < min(n, m))))
     total_ms = sum(r["ms"] for r in results.values())
     total_loop = sum(r["ms_loop"] for r in results.values())
     line = {
@@ -302,6 +315,9 @@ def run_batched(args):
         "config": {"workload": f"batched: 2 batches (p = 0.5, 0.1) of {count} matrices, rows and cols uniform "
                                f"in [64, 2048], every second one rank-deficient; one step = both batches",
                    "per_batch_ms": {str(p): r["ms"] for p, r in results.items()},
+                   "c8_from": c8_from,
+                   "autotune_ms_4bit_8bit": {str(d): v for d, v in tune.items()},
+                   "per_batch_ms_4bit_tables_only": {str(p): r["ms_c4"] for p, r in results.items()},
                    "rank_deficient": {str(p): r["deficient"] for p, r in results.items()}},
         "bitops_per_s": sum(r["ops"] for r in results.values()) / (total_ms / 1000),
         "plain_loop": {"value": 2 * count / (total_loop / 1000), "unit": "matrices/s",

@@ -186,7 +186,9 @@ int gf2_decompose_host(int64_t n, int64_t m, const uint64_t *A_host, int64_t lda
  *   L, E        arrays of count descriptors as gf2_decompose (both or neither;
  *               NULL: rank, perm and pivcols only)
  * The descriptor arrays are read on the host during the call.  The call
- * synchronises the stream once (it reads the padding status back).
+ * synchronises the stream once (it reads the padding status back).  The
+ * workspace depends on the table-size split (gf2_batched_set_c8_from):
+ * size it after setting that.
  * Errors: GF2_ERR_ARG, GF2_ERR_SHAPE, GF2_ERR_PADDING, GF2_ERR_NOMEM,
  * GF2_ERR_UNSUPPORTED (a matrix with more than 4096 rows or columns),
  * GF2_ERR_CUDA.
@@ -195,6 +197,21 @@ size_t gf2_decompose_batched_workspace_bytes(int count, const int64_t *n, const 
 int gf2_decompose_batched(int count, const gf2_mat *A, int32_t *const *perm, int32_t *const *pivcols,
                           int64_t *rank, const gf2_mat *L, const gf2_mat *E, unsigned flags,
                           void *workspace, size_t ws_bytes, void *stream);
+
+/* The batched kernel's table size: matrices whose larger dimension is at
+ * least c8_from use Four Russians tables of 8 bits (64 KB per CTA, three CTAs
+ * per SM), the others tables of 4 bits (8 KB, four CTAs per SM); a batch with
+ * both runs the two kernels side by side.  gf2_batched_autotune times both
+ * on batches of square d x d matrices, d = 128, 256, ... up to max_dim (at
+ * most 4096), and sets c8_from to the smallest d from which 8-bit tables are
+ * faster there and at every larger d tried (2^62: never); *c8_from receives
+ * it, and times_ms (may be NULL; 2 floats per d tried, smallest d first)
+ * the measured batch times with 4- and 8-bit tables.  It allocates up to a
+ * few GB, synchronises the stream and frees it all.  gf2_batched_set_c8_from sets it directly (default 1024).  A
+ * process-wide setting.  Errors: GF2_ERR_ARG, GF2_ERR_NOMEM, GF2_ERR_CUDA. */
+int gf2_batched_autotune(int64_t max_dim, int64_t *c8_from, float *times_ms, void *stream);
+int gf2_batched_set_c8_from(int64_t dim);
+int64_t gf2_batched_c8_from(void);
 
 /* ------------------------------------------------------------------------
  * Linear systems A X = B over F2 from the factors of P*A = L*E (the use of

@@ -72,6 +72,11 @@ def load() -> ctypes.CDLL:
     lib.gf2_mmm_workspace_bytes.argtypes = [I64, I64, I64, ctypes.c_uint]
     lib.gf2_mmm.restype = ctypes.c_int
     lib.gf2_mmm.argtypes = [M, M, M, ctypes.c_int, ctypes.c_uint, P, S, P]
+    lib.gf2_batched_autotune.restype = ctypes.c_int
+    lib.gf2_batched_autotune.argtypes = [I64, ctypes.POINTER(I64), P, P]
+    lib.gf2_batched_set_c8_from.restype = ctypes.c_int
+    lib.gf2_batched_set_c8_from.argtypes = [I64]
+    lib.gf2_batched_c8_from.restype = I64
     lib.gf2_mmm_autotune.restype = ctypes.c_int
     lib.gf2_mmm_autotune.argtypes = [I64, ctypes.POINTER(I64), P]
     lib.gf2_mmm_set_strassen_cutoff.restype = ctypes.c_int
@@ -335,6 +340,32 @@ def mmm_autotune(max_dim: int = 32768, stream=None) -> int:
     out = ctypes.c_int64(0)
     _check(load().gf2_mmm_autotune(int(max_dim), ctypes.byref(out), _stream(stream)), "gf2_mmm_autotune")
     return int(out.value)
+
+
+def batched_autotune(max_dim: int = 4096, stream=None, times: dict | None = None) -> int:
+    """Times the batched kernel with 4- and 8-bit tables on this device and
+    sets the size from which matrices take the 8-bit tables (returned).
+    `times`, when given, receives {d: (ms with 4-bit, ms with 8-bit)}."""
+    out = ctypes.c_int64(0)
+    dims = []
+    d = 128
+    while d <= min(int(max_dim), 4096):
+        dims.append(d)
+        d *= 2
+    buf = (ctypes.c_float * (2 * max(1, len(dims))))()
+    _check(load().gf2_batched_autotune(int(max_dim), ctypes.byref(out), buf, _stream(stream)), "gf2_batched_autotune")
+    if times is not None:
+        for i, d in enumerate(dims):
+            times[d] = (float(buf[2 * i]), float(buf[2 * i + 1]))
+    return int(out.value)
+
+
+def set_batched_c8_from(dim: int) -> None:
+    _check(load().gf2_batched_set_c8_from(int(dim)), "gf2_batched_set_c8_from")
+
+
+def batched_c8_from() -> int:
+    return int(load().gf2_batched_c8_from())
 
 
 def set_strassen_cutoff(cutoff: int) -> None:

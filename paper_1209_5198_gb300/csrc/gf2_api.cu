@@ -748,7 +748,7 @@ namespace {
 constexpr int64_t kBatchMaxDim = 4096;
 
 struct BatchLayout {
-    int grid;
+    int grid, c;
     int64_t nmax, mumax, kmax_max;
     int64_t off_y, off_info, off_pivpanel, off_lint, off_eint, slice_words;
     size_t off_items, off_order, off_sync, off_scratch, total;
@@ -756,9 +756,10 @@ struct BatchLayout {
 
 int64_t round_words(int64_t w) { return (w + 31) / 32 * 32; }  // 256-byte slices
 
-int batch_layout(int count, const int64_t *n, const int64_t *m, bool factors, BatchLayout *L)
+int batch_layout(int count, const int64_t *n, const int64_t *m, bool factors, int c, BatchLayout *L)
 {
     BatchLayout d{};
+    d.c = c;
     for (int i = 0; i < count; ++i) {
         d.nmax = n[i] > d.nmax ? n[i] : d.nmax;
         d.mumax = words_of(m[i]) > d.mumax ? words_of(m[i]) : d.mumax;
@@ -768,7 +769,7 @@ int batch_layout(int count, const int64_t *n, const int64_t *m, bool factors, Ba
     int dev = 0, sms = 1;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return GF2_ERR_CUDA;
-    const int want = sms * batch_ctas_per_sm();
+    const int want = sms * batch_ctas_per_sm(c);
     d.grid = count < want ? (count > 0 ? count : 1) : want;
     const int64_t nm = d.nmax > 0 ? d.nmax : 1;
     const int64_t ldw = round_up_tiles(d.mumax > 0 ? d.mumax : 1);
@@ -790,6 +791,68 @@ int batch_layout(int count, const int64_t *n, const int64_t *m, bool factors, Ba
     return GF2_OK;
 }
 
+// Matrices whose larger dimension is at least this go to the c = 8 kernel,
+// the others to the c = 4 one (gf2_batched_autotune measures it).
+std::atomic<int64_t> g_batch_c8_from{1024};
+
+// A batch split by table size: class 0 (c = 4) and class 1 (c = 8), each with
+// its own items, order, counter and scratch, one status word for both.
+struct BatchPlan {
+    std::vector<int> idx[2];
+    BatchLayout lay[2];
+    size_t off[2];
+    size_t flag_off, total;
+};
+
+int batch_plan(int count, const int64_t *n, const int64_t *m, bool factors, int64_t c8_from, BatchPlan *P)
+{
+    for (int i = 0; i < count; ++i) P->idx[(n[i] > m[i] ? n[i] : m[i]) >= c8_from ? 1 : 0].push_back(i);
+    size_t o = 0;
+    for (int cls = 0; cls < 2; ++cls) {
+        P->off[cls] = o;
+        P->lay[cls] = BatchLayout{};
+        const size_t k = P->idx[cls].size();
+        if (!k) continue;
+        std::vector<int64_t> ns(k), ms(k);
+        for (size_t t = 0; t < k; ++t) {
+            ns[t] = n[P->idx[cls][t]];
+            ms[t] = m[P->idx[cls][t]];
+        }
+        const int st = batch_layout((int)k, ns.data(), ms.data(), factors, cls ? 8 : 4, &P->lay[cls]);
+        if (st) return st;
+        o += align_up(P->lay[cls].total);
+    }
+    P->flag_off = o;
+    P->total = o + kAlign;
+    return GF2_OK;
+}
+
+// A second stream for the c = 4 kernel beside the c = 8 one (per device),
+// with the events that fork it from and join it to the caller's stream;
+// the mutex is held from the fork to the join's enqueue.
+struct BatchSide {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+std::mutex g_batch_side_mutex;
+std::vector<BatchSide> g_batch_side;
+
+int batch_side(BatchSide **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GF2_ERR_CUDA;
+    if ((int)g_batch_side.size() <= dev) g_batch_side.resize(dev + 1);
+    BatchSide &b = g_batch_side[dev];
+    if (!b.s) {
+        if (cudaStreamCreateWithFlags(&b.s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b.join, cudaEventDisableTiming) != cudaSuccess)
+            return GF2_ERR_CUDA;
+    }
+    *out = &b;
+    return GF2_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -797,9 +860,9 @@ extern "C" {
 size_t gf2_decompose_batched_workspace_bytes(int count, const int64_t *n, const int64_t *m, int want_factors)
 {
     if (count < 0 || (count > 0 && (!n || !m))) return 0;
-    BatchLayout d{};
-    if (batch_layout(count, n, m, want_factors != 0, &d) != GF2_OK) return 0;
-    return d.total;
+    BatchPlan P;
+    if (batch_plan(count, n, m, want_factors != 0, g_batch_c8_from.load(), &P) != GF2_OK) return 0;
+    return P.total;
 }
 
 int gf2_decompose_batched(int count, const gf2_mat *A, int32_t *const *perm, int32_t *const *pivcols, int64_t *rank,
@@ -838,48 +901,39 @@ size_t decompose_batched_items_bytes(int count, const BatchItem *items, bool fac
         ns[i] = items[i].n;
         ms[i] = items[i].m;
     }
-    BatchLayout d{};
-    if (batch_layout(count, ns.data(), ms.data(), factors, &d) != GF2_OK) return 0;
-    return d.total;
+    BatchPlan P;
+    if (batch_plan(count, ns.data(), ms.data(), factors, g_batch_c8_from.load(), &P) != GF2_OK) return 0;
+    return P.total;
 }
 
-// The batched decomposition of items already checked (each n, m <= 4096).
-// With GF2_NOCHECK the call does not synchronise the stream.
-int decompose_batched_items(int count, const BatchItem *items, bool factors, unsigned flags, void *workspace,
-                            size_t ws_bytes, void *stream)
+// Enqueues one class of a batch (its items, largest work first) on stream s.
+static int enqueue_batch_class(const BatchPlan &P, int cls, const BatchItem *items, bool factors, unsigned flags, char *ws,
+                        cudaStream_t s)
 {
-    if (count <= 0) return GF2_OK;
-    std::vector<int64_t> ns(count), ms(count);
-    for (int i = 0; i < count; ++i) {
-        ns[i] = items[i].n;
-        ms[i] = items[i].m;
-    }
-    BatchLayout d{};
-    int st = batch_layout(count, ns.data(), ms.data(), factors, &d);
-    if (st) return st;
-    void *ws = nullptr;
-    st = get_workspace(workspace, ws_bytes, d.total, &ws);
-    if (st) return st;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    char *p = static_cast<char *>(ws);
-    // largest work first, so that the CTAs finish together
+    const std::vector<int> &idx = P.idx[cls];
+    const int count = (int)idx.size();
+    if (!count) return GF2_OK;
+    const BatchLayout &d = P.lay[cls];
+    char *p = ws + P.off[cls];
+    std::vector<BatchItem> sub(count);
+    for (int t = 0; t < count; ++t) sub[t] = items[idx[t]];
     std::vector<int32_t> order(count);
     for (int i = 0; i < count; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        const double wa = (double)ns[a] * words_of(ms[a]) * (ns[a] < ms[a] ? ns[a] : ms[a]);
-        const double wb = (double)ns[b] * words_of(ms[b]) * (ns[b] < ms[b] ? ns[b] : ms[b]);
-        return wa > wb;
-    });
+    auto work = [&](int t) {
+        const int64_t n = sub[t].n, m = sub[t].m;
+        return (double)n * words_of(m) * (n < m ? n : m);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
     // (copies from pageable memory: the calls return once the host arrays
     // have been staged)
-    CK(cudaMemcpyAsync(p + d.off_items, items, sizeof(BatchItem) * count, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(p + d.off_items, sub.data(), sizeof(BatchItem) * count, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(p + d.off_order, order.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(p + d.off_sync, 0, kAlign, s));
     BatchCtx b{};
     b.items = reinterpret_cast<const BatchItem *>(p + d.off_items);
     b.order = reinterpret_cast<const int32_t *>(p + d.off_order);
     b.next_item = reinterpret_cast<int32_t *>(p + d.off_sync);
-    b.err = reinterpret_cast<uint32_t *>(p + d.off_sync + 64);
+    b.err = reinterpret_cast<uint32_t *>(ws + P.flag_off);
     b.scratch = reinterpret_cast<uint64_t *>(p + d.off_scratch);
     b.scratch_words = d.slice_words;
     b.off_y = d.off_y;
@@ -890,9 +944,55 @@ int decompose_batched_items(int count, const BatchItem *items, bool factors, uns
     b.count = count;
     b.factors = factors ? 1 : 0;
     b.check = (flags & GF2_NOCHECK) ? 0 : 1;
-    LAUNCH(GF2_KCLASS_PANEL, launch_batch(b, d.grid, s));
+    LAUNCH(GF2_KCLASS_PANEL, launch_batch(b, d.grid, d.c, s));
+    return GF2_OK;
+}
+
+static int batched_with(int count, const BatchItem *items, bool factors, unsigned flags, void *workspace,
+                        size_t ws_bytes, cudaStream_t s, int64_t c8_from)
+{
+    if (count <= 0) return GF2_OK;
+    std::vector<int64_t> ns(count), ms(count);
+    for (int i = 0; i < count; ++i) {
+        ns[i] = items[i].n;
+        ms[i] = items[i].m;
+    }
+    BatchPlan P;
+    int st = batch_plan(count, ns.data(), ms.data(), factors, c8_from, &P);
+    if (st) return st;
+    void *ws = nullptr;
+    st = get_workspace(workspace, ws_bytes, P.total, &ws);
+    if (st) return st;
+    char *p = static_cast<char *>(ws);
+    CK(cudaMemsetAsync(p + P.flag_off, 0, kAlign, s));
+    if (!P.idx[0].empty() && !P.idx[1].empty()) {
+        // both classes: the c = 8 kernel on s, the c = 4 kernel beside it
+        std::lock_guard<std::mutex> lock(g_batch_side_mutex);
+        BatchSide *side = nullptr;
+        st = batch_side(&side);
+        if (st) return st;
+        CK(cudaEventRecord(side->fork, s));
+        CK(cudaStreamWaitEvent(side->s, side->fork, 0));
+        st = enqueue_batch_class(P, 1, items, factors, flags, p, s);
+        if (!st) st = enqueue_batch_class(P, 0, items, factors, flags, p, side->s);
+        CK(cudaEventRecord(side->join, side->s));
+        CK(cudaStreamWaitEvent(s, side->join, 0));
+        if (st) return st;
+    } else {
+        st = enqueue_batch_class(P, P.idx[1].empty() ? 0 : 1, items, factors, flags, p, s);
+        if (st) return st;
+    }
     if (flags & GF2_NOCHECK) return GF2_OK;
-    return check_flag(b.err, s);  // the padding status
+    return check_flag(reinterpret_cast<uint32_t *>(p + P.flag_off), s);  // the padding status
+}
+
+// The batched decomposition of items already checked (each n, m <= 4096).
+// With GF2_NOCHECK the call does not synchronise the stream.
+int decompose_batched_items(int count, const BatchItem *items, bool factors, unsigned flags, void *workspace,
+                            size_t ws_bytes, void *stream)
+{
+    return batched_with(count, items, factors, flags, workspace, ws_bytes, static_cast<cudaStream_t>(stream),
+                        g_batch_c8_from.load());
 }
 
 void add_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -1205,6 +1305,102 @@ int gf2_timing_read(int kernel_class, double *total_ms, int64_t *launches)
     }
     *total_ms = sum;
     *launches = cnt;
+    return GF2_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ batched autotuner
+extern "C" {
+
+int gf2_batched_set_c8_from(int64_t dim)
+{
+    if (dim < 1) return GF2_ERR_ARG;
+    g_batch_c8_from.store(dim);
+    return GF2_OK;
+}
+
+int64_t gf2_batched_c8_from(void) { return g_batch_c8_from.load(); }
+
+int gf2_batched_autotune(int64_t max_dim, int64_t *c8_from, float *times_ms, void *stream)
+{
+    if (!c8_from || max_dim < 128) return GF2_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return GF2_ERR_CUDA;
+    const int64_t top = max_dim < kBatchMaxDim ? max_dim : kBatchMaxDim;
+    std::vector<int64_t> dims;
+    for (int64_t d = 128; d <= top; d *= 2) dims.push_back(d);
+    // time both table sizes on a batch of square d x d matrices (random
+    // words), the smallest d first; c = 8 wins from the first d at which it
+    // is faster there and at every larger d
+    std::vector<float> t4(dims.size(), 0.f), t8(dims.size(), 0.f);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return GF2_ERR_CUDA;
+    int st = GF2_OK;
+    for (size_t di = 0; di < dims.size() && st == GF2_OK; ++di) {
+        const int64_t d = dims[di], mu = d / 64;
+        const int count = (int)(d >= 2048 ? 2 * sms : 4 * sms);
+        const size_t mat = (size_t)d * mu * 8;
+        std::vector<BatchItem> items(count);
+        std::vector<int64_t> ns(count, d), ms(count, d);
+        BatchPlan P4, P8;
+        if ((st = batch_plan(count, ns.data(), ms.data(), true, int64_t(1) << 62, &P4)) != GF2_OK) break;
+        if ((st = batch_plan(count, ns.data(), ms.data(), true, 0, &P8)) != GF2_OK) break;
+        const size_t wsb = P4.total > P8.total ? P4.total : P8.total;
+        const size_t per = 3 * align_up(mat) + align_up((size_t)d * 4) * 2 + kAlign;  // A, L, E, perm, pivcols
+        char *buf = nullptr;
+        if (cudaMalloc(&buf, per * count + (size_t)count * 8 + wsb) != cudaSuccess) {
+            cudaGetLastError();
+            st = GF2_ERR_NOMEM;
+            break;
+        }
+        int64_t *ranks = reinterpret_cast<int64_t *>(buf + per * count);
+        char *ws = buf + per * count + (size_t)count * 8;
+        for (int i = 0; i < count; ++i) {
+            char *q = buf + per * i;
+            uint64_t *A = reinterpret_cast<uint64_t *>(q);
+            uint64_t *L = reinterpret_cast<uint64_t *>(q + align_up(mat));
+            uint64_t *E = reinterpret_cast<uint64_t *>(q + 2 * align_up(mat));
+            int32_t *perm = reinterpret_cast<int32_t *>(q + 3 * align_up(mat));
+            int32_t *piv = perm + align_up((size_t)d * 4) / 4;
+            items[i] = BatchItem{A, d, (int32_t)d, (int32_t)d, perm, piv, ranks + i, L, d, E, d};
+            k_fill_words<<<256, 256, 0, s>>>(A, (int64_t)(mat / 8), 0x5198ull * 1000003ull + (uint64_t)i);
+        }
+        if (cudaGetLastError() != cudaSuccess) st = GF2_ERR_CUDA;
+        g_launches.fetch_add(count, std::memory_order_relaxed);
+        for (int variant = 0; variant < 2 && st == GF2_OK; ++variant) {
+            const int64_t from = variant ? 0 : (int64_t(1) << 62);
+            float best = 1e30f;
+            for (int r = 0; r < 3 && st == GF2_OK; ++r) {  // the first run warms up
+                if (cudaEventRecord(e0, s) != cudaSuccess) st = GF2_ERR_CUDA;
+                if (st == GF2_OK) st = gf2::batched_with(count, items.data(), true, GF2_NOCHECK, ws, wsb, s, from);
+                if (st == GF2_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+                    st = GF2_ERR_CUDA;
+                float ms = 0;
+                if (st == GF2_OK && r > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) best = ms;
+            }
+            (variant ? t8 : t4)[di] = best;
+        }
+        cudaStreamSynchronize(s);
+        cudaFree(buf);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != GF2_OK) return st;
+    int64_t chosen = int64_t(1) << 62;
+    for (size_t di = dims.size(); di-- > 0;) {
+        if (t8[di] < t4[di]) chosen = dims[di];
+        else break;
+    }
+    if (times_ms)
+        for (size_t di = 0; di < dims.size(); ++di) {
+            times_ms[2 * di] = t4[di];
+            times_ms[2 * di + 1] = t8[di];
+        }
+    g_batch_c8_from.store(chosen);
+    *c8_from = chosen;
     return GF2_OK;
 }
 

@@ -189,7 +189,7 @@ cudaError_t launch_xor(uint64_t *D, int64_t ldd, const uint64_t *X, int64_t ldx,
 cudaError_t launch_solve(const SolveCtx &c, cudaStream_t s);  // one cooperative launch
 // one CTA per item, items[0] first; max_n: the largest n among the items
 cudaError_t launch_serve_solve(const ServeItem *items, int count, int32_t *next, int64_t max_n, cudaStream_t s);
-int batch_ctas_per_sm();
+int batch_ctas_per_sm(int c);  // c = 4 or 8: the batched kernel's table size
 // the product on the tensor cores (k < 2^24): A8, B8 are n_pad x k_pad and
 // m_pad x k_pad bytes (dimensions rounded up to mma_pad)
 int64_t mma_pad(int64_t x);
@@ -197,7 +197,7 @@ cudaError_t launch_mma_product(const uint64_t *A, int64_t lda, const uint64_t *B
                                int64_t ldc, int n, int k, int m, int accumulate, uint8_t *A8, uint8_t *B8,
                                cudaStream_t s);
 cudaError_t launch_check_last_block(const uint64_t *last, int rows, uint64_t mask, uint32_t *err, cudaStream_t s);
-cudaError_t launch_batch(const BatchCtx &b, int grid, cudaStream_t s);
+cudaError_t launch_batch(const BatchCtx &b, int grid, int c, cudaStream_t s);
 
 // ---- host helpers shared by the entry points (gf2_api.cu)
 // the batched decomposition of checked items (each n, m <= 4096); with

@@ -9,23 +9,38 @@
 // block j (panel_core.cuh, the same code as the panel kernel), then, with all
 // four warps, y = d Zp and lambda = d Comp for every row, the L multipliers,
 // and the update W ^= y C of every word after column block j by Four Russians
-// tables (c = 4) of the pivot rows, tile by tile.  The working copy lives in a
-// per-CTA slice of the workspace (tiled as in the plain decomposition); the
+// tables of c bits of the pivot rows, tile by tile.  The working copy lives in
+// a per-CTA slice of the workspace (tiled as in the plain decomposition); the
 // factors are written to the caller's column blocks at the end.
+//
+// Two table sizes: c = 4 (8 KB of tables, up to four CTAs per SM: the small
+// matrices, whose panel steps are latency-bound, overlap best) and c = 8
+// (64 KB of tables sharing shared memory with the panel step's state, three
+// CTAs per SM, half the lookups: the larger matrices, whose updates dominate).
+// The host routes each matrix by its size (gf2_batched_autotune measures the
+// crossover on the device) and runs the two kernels side by side.
 #include "m4rm_core.cuh"
 #include "panel_core.cuh"
 
 namespace gf2 {
 namespace {
 
-constexpr int kBatchC = 4;
 constexpr int kBatchU = 2;  // row groups of 16 rows per warp and pass
 
-struct BatchShared {
-    PanelShared panel;
-    __align__(16) uint64_t tab[Tabs<kBatchC>::Words];
+// the update's tables and rows (used between panel steps only)
+template <int C>
+struct BatchUpdateShared {
+    __align__(16) uint64_t tab[Tabs<C>::Words];
     uint64_t crow[64 * kTileWords];
     uint64_t zc[16 * 16 * 2];  // [g][x][y, lambda]
+};
+
+template <int C>
+struct BatchShared {
+    union {
+        PanelShared panel;
+        BatchUpdateShared<C> upd;
+    };
     int item;
     int32_t rank;
 };
@@ -59,7 +74,8 @@ __device__ void batch_ingest(const BatchItem &it, const DecompCtx &c, uint32_t *
 }
 
 // 2b. the update of panel j by the whole CTA
-__device__ void batch_update(const DecompCtx &c, int j, BatchShared &bs)
+template <int C>
+__device__ void batch_update(const DecompCtx &c, int j, BatchUpdateShared<C> &bs)
 {
     const PanelInfo *pi = panel_info(c, j);
     const int R = pi->R, r = pi->r;
@@ -114,7 +130,7 @@ __device__ void batch_update(const DecompCtx &c, int j, BatchShared &bs)
     }
     // W ^= y C on every word after column j, tile by tile
     const int rs = lane / kLanesPerRow, wp = lane % kLanesPerRow, swp = rs & 3;
-    const int ng = tables_used<kBatchC>(r);
+    const int ng = tables_used<C>(r);
     const int ntiles = (c.mu + kTileWords - 1) / kTileWords;
     const ulonglong2 *tab2 = reinterpret_cast<const ulonglong2 *>(bs.tab);
     for (int tile = (j + 1) / kTileWords; tile < ntiles; ++tile) {
@@ -123,9 +139,9 @@ __device__ void batch_update(const DecompCtx &c, int j, BatchShared &bs)
         __syncthreads();
         load_pivot_rows<kPanelThreads>(c, pi->prow, r, q0, bs.crow);
         __syncthreads();
-        build_tables<kBatchC, kPanelThreads>(bs.tab, bs.crow);
+        build_tables<C, kPanelThreads>(bs.tab, bs.crow);
         __syncthreads();
-        if (c.Eint) echelon_rows<kBatchC, kPanelThreads>(c, pi, R, r, q0, j + 1, ng, bs.tab);
+        if (c.Eint) echelon_rows<C, kPanelThreads>(c, pi, R, r, q0, j + 1, ng, bs.tab);
         // (every lane runs the loop; a lane whose words precede column j+1 skips its loads and stores)
         constexpr int STEP = kRowsPerWarp * kBatchU * (kPanelThreads / 32);
         for (int base = warp * kRowsPerWarp * kBatchU; base < n; base += STEP) {
@@ -140,7 +156,7 @@ __device__ void batch_update(const DecompCtx &c, int j, BatchShared &bs)
 #pragma unroll
             for (int u = 0; u < kBatchU; ++u) {
                 if (!y[u]) continue;
-                lookup<kBatchC>(tab2, y[u], wp, swp, ng, a[u]);
+                lookup<C>(tab2, y[u], wp, swp, ng, a[u]);
                 uint64_t *dst = c.W + widx(c, base + u * kRowsPerWarp + rs, col);
                 if (live_lo) *reinterpret_cast<ulonglong2 *>(dst) = a[u];
                 else dst[1] = a[u].y;
@@ -172,9 +188,11 @@ __device__ void batch_finish(const BatchItem &it, const DecompCtx &c, int rank)
     }
 }
 
+template <int C>
 __global__ void __launch_bounds__(kPanelThreads, 4) k_batch(BatchCtx b)
 {
-    __shared__ BatchShared bs;
+    extern __shared__ __align__(16) uint8_t batch_smem[];
+    BatchShared<C> &bs = *reinterpret_cast<BatchShared<C> *>(batch_smem);
     const int tid = threadIdx.x;
     uint64_t *base = scratch_of(b, blockIdx.x);
     for (;;) {
@@ -219,25 +237,53 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_batch(BatchCtx b)
             panel_block(c, j, bs.panel);
             __syncthreads();
             rank += panel_info(c, j)->r;
-            batch_update(c, j, bs);
+            batch_update<C>(c, j, bs.upd);  // (reuses the panel step's shared memory)
+            __syncthreads();
         }
         batch_finish(it, c, rank);
         __syncthreads();
     }
 }
 
-}  // namespace
-
-int batch_ctas_per_sm()
+template <int C>
+cudaError_t prepare_batch()
 {
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BatchShared<C>));
+    if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+    return e;
+}
+
+template <int C>
+int ctas_per_sm()
+{
+    if (prepare_batch<C>() != cudaSuccess) return 1;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kPanelThreads, 0) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<C>, kPanelThreads, sizeof(BatchShared<C>)) !=
+        cudaSuccess)
+        return 1;
     return per_sm > 0 ? per_sm : 1;
 }
 
-cudaError_t launch_batch(const BatchCtx &b, int grid, cudaStream_t s)
+}  // namespace
+
+int batch_ctas_per_sm(int c) { return c == 8 ? ctas_per_sm<8>() : ctas_per_sm<4>(); }
+
+cudaError_t launch_batch(const BatchCtx &b, int grid, int c, cudaStream_t s)
 {
-    k_batch<<<grid, kPanelThreads, 0, s>>>(b);
+    if (c == 8) {
+        const cudaError_t e = prepare_batch<8>();
+        if (e != cudaSuccess) return e;
+        k_batch<8><<<grid, kPanelThreads, sizeof(BatchShared<8>), s>>>(b);
+    } else {
+        const cudaError_t e = prepare_batch<4>();
+        if (e != cudaSuccess) return e;
+        k_batch<4><<<grid, kPanelThreads, sizeof(BatchShared<4>), s>>>(b);
+    }
     return cudaGetLastError();
 }
 

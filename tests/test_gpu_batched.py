@@ -83,3 +83,38 @@ def test_batched_padding_error():
     with pytest.raises(gf2.Gf2Error) as e:
         run_batch([(f2gen.uniform(40, 40, 77), 40), (A, 70)])
     assert e.value.status == gf2.GF2_ERR_PADDING
+
+
+@pytest.mark.parametrize("c8_from", [1, 300, 1 << 62])
+def test_batched_table_sizes_match_oracle(c8_from):
+    """Every matrix on the 8-bit-table kernel (c8_from = 1), every one on the
+    4-bit-table kernel (2^62), and a split batch whose two kernels run side
+    by side (300): the same bits as the oracle."""
+    old = gf2.batched_c8_from()
+    try:
+        gf2.set_batched_c8_from(c8_from)
+        mats = batch_inputs(24, 1, 700, 78)
+        mats.append((f2gen.uniform(1100, 900, 79), 900))
+        for (A, m), got in zip(mats, run_batch(mats)):
+            assert_same_decomposition(A, m, got)
+        # the padding status still comes back from either kernel
+        A = f2gen.uniform(500, 70, 80)
+        A[3, 1] |= np.uint64(1) << np.uint64(20)
+        with pytest.raises(gf2.Gf2Error) as e:
+            run_batch([(f2gen.uniform(40, 40, 81), 40), (A, 70), (f2gen.uniform(600, 600, 82), 600)])
+        assert e.value.status == gf2.GF2_ERR_PADDING
+    finally:
+        gf2.set_batched_c8_from(old)
+
+
+def test_batched_autotune_sets_a_threshold():
+    old = gf2.batched_c8_from()
+    try:
+        t = gf2.batched_autotune(1024)
+        assert t == gf2.batched_c8_from()
+        assert t in (128, 256, 512, 1024) or t == 1 << 62
+        mats = batch_inputs(10, 100, 600, 83)
+        for (A, m), got in zip(mats, run_batch(mats)):
+            assert_same_decomposition(A, m, got)
+    finally:
+        gf2.set_batched_c8_from(old)
