@@ -697,6 +697,26 @@ def verify_serving(w: ServeWorkload, done, count: int):
 
 # ------------------------------------------------------------------ ours
 
+def reduce_over_ranks(x: float, op: str, dist, device) -> float:
+    """The whole-job value of a per-rank number: the slowest rank's time
+    ("max") or the total work ("sum"); x itself on one process."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_line_values(per_rank_ms: float, per_rank_ops: float, dist, device):
+    """(ms per step, whole-job bit-op/s) under weak scaling: every rank
+    decomposes its own matrix; the job takes as long as its slowest rank and
+    does the work of all of them."""
+    ms = reduce_over_ranks(per_rank_ms, "max", dist, device)
+    ops = reduce_over_ranks(per_rank_ops, "sum", dist, device)
+    return ms, ops / (ms / 1000.0)
+
+
 def run_ours(args):
     import torch
 
@@ -737,19 +757,7 @@ def run_ours(args):
         if dist:
             dist.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x: float) -> float:
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    max_over_ranks = lambda x: reduce_over_ranks(x, "max", dist, dev)
 
     # ---- timed region: K decompositions, nothing else on the stream
     sampler = ClockSampler(dev.index if world == 1 else local)
@@ -771,9 +779,8 @@ def run_ours(args):
     pivh = piv.cpu().numpy()[: int(rk.item())]
     my_ops = bitops(n, m, pivh)
     r = int(rk.item())
-    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
-    total_ops = sum_over_ranks(my_ops)
-    value = total_ops / (ms / 1000.0)
+    ms, value = job_line_values(ev0.elapsed_time(ev1) / args.steps, my_ops, dist, dev)
+    total_ops = value * ms / 1000.0
 
     # ---- per-kernel-class device time: CUDA events recorded by the library on
     # the launching stream around every launch of one more step
