@@ -189,6 +189,11 @@ cudaError_t launch_xor(uint64_t *D, int64_t ldd, const uint64_t *X, int64_t ldx,
 cudaError_t launch_solve(const SolveCtx &c, cudaStream_t s);  // one cooperative launch
 // one CTA per item, items[0] first; max_n: the largest n among the items
 cudaError_t launch_serve_solve(const ServeItem *items, int count, int32_t *next, int64_t max_n, cudaStream_t s);
+// large systems: one cluster of kServeClusterCTAs CTAs per item (items[0 ..
+// count)); max_n the largest n
+constexpr int kServeClusterCTAs = 8;
+bool serve_by_cluster(int64_t n);
+cudaError_t launch_serve_cluster(const ServeItem *items, int count, int64_t max_n, cudaStream_t s);
 int batch_ctas_per_sm(int c);  // c = 4 or 8: the batched kernel's table size
 // the product on the tensor cores (k < 2^24): A8, B8 are n_pad x k_pad and
 // m_pad x k_pad bytes (dimensions rounded up to mma_pad)

@@ -31,6 +31,7 @@ constexpr int kServeU = 8;
 // solution (64 + 64), 8 words of flags, one 64-word row buffer per warp
 constexpr int kServeFixedWords = 8 * 256 + 64 + 64 + 8 + kServeWarps * 64;
 constexpr int kServeMaxSmem = 226 * 1024;  // dynamic part: the opt-in limit (227 KB) less the static words
+constexpr int64_t kServeClusterMin = 4096;  // systems from this size take a cluster
 
 template <bool VS>
 __device__ void solve_cta(const SolveCtx &c, uint64_t *smem)
@@ -183,7 +184,207 @@ __global__ void __launch_bounds__(kServeThreads, 2) k_serve(const ServeItem *ite
     }
 }
 
+// ---------------------------------------------------------------- clusters
+// The same solve for one large system by a cluster of kClusterCTAs CTAs
+// (co-scheduled by the hardware on one GPC).  CTA c of the cluster keeps rows
+// [c S, (c+1) S) of v and of y (S a multiple of 64) in its own shared memory,
+// so a 64-row block lives in one CTA.  Per block every CTA reads the block's
+// 64 values from the CTA that holds them through distributed shared memory,
+// solves the diagonal block itself (the same 64 words in every CTA), and
+// updates its own rows; one hardware cluster barrier per block orders the
+// steps (no flag is polled).  Eight SMs stream L and E instead of one.
+constexpr int kClusterCTAs = kServeClusterCTAs;
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// word p of the shared memory of CTA `rank` of this cluster (p: the same
+// variable in this CTA's shared memory)
+__device__ __forceinline__ uint64_t ld_peer(const uint64_t *p, uint32_t rank)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    uint64_t v;
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(ra) : "memory");
+    return v;
+}
+
+__global__ void __launch_bounds__(kServeThreads, 1) k_serve_cluster(const ServeItem *items, int slice)
+{
+    constexpr int T = kServeThreads, U = kServeU, CL = kClusterCTAs;
+    extern __shared__ __align__(16) uint64_t smem[];
+    uint64_t *tab = smem, *vec = tab + 8 * 256, *res = vec + 64, *flags = res + 64, *wrows = flags + 8;
+    uint64_t *vs = wrows + kServeWarps * 64;  // this CTA's rows of v
+    uint64_t *ys = vs + slice;                // and of y
+    const int cr = (int)cluster_rank();
+    const ServeItem &it = items[blockIdx.x / CL];
+    const SolveCtx &c = it.c;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = c.n, m = c.m, kmax = min(n, m);
+    const int r = (int)min(max(*c.rank, (int64_t)0), (int64_t)kmax);
+    const int mu = (m + 63) / 64, nbl = (r + 63) / 64;
+    const int S = slice, lo = cr * S, hi = min(n, lo + S);  // this CTA's rows [lo, hi)
+    const int gtid = cr * T + tid, CT = CL * T, gw = cr * kServeWarps + warp, GW = CL * kServeWarps;
+    cluster_sync();  // every CTA of the cluster runs (its shared memory exists)
+    if (it.nrhs > 0) {
+        // ---- v = P B on this CTA's rows, X = 0, qstart, the diagonal inverses
+        for (int i0 = lo + tid; i0 < hi; i0 += T * U) {
+            int p[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) p[u] = i0 + u * T < hi ? c.perm[i0 + u * T] : -1;
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (i0 + u * T < hi) vs[i0 + u * T - lo] = ((unsigned)p[u] < (unsigned)n ? c.B[p[u]] : 0) & c.rhs_mask;
+        }
+        for (int i = gtid; i < m; i += CT) c.X[i] = 0;
+        for (int t = gtid; t < r; t += CT) {
+            const int q = min(max(c.pivcols[t] >> 6, 0), mu - 1);
+            const int qp = t == 0 ? -1 : min(max(c.pivcols[t - 1] >> 6, -1), q);
+            for (int qq = qp + 1; qq <= q; ++qq) c.qstart[qq] = t;
+        }
+        {
+            const int qlast = r > 0 ? min(max(c.pivcols[r - 1] >> 6, -1), mu - 1) : -1;
+            for (int qq = qlast + 1 + gtid; qq <= mu; qq += CT) c.qstart[qq] = r;
+        }
+        if (cr == 0 && tid == 0) *c.bad = 0;
+        for (int J = gw; J < nbl; J += GW) lower_block_inverse(c, J, r, wrows + warp * 64, lane);
+        cluster_sync();  // qstart (read by the inverses of E's blocks), linv, bad
+        for (int q = gw; q < mu; q += GW) upper_block_inverse(c, q, r, wrows + warp * 64, lane);
+
+        // ---- forward substitution
+        for (int J = 0; J < nbl; ++J) {
+            const int base = 64 * J, cnt = min(64, r - base), owner = base / S;
+            if (tid < 64) vec[tid] = tid < cnt ? ld_peer(vs + (base - owner * S) + tid, owner) : 0;
+            __syncthreads();
+            if (tid < 64) {
+                const uint64_t li = c.linv[(int64_t)J * 64 + tid];
+                uint64_t acc = 0;
+#pragma unroll 16
+                for (int t = 0; t < 64; ++t)
+                    if ((li >> t) & 1) acc ^= vec[t];
+                res[tid] = acc;
+                if (cr == owner && tid < cnt) ys[base - lo + tid] = acc;
+            }
+            __syncthreads();
+            solve_tables<T>(tab, res);
+            __syncthreads();
+            const uint64_t *LJ = c.L + (int64_t)J * c.ldl;
+            for (int i0 = max(lo, min(base + 64, r)) + tid; i0 < hi; i0 += T * U) {
+                uint64_t w[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) w[u] = i0 + u * T < hi ? LJ[i0 + u * T] : 0;
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (w[u]) vs[i0 + u * T - lo] ^= solve_lookup(tab, w[u]);
+            }
+            cluster_sync();  // block J+1's rows are final before anyone reads them
+        }
+
+        // ---- consistency: OR of the residual rows
+        {
+            uint64_t bad = 0;
+            for (int i = max(lo, r) + tid; i < hi; i += T) bad |= vs[i - lo];
+#pragma unroll
+            for (int off = 16; off; off >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, off);
+            if (lane == 0 && bad) atomicOr(reinterpret_cast<unsigned long long *>(c.bad), (unsigned long long)bad);
+        }
+        cluster_sync();
+        const uint64_t ok = c.rhs_mask & ~__ldcg(c.bad);
+        if (cr == 0 && tid == 0) *c.consistent = ok;
+
+        // ---- back substitution
+        for (int q = mu - 1; q >= 0; --q) {
+            const int t0 = min(max(__ldcg(c.qstart + q), 0), r);
+            const int cnt = min(max(__ldcg(c.qstart + q + 1) - t0, 0), min(64, r - t0));
+            if (cnt == 0) continue;  // the same in every CTA
+            if (tid < 64) {
+                const int t = t0 + tid;
+                vec[tid] = tid < cnt ? ld_peer(ys + (t - (t / S) * S), t / S) : 0;
+                res[tid] = 0;
+            }
+            __syncthreads();
+            if (tid < cnt) {
+                const uint64_t ui = c.uinv[(int64_t)q * 64 + tid];
+                uint64_t acc = 0;
+#pragma unroll 16
+                for (int t = 0; t < 64; ++t)
+                    if ((ui >> t) & 1) acc ^= vec[t];
+                const int col = c.pivcols[t0 + tid];
+                res[(col - 64 * q) & 63] = acc;
+                if (cr == 0 && (unsigned)col < (unsigned)m) c.X[col] = acc & ok;
+            }
+            __syncthreads();
+            solve_tables<T>(tab, res);
+            __syncthreads();
+            const uint64_t *Eq = c.E + (int64_t)q * c.lde;
+            const int te = min(hi, t0);
+            for (int i0 = lo + tid; i0 < te; i0 += T * U) {
+                uint64_t w[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) w[u] = i0 + u * T < te ? Eq[i0 + u * T] : 0;
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (w[u]) ys[i0 + u * T - lo] ^= solve_lookup(tab, w[u]);
+            }
+            cluster_sync();
+        }
+    }
+    if (cr == 0 && tid == 0) *it.rank_out = min(max(*c.rank, (int64_t)0), (int64_t)kmax);
+    __threadfence_system();
+    cluster_sync();  // every CTA's outputs are written; no peer reads this CTA's shared memory any more
+    if (cr == 0 && tid == 0) asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(it.done), "r"(1u) : "memory");
+}
+
 }  // namespace
+
+// rows per CTA of a cluster for an n-row system (a multiple of 64), and
+// whether a cluster serves it (larger systems only, their slices in shared
+// memory)
+int64_t serve_cluster_slice(int64_t n) { return ((n + kClusterCTAs - 1) / kClusterCTAs + 63) / 64 * 64; }
+
+bool serve_by_cluster(int64_t n)
+{
+    return n >= kServeClusterMin && (kServeFixedWords + 2 * serve_cluster_slice(n)) * 8 <= kServeMaxSmem;
+}
+
+cudaError_t launch_serve_cluster(const ServeItem *items, int count, int64_t max_n, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    const int slice = (int)serve_cluster_slice(max_n);
+    const size_t bytes = (size_t)(kServeFixedWords + 2 * slice) * 8;
+    static bool attr_done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+        e = cudaFuncSetAttribute(k_serve_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, kServeMaxSmem);
+        if (e != cudaSuccess) return e;
+        attr_done[dev] = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(count * kClusterCTAs));
+    cfg.blockDim = dim3(kServeThreads);
+    cfg.dynamicSmemBytes = bytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kClusterCTAs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_serve_cluster, items, slice);
+}
 
 cudaError_t launch_serve_solve(const ServeItem *items, int count, int32_t *next, int64_t max_n, cudaStream_t s)
 {

@@ -22,7 +22,9 @@
 //      launch, every other one by the plain decomposition;
 //   5. every admitted request whose factors are ready joins one solve
 //      launch on a free slot (four slots: up to four launches in flight),
-//      one CTA per request, largest first.
+//      one CTA per request, largest first -- while that leaves SMs idle, a
+//      system of 4096 rows or more gets a cluster of eight CTAs instead, in
+//      a launch beside that one.
 // With GF2_SERVE_SERIAL the loop instead takes one request at a time and
 // runs gf2_decompose / gf2_solve on it to the end (the baseline).
 #include <algorithm>
@@ -156,7 +158,8 @@ struct DecompJob {
 // One solve launch in flight (or a free slot).
 struct Slot {
     cudaStream_t stream = nullptr;
-    cudaEvent_t ev = nullptr;
+    cudaStream_t stream2 = nullptr;  // the cluster launch of the large systems, beside the other one
+    cudaEvent_t ev = nullptr, fork = nullptr, join = nullptr;
     char *in_host = nullptr;   // pinned: the launch's items and right-hand sides
     size_t in_cap = 0;
     char *out_host = nullptr;  // pinned and mapped: per request done, rank, consistent, X
@@ -202,6 +205,7 @@ struct gf2_server {
     unsigned flags = 0;
     int64_t max_n = 0, max_m = 0;
     int max_batch = 1;
+    int sms = 1;
     Clock::time_point t0;
     Arena arena;        // factors, staging of A, batched-decomposition workspaces
     Arena solve_arena;  // right-hand sides and scratch of the solve launches in flight
@@ -678,22 +682,41 @@ bool launch_solves(gf2_server *S)
             }
             // (the host wrote the done words before the launch is enqueued)
             std::atomic_thread_fence(std::memory_order_seq_cst);
-            int64_t max_n = 0;
-            for (Req *q : take) max_n = std::max(max_n, q->r.n);
+            // the large systems (first: the items are sorted by size) take one
+            // cluster each on the second stream, the others one CTA each
+            // -- while the SMs would otherwise idle: with a cluster per large
+            // system the launch must still fit in one wave (a full launch is
+            // served best by one CTA per system, all SMs busy)
+            size_t nl = 0;
+            while (nl < cnt && serve_by_cluster(take[nl]->r.n)) ++nl;
+            if ((int64_t)cnt + (int64_t)nl * (kServeClusterCTAs - 1) > S->sms) nl = 0;
+            const ServeItem *dev_items = reinterpret_cast<const ServeItem *>(dev + kAl);
             cudaError_t ce = cudaMemcpyAsync(dev, hin, in_bytes, cudaMemcpyHostToDevice, sl->stream);
-            if (ce == cudaSuccess)
-                ce = launch_serve_solve(reinterpret_cast<const ServeItem *>(dev + kAl), (int)cnt,
-                                        reinterpret_cast<int32_t *>(dev), max_n, sl->stream);
+            int launches = 0;
+            if (ce == cudaSuccess && nl > 0) {
+                ce = cudaEventRecord(sl->fork, sl->stream);
+                if (ce == cudaSuccess) ce = cudaStreamWaitEvent(sl->stream2, sl->fork, 0);
+                if (ce == cudaSuccess) ce = launch_serve_cluster(dev_items, (int)nl, take[0]->r.n, sl->stream2);
+                if (ce == cudaSuccess) ce = cudaEventRecord(sl->join, sl->stream2);
+                ++launches;
+            }
+            if (ce == cudaSuccess && nl < cnt) {
+                ce = launch_serve_solve(dev_items + nl, (int)(cnt - nl), reinterpret_cast<int32_t *>(dev),
+                                        take[nl]->r.n, sl->stream);
+                ++launches;
+            }
+            if (ce == cudaSuccess && nl > 0) ce = cudaStreamWaitEvent(sl->stream, sl->join, 0);
             if (ce == cudaSuccess) ce = cudaEventRecord(sl->ev, sl->stream);
             if (ce != cudaSuccess) {
                 cudaGetLastError();
                 cudaStreamSynchronize(sl->stream);
+                cudaStreamSynchronize(sl->stream2);
                 S->solve_arena.release(off, in_bytes + scratch);
                 S->sticky = GF2_ERR_CUDA;
                 for (Req *q : take) complete(S, q, GF2_ERR_CUDA, 0, 0);
                 return true;
             }
-            add_launches(1);
+            add_launches(launches);
             sl->busy = true;
             sl->dev_off = off;
             sl->dev_bytes = in_bytes + scratch;
@@ -870,8 +893,10 @@ void engine_main(gf2_server *S)
         S->cv_in.wait_for(lock, std::chrono::microseconds((int64_t)wait_us));
     }
     // every request is complete; wait for the GPU before the memory goes
-    for (Slot &s : S->slots)
+    for (Slot &s : S->slots) {
         if (s.stream) cudaStreamSynchronize(s.stream);
+        if (s.stream2) cudaStreamSynchronize(s.stream2);
+    }
     for (cudaStream_t d : S->dec_stream)
         if (d) cudaStreamSynchronize(d);
 }
@@ -903,7 +928,10 @@ void destroy_resources(gf2_server *S)
 {
     for (Slot &s : S->slots) {
         if (s.stream) cudaStreamDestroy(s.stream);
+        if (s.stream2) cudaStreamDestroy(s.stream2);
         if (s.ev) cudaEventDestroy(s.ev);
+        if (s.fork) cudaEventDestroy(s.fork);
+        if (s.join) cudaEventDestroy(s.join);
         if (s.in_host) cudaFreeHost(s.in_host);
         if (s.out_host) cudaFreeHost(s.out_host);
     }
@@ -939,6 +967,7 @@ int gf2_server_create(int64_t device_bytes, int64_t max_n, int64_t max_m, int ma
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S->device) != cudaSuccess ||
         cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess)
         st = GF2_ERR_CUDA;
+    S->sms = sms;
     // the solve launches get their own arena, so that resident factors can
     // never crowd out the solves that release them
     const size_t one = solve_scratch_bytes(max_n, max_m) + up((size_t)max_n * 8) + 2 * kAl + up(sizeof(ServeItem));
@@ -963,7 +992,10 @@ int gf2_server_create(int64_t device_bytes, int64_t max_n, int64_t max_m, int ma
     for (Slot &s : S->slots) {
         if (st != GF2_OK) break;
         if (cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, hi) != cudaSuccess ||
-            cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess)
+            cudaStreamCreateWithPriority(&s.stream2, cudaStreamNonBlocking, hi) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s.fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s.join, cudaEventDisableTiming) != cudaSuccess)
             st = GF2_ERR_CUDA;
     }
     if (st != GF2_OK) {

@@ -184,3 +184,24 @@ def test_request_errors_complete_with_their_status():
     assert first[2]["status"] == gf2.GF2_ERR_UNSUPPORTED
     assert first[3]["status"] == gf2.GF2_OK and first[3]["rank"] == oracle.rank(A, 70)
     assert second[4]["status"] == gf2.GF2_ERR_SHAPE
+
+
+def test_large_systems_by_cluster_match_oracle():
+    """Systems of 4096 rows or more are solved by a cluster of CTAs (rows
+    split across their shared memories): square, wide, tall and
+    rank-deficient ones, alone and mixed with small systems in one launch."""
+    sizes = [(4096, 4096), (4500, 4200), (6000, 4096), (4096, 4160), (300, 200), (64, 64)]
+    w = Workload(16, seed=15, sizes=sizes)
+    with gf2.Server(2 << 30, 8192, 8192, max_batch=64) as s:
+        got = run(s, w)
+    w.check(got)
+    alone = {}
+    with gf2.Server(2 << 30, 8192, 8192, max_batch=64) as s:
+        for i in range(len(w.req)):
+            w.X[i][:] = 0
+            s.submit(w.req[i:i + 1])
+            c = s.wait_all(1, timeout_s=120)
+            assert c[0]["status"] == gf2.GF2_OK
+            alone[i] = (int(c[0]["rank"]), int(c[0]["consistent"]), w.X[i].copy())
+    for i in range(len(w.req)):
+        assert got[i][:2] == alone[i][:2] and np.array_equal(got[i][2], alone[i][2]), i
