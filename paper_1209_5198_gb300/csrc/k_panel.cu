@@ -9,6 +9,12 @@ namespace {
 __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
 {
     __shared__ PanelShared sh;
+    // Launched as a programmatic dependent of the previous panel: wait until
+    // that launch has completed and its writes are visible, then let the
+    // next panel be scheduled (it waits here in turn).  Without the launch
+    // attribute both are no-ops.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     panel_block(c, j, sh);
 }
 
@@ -37,8 +43,20 @@ cudaError_t launch_panel(const DecompCtx &c, int j, cudaStream_t s)
 {
     const cudaError_t e = prepare_panel_kernel();
     if (e != cudaSuccess) return e;
-    k_panel<<<1, kPanelThreads, kPanelReserveBytes, s>>>(c, j);
-    return cudaGetLastError();
+    // programmatic stream serialization: the launch may start as soon as the
+    // previous panel triggers (its CTA then waits in griddepcontrol.wait),
+    // which hides the launch latency on the panel chain
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(kPanelThreads);
+    cfg.dynamicSmemBytes = kPanelReserveBytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_panel, c, j);
 }
 
 }  // namespace gf2
