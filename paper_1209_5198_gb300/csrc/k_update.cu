@@ -273,6 +273,11 @@ template <int C, int U, int NP>
 __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int ntiles)
 {
     static_assert(NP == 1 || NP == 2, "one panel or a pair");
+    // a programmatic dependent of the previous update on this stream: wait
+    // for it to complete (and its writes to be visible), then let the next
+    // one be scheduled
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     extern __shared__ __align__(16) uint64_t smem[];
     uint64_t *tab = smem;                          // [NP * K tables][X][kTileWords]
     uint64_t *crow = smem + NP * Tabs<C>::Words;   // [NP][64 x kTileWords]
@@ -471,13 +476,27 @@ cudaError_t launch_rest(const DecompCtx &c, int j, int np, int est_active_rows, 
     if (items < grid) grid = (int)items;
     cudaError_t e = prepare_update_kernels();
     if (e != cudaSuccess) return e;
-    if (np == 2)
-        k_rest<8, kRest2U, 2><<<grid, kRestThreads, rest_smem_bytes<8, 2>(), s>>>(c, j, tile_first, ntiles);
-    else if (est_active_rows >= 4096)
-        k_rest<8, kRestU, 1><<<grid, kRestThreads, rest_smem_bytes<8, 1>(), s>>>(c, j, tile_first, ntiles);
-    else
-        k_rest<4, kRestU, 1><<<grid, kRestThreads, rest_smem_bytes<4, 1>(), s>>>(c, j, tile_first, ntiles);
-    return cudaGetLastError();
+    // programmatic stream serialization: the launch may be scheduled while
+    // the previous update runs (its CTAs wait in griddepcontrol.wait)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kRestThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (np == 2) {
+        cfg.dynamicSmemBytes = rest_smem_bytes<8, 2>();
+        return cudaLaunchKernelEx(&cfg, k_rest<8, kRest2U, 2>, c, j, tile_first, ntiles);
+    }
+    if (est_active_rows >= 4096) {
+        cfg.dynamicSmemBytes = rest_smem_bytes<8, 1>();
+        return cudaLaunchKernelEx(&cfg, k_rest<8, kRestU, 1>, c, j, tile_first, ntiles);
+    }
+    cfg.dynamicSmemBytes = rest_smem_bytes<4, 1>();
+    return cudaLaunchKernelEx(&cfg, k_rest<4, kRestU, 1>, c, j, tile_first, ntiles);
 }
 
 }  // namespace gf2
