@@ -125,6 +125,38 @@ def test_full_size_decomposition_32768():
     freivalds(A, perm, L, E, N, N, random_vectors(8, N, 77))
 
 
+def first_columns_match_oracle(A, n, m, perm, piv, r, L, E, cols=256):
+    """The oracle run on the first `cols` columns only (every decision there is
+    final): pivot columns, the rows at the first positions, their echelon
+    rows, and every row's L multipliers for those pivots."""
+    ref = oracle.ple(A, m, want_L=True, want_E=True, col_limit=cols, nthreads=NTHREADS)
+    rc = ref["rank"]
+    assert np.array_equal(piv[:rc], ref["pivcols"])
+    assert rc == int((piv[:r] < cols).sum())
+    assert np.array_equal(perm[:rc], ref["perm"][:rc])
+    assert np.array_equal(E[:rc], ref["E"][:rc])
+    inv_gpu = np.empty(n, dtype=np.int64)
+    inv_gpu[perm] = np.arange(n)
+    inv_ref = np.empty(n, dtype=np.int64)
+    inv_ref[ref["perm"]] = np.arange(n)
+    w = (rc + 63) // 64
+    mask = np.full(w, ~np.uint64(0), dtype=np.uint64)
+    if rc % 64:
+        mask[-1] = (np.uint64(1) << np.uint64(rc % 64)) - np.uint64(1)
+    assert np.array_equal(L[inv_gpu, :w] & mask, ref["L"][inv_ref, :w] & mask)
+
+
+@pytest.mark.parametrize("n,m", [(65536, 65536), (16384, 65536), (65536, 16384)])
+def test_full_size_scale_configurations(n, m):
+    """The largest square and the two rectangular scale configurations."""
+    A = f2gen.uniform(n, m, f2gen.BASE_SEED, 2, n // 1024 + m // 1024)
+    perm, piv, r, L, E, _ = gpu_factors(A, m)
+    assert r >= min(n, m) - 8 if n == m else r == min(n, m)
+    check_shapes(perm, piv, r, L, E, n, m)
+    first_columns_match_oracle(A, n, m, perm, piv, r, L, E)
+    freivalds(A, perm, L, E, m, min(n, m), random_vectors(4, m, 83))
+
+
 @pytest.mark.parametrize("r", [8192, 16384 - 64])
 def test_full_size_fixed_rank_16384(r):
     n = 16384
