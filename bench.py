@@ -484,8 +484,9 @@ SIZES_METRIC = "decomposition time and GF(2) bit-op/s across the scale configura
 
 
 def run_sizes(args):
-    """The scale configurations of the plain decomposition: square 16384,
-    32768, 65536 Bernoulli(1/2); rectangular 16384 x 65536 and 65536 x 16384;
+    """The scale configurations of the plain decomposition: square 1024 (the
+    single-matrix configuration), 16384, 32768, 65536 Bernoulli(1/2);
+    rectangular 16384 x 65536 and 65536 x 16384;
     fixed rank r = n/2 and n - 64 (A = X Y, X n x r and Y r x n Bernoulli(1/2),
     full rank with overwhelming probability, formed with the library's
     product).  Inputs made on the GPU with torch's seeded generator."""
@@ -497,7 +498,7 @@ def run_sizes(args):
     stream = torch.cuda.current_stream()
     lib = gf2.load()
     g = torch.Generator(device=dev).manual_seed(0x5198)
-    cfgs = [(16384, 16384, None), (32768, 32768, None), (65536, 65536, None), (16384, 65536, None),
+    cfgs = [(1024, 1024, None), (16384, 16384, None), (32768, 32768, None), (65536, 65536, None), (16384, 65536, None),
             (65536, 16384, None), (16384, 16384, 8192), (16384, 16384, 16320), (32768, 32768, 16384),
             (32768, 32768, 32704)]
     rows = []
