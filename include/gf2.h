@@ -167,7 +167,9 @@ int gf2_rank_noalloc(const gf2_mat *A, int64_t *rank_dev, void *stream);
  * back to the host buffers given (L_host/E_host may be NULL; their column
  * blocks use ld = n and ld = min(n,m)).  Host buffers should be pinned for
  * full copy bandwidth.  Device memory comes from the workspace (see
- * gf2_decompose_host_workspace_bytes).  Synchronises the stream. */
+ * gf2_decompose_host_workspace_bytes).  The padding bits are checked on the
+ * host copy (GF2_ERR_PADDING before any device work).  Synchronises the
+ * stream once, at the end. */
 size_t gf2_decompose_host_workspace_bytes(int64_t n, int64_t m, int want_factors);
 int gf2_decompose_host(int64_t n, int64_t m, const uint64_t *A_host, int64_t lda,
                        int32_t *perm_host, int32_t *pivcols_host, int64_t *rank_host,

@@ -643,6 +643,16 @@ int gf2_decompose_host(int64_t n, int64_t m, const uint64_t *A_host, int64_t lda
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t mu = words_of(m), kmax = n < m ? n : m, lw = words_of(kmax);
     const bool factors = L_host || E_host;
+    if (flags & ~GF2_NOCHECK) return GF2_ERR_ARG;
+    // the padding bits are checked here, on the host copy, before any device
+    // work, so that the device work is not interrupted by a synchronisation
+    // to read them back
+    if (!(flags & GF2_NOCHECK) && n > 0 && (m % 64)) {
+        const uint64_t keep = last_word_mask(m), *last = A_host + (mu - 1) * lda;
+        uint64_t bad = 0;
+        for (int64_t i = 0; i < n; ++i) bad |= last[i] & ~keep;
+        if (bad) return GF2_ERR_PADDING;
+    }
     const size_t need = gf2_decompose_host_workspace_bytes(n, m, factors);
     void *ws = nullptr;
     int st = get_workspace(workspace, ws_bytes, need, &ws);
@@ -666,7 +676,8 @@ int gf2_decompose_host(int64_t n, int64_t m, const uint64_t *A_host, int64_t lda
     gf2_mat A{Ad, n, m, n > 0 ? n : 1};
     gf2_mat L{Ld, n, kmax, n > 0 ? n : 1};
     gf2_mat E{Ed, kmax, m, kmax > 0 ? kmax : 1};
-    st = decompose_impl(&A, permd, pivd, rkd, factors ? &L : nullptr, factors ? &E : nullptr, flags, p, dec, s);
+    st = decompose_impl(&A, permd, pivd, rkd, factors ? &L : nullptr, factors ? &E : nullptr, flags | GF2_NOCHECK, p,
+                        dec, s);
     if (st) return st;
     CK(cudaMemcpyAsync(rank_host, rkd, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     if (n > 0) CK(cudaMemcpyAsync(perm_host, permd, (size_t)n * 4, cudaMemcpyDeviceToHost, s));

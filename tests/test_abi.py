@@ -140,3 +140,20 @@ def test_server_argument_errors_without_gpu(lib):
     cnt = ctypes.c_int(0)
     assert lib.gf2_server_poll(None, None, 0, 0, ctypes.byref(cnt)) == g.GF2_ERR_ARG
     assert lib.gf2_server_destroy(None) == g.GF2_ERR_ARG
+
+
+def test_host_entry_point_checks_padding_on_the_host(lib):
+    """gf2_decompose_host reads the padding bits of its host input before any
+    device work: a bit beyond the last column is reported without a GPU."""
+    import numpy as np
+    import paper_1209_5198_gb300 as g
+    n, m = 10, 70  # two column blocks, 6 columns used in the second
+    A = np.zeros((2, n), dtype=np.uint64)
+    A[1, 3] = np.uint64(1) << np.uint64(40)  # column 104 >= 70
+    perm = np.zeros(n, dtype=np.int32)
+    rank = np.zeros(1, dtype=np.int64)
+    lib.gf2_decompose_host.restype = ctypes.c_int
+    st = lib.gf2_decompose_host(ctypes.c_int64(n), ctypes.c_int64(m), A.ctypes.data_as(ctypes.c_void_p), ctypes.c_int64(n),
+                                perm.ctypes.data_as(ctypes.c_void_p), None, rank.ctypes.data_as(ctypes.c_void_p),
+                                None, None, ctypes.c_uint(0), None, ctypes.c_size_t(0), None)
+    assert st == g.GF2_ERR_PADDING
