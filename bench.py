@@ -359,7 +359,7 @@ def run_product(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
     lib = gf2.load()
-    cutoff = gf2.mmm_autotune(32768)
+    cutoff = gf2.mmm_autotune(min(32768, max(args.product_sizes)))
     g = torch.Generator(device=dev).manual_seed(0x1209)
     backends = {"m4rm": gf2.GF2_MMM_TABLES, "strassen": 0, "tensor": gf2.GF2_MMM_TENSOR}
     table, main = [], None

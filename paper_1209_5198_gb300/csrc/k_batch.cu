@@ -28,10 +28,12 @@ namespace {
 constexpr int kBatchU = 2;  // row groups of 16 rows per warp and pass
 
 // the update's tables and rows (used between panel steps only)
+constexpr int kBatchPad = 4;  // bank skew of the staged pivot rows (build_tables)
+
 template <int C>
 struct BatchUpdateShared {
     __align__(16) uint64_t tab[Tabs<C>::Words];
-    uint64_t crow[64 * kTileWords];
+    uint64_t crow[crow_words<C, kBatchPad>()];
     uint64_t zc[16 * 16 * 2];  // [g][x][y, lambda]
 };
 
@@ -137,9 +139,9 @@ __device__ void batch_update(const DecompCtx &c, int j, BatchUpdateShared<C> &bs
         const int q0 = tile * kTileWords, col = q0 + 2 * wp;
         const bool live_hi = col + 1 >= j + 1, live_lo = col >= j + 1;
         __syncthreads();
-        load_pivot_rows<kPanelThreads>(c, pi->prow, r, q0, bs.crow);
+        load_pivot_rows<kPanelThreads, C, kBatchPad>(c, pi->prow, r, q0, bs.crow);
         __syncthreads();
-        build_tables<C, kPanelThreads>(bs.tab, bs.crow);
+        build_tables<C, kPanelThreads, kBatchPad>(bs.tab, bs.crow);
         __syncthreads();
         if (c.Eint) echelon_rows<C, kPanelThreads>(c, pi, R, r, q0, j + 1, ng, bs.tab);
         // (every lane runs the loop; a lane whose words precede column j+1 skips its loads and stores)

@@ -25,7 +25,8 @@ constexpr int kPThreads = 512;
 constexpr int kPWarps = kPThreads / 32;
 constexpr int kPC = 8;  // bits per lookup
 
-constexpr int kPSmemBytes = (Tabs<kPC>::Words + 64 * kTileWords) * 8;
+constexpr int kPPad = 4;  // words between the 8-row groups of the staged slice of B
+constexpr int kPSmemBytes = (Tabs<kPC>::Words + 64 * kTileWords + kPPad * (64 / kPC)) * 8;
 
 template <int U, int MINB>
 __global__ void __launch_bounds__(kPThreads, MINB) k_mmm(MmmCtx c, int kb_per_split)
@@ -50,7 +51,7 @@ __global__ void __launch_bounds__(kPThreads, MINB) k_mmm(MmmCtx c, int kb_per_sp
         if (tid < 64 * kTileWords) {
             const int t = tid / kTileWords, w = tid % kTileWords;
             const int64_t r = 64 * (int64_t)kb + t;
-            crow[tid] = (r < c.k && q0 + w < c.mw) ? c.B[(int64_t)(q0 + w) * c.ldb + r] : 0;
+            crow[tid + kPPad * (t / kPC)] = (r < c.k && q0 + w < c.mw) ? c.B[(int64_t)(q0 + w) * c.ldb + r] : 0;
         }
         // this slice's word of A for every row (consumed after the table build)
         uint64_t y[U];
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(kPThreads, MINB) k_mmm(MmmCtx c, int kb_per_sp
 #pragma unroll
         for (int u = 0; u < U; ++u) y[u] = base + u * kStride < c.n ? Ak[base + u * kStride] : 0;
         __syncthreads();  // the previous slice's lookups are done; crow is complete
-        build_tables<kPC, kPThreads>(tab, crow);
+        build_tables<kPC, kPThreads, kPPad>(tab, crow);
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < U; ++u) {

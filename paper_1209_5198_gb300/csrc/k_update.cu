@@ -261,10 +261,12 @@ constexpr int kRestChunk = 256;  // list entries per work item
 constexpr int kRestU = 6;        // row groups of 16 rows per warp and iteration (one panel)
 constexpr int kRest2U = 4;       // the same for a pair
 
+constexpr int kRestPad = 4;  // bank skew of the staged pivot rows (build_tables)
+
 template <int C, int NP>
 constexpr int rest_smem_bytes()
 {
-    return (NP * Tabs<C>::Words + NP * 64 * kTileWords) * 8;
+    return (NP * Tabs<C>::Words + NP * crow_words<C, kRestPad>()) * 8;
 }
 
 template <int C, int U, int NP>
@@ -280,7 +282,8 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     extern __shared__ __align__(16) uint64_t smem[];
     uint64_t *tab = smem;                          // [NP * K tables][X][kTileWords]
-    uint64_t *crow = smem + NP * Tabs<C>::Words;   // [NP][64 x kTileWords]
+    uint64_t *crow = smem + NP * Tabs<C>::Words;   // [NP][crow_words]: 64 x kTileWords, skewed
+    uint64_t *crow1 = crow + crow_words<C, kRestPad>();
     constexpr int K = Tabs<C>::K;
     const PanelInfo *pi0 = c.info + j;
     const PanelInfo *pi1 = c.info + j + NP - 1;
@@ -315,10 +318,10 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
         it = seg_end;
         const int q0 = tile * kTileWords;
         __syncthreads();
-        load_pivot_rows<kRestThreads>(c, pi0->prow, r0, q0, crow);
-        if (NP == 2) load_pivot_rows<kRestThreads>(c, pi1->prow, r1, q0, crow + 64 * kTileWords);
+        load_pivot_rows<kRestThreads, C, kRestPad>(c, pi0->prow, r0, q0, crow);
+        if (NP == 2) load_pivot_rows<kRestThreads, C, kRestPad>(c, pi1->prow, r1, q0, crow1);
         __syncthreads();
-        build_tables<C, kRestThreads>(tab, crow);
+        build_tables<C, kRestThreads, kRestPad>(tab, crow);
         if (NP == 2) {
             // Panel j+1's pivot rows are not on the active list: give them
             // panel j's update on this tile here (with panel j's tables),
@@ -331,10 +334,10 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
                 uint64_t acc = 0;
                 for (int g = 0; g < ng0; ++g)
                     acc ^= tab[tab_entry<C>(g, (int)((y >> (C * g)) & (Tabs<C>::X - 1))) * kTileWords + idx % kTileWords];
-                crow[64 * kTileWords + idx] ^= acc;
+                crow1[idx + kRestPad * (idx / kTileWords / C)] ^= acc;
             }
             __syncthreads();
-            build_tables<C, kRestThreads>(tab, crow + 64 * kTileWords, K);
+            build_tables<C, kRestThreads, kRestPad>(tab, crow1, K);
         }
         __syncthreads();
         if (c.Eint && chunk == 0) {

@@ -35,10 +35,13 @@ __device__ __forceinline__ int tables_used(int r)
     return ((r + C - 1) / C + 3) & ~3;
 }
 
-// Tables g0.. of the 64 tile rows in crow (rows beyond r are zero).
+// Tables g0.. of the 64 tile rows in crow (rows beyond r are zero): row t,
+// word w at crow[t * kTileWords + w + PAD * (t / C)] (PAD = 4 skews the C-row
+// groups across the banks, so that a warp's reads of one row of each group
+// do not collide).
 // Thread -> (word w, table g, sub-range of x); each sub-range walks its low
 // bits in Gray order, one XOR per entry.
-template <int C, int T>
+template <int C, int T, int PAD = 0>
 __device__ __forceinline__ void build_tables(uint64_t *tab, const uint64_t *crow, int g0 = 0)
 {
     constexpr int K = Tabs<C>::K, X = Tabs<C>::X;
@@ -52,7 +55,7 @@ __device__ __forceinline__ void build_tables(uint64_t *tab, const uint64_t *crow
     const int w = tid % kTileWords, g = (tid / kTileWords) % K, sub = tid / (kTileWords * K);
     uint64_t cb[C];
 #pragma unroll
-    for (int b = 0; b < C; ++b) cb[b] = crow[(C * g + b) * kTileWords + w];
+    for (int b = 0; b < C; ++b) cb[b] = crow[(C * g + b) * kTileWords + w + PAD * g];
     const int x0 = sub * Q;
     uint64_t v = 0;
 #pragma unroll
@@ -81,16 +84,24 @@ __device__ __forceinline__ void lookup(const ulonglong2 *tab2, uint64_t y, int w
     }
 }
 
+// Words of a staged block of 64 tile rows with the bank skew of build_tables
+// (PAD words after every C rows).
+template <int C, int PAD>
+constexpr int crow_words()
+{
+    return 64 * kTileWords + PAD * (64 / C);
+}
+
 // Loads the C rows of panel j (the pivot rows, by their storage rows prow)
-// for the tile starting at word q0 (zero beyond r).
-template <int T>
+// for the tile starting at word q0 (zero beyond r), in build_tables' layout.
+template <int T, int C = 8, int PAD = 0>
 __device__ __forceinline__ void load_pivot_rows(const DecompCtx &c, const int32_t *prow, int r, int q0, uint64_t *crow)
 {
     for (int idx = threadIdx.x; idx < 64 * kTileWords; idx += T) {
         const int t = idx / kTileWords, w = idx % kTileWords;
         uint64_t v = 0;
         if (t < r) v = c.W[widx(c, prow[t], q0 + w)];
-        crow[idx] = v;
+        crow[idx + PAD * (t / C)] = v;
     }
 }
 
