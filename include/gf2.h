@@ -344,6 +344,52 @@ int gf2_timing_enable(int on);
 int gf2_timing_reset(void);
 int gf2_timing_read(int kernel_class, double *total_ms, int64_t *launches);
 
+/* ------------------------------------------------------------------------
+ * Operation counts (the cost model of Section 6 and of the complexity
+ * estimate of Section 7).  Only the op-counting build of the library
+ * (compiled with -DGF2_COUNT_OPS, a separate libgf2_count.so) counts; the
+ * release build returns GF2_ERR_UNSUPPORTED and has no counting code in its
+ * kernels.
+ *
+ * Every count is in operations on 64-bit words (the paper's Xor_b, b = 64):
+ *   GF2_OP_UPDATES     (panel, row, word) triples of the trailing update
+ *                      A(j+1) = E + Y C: a word of a row below panel j's
+ *                      pivots that receives panel j's update (rows whose
+ *                      multiplier y is zero take none)
+ *   GF2_OP_YROWS       rows whose multiplier y = d Z is formed (Y = D Z)
+ *   GF2_OP_LOOKUPS8    table lookups XORed into a word, c = 8 tables (the
+ *                      wide update)
+ *   GF2_OP_LOOKUPS4    the same, c = 4 tables (the look-ahead update, and
+ *                      the one-panel wide update of fewer than 4096 rows)
+ *   GF2_OP_TABLE8      table entries x != 0 formed, per word, c = 8 tables
+ *   GF2_OP_TABLE4      the same, c = 4 tables
+ *   GF2_OP_MMM_LOOKUPS the product's table lookups (c = 8) XORed into a word
+ *   GF2_OP_MMM_TABLE   the product's table entries x != 0 formed, per word
+ *   GF2_OP_MMM_ADDS    words of the explicit matrix additions of the
+ *                      Strassen-Winograd recursion
+ * Words past the last column block (tile padding) are not counted.  The
+ * update and lookup counts take each (panel, row, word) once, also where
+ * several CTAs that share a column tile each redo the update of the second
+ * panel's pivot rows of a pair; the table counts take every copy that a CTA
+ * builds for itself.
+ *
+ * gf2_op_counts(out, count, reset): synchronises the current device, writes
+ * min(count, GF2_NUM_OPS) counters to out (host memory) and, when reset is
+ * nonzero, sets them to zero.  Returns GF2_OK, GF2_ERR_ARG (out null or
+ * count < 0), GF2_ERR_UNSUPPORTED (release build) or GF2_ERR_CUDA.
+ */
+#define GF2_OP_UPDATES 0
+#define GF2_OP_YROWS 1
+#define GF2_OP_LOOKUPS8 2
+#define GF2_OP_LOOKUPS4 3
+#define GF2_OP_TABLE8 4
+#define GF2_OP_TABLE4 5
+#define GF2_OP_MMM_LOOKUPS 6
+#define GF2_OP_MMM_TABLE 7
+#define GF2_OP_MMM_ADDS 8
+#define GF2_NUM_OPS 9
+int gf2_op_counts(uint64_t *out, int count, int reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,11 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgf2.so")
+# GF2_COUNT_OPS=1 in the environment selects the op-counting build of the
+# same ABI (libgf2_count.so, ``_build.build(counting=True)``): its kernels
+# count their word operations for ``op_counts``; it is never the default
+COUNTING = os.environ.get("GF2_COUNT_OPS") == "1"
+LIB_PATH = os.path.join(_HERE, "libgf2_count.so" if COUNTING else "libgf2.so")
 
 GF2_OK = 0
 GF2_MMM_TABLES = 2
@@ -115,6 +119,8 @@ def load() -> ctypes.CDLL:
     lib.gf2_server_destroy.restype = ctypes.c_int
     lib.gf2_server_destroy.argtypes = [P]
     lib.gf2_launch_count.restype = ctypes.c_int64
+    lib.gf2_op_counts.restype = ctypes.c_int
+    lib.gf2_op_counts.argtypes = [P, ctypes.c_int, ctypes.c_int]
     lib.gf2_timing_enable.argtypes = [ctypes.c_int]
     lib.gf2_timing_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)]
     _lib = lib
@@ -381,6 +387,19 @@ def strassen_cutoff() -> int:
 def launch_count() -> int:
     """Kernels the library has launched since it was loaded."""
     return int(load().gf2_launch_count())
+
+
+# the counters of gf2_op_counts, in the order of GF2_OP_* (include/gf2.h)
+OPS = ("updates", "yrows", "lookups8", "lookups4", "table8", "table4", "mmm_lookups", "mmm_table", "mmm_adds")
+
+
+def op_counts(reset: bool = False) -> dict:
+    """Word-operation counters of the op-counting build (GF2_COUNT_OPS=1):
+    synchronises the device, returns {name: count} and optionally zeroes
+    them.  The release build raises Gf2Error(GF2_ERR_UNSUPPORTED)."""
+    out = (ctypes.c_uint64 * len(OPS))()
+    _check(load().gf2_op_counts(ctypes.cast(out, ctypes.c_void_p), len(OPS), int(reset)), "gf2_op_counts")
+    return {k: int(v) for k, v in zip(OPS, out)}
 
 
 def timing(on: bool) -> None:

@@ -15,6 +15,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libgf2.so")
 OBJDIR = os.path.join(HERE, "_build")
+# the op-counting variant (same ABI; its kernels count word operations, see
+# gf2_op_counts in include/gf2.h): built only on request
+COUNT_OUT = os.path.join(HERE, "libgf2_count.so")
+COUNT_OBJDIR = os.path.join(HERE, "_build_count")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", os.path.join(os.path.dirname(HERE), "include")]
@@ -31,23 +35,26 @@ def sources() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _stale() -> bool:
-    if not os.path.exists(OUT):
+def _stale(out: str) -> bool:
+    if not os.path.exists(out):
         return True
-    t = os.path.getmtime(OUT)
+    t = os.path.getmtime(out)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(os.path.dirname(HERE), "include", "gf2.h"), __file__]
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    if not force and not _stale():
-        return OUT
-    os.makedirs(OBJDIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, counting: bool = False) -> str:
+    """Builds libgf2.so, or with counting=True the op-counting variant
+    libgf2_count.so (-DGF2_COUNT_OPS); returns the library's path."""
+    out, objdir = (COUNT_OUT, COUNT_OBJDIR) if counting else (OUT, OBJDIR)
+    if not force and not _stale(out):
+        return out
+    os.makedirs(objdir, exist_ok=True)
     cc = nvcc()
-    extra = extra or []
+    extra = (extra or []) + (["-DGF2_COUNT_OPS"] if counting else [])
 
     def one(src):
-        obj = os.path.join(OBJDIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
         cmd = [cc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -58,16 +65,16 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
     with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(one, sources()))
-    tmp = OUT + ".tmp"
+    tmp = out + ".tmp"
     cmd = [cc, *ARCH, "-shared", *objs, "-o", tmp]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, OUT)
-    return OUT
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":  # pragma: no cover
     import sys
     print(build(force="--force" in sys.argv, verbose=True,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))
+                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None, counting="--counting" in sys.argv))

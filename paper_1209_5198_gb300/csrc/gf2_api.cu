@@ -1283,6 +1283,28 @@ int gf2_mmm_autotune(int64_t max_dim, int64_t *cutoff, void *stream)
 
 int64_t gf2_launch_count(void) { return g_launches.load(); }
 
+static_assert(GF2_OP_UPDATES == kOpUpdates && GF2_OP_YROWS == kOpYRows && GF2_OP_LOOKUPS8 == kOpLookups8 &&
+                  GF2_OP_LOOKUPS4 == kOpLookups4 && GF2_OP_TABLE8 == kOpTable8 && GF2_OP_TABLE4 == kOpTable4 &&
+                  GF2_OP_MMM_LOOKUPS == kOpMmmLookups && GF2_OP_MMM_TABLE == kOpMmmTable &&
+                  GF2_OP_MMM_ADDS == kOpMmmAdds && GF2_NUM_OPS == kNumOps,
+              "operation counter kinds of the ABI and of the kernels");
+
+int gf2_op_counts(uint64_t *out, int count, int reset)
+{
+    if (!out || count < 0) return GF2_ERR_ARG;
+#ifdef GF2_COUNT_OPS
+    if (cudaDeviceSynchronize() != cudaSuccess) return GF2_ERR_CUDA;
+    unsigned long long acc[kNumOps] = {};
+    if (read_update_ops(acc, reset != 0) != cudaSuccess || read_mmm_ops(acc, reset != 0) != cudaSuccess)
+        return GF2_ERR_CUDA;
+    for (int i = 0; i < count && i < kNumOps; ++i) out[i] = acc[i];
+    return GF2_OK;
+#else
+    (void)reset;
+    return GF2_ERR_UNSUPPORTED;
+#endif
+}
+
 int gf2_timing_enable(int on)
 {
     g_timing.store(on != 0);

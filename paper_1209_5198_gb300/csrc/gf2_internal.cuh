@@ -212,4 +212,28 @@ int decompose_batched_items(int count, const BatchItem *items, bool factors, uns
                             size_t ws_bytes, void *stream);
 void add_launches(int64_t k);  // kernels launched outside the entry points' own counting
 
+// ---- operation counters of the op-counting build (-DGF2_COUNT_OPS; the
+// counter kinds are GF2_OP_* of include/gf2.h).  Each translation unit with
+// counted kernels keeps its own device array (no relocatable device code)
+// and adds it into acc (GF2_NUM_OPS entries) from the host.
+enum OpKind {
+    kOpUpdates = 0,
+    kOpYRows = 1,
+    kOpLookups8 = 2,
+    kOpLookups4 = 3,
+    kOpTable8 = 4,
+    kOpTable4 = 5,
+    kOpMmmLookups = 6,
+    kOpMmmTable = 7,
+    kOpMmmAdds = 8,
+    kNumOps = 9
+};
+#ifdef GF2_COUNT_OPS
+#define GF2_OPS(...) __VA_ARGS__
+cudaError_t read_update_ops(unsigned long long *acc, bool reset);  // csrc/k_update.cu
+cudaError_t read_mmm_ops(unsigned long long *acc, bool reset);     // csrc/k_mmm.cu
+#else
+#define GF2_OPS(...)
+#endif
+
 }  // namespace gf2

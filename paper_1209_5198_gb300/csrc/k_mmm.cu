@@ -25,6 +25,10 @@ constexpr int kPThreads = 512;
 constexpr int kPWarps = kPThreads / 32;
 constexpr int kPC = 8;  // bits per lookup
 
+#ifdef GF2_COUNT_OPS
+__device__ unsigned long long g_mmm_ops[kNumOps];  // the op-counting build's counters
+#endif
+
 constexpr int kPPad = 4;  // words between the 8-row groups of the staged slice of B
 constexpr int kPSmemBytes = (Tabs<kPC>::Words + 64 * kTileWords + kPPad * (64 / kPC)) * 8;
 
@@ -46,6 +50,7 @@ __global__ void __launch_bounds__(kPThreads, MINB) k_mmm(MmmCtx c, int kb_per_sp
     ulonglong2 acc[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) acc[u] = make_ulonglong2(0, 0);
+    GF2_OPS(unsigned long long n_lk = 0, n_tab = 0; const int lw = (col < c.mw) + (col + 1 < c.mw);)
     for (int kb = kb0; kb < kb1; ++kb) {
         // rows 64 kb .. of B on this tile (zero beyond k and beyond the last word)
         if (tid < 64 * kTileWords) {
@@ -60,10 +65,12 @@ __global__ void __launch_bounds__(kPThreads, MINB) k_mmm(MmmCtx c, int kb_per_sp
         for (int u = 0; u < U; ++u) y[u] = base + u * kStride < c.n ? Ak[base + u * kStride] : 0;
         __syncthreads();  // the previous slice's lookups are done; crow is complete
         build_tables<kPC, kPThreads, kPPad>(tab, crow);
+        GF2_OPS(if (tid == 0) n_tab += (unsigned long long)Tabs<kPC>::K * (Tabs<kPC>::X - 1) * live_words(q0, c.mw);)
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (!y[u]) continue;
+            GF2_OPS(n_lk += (unsigned long long)Tabs<kPC>::K * lw;)
 #pragma unroll
             for (int g = 0; g < 8; ++g) {
                 const int gg = g ^ swp;
@@ -89,6 +96,7 @@ __global__ void __launch_bounds__(kPThreads, MINB) k_mmm(MmmCtx c, int kb_per_sp
             else if (v) atomicXor(reinterpret_cast<unsigned long long *>(dst), (unsigned long long)v);
         }
     }
+    GF2_OPS(add_ops(g_mmm_ops, kOpMmmLookups, n_lk); add_ops(g_mmm_ops, kOpMmmTable, n_tab);)
 }
 
 // D = X ^ Y: threads along the rows of a column block, column blocks over
@@ -96,12 +104,16 @@ __global__ void __launch_bounds__(kPThreads, MINB) k_mmm(MmmCtx c, int kb_per_sp
 __global__ void k_xor(uint64_t *__restrict__ D, int64_t ldd, const uint64_t *X, int64_t ldx, const uint64_t *Y,
                       int64_t ldy, int64_t rows, int64_t words)
 {
+    GF2_OPS(unsigned long long n_add = 0;)
     for (int64_t q = blockIdx.y; q < words; q += gridDim.y) {
         uint64_t *d = D + q * ldd;
         const uint64_t *x = X + q * ldx, *y = Y + q * ldy;
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x) {
             d[i] = x[i] ^ y[i];
+            GF2_OPS(++n_add;)
+        }
     }
+    GF2_OPS(add_ops(g_mmm_ops, kOpMmmAdds, n_add);)
 }
 
 int g_sms = 0;
@@ -214,6 +226,21 @@ cudaError_t launch_mmm(MmmCtx c, cudaStream_t s)
     default: return launch_u<12, 1>(c, bsplit, s);
     }
 }
+
+#ifdef GF2_COUNT_OPS
+cudaError_t read_mmm_ops(unsigned long long *acc, bool reset)
+{
+    unsigned long long h[kNumOps];
+    cudaError_t e = cudaMemcpyFromSymbol(h, g_mmm_ops, sizeof(h));
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < kNumOps; ++i) acc[i] += h[i];
+    if (reset) {
+        const unsigned long long z[kNumOps] = {};
+        e = cudaMemcpyToSymbol(g_mmm_ops, z, sizeof(z));
+    }
+    return e;
+}
+#endif
 
 cudaError_t launch_xor(uint64_t *D, int64_t ldd, const uint64_t *X, int64_t ldx, const uint64_t *Y, int64_t ldy,
                        int64_t rows, int64_t words, cudaStream_t s)

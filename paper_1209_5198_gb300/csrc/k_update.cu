@@ -33,6 +33,10 @@
 namespace gf2 {
 namespace {
 
+#ifdef GF2_COUNT_OPS
+__device__ unsigned long long g_update_ops[kNumOps];  // the op-counting build's counters
+#endif
+
 // -------------------------------------------------------------------- k_next
 // Look-ahead of panel j over the rows still active before it (256 per CTA):
 //   d      = the row's word j with every panel < j applied (F[j%2]; W for j = 0)
@@ -138,6 +142,13 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
     if (r > 0)
         for (int tt = 0; tt < nt; ++tt)
             build_tables<kNextC, kNextThreads>(tab + tt * Tabs<kNextC>::Words, crow + tt * 64 * kTileWords);
+    GF2_OPS(unsigned long long n_upd = 0, n_y = 0, n_lk = 0, n_tab = 0;
+            if (tid == 0 && r > 0) {
+                constexpr int E4 = Tabs<kNextC>::X - 1;
+                n_tab += has_f ? 16 * E4 : 0;  // the tables of word j+1 (c1)
+                for (int tt = 0; tt < nt; ++tt)
+                    n_tab += (unsigned long long)Tabs<kNextC>::K * E4 * live_words(q0 + tt * kTileWords, c.mu);
+            })
     // the rows that stay active, appended to the list of panel j in list order
     const int kept_row = keep_row[tid];
     const unsigned kept_mask = __ballot_sync(0xffffffffu, kept_row >= 0);
@@ -179,6 +190,7 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
             }
         }
         yv[u] = y;
+        GF2_OPS(if (wp == 0 && ((active >> u) & 1)) n_y += 1;)
         if (wp == 0) {
             Ynext[row] = y;
             if (c.Lint && l) {  // this panel's bits of the L row: disjoint from every other panel's
@@ -191,12 +203,15 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
                 if (y) {
 #pragma unroll
                     for (int g = 0; g < 16; ++g) f ^= c1[g * 16 + (int)((y >> (4 * g)) & 15)];
+                    GF2_OPS(n_upd += 1; n_lk += 16;)
                 }
                 Fn[row] = f;
             }
         }
         if (live_hi && y) {
             lookup<kNextC>(tab2, y, wp, swp, ng, a[u]);
+            GF2_OPS(const int lw = (live_lo && col < c.mu) + (col + 1 < c.mu); n_upd += lw;
+                    n_lk += (unsigned long long)ng * lw;)
             uint64_t *dst = c.W + widx(c, row, col);
             if (live_lo) *reinterpret_cast<ulonglong2 *>(dst) = a[u];
             else dst[1] = a[u].y;
@@ -216,8 +231,12 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
             if (rows[u] < 0 || !yv[u]) continue;
             lookup<kNextC>(tab2b, yv[u], wp, swp, ng, b2[u]);
             *reinterpret_cast<ulonglong2 *>(c.W + widx(c, rows[u], col2)) = b2[u];
+            GF2_OPS(const int lw = (col2 < c.mu) + (col2 + 1 < c.mu); n_upd += lw;
+                    n_lk += (unsigned long long)ng * lw;)
         }
     }
+    GF2_OPS(add_ops(g_update_ops, kOpUpdates, n_upd); add_ops(g_update_ops, kOpYRows, n_y);
+            add_ops(g_update_ops, kOpLookups4, n_lk); add_ops(g_update_ops, kOpTable4, n_tab);)
 
     if (blockIdx.x == 0 && r > 0) {
         // the pivot rows: their L rows (T) and echelon words j and j+1
@@ -275,6 +294,7 @@ template <int C, int U, int NP>
 __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int ntiles)
 {
     static_assert(NP == 1 || NP == 2, "one panel or a pair");
+    static_assert(C == 4 || C == 8, "4- or 8-bit tables");
     // a programmatic dependent of the previous update on this stream: wait
     // for it to complete (and its writes to be visible), then let the next
     // one be scheduled
@@ -308,6 +328,7 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
     const int rs = lane / kLanesPerRow, wp = lane % kLanesPerRow, swp = rs & 3;
     constexpr int NW = kRestThreads / 32;
     const ulonglong2 *tab2 = reinterpret_cast<const ulonglong2 *>(tab);
+    GF2_OPS(unsigned long long n_upd = 0, n_lk = 0, n_tab = 0;)
     // The item range is split into segments of one tile each: one table
     // build per segment, then one pipelined pass over its rows.
     for (int64_t it = i0; it < i1;) {
@@ -322,6 +343,7 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
         if (NP == 2) load_pivot_rows<kRestThreads, C, kRestPad>(c, pi1->prow, r1, q0, crow1);
         __syncthreads();
         build_tables<C, kRestThreads, kRestPad>(tab, crow);
+        GF2_OPS(if (tid == 0) n_tab += (unsigned long long)NP * K * (Tabs<C>::X - 1) * live_words(q0, c.mu);)
         if (NP == 2) {
             // Panel j+1's pivot rows are not on the active list: give them
             // panel j's update on this tile here (with panel j's tables),
@@ -335,6 +357,8 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
                 for (int g = 0; g < ng0; ++g)
                     acc ^= tab[tab_entry<C>(g, (int)((y >> (C * g)) & (Tabs<C>::X - 1))) * kTileWords + idx % kTileWords];
                 crow1[idx + kRestPad * (idx / kTileWords / C)] ^= acc;
+                // (every CTA that shares the tile redoes this; counted once, by the one with chunk 0)
+                GF2_OPS(if (chunk == 0 && q0 + idx % kTileWords < c.mu) { n_upd += 1; n_lk += ng0; })
             }
             __syncthreads();
             build_tables<C, kRestThreads, kRestPad>(tab, crow1, K);
@@ -406,8 +430,15 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
 #pragma unroll
             for (int u = 0; u < U; ++u)
                 if (y0[u] | y1[u]) *reinterpret_cast<ulonglong2 *>(Wt + (int64_t)row[u] * kTileWords) = a[u];
+            GF2_OPS(const int lw = (q0 + 2 * wp < c.mu) + (q0 + 2 * wp + 1 < c.mu);
+                    for (int u = 0; u < U; ++u) {
+                        if (y0[u]) { n_upd += lw; n_lk += (unsigned long long)ng0 * lw; }
+                        if (NP == 2 && y1[u]) { n_upd += lw; n_lk += (unsigned long long)ng1 * lw; }
+                    })
         }
     }
+    GF2_OPS(add_ops(g_update_ops, kOpUpdates, n_upd); add_ops(g_update_ops, C == 8 ? kOpLookups8 : kOpLookups4, n_lk);
+            add_ops(g_update_ops, C == 8 ? kOpTable8 : kOpTable4, n_tab);)
 }
 
 int g_num_sms = 0;
@@ -448,6 +479,21 @@ cudaError_t prepare_update_kernels()
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }
+
+#ifdef GF2_COUNT_OPS
+cudaError_t read_update_ops(unsigned long long *acc, bool reset)
+{
+    unsigned long long h[kNumOps];
+    cudaError_t e = cudaMemcpyFromSymbol(h, g_update_ops, sizeof(h));
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < kNumOps; ++i) acc[i] += h[i];
+    if (reset) {
+        const unsigned long long z[kNumOps] = {};
+        e = cudaMemcpyToSymbol(g_update_ops, z, sizeof(z));
+    }
+    return e;
+}
+#endif
 
 cudaError_t launch_next(const DecompCtx &c, int j, cudaStream_t s)
 {

@@ -84,6 +84,20 @@ __device__ __forceinline__ void lookup(const ulonglong2 *tab2, uint64_t y, int w
     }
 }
 
+#ifdef GF2_COUNT_OPS
+// adds a thread's tally to a counter of the op-counting build
+__device__ __forceinline__ void add_ops(unsigned long long *ops, int kind, unsigned long long v)
+{
+    if (v) atomicAdd(ops + kind, v);
+}
+
+// words of the tile at word q0 before the last column block's end (mu words)
+__device__ __forceinline__ int live_words(int q0, int mu)
+{
+    return max(0, min(kTileWords, mu - q0));
+}
+#endif
+
 // Words of a staged block of 64 tile rows with the bank skew of build_tables
 // (PAD words after every C rows).
 template <int C, int PAD>
