@@ -139,6 +139,23 @@ int gf2_decompose(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *ra
                   gf2_mat *L, gf2_mat *E, unsigned flags,
                   void *workspace, size_t ws_bytes, void *stream);
 
+/* Reduced row echelon form, in place (Gauss-Jordan: the paper names it
+ * among the uses of the decomposition, Section 1, and leaves it to the
+ * textbook).  E (k x m, column blocks, device) is an echelon factor as
+ * gf2_decompose leaves it: row t has its leading one at pivcols[t] (device
+ * int32[k], increasing) when pivcols[t] >= 0, and rows with pivcols[t] = -1
+ * are zero.  E becomes R = U^-1 E, U = E restricted to the pivot columns
+ * (unit upper triangular): every pivot column is then a unit column.  R is
+ * the unique reduced form of the row space, whatever the pivot order.  An E
+ * not in that form gives an unspecified result (it is not checked).
+ * Asynchronous on `stream`; scratch from the workspace
+ * (gf2_rref_workspace_bytes(k, m)) or, with workspace = NULL, from the
+ * library's own.  Errors: GF2_ERR_ARG (E or pivcols null with k, m > 0),
+ * GF2_ERR_SHAPE (ld < rows), GF2_ERR_NOMEM, GF2_ERR_UNSUPPORTED (k or
+ * m >= 2^31), GF2_ERR_CUDA. */
+size_t gf2_rref_workspace_bytes(int64_t k, int64_t m);
+int gf2_rref(gf2_mat *E, const int32_t *pivcols, void *workspace, size_t ws_bytes, void *stream);
+
 /* Rank of A (n x m) only: the decomposition without storing L and E
  * (Lemma 4.1: rank(A) = sum of the r_j).  rank_host receives the value; the
  * call synchronises the stream.  Errors as gf2_decompose. */

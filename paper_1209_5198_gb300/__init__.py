@@ -90,6 +90,10 @@ def load() -> ctypes.CDLL:
     lib.gf2_decompose_workspace_bytes.argtypes = [I64, I64, ctypes.c_int]
     lib.gf2_decompose.restype = ctypes.c_int
     lib.gf2_decompose.argtypes = [M, P, P, P, M, M, ctypes.c_uint, P, S, P]
+    lib.gf2_rref_workspace_bytes.restype = S
+    lib.gf2_rref_workspace_bytes.argtypes = [I64, I64]
+    lib.gf2_rref.restype = ctypes.c_int
+    lib.gf2_rref.argtypes = [M, P, P, S, P]
     lib.gf2_rank_workspace_bytes.restype = S
     lib.gf2_rank_workspace_bytes.argtypes = [I64, I64]
     lib.gf2_rank.restype = ctypes.c_int
@@ -220,6 +224,17 @@ def gf2_decompose(A: Mat, perm: torch.Tensor, pivcols: torch.Tensor, rank: torch
                              flags, workspace.data_ptr(), workspace.numel(), _stream(stream)), "gf2_decompose")
 
 
+def gf2_rref(E: Mat, pivcols: torch.Tensor, workspace=None, stream=None) -> None:
+    """E (an echelon factor from gf2_decompose, with its pivot columns) ->
+    its reduced row echelon form, in place."""
+    lib = load()
+    if workspace is None:
+        workspace = _workspace(lib.gf2_rref_workspace_bytes(E.rows, E.cols), E.t.device)
+    e = E.c()
+    _check(lib.gf2_rref(ctypes.byref(e), _ptr(pivcols), workspace.data_ptr(), workspace.numel(), _stream(stream)),
+           "gf2_rref")
+
+
 def gf2_rank(A: Mat, flags: int = 0, workspace=None, stream=None) -> int:
     """rank(A); synchronises the stream."""
     lib = load()
@@ -319,6 +334,13 @@ def decompose_batched(As: list, factors: bool = True, flags: int = 0, stream=Non
         out.append(dict(perm=perms[i][:a.rows], pivcols=pivs[i][:k], rank=ranks[i:i + 1],
                         L=Ls[i] if factors else None, E=Es[i] if factors else None))
     return out
+
+
+def rref(factors: dict, stream=None) -> Mat:
+    """The reduced row echelon form of the E factor of decompose() (in place;
+    returns it)."""
+    gf2_rref(factors["E"], factors["pivcols"], stream=stream)
+    return factors["E"]
 
 
 def solve(factors: dict, B: Mat, m: int, stream=None) -> dict:

@@ -543,6 +543,48 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
     return GF2_OK;
 }
 
+// ------------------------------------------------------------ RREF
+// Scratch of gf2_rref: the blocks' inverses (64 words per 64-row block) and
+// the gathered left operand of the largest product of the recursion (the
+// top level's: the top half's rows at the bottom half's pivot columns).
+struct RrefLayout {
+    size_t oV, oTmp, total;
+};
+
+int64_t rref_split(int64_t a, int64_t b) { return a + 64 * (((b - a + 63) / 64) / 2); }
+
+RrefLayout rref_layout(int64_t k)
+{
+    RrefLayout d{};
+    d.oV = 0;
+    d.oTmp = align_up((size_t)((k + 63) / 64) * 64 * 8);
+    size_t tmp = 0;
+    if (k > 64) {
+        const int64_t mid = rref_split(0, k);
+        tmp = (size_t)mid * (size_t)words_of(k - mid) * 8;
+    }
+    d.total = d.oTmp + align_up(tmp > 0 ? tmp : 1);
+    return d;
+}
+
+// Rows [a, b) of E, whose 64-row blocks are already reduced by their own
+// pivot columns: the bottom half [mid, b) recursively, then the top half
+// takes E_top ^= E_top[:, pivots of the bottom] * R_bottom -- which clears
+// the top rows at the bottom's pivot columns and leaves the top's own
+// pivot columns as they were -- then the top half recursively.
+int rref_rec(const gf2_mat &E, const int32_t *piv, int64_t a, int64_t b, uint64_t *tmp, cudaStream_t s)
+{
+    if (b - a <= 64) return GF2_OK;
+    const int64_t mid = rref_split(a, b);
+    int st = rref_rec(E, piv, mid, b, tmp, s);
+    if (st) return st;
+    const int64_t rows = mid - a, kk = b - mid;
+    LAUNCH(GF2_KCLASS_LAYOUT, launch_gather_cols(E.w, E.ld, E.cols, piv, a, rows, mid, kk, tmp, rows, s));
+    MmmCtx c{tmp, rows, E.w + mid, E.ld, E.w + a, E.ld, (int32_t)rows, (int32_t)kk, (int32_t)words_of(E.cols), kMmmXor};
+    LAUNCH(GF2_KCLASS_UPDATE, launch_mmm(c, s));
+    return rref_rec(E, piv, a, mid, tmp, s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -592,6 +634,31 @@ int gf2_decompose(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *ra
 {
     return decompose_impl(A, perm, pivcols, rank, L, E, flags, workspace, ws_bytes,
                           static_cast<cudaStream_t>(stream));
+}
+
+size_t gf2_rref_workspace_bytes(int64_t k, int64_t m)
+{
+    if (k < 0 || m < 0) return 0;
+    return rref_layout(k).total;
+}
+
+int gf2_rref(gf2_mat *E, const int32_t *pivcols, void *workspace, size_t ws_bytes, void *stream)
+{
+    if (!E || E->rows < 0 || E->cols < 0) return GF2_ERR_ARG;
+    const int64_t k = E->rows, m = E->cols;
+    if (k == 0 || m == 0) return GF2_OK;
+    if (!E->w || !pivcols) return GF2_ERR_ARG;
+    if (E->ld < k) return GF2_ERR_SHAPE;
+    if (k >= (1ll << 31) - 64 || m >= (1ll << 31) - 64) return GF2_ERR_UNSUPPORTED;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const RrefLayout d = rref_layout(k);
+    void *ws = nullptr;
+    int st = get_workspace(workspace, ws_bytes, d.total, &ws);
+    if (st) return st;
+    char *base = static_cast<char *>(ws);
+    uint64_t *V = reinterpret_cast<uint64_t *>(base + d.oV), *tmp = reinterpret_cast<uint64_t *>(base + d.oTmp);
+    LAUNCH(GF2_KCLASS_LAYOUT, launch_rref_diag(E->w, E->ld, pivcols, k, m, V, s));
+    return rref_rec(*E, pivcols, 0, k, tmp, s);
 }
 
 size_t gf2_rank_workspace_bytes(int64_t n, int64_t m)
