@@ -526,6 +526,19 @@ def run_sizes(args):
         ops = bitops(n, m, piv.cpu().numpy()[:rank])
         rows.append({"n": n, "m": m, "kind": "fixed rank" if r else "Bernoulli(1/2)", "r_built": r,
                      "rank": rank, "ms": ms, "bitops_per_s": ops / (ms / 1000)})
+        if r is None and n == m and n <= 32768:
+            # the reduced row echelon form of E (gf2_rref, in place): each
+            # timed call starts from a fresh copy of the echelon factor
+            E0 = E.t.clone()
+            rws = torch.empty(lib.gf2_rref_workspace_bytes(k, m), dtype=torch.uint8, device=dev)
+            times = []
+            for it in range(2 + 3):
+                E.t.copy_(E0)
+                t = time_calls(lambda: gf2.gf2_rref(E, piv, workspace=rws, stream=stream), 1, stream)
+                if it >= 2:
+                    times.append(t)
+            rows[-1]["rref_ms"] = min(times)
+            del E0, rws
         print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
         del A, L, E, ws
         torch.cuda.empty_cache()
