@@ -539,6 +539,19 @@ def run_sizes(args):
                     times.append(t)
             rows[-1]["rref_ms"] = min(times)
             del E0, rws
+        if n < m:
+            # the rank alone: gf2_rank (which ranks the m x n transpose) against
+            # the rank-only decomposition of the n x m matrix itself
+            rws = torch.empty(lib.gf2_rank_workspace_bytes(n, m), dtype=torch.uint8, device=dev)
+            dws = torch.empty(lib.gf2_decompose_workspace_bytes(n, m, 0), dtype=torch.uint8, device=dev)
+            f_rank = lambda: gf2.gf2_rank(A, workspace=rws, stream=stream)
+            f_direct = lambda: gf2.gf2_decompose(A, perm, piv, rk, None, None, workspace=dws, stream=stream)
+            for _ in range(max(2, args.warmup)):
+                f_rank()
+                f_direct()
+            rows[-1]["rank_transposed_ms"] = time_calls(f_rank, 2, stream)
+            rows[-1]["rank_direct_ms"] = time_calls(f_direct, 2, stream)
+            del rws, dws
         print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
         del A, L, E, ws
         torch.cuda.empty_cache()
@@ -549,6 +562,55 @@ def run_sizes(args):
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": "plain decomposition (L and E) over the scale configurations; value = the "
                                "32768 x 32768 Bernoulli(1/2) case", "configs": rows},
+    }
+    print(json.dumps(line), flush=True)
+
+
+SPARSE_METRIC = "decomposition time and GF(2) bit-op/s on the sparse S_n set (i nonzeros per row)"
+
+
+def run_sparse(args):
+    """The paper's sparse low-rank family S_n (Section 7): n x n matrices
+    whose every row has exactly i ones at distinct uniform positions
+    (f2gen.sparse_rows, seeded; i = 2, 10, 40), n = 16384, 32768, 65536.
+    Plain decomposition with L and E, timed like the sizes workload; their
+    ranks are below n, so many panels have few pivots (the low-rank path).
+    value = the n = 32768, i = 10 case."""
+    import torch
+
+    import f2gen
+    import paper_1209_5198_gb300 as gf2
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    lib = gf2.load()
+    rows = []
+    for n in args.sparse_sizes:
+        for i in (2, 10, 40):
+            A = gf2.Mat.from_rowmajor(f2gen.sparse_rows(n, n, i, f2gen.BASE_SEED, 7), n, device=dev)
+            perm = torch.empty(n, dtype=torch.int32, device=dev)
+            piv = torch.empty(n, dtype=torch.int32, device=dev)
+            rk = torch.zeros(1, dtype=torch.int64, device=dev)
+            L = gf2.Mat.empty(n, n, dev)
+            E = gf2.Mat.empty(n, n, dev)
+            ws = torch.empty(lib.gf2_decompose_workspace_bytes(n, n, 1), dtype=torch.uint8, device=dev)
+            fn = lambda: gf2.gf2_decompose(A, perm, piv, rk, L, E, workspace=ws, stream=stream)
+            for _ in range(max(2, args.warmup)):  # the second call captures the graph
+                fn()
+            ms = time_calls(fn, 2, stream)
+            rank = int(rk.item())
+            ops = bitops(n, n, piv.cpu().numpy()[:rank])
+            rows.append({"n": n, "i": i, "rank": rank, "ms": ms, "bitops_per_s": ops / (ms / 1000)})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+            del A, L, E, ws
+            torch.cuda.empty_cache()
+    main = next((x for x in rows if x["n"] == 32768 and x["i"] == 10), rows[-1])
+    line = {
+        "metric": SPARSE_METRIC, "value": main["bitops_per_s"], "unit": "bit-op/s", "n_gpus": 1, "steps": 2,
+        "warmup": max(2, args.warmup), "ms_per_step": main["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"plain decomposition (L and E) of S_n: n x n, i ones per row at distinct uniform "
+                               f"positions; value = n {main['n']}, i {main['i']}", "configs": rows},
     }
     print(json.dumps(line), flush=True)
 
@@ -911,11 +973,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="decompose", choices=["decompose", "batched", "serving", "product", "sizes"],
+    ap.add_argument("--workload", default="decompose", choices=["decompose", "batched", "serving", "product", "sizes", "sparse"],
                     help="decompose: the headline 32768^2 decomposition; batched: many small matrices in one "
                          "launch; serving: a request stream on resident factors")
     ap.add_argument("--requests", type=int, default=20000, help="requests in the serving trace")
     ap.add_argument("--product-sizes", type=int, nargs="+", default=[8192, 16384, 32768, 65536])
+    ap.add_argument("--sparse-sizes", type=int, nargs="+", default=[16384, 32768, 65536])
     ap.add_argument("--tensor-max", type=int, default=32768, help="largest n timed on the tensor-core backend")
     ap.add_argument("--batch", type=int, default=4096, help="matrices per batch (batched workload)")
     args = ap.parse_args()
@@ -928,6 +991,8 @@ def main():
         run_serving(args)
     elif args.workload == "product":
         run_product(args)
+    elif args.workload == "sparse":
+        run_sparse(args)
     elif args.workload == "sizes":
         run_sizes(args)
     else:

@@ -156,9 +156,28 @@ int gf2_decompose(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *ra
 size_t gf2_rref_workspace_bytes(int64_t k, int64_t m);
 int gf2_rref(gf2_mat *E, const int32_t *pivcols, void *workspace, size_t ws_bytes, void *stream);
 
+/* Null-space basis (Section 1 names it among the uses of the
+ * decomposition): from the reduced row echelon form R (k x m, as gf2_rref
+ * leaves E; device), its pivot columns (device int32, the first `rank`
+ * entries increasing) and the rank (host value), the m x (m - rank) matrix
+ * N (column blocks, device) whose columns are a basis of {x : A x = 0}:
+ * column j belongs to the j-th free (non-pivot) column f_j, increasing --
+ * N[f_j][j] = 1, N[pivcols[t]][j] = R[t][f_j], every other entry 0.  Given
+ * R this basis is unique.  Asynchronous on `stream`; scratch: m - rank
+ * int32 (gf2_nullspace_workspace_bytes; workspace = NULL: the library's).
+ * Errors: GF2_ERR_ARG (null pointers, rank < 0 or > min(k, m)),
+ * GF2_ERR_SHAPE (N not m x (m - rank), ld < rows), GF2_ERR_NOMEM,
+ * GF2_ERR_UNSUPPORTED (m >= 2^31), GF2_ERR_CUDA. */
+size_t gf2_nullspace_workspace_bytes(int64_t m, int64_t rank);
+int gf2_nullspace(const gf2_mat *R, const int32_t *pivcols, int64_t rank, gf2_mat *N, void *workspace,
+                  size_t ws_bytes, void *stream);
+
 /* Rank of A (n x m) only: the decomposition without storing L and E
- * (Lemma 4.1: rank(A) = sum of the r_j).  rank_host receives the value; the
- * call synchronises the stream.  Errors as gf2_decompose. */
+ * (Lemma 4.1: rank(A) = sum of the r_j).  A wide matrix (n < m) is ranked
+ * through its transpose, formed in the workspace (rank(A) = rank(A^T); with
+ * more rows than columns the decomposition takes fewer panels, Section 7).
+ * rank_host receives the value; the call synchronises the stream.  Errors as
+ * gf2_decompose. */
 size_t gf2_rank_workspace_bytes(int64_t n, int64_t m);
 int gf2_rank(const gf2_mat *A, int64_t *rank_host, unsigned flags,
              void *workspace, size_t ws_bytes, void *stream);

@@ -189,5 +189,41 @@ def rank(A: np.ndarray, m: int, nthreads: int = 1) -> int:
     return ple(A, m, want_L=False, want_E=False, nthreads=nthreads)["rank"]
 
 
+def _unpack(words: np.ndarray, cols: int) -> np.ndarray:
+    """Row-major uint64 words -> bool (rows, cols), bit t of word q = column 64q+t."""
+    words = np.ascontiguousarray(np.asarray(words, dtype=np.uint64))
+    if cols == 0 or words.shape[0] == 0:
+        return np.zeros((words.shape[0], cols), dtype=bool)
+    by = words.view(np.uint8).reshape(words.shape[0], -1)
+    return np.unpackbits(by, axis=1, bitorder="little")[:, :cols].astype(bool)
+
+
+def _pack(bits: np.ndarray) -> np.ndarray:
+    """bool (rows, cols) -> row-major uint64 words (rows, max(1, ceil(cols/64)))."""
+    rows, cols = bits.shape
+    mu = max(1, (cols + 63) // 64)
+    padded = np.zeros((rows, 64 * mu), dtype=np.uint8)
+    padded[:, :cols] = bits
+    return np.packbits(padded, axis=1, bitorder="little").view(np.uint64).reshape(rows, mu)
+
+
+def nullspace(A: np.ndarray, m: int) -> dict:
+    """A basis of {x : A x = 0}, read off the reduced row echelon form as in
+    the textbook: for the j-th free (non-pivot) column f_j, in increasing
+    order, basis vector j has x[f_j] = 1, x[pivcols[t]] = R[t][f_j] and every
+    other entry 0.  Returns dict(N row-major words (m, ceil(nul/64)) with row
+    i = variable i and bit j = basis vector j, nul, rank)."""
+    red = rref(A, m)
+    r, piv = red["rank"], red["pivcols"].astype(np.int64)
+    Rb = _unpack(red["R"], m)
+    free = np.setdiff1d(np.arange(m), piv)
+    nul = m - r
+    Nb = np.zeros((m, nul), dtype=bool)
+    Nb[free, np.arange(nul)] = True
+    if r and nul:
+        Nb[piv, :] = Rb[:, free]
+    return dict(N=_pack(Nb), nul=nul, rank=r)
+
+
 if __name__ == "__main__":  # pragma: no cover - manual build helper
     print(build(force="--force" in sys.argv))

@@ -90,6 +90,10 @@ def load() -> ctypes.CDLL:
     lib.gf2_decompose_workspace_bytes.argtypes = [I64, I64, ctypes.c_int]
     lib.gf2_decompose.restype = ctypes.c_int
     lib.gf2_decompose.argtypes = [M, P, P, P, M, M, ctypes.c_uint, P, S, P]
+    lib.gf2_nullspace_workspace_bytes.restype = S
+    lib.gf2_nullspace_workspace_bytes.argtypes = [I64, I64]
+    lib.gf2_nullspace.restype = ctypes.c_int
+    lib.gf2_nullspace.argtypes = [M, P, I64, M, P, S, P]
     lib.gf2_rref_workspace_bytes.restype = S
     lib.gf2_rref_workspace_bytes.argtypes = [I64, I64]
     lib.gf2_rref.restype = ctypes.c_int
@@ -334,6 +338,28 @@ def decompose_batched(As: list, factors: bool = True, flags: int = 0, stream=Non
         out.append(dict(perm=perms[i][:a.rows], pivcols=pivs[i][:k], rank=ranks[i:i + 1],
                         L=Ls[i] if factors else None, E=Es[i] if factors else None))
     return out
+
+
+def gf2_nullspace(R: Mat, pivcols: torch.Tensor, rank: int, N: Mat, workspace=None, stream=None) -> None:
+    """N (m x (m - rank)) <- the null-space basis read off the reduced row
+    echelon form R and its pivot columns."""
+    lib = load()
+    if workspace is None:
+        workspace = _workspace(lib.gf2_nullspace_workspace_bytes(R.cols, rank), N.t.device)
+    r, nn = R.c(), N.c()
+    _check(lib.gf2_nullspace(ctypes.byref(r), _ptr(pivcols), int(rank), ctypes.byref(nn), workspace.data_ptr(),
+                             workspace.numel(), _stream(stream)), "gf2_nullspace")
+
+
+def nullspace(A: Mat, stream=None) -> Mat:
+    """A basis of {x : A x = 0} as the columns of an m x (m - rank) Mat:
+    decompose, reduce E, read the basis off (synchronises once for the rank)."""
+    out = decompose(A, stream=stream)
+    R = rref(out, stream=stream)
+    r = int(out["rank"].item())
+    N = Mat.empty(A.cols, A.cols - r, A.t.device)
+    gf2_nullspace(R, out["pivcols"], r, N, stream=stream)
+    return N
 
 
 def rref(factors: dict, stream=None) -> Mat:

@@ -636,6 +636,35 @@ int gf2_decompose(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *ra
                           static_cast<cudaStream_t>(stream));
 }
 
+size_t gf2_nullspace_workspace_bytes(int64_t m, int64_t rank)
+{
+    if (m < 0 || rank < 0 || rank > m) return 0;
+    return align_up((size_t)(m - rank > 0 ? m - rank : 1) * 4) + kAlign;
+}
+
+int gf2_nullspace(const gf2_mat *R, const int32_t *pivcols, int64_t rank, gf2_mat *N, void *workspace,
+                  size_t ws_bytes, void *stream)
+{
+    if (!R || !N || R->rows < 0 || R->cols < 0 || rank < 0) return GF2_ERR_ARG;
+    const int64_t k = R->rows, m = R->cols;
+    if (rank > (k < m ? k : m)) return GF2_ERR_ARG;
+    if (m >= (1ll << 31) - 64) return GF2_ERR_UNSUPPORTED;
+    const int64_t nul = m - rank;
+    if (!mat_ok(N) || N->rows != m || N->cols != nul) return GF2_ERR_SHAPE;
+    if (nul == 0 || m == 0) return GF2_OK;
+    if (rank > 0 && (!mat_ok(R) || !R->w || !pivcols)) return GF2_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *ws = nullptr;
+    int st = get_workspace(workspace, ws_bytes, gf2_nullspace_workspace_bytes(m, rank), &ws);
+    if (st) return st;
+    // (the free list is fully written for a valid pivot list; cleared first so
+    // that any other list reads as -1 entries, which contribute nothing)
+    CK(cudaMemsetAsync(ws, 0xff, (size_t)nul * 4, s));
+    LAUNCH(GF2_KCLASS_LAYOUT, launch_nullspace(R->w, R->ld, pivcols, rank, m, static_cast<int32_t *>(ws), N->w,
+                                               N->ld, s));
+    return GF2_OK;
+}
+
 size_t gf2_rref_workspace_bytes(int64_t k, int64_t m)
 {
     if (k < 0 || m < 0) return 0;
@@ -661,35 +690,90 @@ int gf2_rref(gf2_mat *E, const int32_t *pivcols, void *workspace, size_t ws_byte
     return rref_rec(*E, pivcols, 0, k, tmp, s);
 }
 
-size_t gf2_rank_workspace_bytes(int64_t n, int64_t m)
+}  // extern "C"
+namespace {
+// gf2_rank: a wide matrix (n < m) is ranked through its transpose (m x n,
+// more rows than columns: fewer panels and a cheaper update, Section 7),
+// which sits at the front of the workspace; then the decomposition's own
+// workspace, perm (one entry per row of the matrix decomposed), pivcols and
+// the rank.
+struct RankLayout {
+    bool transposed;
+    int64_t rows, cols;  // of the matrix decomposed
+    size_t oT, oDec, oPerm, oPiv, oRank, total;
+};
+
+RankLayout rank_layout(int64_t n, int64_t m)
 {
-    if (n < 0 || m < 0) return 0;
+    RankLayout d{};
+    d.transposed = n > 0 && n < m;
+    d.rows = d.transposed ? m : n;
+    d.cols = d.transposed ? n : m;
     const int64_t kmax = n < m ? n : m;
-    return gf2_decompose_workspace_bytes(n, m, 0) + align_up((size_t)(n > 0 ? n : 1) * 4) +
-           align_up((size_t)(kmax > 0 ? kmax : 1) * 4) + kAlign;
+    size_t o = 0;
+    d.oT = o;
+    if (d.transposed) o += align_up((size_t)words_of(n) * (size_t)m * 8);
+    d.oDec = o;
+    o += gf2_decompose_workspace_bytes(d.rows, d.cols, 0);
+    d.oPerm = o;
+    o += align_up((size_t)(d.rows > 0 ? d.rows : 1) * 4);
+    d.oPiv = o;
+    o += align_up((size_t)(kmax > 0 ? kmax : 1) * 4);
+    d.oRank = o;
+    o += kAlign;
+    d.total = o + kAlign;  // + the padding flag of the transposed route
+    return d;
 }
 
-int gf2_rank(const gf2_mat *A, int64_t *rank_host, unsigned flags, void *workspace, size_t ws_bytes, void *stream)
+int rank_impl(const gf2_mat *A, int64_t *rank_host, unsigned flags, void *workspace, size_t ws_bytes, cudaStream_t s)
 {
-    if (!A || !rank_host) return GF2_ERR_ARG;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!A || !rank_host || (flags & ~GF2_NOCHECK) || !mat_ok(A)) return GF2_ERR_ARG;
     const int64_t n = A->rows, m = A->cols;
-    const int64_t kmax = n < m ? n : m;
-    // perm, pivcols and the rank live in a small tail of the workspace
-    const size_t dec = gf2_decompose_workspace_bytes(n, m, 0);
-    const size_t extra = align_up((size_t)(n > 0 ? n : 1) * 4) + align_up((size_t)(kmax > 0 ? kmax : 1) * 4) + kAlign;
+    const RankLayout d = rank_layout(n, m);
     void *ws = nullptr;
-    int st = get_workspace(workspace, ws_bytes, gf2_rank_workspace_bytes(n, m), &ws);
+    int st = get_workspace(workspace, ws_bytes, d.total, &ws);
     if (st) return st;
     char *base = static_cast<char *>(ws);
-    int32_t *perm = reinterpret_cast<int32_t *>(base + dec);
-    int32_t *piv = reinterpret_cast<int32_t *>(base + dec + align_up((size_t)(n > 0 ? n : 1) * 4));
-    int64_t *rk = reinterpret_cast<int64_t *>(base + dec + extra - kAlign);
-    st = decompose_impl(A, perm, piv, rk, nullptr, nullptr, flags, base, dec, s);
+    int32_t *perm = reinterpret_cast<int32_t *>(base + d.oPerm);
+    int32_t *piv = reinterpret_cast<int32_t *>(base + d.oPiv);
+    int64_t *rk = reinterpret_cast<int64_t *>(base + d.oRank);
+    const size_t dec = gf2_decompose_workspace_bytes(d.rows, d.cols, 0);
+    if (!d.transposed) {
+        st = decompose_impl(A, perm, piv, rk, nullptr, nullptr, flags, base + d.oDec, dec, s);
+    } else {
+        if (n >= (1ll << 31) - 64 || m >= (1ll << 31) - 64) return GF2_ERR_UNSUPPORTED;
+        if (!(flags & GF2_NOCHECK) && (m % 64)) {
+            // the padding bits of A's last column block (they would become
+            // rows past m of the transpose, which are not written)
+            uint32_t *flag = reinterpret_cast<uint32_t *>(base + d.total - kAlign);
+            CK(cudaMemsetAsync(flag, 0, sizeof(uint32_t), s));
+            LAUNCH(GF2_KCLASS_LAYOUT, launch_check_last_block(A->w + (words_of(m) - 1) * A->ld, (int)n,
+                                                              last_word_mask(m), flag, s));
+            st = check_flag(flag, s);
+            if (st) return st;
+        }
+        uint64_t *T = reinterpret_cast<uint64_t *>(base + d.oT);
+        LAUNCH(GF2_KCLASS_LAYOUT, launch_transpose_bits(A->w, A->ld, n, m, T, m, s));
+        const gf2_mat At{T, m, n, m};
+        st = decompose_impl(&At, perm, piv, rk, nullptr, nullptr, flags | GF2_NOCHECK, base + d.oDec, dec, s);
+    }
     if (st) return st;
     CK(cudaMemcpyAsync(rank_host, rk, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return GF2_OK;
+}
+}  // namespace
+extern "C" {
+
+size_t gf2_rank_workspace_bytes(int64_t n, int64_t m)
+{
+    if (n < 0 || m < 0) return 0;
+    return rank_layout(n, m).total;
+}
+
+int gf2_rank(const gf2_mat *A, int64_t *rank_host, unsigned flags, void *workspace, size_t ws_bytes, void *stream)
+{
+    return rank_impl(A, rank_host, flags, workspace, ws_bytes, static_cast<cudaStream_t>(stream));
 }
 
 size_t gf2_decompose_host_workspace_bytes(int64_t n, int64_t m, int want_factors)

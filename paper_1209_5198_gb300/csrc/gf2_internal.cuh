@@ -203,6 +203,9 @@ cudaError_t launch_mma_product(const uint64_t *A, int64_t lda, const uint64_t *B
                                cudaStream_t s);
 cudaError_t launch_check_last_block(const uint64_t *last, int rows, uint64_t mask, uint32_t *err, cudaStream_t s);
 cudaError_t launch_batch(const BatchCtx &b, int grid, int c, cudaStream_t s);
+// T = A^T for A n x m in column blocks (T: m x n, ld ldt >= m; csrc/k_transpose.cu)
+cudaError_t launch_transpose_bits(const uint64_t *A, int64_t lda, int64_t n, int64_t m, uint64_t *T, int64_t ldt,
+                                  cudaStream_t s);
 // the reduced row echelon form (csrc/k_rref.cu): every 64-row block of E
 // (k x m) reduced by its own pivot columns (V: 64 ceil(k/64) words of
 // scratch), and the bits of rows [a, a+rows) at the columns
@@ -211,6 +214,10 @@ cudaError_t launch_rref_diag(uint64_t *E, int64_t ld, const int32_t *pivcols, in
                              cudaStream_t s);
 cudaError_t launch_gather_cols(const uint64_t *E, int64_t ld, int64_t m, const int32_t *pivcols, int64_t a, int64_t rows,
                                int64_t c0, int64_t ncols, uint64_t *out, int64_t ldo, cudaStream_t s);
+// the null-space basis N (m x (m - r), ld ldn) from R and its r pivot
+// columns (free: m - r int32 of scratch)
+cudaError_t launch_nullspace(const uint64_t *R, int64_t ldr, const int32_t *pivcols, int64_t r, int64_t m, int32_t *free,
+                             uint64_t *N, int64_t ldn, cudaStream_t s);
 
 // ---- host helpers shared by the entry points (gf2_api.cu)
 // the batched decomposition of checked items (each n, m <= 4096); with

@@ -14,6 +14,7 @@
 //   k_gather_cols the bits of a range of rows at a range of pivot columns,
 //                 as a matrix in column blocks: the left operand of the
 //                 product E_top ^= E_top[:, pivots of the bottom] R_bottom.
+// And the null-space basis read off R (k_free_cols, k_nullspace_fill).
 #include "m4rm_core.cuh"
 #include "panel_core.cuh"
 
@@ -116,6 +117,58 @@ __global__ void k_gather_cols(const uint64_t *__restrict__ E, int64_t ld, int64_
     }
 }
 
+// the first t < r with pivcols[t] >= c (pivcols increasing)
+__device__ __forceinline__ int64_t pivot_lower_bound(const int32_t *pivcols, int64_t r, int64_t c)
+{
+    int64_t lo = 0, hi = r;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if (pivcols[mid] < c) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// free[j] = the j-th column (increasing) that is not a pivot column
+__global__ void k_free_cols(const int32_t *__restrict__ pivcols, int64_t r, int64_t m, int32_t *__restrict__ free)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < m; c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t lb = pivot_lower_bound(pivcols, r, c);
+        if (lb < r && pivcols[lb] == c) continue;
+        if (c - lb < m - r) free[c - lb] = (int32_t)c;  // (in range for any pivot list)
+    }
+}
+
+// The null-space basis read off the reduced row echelon form R (Section 1
+// names it among the uses of the decomposition): N (m x nul, nul = m - r)
+// has column j = the solution of R x = 0 with free variable f_j = 1 and the
+// other free variables 0, so row f_j of N is the unit word e_j and row
+// pivcols[t] is R's row t at the free columns.  Thread per row of N.
+__global__ void k_nullspace_fill(const uint64_t *__restrict__ R, int64_t ldr, const int32_t *__restrict__ pivcols,
+                                 int64_t r, const int32_t *__restrict__ free, int64_t nul, uint64_t *__restrict__ N,
+                                 int64_t ldn, int64_t m)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int64_t lb = pivot_lower_bound(pivcols, r, i);
+    const bool pivot = lb < r && pivcols[lb] == i;
+    const int64_t words = (nul + 63) / 64;
+    for (int64_t q = blockIdx.y; q < words; q += gridDim.y) {
+        uint64_t v = 0;
+        if (pivot) {
+            const int tmax = (int)(nul - 64 * q < 64 ? nul - 64 * q : 64);
+            for (int b = 0; b < tmax; ++b) {
+                const int f = free[64 * q + b];
+                if (f >= 0 && f < m) v |= ((R[(int64_t)(f >> 6) * ldr + lb] >> (f & 63)) & 1ull) << b;
+            }
+        } else {
+            const int64_t j = i - lb;  // this free column's index
+            v = (j >> 6) == q ? 1ull << (j & 63) : 0;
+        }
+        N[q * ldn + i] = v;
+    }
+}
+
 int rref_sms()
 {
     static int sms = 0;
@@ -155,6 +208,22 @@ cudaError_t launch_gather_cols(const uint64_t *E, int64_t ld, int64_t m, const i
     const int64_t words = (ncols + 63) / 64;
     const int64_t gx = (rows + 255) / 256, gy = words < 65535 ? words : 65535;
     k_gather_cols<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(E, ld, m, pivcols, a, rows, c0, ncols, out, ldo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nullspace(const uint64_t *R, int64_t ldr, const int32_t *pivcols, int64_t r, int64_t m, int32_t *free,
+                             uint64_t *N, int64_t ldn, cudaStream_t s)
+{
+    const int64_t nul = m - r;
+    if (m <= 0 || nul <= 0) return cudaSuccess;
+    int64_t g = (m + 255) / 256;
+    if (g > 16 * (int64_t)rref_sms()) g = 16 * (int64_t)rref_sms();
+    k_free_cols<<<(unsigned)g, 256, 0, s>>>(pivcols, r, m, free);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t words = (nul + 63) / 64;
+    const int64_t gx = (m + 255) / 256, gy = words < 65535 ? words : 65535;
+    k_nullspace_fill<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(R, ldr, pivcols, r, free, nul, N, ldn, m);
     return cudaGetLastError();
 }
 
