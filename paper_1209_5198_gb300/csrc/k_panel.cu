@@ -5,24 +5,31 @@
 namespace gf2 {
 namespace {
 
+// Dynamic shared memory of the panel kernel (see kPanelReserveBytes): the
+// first kPanelListCap entries of the row list of the general path.
+constexpr int kPanelReserveBytes = 160 * 1024;
+constexpr int kPanelListCap = kPanelReserveBytes / 12 / 8 * 8;
+
 // <= 128 registers: 128 x 128 fits next to a 512 x 96 k_rest CTA on one SM
 __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
 {
     __shared__ PanelShared sh;
+    extern __shared__ __align__(16) uint64_t panel_dyn[];
     // Launched as a programmatic dependent of the previous panel: wait until
     // that launch has completed and its writes are visible, then let the
     // next panel be scheduled (it waits here in turn).  Without the launch
     // attribute both are no-ops.
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    panel_block(c, j, sh);
+    panel_block(c, j, sh, panel_dyn, kPanelListCap);
 }
 
-// Unused dynamic shared memory that keeps a panel CTA off any SM holding a
+// The dynamic shared memory also keeps a panel CTA off any SM holding a
 // persistent k_rest CTA (about 67 KB; with this reserve the two need more
 // than the 228 KB of an SM): the panel runs on the SM k_rest leaves free,
-// without other warps competing for its scheduler.
-constexpr int kPanelReserveBytes = 160 * 1024;
+// without other warps competing for its scheduler.  The general path keeps
+// its row list there.
+static_assert(kPanelListCap * 12 <= kPanelReserveBytes, "row list in the reserve");
 
 }  // namespace
 

@@ -96,6 +96,13 @@ struct PanelShared {
     uint64_t mask;
     unsigned long long orv;
     int req, from, found;
+    // the panel's list of nonzero rows behind the window (general path, when
+    // the context provides zpos / zraw): entries [0, zn) are the positions
+    // with a nonzero panel word among [zfrom, zto), in position order, and
+    // their raw words; zhead: the first entry at or after the current scan's
+    // start; found_idx: the entry of the row a scan found
+    int zn, zfrom, zto, zhead, found_idx;
+    int wcnt[kPanelThreads / 32];
 };
 
 // Word j of storage row i with the updates of every panel < j.  W holds it
@@ -149,19 +156,122 @@ __device__ __forceinline__ uint64_t reduce_word(const PanelShared &sh, uint64_t 
     return r;
 }
 
+// Storage of the row list: entries below cap in shared memory (the panel
+// kernel's otherwise unused dynamic shared memory), the rest in c.zpos /
+// c.zraw (same index).
+struct RowList {
+    uint64_t *raw;
+    int32_t *pos;
+    int cap;
+};
+
+__device__ __forceinline__ int32_t list_pos(const DecompCtx &c, const RowList &L, int e)
+{
+    return e < L.cap ? L.pos[e] : c.zpos[e];
+}
+
+__device__ __forceinline__ uint64_t list_raw(const DecompCtx &c, const RowList &L, int e)
+{
+    return e < L.cap ? L.raw[e] : c.zraw[e];
+}
+
+__device__ __forceinline__ void list_put(const DecompCtx &c, const RowList &L, int e, int32_t p, uint64_t v)
+{
+    if (e < L.cap) {
+        L.pos[e] = p;
+        L.raw[e] = v;
+    } else {
+        c.zpos[e] = p;
+        c.zraw[e] = v;
+    }
+}
+
 // Positions [from, n): first one whose panel word w has parity(w & mask) = 1.
 // The same pass ORs the fully reduced words into sh.orv, so that when no
 // position qualifies sh.orv holds the OR over all of them (a block whose
 // remaining rows are zero, as once the rank is used up, costs one pass).
-__device__ void scan_find(const DecompCtx &c, const uint64_t *Wj, const PrevPanel &pv, PanelShared &sh)
+//
+// With a row list (c.zpos): the rows already read in this panel are tested
+// from the list of the nonzero ones (a zero row never qualifies and adds
+// nothing to the OR), and the pass over the rows behind the list appends the
+// nonzero rows it reads.  So every row is read from memory at most once per
+// panel, however many bits need a scan -- sparse blocks, where most rows are
+// zero and most bits find no candidate in the window, scan for nearly every
+// bit.  A raw word does not change during the panel (the parity test takes
+// the current pivots through the mask); the exchange that moves the pivot
+// slot's row to a listed position updates that entry.
+__device__ __noinline__ void scan_find(const DecompCtx &c, const uint64_t *Wj, const PrevPanel pv, PanelShared &sh,
+                                       const RowList L)
 {
-    constexpr int U = 4;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     build_reduction_tables(sh);
     const int from = sh.from, n = c.n;
     const uint64_t mask = sh.mask;
     uint64_t acc = 0;
-    for (int base = from; base < n; base += kPanelThreads * U) {
+    if (!c.zpos) {
+        constexpr int U = 4;
+        for (int base = from; base < n; base += kPanelThreads * U) {
+            int srow[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int q = base + u * kPanelThreads + tid;
+                srow[u] = q < n ? c.perm[q] : -1;
+            }
+            uint64_t v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = srow[u] >= 0 ? panel_word(Wj, pv, sh, srow[u]) : 0;
+            int hit = 0;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                acc |= reduce_word(sh, v[u]);
+                if (!hit && (__popcll(v[u] & mask) & 1)) {
+                    atomicMin(&sh.found, base + u * kPanelThreads + tid);
+                    hit = 1;
+                }
+            }
+            if (__syncthreads_or(hit)) break;
+        }
+        acc = warp_or(acc);
+        if (lane == 0 && acc) atomicOr(&sh.orv, (unsigned long long)acc);
+        return;
+    }
+
+    // the list: started by the panel's first scan; its head moved to `from`
+    if (tid == 0) {
+        if (sh.zfrom < 0) {
+            sh.zfrom = sh.zto = from;
+            sh.zn = 0;
+            sh.zhead = 0;
+        }
+        int h = sh.zhead;
+        while (h < sh.zn && list_pos(c, L, h) < from) ++h;
+        sh.zhead = h;
+    }
+    __syncthreads();
+    bool found = false;
+    {
+        const int zn = sh.zn;
+        for (int b = sh.zhead; b < zn && !found; b += kPanelThreads * 4) {
+            int hit = 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = b + u * kPanelThreads + tid;
+                if (e < zn) {
+                    const uint64_t v = list_raw(c, L, e);
+                    acc |= reduce_word(sh, v);
+                    if (!hit && (__popcll(v & mask) & 1)) {
+                        atomicMin(&sh.found_idx, e);
+                        hit = 1;
+                    }
+                }
+            }
+            found = __syncthreads_or(hit);
+        }
+    }
+    // the rows behind the list, appended in position order
+    constexpr int U = 8;
+    const int p0 = max(from, sh.zto);
+    for (int base = p0; base < n && !found; base += kPanelThreads * U) {
         int srow[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -171,19 +281,45 @@ __device__ void scan_find(const DecompCtx &c, const uint64_t *Wj, const PrevPane
         uint64_t v[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) v[u] = srow[u] >= 0 ? panel_word(Wj, pv, sh, srow[u]) : 0;
-        int hit = 0;
+        uint64_t any = 0;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             acc |= reduce_word(sh, v[u]);
-            if (!hit && (__popcll(v[u] & mask) & 1)) {
-                atomicMin(&sh.found, base + u * kPanelThreads + tid);
-                hit = 1;
+            any |= v[u];
+        }
+        int hit = 0;
+        if (__syncthreads_or(any != 0)) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool nz = v[u] != 0;
+                const unsigned bal = __ballot_sync(kFull, nz);
+                if (lane == 0) sh.wcnt[warp] = __popc(bal);
+                __syncthreads();
+                int off = sh.zn, total = 0;
+#pragma unroll
+                for (int w = 0; w < kPanelThreads / 32; ++w) {
+                    off += w < warp ? sh.wcnt[w] : 0;
+                    total += sh.wcnt[w];
+                }
+                if (nz) {
+                    const int e = off + __popc(bal & ((1u << lane) - 1));
+                    list_put(c, L, e, base + u * kPanelThreads + tid, v[u]);
+                    if (!hit && (__popcll(v[u] & mask) & 1)) {
+                        atomicMin(&sh.found_idx, e);
+                        hit = 1;
+                    }
+                }
+                __syncthreads();  // every thread has read sh.zn and the counts
+                if (tid == 0) sh.zn += total;
             }
         }
-        if (__syncthreads_or(hit)) break;
+        if (tid == 0) sh.zto = min(base + kPanelThreads * U, n);
+        found = __syncthreads_or(hit);
     }
     acc = warp_or(acc);
-    if ((tid & 31) == 0 && acc) atomicOr(&sh.orv, (unsigned long long)acc);
+    if (lane == 0 && acc) atomicOr(&sh.orv, (unsigned long long)acc);
+    __syncthreads();
+    if (tid == 0 && found) sh.found = list_pos(c, L, sh.found_idx);
 }
 
 // Fast-path state of warp 0.  The 96 rows of positions R..R+95 are held
@@ -292,8 +428,12 @@ __device__ __forceinline__ bool fast_phase(FastCols &st, int nbits, int smax, bo
 
 // The panel step of block j, run by one CTA of kPanelThreads threads (warp 0
 // searches, warps 1..3 serve the scans of the general path).
-__device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShared &sh)
+// zs / zcap: shared memory for the first zcap entries of the row list (zcap
+// words of raw rows, then zcap int32 positions), or none.
+__device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShared &sh, uint64_t *zs = nullptr,
+                                            int zcap = 0)
 {
+    const RowList L{zs, zs ? reinterpret_cast<int32_t *>(zs + zcap) : nullptr, zs ? zcap : 0};
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int R = j == 0 ? 0 : panel_info(c, j - 1)->R + panel_info(c, j - 1)->r;
     const int n = c.n;
@@ -301,6 +441,7 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
     PanelInfo *pi = panel_info(c, j);
     const uint64_t *Wj = c.W + (int64_t)(j / kTileWords) * c.tstride + (j % kTileWords);  // word j of row i: Wj[T i]
 
+    if (tid == 0) sh.zfrom = -1;  // no row list yet in this panel
     if (R >= n || nbits <= 0) {
         if (tid == 0) {
             pi->R = R;
@@ -366,7 +507,7 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
             bar_sync(1, kPanelThreads);
             const int req = sh.req;
             if (req == kReqDone) return;
-            scan_find(c, Wj, pv, sh);
+            scan_find(c, Wj, pv, sh, L);
             bar_sync(2, kPanelThreads);
         }
     }
@@ -386,11 +527,12 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
             sh.from = from;
             sh.mask = mask;
             sh.found = INT_MAX;
+            sh.found_idx = INT_MAX;
             sh.orv = orv;
         }
         __syncwarp();
         bar_sync(1, kPanelThreads);
-        scan_find(c, Wj, pv, sh);
+        scan_find(c, Wj, pv, sh, L);
         bar_sync(2, kPanelThreads);
     };
 
@@ -599,6 +741,8 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
                     if (lane == 0) {
                         c.perm[ib] = psrow;
                         c.perm[q] = sh.slot_srow[hs];
+                        if (c.zpos)  // the list entry of position q
+                            list_put(c, L, sh.found_idx, q, sh.slot_raw[hs]);
                         c.pivpanel[psrow] = j;
                         sh.B[s] = v;
                         sh.prow[s] = psrow;
