@@ -102,6 +102,7 @@ struct PanelShared {
     // their raw words; zhead: the first entry at or after the current scan's
     // start; found_idx: the entry of the row a scan found
     int zn, zfrom, zto, zhead, found_idx;
+    uint64_t found_raw;  // the raw word of the row found (with the list)
     int wcnt[kPanelThreads / 32];
 };
 
@@ -204,11 +205,11 @@ __device__ __noinline__ void scan_find(const DecompCtx &c, const uint64_t *Wj, c
                                        const RowList L)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    build_reduction_tables(sh);
     const int from = sh.from, n = c.n;
     const uint64_t mask = sh.mask;
     uint64_t acc = 0;
     if (!c.zpos) {
+        build_reduction_tables(sh);
         constexpr int U = 4;
         for (int base = from; base < n; base += kPanelThreads * U) {
             int srow[U];
@@ -258,7 +259,6 @@ __device__ __noinline__ void scan_find(const DecompCtx &c, const uint64_t *Wj, c
                 const int e = b + u * kPanelThreads + tid;
                 if (e < zn) {
                     const uint64_t v = list_raw(c, L, e);
-                    acc |= reduce_word(sh, v);
                     if (!hit && (__popcll(v & mask) & 1)) {
                         atomicMin(&sh.found_idx, e);
                         hit = 1;
@@ -283,10 +283,7 @@ __device__ __noinline__ void scan_find(const DecompCtx &c, const uint64_t *Wj, c
         for (int u = 0; u < U; ++u) v[u] = srow[u] >= 0 ? panel_word(Wj, pv, sh, srow[u]) : 0;
         uint64_t any = 0;
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            acc |= reduce_word(sh, v[u]);
-            any |= v[u];
-        }
+        for (int u = 0; u < U; ++u) any |= v[u];
         int hit = 0;
         if (__syncthreads_or(any != 0)) {
 #pragma unroll
@@ -316,10 +313,21 @@ __device__ __noinline__ void scan_find(const DecompCtx &c, const uint64_t *Wj, c
         if (tid == 0) sh.zto = min(base + kPanelThreads * U, n);
         found = __syncthreads_or(hit);
     }
-    acc = warp_or(acc);
-    if (lane == 0 && acc) atomicOr(&sh.orv, (unsigned long long)acc);
+    // no row qualifies: every nonzero row behind the window is now listed, so
+    // their OR comes from the list (only this case needs the reduction
+    // tables; a scan that finds its row skips them)
+    if (!found) {
+        build_reduction_tables(sh);
+        const int zh = sh.zhead, zn = sh.zn;
+        for (int e = zh + tid; e < zn; e += kPanelThreads) acc |= reduce_word(sh, list_raw(c, L, e));
+        acc = warp_or(acc);
+        if (lane == 0 && acc) atomicOr(&sh.orv, (unsigned long long)acc);
+    }
     __syncthreads();
-    if (tid == 0 && found) sh.found = list_pos(c, L, sh.found_idx);
+    if (tid == 0 && found) {
+        sh.found = list_pos(c, L, sh.found_idx);
+        sh.found_raw = list_raw(c, L, sh.found_idx);
+    }
 }
 
 // Fast-path state of warp 0.  The 96 rows of positions R..R+95 are held
@@ -726,7 +734,7 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
                     // pivot outside the window; the row in the pivot slot
                     // moves there and leaves the window
                     const int psrow = c.perm[q];
-                    const uint64_t v = panel_word(Wj, pv, sh, psrow);
+                    const uint64_t v = c.zpos ? sh.found_raw : panel_word(Wj, pv, sh, psrow);
                     uint64_t red = 0;
                     for (uint64_t b = v; b; b &= b - 1) red ^= sh.pred[__ffsll((long long)b) - 1];
                     const uint32_t eA = (red >> lane) & 1, eB = (red >> (lane + 32)) & 1;
