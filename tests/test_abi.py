@@ -157,3 +157,37 @@ def test_host_entry_point_checks_padding_on_the_host(lib):
                                 perm.ctypes.data_as(ctypes.c_void_p), None, rank.ctypes.data_as(ctypes.c_void_p),
                                 None, None, ctypes.c_uint(0), None, ctypes.c_size_t(0), None)
     assert st == g.GF2_ERR_PADDING
+
+
+def test_reduced_form_null_space_and_rank_workspaces_without_gpu(lib):
+    """Workspace queries and argument checks of gf2_rref, gf2_nullspace,
+    gf2_rank's transposed route and gf2_op_counts answer on the host."""
+    S = ctypes.c_size_t
+    lib.gf2_rref_workspace_bytes.restype = S
+    lib.gf2_nullspace_workspace_bytes.restype = S
+    lib.gf2_rank_workspace_bytes.restype = S
+    lib.gf2_decompose_workspace_bytes.restype = S
+    I64 = ctypes.c_int64
+    lib.gf2_rref_workspace_bytes.argtypes = [I64, I64]
+    lib.gf2_nullspace_workspace_bytes.argtypes = [I64, I64]
+    lib.gf2_rank_workspace_bytes.argtypes = [I64, I64]
+    lib.gf2_decompose_workspace_bytes.argtypes = [I64, I64, ctypes.c_int]
+    # RREF: 64 words per 64-row block plus the top level's gathered operand
+    k = m = 32768
+    assert lib.gf2_rref_workspace_bytes(k, m) >= k * 8 + (k // 2) * (k // 2 // 64) * 8
+    assert lib.gf2_rref_workspace_bytes(-1, 3) == 0
+    assert lib.gf2_rref_workspace_bytes(64, 100) > 0  # one block: no product
+    # null space: one int32 per free column
+    assert lib.gf2_nullspace_workspace_bytes(1000, 300) >= 700 * 4
+    assert lib.gf2_nullspace_workspace_bytes(10, 11) == 0  # rank > m
+    # rank: a wide matrix holds its transpose on top of the decomposition's workspace
+    wide = lib.gf2_rank_workspace_bytes(1000, 5000)
+    assert wide >= ((1000 + 63) // 64) * 5000 * 8 + lib.gf2_decompose_workspace_bytes(5000, 1000, 0)
+    assert lib.gf2_rank_workspace_bytes(5000, 1000) >= lib.gf2_decompose_workspace_bytes(5000, 1000, 0)
+    # argument errors before any device work
+    assert lib.gf2_rref(None, None, None, S(0), None) == 1  # GF2_ERR_ARG
+    assert lib.gf2_nullspace(None, None, I64(0), None, None, S(0), None) == 1
+    out = (ctypes.c_uint64 * 9)()
+    assert lib.gf2_op_counts(None, 9, 0) == 1
+    assert lib.gf2_op_counts(out, -1, 0) == 1
+    assert lib.gf2_op_counts(out, 9, 0) == 7  # GF2_ERR_UNSUPPORTED: the release build counts nothing
