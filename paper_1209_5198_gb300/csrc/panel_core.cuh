@@ -705,6 +705,12 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
     }
 
     if (!fast_complete) refill();
+    // red(e_lane), red(e_lane+32) (the reduced unit rows) in registers: from
+    // the pivots so far at the panel's first scan, then updated with every
+    // pivot added (a new pivot reduces last, so red(e_p) takes its row when
+    // it has the pivot's bit)
+    uint64_t P0 = 0, P1 = 0;
+    bool pred_ok = false;
     while (!fast_complete && k < nbits && ib < n) {
         if (fill < n && fill - ib <= kWin / 2) refill();  // keep the window at least half full
         const uint64_t ck0 = __shfl_sync(kFull, k < 32 ? A : B, k & 31);
@@ -722,9 +728,19 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
             replay();
             if (fill < n) {
                 // the window is full and has no candidate: scan the rows behind it
-                publish_reduced_units();
-                uint64_t ck = 0;  // bit p: entry k of red(e_p)
-                for (int p = 0; p < 64; ++p) ck |= ((sh.pred[p] >> k) & 1) << p;
+                if (!pred_ok) {
+                    publish_reduced_units();
+                    P0 = sh.pred[lane];
+                    P1 = sh.pred[lane + 32];
+                    pred_ok = true;
+                } else {
+                    sh.pred[lane] = P0;
+                    sh.pred[lane + 32] = P1;
+                    __syncwarp();
+                }
+                // bit p: entry k of red(e_p)
+                const uint64_t ck = (uint64_t)__ballot_sync(kFull, (P0 >> k) & 1) |
+                                    ((uint64_t)__ballot_sync(kFull, (P1 >> k) & 1) << 32);
                 // (the OR of the window's reduced rows seeds the scan's OR)
                 const uint64_t wor = (uint64_t)__ballot_sync(kFull, (A & valid) != 0) |
                                      ((uint64_t)__ballot_sync(kFull, (B & valid) != 0) << 32);
@@ -746,6 +762,8 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
                     B &= ~hm;
                     EA |= (uint64_t)eA << s;
                     EB |= (uint64_t)eB << s;
+                    if ((P0 >> k) & 1) P0 ^= red;  // the new pivot's row E_s = red
+                    if ((P1 >> k) & 1) P1 ^= red;
                     if (lane == 0) {
                         c.perm[ib] = psrow;
                         c.perm[q] = sh.slot_srow[hs];
@@ -798,6 +816,11 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
         if (eB) B ^= ck1;
         EA |= (uint64_t)eA << s;
         EB |= (uint64_t)eB << s;
+        if (pred_ok) {  // (only after a scan in this panel)
+            const uint64_t Es = (uint64_t)__ballot_sync(kFull, eA) | ((uint64_t)__ballot_sync(kFull, eB) << 32);
+            if ((P0 >> k) & 1) P0 ^= Es;
+            if ((P1 >> k) & 1) P1 ^= Es;
+        }
         const uint32_t rec = (uint32_t)k | ((uint32_t)f << 8);
         recA = (lane == s) ? rec : recA;
         recB = (lane + 32 == s) ? rec : recB;
