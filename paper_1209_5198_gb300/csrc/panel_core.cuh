@@ -251,11 +251,15 @@ __device__ __noinline__ void scan_find(const DecompCtx &c, const uint64_t *Wj, c
     __syncthreads();
     bool found = false;
     {
+        // (2 entries per thread between barriers: the qualifying row is
+        // usually near the head of the list, and larger steps test rows past
+        // it -- 16 per thread measured 12% slower on S_n, 4 about 1% slower)
+        constexpr int UL = 2;
         const int zn = sh.zn;
-        for (int b = sh.zhead; b < zn && !found; b += kPanelThreads * 4) {
+        for (int b = sh.zhead; b < zn && !found; b += kPanelThreads * UL) {
             int hit = 0;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < UL; ++u) {
                 const int e = b + u * kPanelThreads + tid;
                 if (e < zn) {
                     const uint64_t v = list_raw(c, L, e);
