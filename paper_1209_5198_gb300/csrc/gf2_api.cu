@@ -392,7 +392,7 @@ int enqueue_factorization(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat
 
 struct DecompLayout {
     int64_t mu, ldw, kmax, ldl;
-    size_t oW, oY, oF, oAct, oNact, oPP, oInfo, oZpos, oZraw, oZsrow, oLint, oEint, oFlag, total;
+    size_t oW, oY, oF, oAct, oNact, oPP, oInfo, oZpos, oZraw, oLint, oEint, oFlag, total;
 };
 
 DecompLayout decomp_layout(int64_t n, int64_t m, bool factors)
@@ -412,7 +412,6 @@ DecompLayout decomp_layout(int64_t n, int64_t m, bool factors)
     d.oInfo = o; o += align_up((size_t)(d.mu > 0 ? d.mu : 1) * sizeof(PanelInfo));
     d.oZpos = o; o += align_up((size_t)(n > 0 ? n : 1) * 4);
     d.oZraw = o; o += align_up((size_t)(n > 0 ? n : 1) * 8);
-    d.oZsrow = o; o += align_up((size_t)(n > 0 ? n : 1) * 4);
     d.oLint = o; if (factors) o += align_up((size_t)n * d.ldl * 8);
     d.oEint = o; if (factors) o += align_up((size_t)d.kmax * d.ldw * 8);
     d.oFlag = o; o += kAlign;
@@ -451,7 +450,6 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
     c.pivpanel = reinterpret_cast<int32_t *>(base + d.oPP);
     c.zpos = reinterpret_cast<int32_t *>(base + d.oZpos);
     c.zraw = reinterpret_cast<uint64_t *>(base + d.oZraw);
-    c.zsrow = reinterpret_cast<int32_t *>(base + d.oZsrow);
     c.Lint = factors ? reinterpret_cast<uint64_t *>(base + d.oLint) : nullptr;
     c.ldl = d.ldl;
     c.Eint = factors ? reinterpret_cast<uint64_t *>(base + d.oEint) : nullptr;

@@ -73,8 +73,7 @@ struct DecompCtx {
     uint64_t *Eint;     // [k x lde] per pivot index (row-major), or null
     int32_t n, m, mu, kmax;
     int32_t *zpos;      // [n] the panel's list of nonzero rows behind its window (positions), or null
-    uint64_t *zraw;     // [n] their raw panel words (all three null: the panel scans without a list)
-    int32_t *zsrow;     // [n] their storage rows
+    uint64_t *zraw;     // [n] their raw panel words (both null: the panel scans without a list)
     int32_t pair;       // wide updates by pairs of panels (j even, j+1)
     int32_t info_ring;  // info holds only panels j-1 and j (info[j % 2]): the batched form
 };

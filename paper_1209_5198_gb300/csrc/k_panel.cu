@@ -8,7 +8,7 @@ namespace {
 // Dynamic shared memory of the panel kernel (see kPanelReserveBytes): the
 // first kPanelListCap entries of the row list of the general path.
 constexpr int kPanelReserveBytes = 160 * 1024;
-constexpr int kPanelListCap = kPanelReserveBytes / 16 / 8 * 8;  // 16 bytes per entry
+constexpr int kPanelListCap = kPanelReserveBytes / 12 / 8 * 8;
 
 // <= 128 registers: 128 x 128 fits next to a 512 x 96 k_rest CTA on one SM
 __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
 // than the 228 KB of an SM): the panel runs on the SM k_rest leaves free,
 // without other warps competing for its scheduler.  The general path keeps
 // its row list there.
-static_assert(kPanelListCap * 16 <= kPanelReserveBytes, "row list in the reserve");
+static_assert(kPanelListCap * 12 <= kPanelReserveBytes, "row list in the reserve");
 
 }  // namespace
 

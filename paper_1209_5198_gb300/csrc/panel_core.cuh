@@ -102,8 +102,7 @@ struct PanelShared {
     // their raw words; zhead: the first entry at or after the current scan's
     // start; found_idx: the entry of the row a scan found
     int zn, zfrom, zto, zhead, found_idx;
-    uint64_t found_raw;  // the raw word and storage row of the row found (with the list)
-    int found_srow;
+    uint64_t found_raw;  // the raw word of the row found (with the list)
     int wcnt[kPanelThreads / 32];
 };
 
@@ -160,11 +159,10 @@ __device__ __forceinline__ uint64_t reduce_word(const PanelShared &sh, uint64_t 
 
 // Storage of the row list: entries below cap in shared memory (the panel
 // kernel's otherwise unused dynamic shared memory), the rest in c.zpos /
-// c.zraw / c.zsrow (same index).  An entry: a position, the raw word of the
-// row there and its storage row.
+// c.zraw (same index).
 struct RowList {
     uint64_t *raw;
-    int32_t *pos, *srow;
+    int32_t *pos;
     int cap;
 };
 
@@ -178,22 +176,14 @@ __device__ __forceinline__ uint64_t list_raw(const DecompCtx &c, const RowList &
     return e < L.cap ? L.raw[e] : c.zraw[e];
 }
 
-__device__ __forceinline__ int32_t list_srow(const DecompCtx &c, const RowList &L, int e)
-{
-    return e < L.cap ? L.srow[e] : c.zsrow[e];
-}
-
-__device__ __forceinline__ void list_put(const DecompCtx &c, const RowList &L, int e, int32_t p, uint64_t v,
-                                         int32_t sr)
+__device__ __forceinline__ void list_put(const DecompCtx &c, const RowList &L, int e, int32_t p, uint64_t v)
 {
     if (e < L.cap) {
         L.pos[e] = p;
         L.raw[e] = v;
-        L.srow[e] = sr;
     } else {
         c.zpos[e] = p;
         c.zraw[e] = v;
-        c.zsrow[e] = sr;
     }
 }
 
@@ -314,7 +304,7 @@ __device__ __noinline__ void scan_find(const DecompCtx &c, const uint64_t *Wj, c
                 }
                 if (nz) {
                     const int e = off + __popc(bal & ((1u << lane) - 1));
-                    list_put(c, L, e, base + u * kPanelThreads + tid, v[u], srow[u]);
+                    list_put(c, L, e, base + u * kPanelThreads + tid, v[u]);
                     if (!hit && (__popcll(v[u] & mask) & 1)) {
                         atomicMin(&sh.found_idx, e);
                         hit = 1;
@@ -341,7 +331,6 @@ __device__ __noinline__ void scan_find(const DecompCtx &c, const uint64_t *Wj, c
     if (tid == 0 && found) {
         sh.found = list_pos(c, L, sh.found_idx);
         sh.found_raw = list_raw(c, L, sh.found_idx);
-        sh.found_srow = list_srow(c, L, sh.found_idx);
     }
 }
 
@@ -452,13 +441,11 @@ __device__ __forceinline__ bool fast_phase(FastCols &st, int nbits, int smax, bo
 // The panel step of block j, run by one CTA of kPanelThreads threads (warp 0
 // searches, warps 1..3 serve the scans of the general path).
 // zs / zcap: shared memory for the first zcap entries of the row list (zcap
-// words of raw rows, then zcap int32 positions and zcap int32 storage rows),
-// or none.
+// words of raw rows, then zcap int32 positions), or none.
 __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShared &sh, uint64_t *zs = nullptr,
                                             int zcap = 0)
 {
-    const RowList L{zs, zs ? reinterpret_cast<int32_t *>(zs + zcap) : nullptr,
-                    zs ? reinterpret_cast<int32_t *>(zs + zcap) + zcap : nullptr, zs ? zcap : 0};
+    const RowList L{zs, zs ? reinterpret_cast<int32_t *>(zs + zcap) : nullptr, zs ? zcap : 0};
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int R = j == 0 ? 0 : panel_info(c, j - 1)->R + panel_info(c, j - 1)->r;
     const int n = c.n;
@@ -766,7 +753,7 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
                 if (q != INT_MAX) {
                     // pivot outside the window; the row in the pivot slot
                     // moves there and leaves the window
-                    const int psrow = c.zpos ? sh.found_srow : c.perm[q];
+                    const int psrow = c.perm[q];
                     const uint64_t v = c.zpos ? sh.found_raw : panel_word(Wj, pv, sh, psrow);
                     uint64_t red = 0;
                     for (uint64_t b = v; b; b &= b - 1) red ^= sh.pred[__ffsll((long long)b) - 1];
@@ -785,7 +772,7 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
                         c.perm[ib] = psrow;
                         c.perm[q] = sh.slot_srow[hs];
                         if (c.zpos)  // the list entry of position q
-                            list_put(c, L, sh.found_idx, q, sh.slot_raw[hs], sh.slot_srow[hs]);
+                            list_put(c, L, sh.found_idx, q, sh.slot_raw[hs]);
                         c.pivpanel[psrow] = j;
                         sh.B[s] = v;
                         sh.prow[s] = psrow;
