@@ -19,9 +19,13 @@
  *                   Procedure buildZ (first qualifying row in current order,
  *                   transposition with the current pivot slot), Section 4.3.
  *   f2o_blockdecomp The iterative block decomposition of Section 4 (eq. (Aj),
- *                   Lemma 4.1) with Procedure buildZ (Sections 4.1-4.4) for
- *                   a general word size b <= 64, and in-place storage as in
- *                   Figure 1.  Second, independent route to the same P.
+ *                   Lemma 4.1) for a general word size b <= 64, with the
+ *                   pivot rows and pseudo-inverse of each block grown by the
+ *                   incremental inverse of Section 4.2 (eqs. Bk:FACT,
+ *                   cond:nonsing:Bk, fact:pre:Z), the row exchanges of
+ *                   Section 4.3 and the inserted rows of Section 4.4, and
+ *                   in-place storage as in Figure 1.  Second, independent
+ *                   route to the same P.
  *   f2o_mmm         The definition of the matrix product over F2 (Section 1):
  *                   C[i] = XOR over k with A[i][k] = 1 of B[k].
  *   f2o_rref        Reduced row echelon form by textbook Gauss-Jordan
@@ -138,71 +142,79 @@ int f2o_ple(int64_t n, int64_t m, const uint64_t *A, int64_t lda,
     return F2O_OK;
 }
 
-/* --------------------------------------------------------------- buildZ --
- * Procedure buildZ of Section 4.4 on one column block of b-bit words
- * a[0..rows): it selects the pivot rows (swapping them into slots 0,1,..),
- * records in P[k] the row where the pivot of bit k was found (-1 if none),
- * and returns Z, the pseudo-inverse with B*Z = I and D*Z = Y (eq. pre:W),
- * compressed to its r columns.  The test mask c of bit k is the parity
- * condition (eq. cond:nonsing:Bk) written through the current M; a bit with
- * no qualifying row gets the virtual row (0,1,0) of Section 4.4.
+/* ------------------------------------------------- block pivot search --
+ * Row selection and pseudo-inverse of one column block of b-bit words
+ * a[0..rows), written from the equations of Sections 4.2-4.4 (not from the
+ * printed procedure):
+ *
+ *   The square matrix S = J B + R of Section 4.1 is grown one row at a time.
+ *   After k rows its leading k x k minor S_k is nonsingular; its inverse Z_k
+ *   is held as k explicit COLUMN vectors zc[0..k) (bit i of zc[t] = entry
+ *   (i, t) of Z_k) and the rows of S as b-bit words srow[0..k).
+ *   For bit k let c = column k of S_k (bit i = bit k of srow[i]) and
+ *   ct = Z_k c.  A candidate row (r^T, alpha, beta^T) -- r its first k bits,
+ *   alpha its bit k -- extends S_k to a nonsingular S_{k+1} iff
+ *   alpha xor r^T Z_k c = alpha xor parity(r & ct) = 1 (eq. cond:nonsing:Bk).
+ *   The first candidate at or after the current pivot slot, in the current
+ *   row order, is exchanged with that slot (Section 4.3).  If no row
+ *   qualifies, the virtual row (0^T, 1, 0^T) of Section 4.4 is inserted:
+ *   r = 0 and alpha = 1 satisfy the condition trivially.
+ *   Z_{k+1} follows eq. (fact:pre:Z): with rho^T = r^T Z_k,
+ *     column t < k becomes zc[t] xor rho_t ct, with rho_t as its entry k
+ *     (the rank-one update Z_k xor ct rho^T and the new bottom row rho^T),
+ *     and the new column k is ct with entry k equal to 1.
+ * At the end Z = S^{-1} J (eq. pre:W): the columns of S^{-1} at the real
+ * rows, so that B Z = I and D Z = Y.  It is returned by rows (Zr[i] bit s =
+ * entry (i, s), s < r).  P[k] = index in a[] (before the exchange) of the
+ * row chosen for bit k, or -1 for an inserted row.  Returns r.
  */
-static int buildz(uint64_t *a, int64_t rows, int b, uint64_t *Z, int64_t *P)
+static int select_block_pivots(uint64_t *a, int64_t rows, int b, uint64_t *Zr, int64_t *P)
 {
-    uint64_t M[64];
-    int64_t ib = 0;
-    for (int j = 0; j < b; ++j) {
-        Z[j] = (uint64_t)1 << j;
-        M[j] = (uint64_t)1 << j;
-        P[j] = -1;
-    }
+    uint64_t zc[64], srow[64];
+    int real[64];
+    int64_t slot = 0;
+    int r = 0;
     for (int k = 0; k < b; ++k) {
-        const uint64_t bk = (uint64_t)1 << k;
-        uint64_t c = bk;
-        for (int i = 0; i < k; ++i)
-            if (M[i] & bk) c ^= (uint64_t)1 << i;
-        for (int64_t i = ib; i < rows; ++i) {
-            if (popcount_odd(c & a[i])) {
+        const uint64_t kbit = (uint64_t)1 << k;
+        const uint64_t low = kbit - 1; /* the first k columns */
+        uint64_t ct = 0;               /* Z_k c */
+        for (int t = 0; t < k; ++t)
+            if (srow[t] & kbit) ct ^= zc[t];
+        uint64_t row = kbit; /* the virtual row unless a real one qualifies */
+        P[k] = -1;
+        for (int64_t i = slot; i < rows; ++i) {
+            const int alpha = (int)((a[i] >> k) & 1);
+            if (alpha ^ popcount_odd(a[i] & low & ct)) {
                 P[k] = i;
-                uint64_t tmp = a[i]; a[i] = a[ib]; a[ib] = tmp;
-                M[k] = a[ib];
-                ++ib;
+                row = a[i];
+                a[i] = a[slot];
+                a[slot] = row;
+                ++slot;
                 break;
             }
         }
-        /* update of Z and M (eq. fact:pre:Z1 and the M_{k+1} update) */
-        const uint64_t y = M[k];
-        for (int j = 0; j < k; ++j) {
-            if (y & ((uint64_t)1 << j)) {
-                Z[k] ^= Z[j];
-                M[k] ^= M[j];
-            }
-        }
-        for (int j = 0; j < k; ++j) {
-            if (c & ((uint64_t)1 << j)) {
-                Z[j] ^= Z[k];
-                M[j] ^= M[k];
-            }
-        }
+        const uint64_t rk = row & low;
+        for (int t = 0; t < k; ++t)
+            if (popcount_odd(rk & zc[t])) zc[t] ^= ct | kbit;
+        zc[k] = ct | kbit;
+        srow[k] = row;
+        if (P[k] >= 0) real[r++] = k;
     }
-    /* compress the columns of Z to the r real rows (drop inserted ones) */
-    uint64_t msk = 0;
     for (int i = 0; i < b; ++i) {
-        if (P[i] == -1) {
-            for (int j = 0; j < b; ++j) Z[j] = ((Z[j] >> 1) & ~msk) ^ (Z[j] & msk);
-        } else {
-            msk = 2 * msk + 1;
-        }
+        uint64_t w = 0;
+        for (int s = 0; s < r; ++s)
+            if ((zc[real[s]] >> i) & 1) w |= (uint64_t)1 << s;
+        Zr[i] = w;
     }
-    return (int)ib;
+    return r;
 }
 
 /* -------------------------------------------------------- block driver --
  * Iterative block decomposition of Section 4 with word size b (1..64).
  * The matrix is held as the paper does: column blocks of b-bit words,
  * word (i, q) at Wb[q*n + i].  For each block j:
- *   buildZ on rows R..n of block j (selects B^(j), gives Z and r_j);
- *   the same transpositions are applied to the whole rows (every other
+ *   the pivot search on rows R..n of block j (selects B^(j), gives Z and
+ *   r_j); the same transpositions are applied to the whole rows (every other
  *   block, including the L multipliers stored to the left, and perm);
  *   Y = D * Z for the rows below the pivots (eq. pre:W);
  *   A^(j+1) = E xor Y * C on the blocks to the right (eq. Aj);
@@ -233,9 +245,9 @@ int f2o_blockdecomp(int64_t n, int64_t m, int b, const uint64_t *A, int64_t lda,
         int64_t P[64];
         uint64_t *panel = Wb + j * n + R;
         const int bj = (int)((m - j * b) < b ? (m - j * b) : b);
-        const int r = buildz(panel, n - R, bj, Z, P);
+        const int r = select_block_pivots(panel, n - R, bj, Z, P);
         if (rblock) rblock[j] = r;
-        /* the transpositions, in the order buildZ made them */
+        /* the transpositions, in the order the search made them */
         int s = 0;
         for (int k = 0; k < bj; ++k) {
             if (P[k] < 0) continue;
@@ -243,7 +255,7 @@ int f2o_blockdecomp(int64_t n, int64_t m, int b, const uint64_t *A, int64_t lda,
             pivcols[R + s] = (int32_t)(j * b + k);
             if (r1 != r2) {
                 for (int64_t q = 0; q < mub; ++q) {
-                    if (q == j) continue; /* block j was swapped by buildZ */
+                    if (q == j) continue; /* block j was exchanged by the search */
                     uint64_t tmp = Wb[q * n + r1]; Wb[q * n + r1] = Wb[q * n + r2]; Wb[q * n + r2] = tmp;
                 }
                 int32_t tp = pr[r1]; pr[r1] = pr[r2]; pr[r2] = tp;

@@ -31,9 +31,11 @@ MUTATIONS = {
         "int32_t tmp = pr[piv]; pr[piv] = pr[t]; pr[t] = tmp;", ""),
     "L-rows-not-swapped": (
         "swap_words(Lw + piv * lw, Lw + t * lw, lw);", ""),
-    "buildz-drops-mask-term": (
-        "if (M[i] & bk) c ^= (uint64_t)1 << i;", "if (M[i] & bk) c ^= 0;"),
-    "buildz-transposed-swap": (
+    "pivot-search-drops-rank-one-term": (
+        "if (popcount_odd(rk & zc[t])) zc[t] ^= ct | kbit;", "if (popcount_odd(rk & zc[t])) zc[t] ^= kbit;"),
+    "pivot-search-condition-drops-reduction": (
+        "if (alpha ^ popcount_odd(a[i] & low & ct)) {", "if (alpha) {"),
+    "pivot-search-transposed-swap": (
         "const int64_t r1 = R + s, r2 = R + P[k];", "const int64_t r1 = R + s, r2 = R + P[k] + (P[k] > s);"),
     "mmm-transposed-operand": (
         "if (!getbit(A + i * lda, t)) continue;", "if (!getbit(A + t * lda, i)) continue;"),
