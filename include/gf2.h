@@ -84,8 +84,9 @@ int gf2_release_workspace(void);
  *       even number of words.  The cutoff is off until gf2_mmm_autotune or
  *       gf2_mmm_set_strassen_cutoff sets it.
  *   GF2_MMM_TABLES: M4RM alone (no recursion).
- *   GF2_MMM_TENSOR: the tensor cores (every entry an e4m3 0 or 1, exact
- *       integer sums in fp32, entry = lowest bit; k < 2^24, else M4RM).
+ *   GF2_MMM_TENSOR: the tensor cores (every entry an e4m3 0 or 1, integer
+ *       sums in fp32 folded into parity bits every 4096 of the inner
+ *       dimension, entry = lowest bit; k < 2^24, else M4RM).
  * The workspace depends on the backend and the recursion depth: size it
  * with the same flags (and after the same cutoff setting).
  * Errors: GF2_ERR_ARG (NULL, both backend flags), GF2_ERR_SHAPE (A.cols !=
@@ -425,6 +426,27 @@ int gf2_timing_read(int kernel_class, double *total_ms, int64_t *launches);
 #define GF2_OP_MMM_ADDS 8
 #define GF2_NUM_OPS 9
 int gf2_op_counts(uint64_t *out, int count, int reset);
+
+/* Device timeline of the decomposition's kernels, in the trace build only
+ * (libgf2_trace.so, compiled with -DGF2_TRACE; the kernels read the GPU's
+ * global timer).  No counterpart in the paper: it measures where the time
+ * of the serial panel chain goes.  Per panel j < 4096 it keeps eight
+ * nanosecond stamps, slot-major (out[slot * 4096 + j]):
+ *   0 panel kernel released, 1 its rows loaded and the previous panel's
+ *   update applied, 2 pivot loop done, 3 coordinate maps written (end),
+ *   4 / 5 first start / last end of the look-ahead kernel of panel j,
+ *   6 / 7 first start / last end of the trailing update(s) of panel j (a
+ *   pair's update is filed under its second panel).
+ * 0 = not recorded.  The panel stamps are overwritten by every run; the
+ * launch spans accumulate (earliest start, latest end) until a read with
+ * reset = 1 clears every stamp, so clear them right before the
+ * decomposition to trace.  gf2_trace_read(out, count,
+ * reset) synchronises the current device and writes min(count, 8 * 4096)
+ * values.  Returns GF2_OK, GF2_ERR_ARG (out null or count < 0),
+ * GF2_ERR_UNSUPPORTED (every other build) or GF2_ERR_CUDA. */
+#define GF2_TRACE_PANELS 4096
+#define GF2_TRACE_SLOTS 8
+int gf2_trace_read(uint64_t *out, int64_t count, int reset);
 
 #ifdef __cplusplus
 }

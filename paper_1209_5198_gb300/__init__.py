@@ -26,7 +26,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 # same ABI (libgf2_count.so, ``_build.build(counting=True)``): its kernels
 # count their word operations for ``op_counts``; it is never the default
 COUNTING = os.environ.get("GF2_COUNT_OPS") == "1"
-LIB_PATH = os.path.join(_HERE, "libgf2_count.so" if COUNTING else "libgf2.so")
+# GF2_TRACE=1 selects the trace build (libgf2_trace.so,
+# ``_build.build(trace=True)``): its decomposition kernels stamp a device
+# timeline for ``trace_read``; it is never the default either
+TRACING = os.environ.get("GF2_TRACE") == "1" and not COUNTING
+LIB_PATH = os.path.join(_HERE, "libgf2_count.so" if COUNTING else "libgf2_trace.so" if TRACING else "libgf2.so")
 
 GF2_OK = 0
 GF2_MMM_TABLES = 2
@@ -129,6 +133,8 @@ def load() -> ctypes.CDLL:
     lib.gf2_launch_count.restype = ctypes.c_int64
     lib.gf2_op_counts.restype = ctypes.c_int
     lib.gf2_op_counts.argtypes = [P, ctypes.c_int, ctypes.c_int]
+    lib.gf2_trace_read.restype = ctypes.c_int
+    lib.gf2_trace_read.argtypes = [P, ctypes.c_int64, ctypes.c_int]
     lib.gf2_timing_enable.argtypes = [ctypes.c_int]
     lib.gf2_timing_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)]
     _lib = lib
@@ -448,6 +454,21 @@ def op_counts(reset: bool = False) -> dict:
     out = (ctypes.c_uint64 * len(OPS))()
     _check(load().gf2_op_counts(ctypes.cast(out, ctypes.c_void_p), len(OPS), int(reset)), "gf2_op_counts")
     return {k: int(v) for k, v in zip(OPS, out)}
+
+
+TRACE_PANELS = 4096
+TRACE_SLOTS = ("panel_start", "panel_loaded", "panel_loop", "panel_end", "next_start", "next_end", "rest_start",
+               "rest_end")
+
+
+def trace_read(reset: bool = False) -> dict:
+    """The trace build's device timeline (GF2_TRACE=1): {slot: int64 array of
+    nanosecond stamps per panel, 0 = none}; see gf2_trace_read.  The release
+    build raises Gf2Error(GF2_ERR_UNSUPPORTED)."""
+    out = np.zeros(len(TRACE_SLOTS) * TRACE_PANELS, dtype=np.uint64)
+    _check(load().gf2_trace_read(ctypes.c_void_p(out.ctypes.data), out.size, int(reset)), "gf2_trace_read")
+    v = out.astype(np.int64).reshape(len(TRACE_SLOTS), TRACE_PANELS)
+    return {k: v[i] for i, k in enumerate(TRACE_SLOTS)}
 
 
 def timing(on: bool) -> None:

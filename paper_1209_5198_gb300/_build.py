@@ -19,6 +19,10 @@ OBJDIR = os.path.join(HERE, "_build")
 # gf2_op_counts in include/gf2.h): built only on request
 COUNT_OUT = os.path.join(HERE, "libgf2_count.so")
 COUNT_OBJDIR = os.path.join(HERE, "_build_count")
+# the trace variant (same ABI; its decomposition kernels stamp a device
+# timeline, see gf2_trace_read): built only on request
+TRACE_OUT = os.path.join(HERE, "libgf2_trace.so")
+TRACE_OBJDIR = os.path.join(HERE, "_build_trace")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", os.path.join(os.path.dirname(HERE), "include")]
@@ -43,15 +47,19 @@ def _stale(out: str) -> bool:
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, counting: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, counting: bool = False,
+          trace: bool = False) -> str:
     """Builds libgf2.so, or with counting=True the op-counting variant
-    libgf2_count.so (-DGF2_COUNT_OPS); returns the library's path."""
-    out, objdir = (COUNT_OUT, COUNT_OBJDIR) if counting else (OUT, OBJDIR)
+    libgf2_count.so (-DGF2_COUNT_OPS), or with trace=True the trace variant
+    libgf2_trace.so (-DGF2_TRACE); returns the library's path."""
+    if counting and trace:
+        raise ValueError("one variant at a time")
+    out, objdir = (COUNT_OUT, COUNT_OBJDIR) if counting else (TRACE_OUT, TRACE_OBJDIR) if trace else (OUT, OBJDIR)
     if not force and not _stale(out):
         return out
     os.makedirs(objdir, exist_ok=True)
     cc = nvcc()
-    extra = (extra or []) + (["-DGF2_COUNT_OPS"] if counting else [])
+    extra = (extra or []) + (["-DGF2_COUNT_OPS"] if counting else []) + (["-DGF2_TRACE"] if trace else [])
 
     def one(src):
         obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
@@ -77,4 +85,5 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 if __name__ == "__main__":  # pragma: no cover
     import sys
     print(build(force="--force" in sys.argv, verbose=True,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None, counting="--counting" in sys.argv))
+                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None, counting="--counting" in sys.argv,
+                trace="--trace" in sys.argv))

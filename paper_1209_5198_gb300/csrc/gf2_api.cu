@@ -1460,6 +1460,30 @@ int gf2_op_counts(uint64_t *out, int count, int reset)
 #endif
 }
 
+int gf2_trace_read(uint64_t *out, int64_t count, int reset)
+{
+    if (!out || count < 0) return GF2_ERR_ARG;
+#ifdef GF2_TRACE
+    if (cudaDeviceSynchronize() != cudaSuccess) return GF2_ERR_CUDA;
+    std::vector<unsigned long long> a(kTrSlots * kTraceMaxPanels), b(kTrSlots * kTraceMaxPanels);
+    if (read_panel_trace(a.data(), reset != 0) != cudaSuccess || read_update_trace(b.data(), reset != 0) != cudaSuccess)
+        return GF2_ERR_CUDA;
+    // each slot lives in one translation unit: the panel phases in the
+    // panel's, the launch spans in the update kernels'; start slots are kept
+    // complemented on the device
+    for (int64_t i = 0; i < count && i < (int64_t)a.size(); ++i) {
+        const int slot = (int)(i / kTraceMaxPanels);
+        unsigned long long v = slot <= kTrPanelEnd ? a[i] : b[i];
+        if ((slot == kTrNextStart || slot == kTrRestStart) && v) v = ~v;
+        out[i] = v;
+    }
+    return GF2_OK;
+#else
+    (void)reset;
+    return GF2_ERR_UNSUPPORTED;
+#endif
+}
+
 int gf2_timing_enable(int on)
 {
     g_timing.store(on != 0);

@@ -245,6 +245,53 @@ enum OpKind {
     kOpMmmAdds = 8,
     kNumOps = 9
 };
+// ---- device timeline of the trace build (-DGF2_TRACE; gf2_trace_read of
+// include/gf2.h): globaltimer stamps (ns) per panel j, slot-major
+// ([slot][j], kTraceMaxPanels entries per slot).  Panel phases come from the
+// CTA's thread 0; a multi-CTA launch keeps the earliest start (atomicMin)
+// and the latest end (atomicMax) over its CTAs' threads 0.  Each translation
+// unit with traced kernels keeps its own array and the host merges them
+// (panels: csrc/k_panel.cu, look-ahead and updates: csrc/k_update.cu).
+constexpr int kTraceMaxPanels = 4096;
+enum TraceSlot {
+    kTrPanelStart = 0,  // panel kernel released (after griddepcontrol.wait)
+    kTrPanelLoaded = 1, // its rows loaded and the previous panel's update applied (fast path ready)
+    kTrPanelLoop = 2,   // pivot loop and exchanges done
+    kTrPanelEnd = 3,    // coordinate maps written (end of the kernel)
+    kTrNextStart = 4,
+    kTrNextEnd = 5,
+    kTrRestStart = 6,   // every update launch of panel j (pair: j = the second panel)
+    kTrRestEnd = 7,
+    kTrSlots = 8
+};
+#ifdef GF2_TRACE
+#define GF2_TR(...) __VA_ARGS__
+__device__ __forceinline__ unsigned long long trace_clock()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Start and end of one launch: thread 0 of every CTA keeps the earliest
+// start (stored complemented, so that both slots take atomicMax from zero)
+// and, when it leaves the kernel by any return, the latest end.
+struct TraceSpan {
+    unsigned long long *end_slot;
+    __device__ TraceSpan(unsigned long long *start_slot, unsigned long long *end) : end_slot(end)
+    {
+        if (threadIdx.x == 0) atomicMax(start_slot, ~trace_clock());
+    }
+    __device__ ~TraceSpan()
+    {
+        if (threadIdx.x == 0) atomicMax(end_slot, trace_clock());
+    }
+};
+cudaError_t read_panel_trace(unsigned long long *out, bool reset);   // csrc/k_panel.cu
+cudaError_t read_update_trace(unsigned long long *out, bool reset);  // csrc/k_update.cu
+#else
+#define GF2_TR(...)
+#endif
+
 #ifdef GF2_COUNT_OPS
 #define GF2_OPS(...) __VA_ARGS__
 cudaError_t read_update_ops(unsigned long long *acc, bool reset);  // csrc/k_update.cu

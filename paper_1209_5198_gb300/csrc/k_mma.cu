@@ -2,9 +2,12 @@
 // alternative to the Four Russians kernel for a long inner dimension).
 //
 // Every entry of A and B becomes an e4m3 byte, 1.0 (0x38) or 0, and an
-// mma.sync m16n8k32 e4m3 x e4m3 -> f32 product sums them exactly: a sum of
-// at most k <= 2^24 ones is an integer an fp32 accumulator holds exactly,
-// and entry (i, j) of C over F2 is that integer's lowest bit.  Because the
+// mma.sync m16n8k32 e4m3 x e4m3 -> f32 product sums them; entry (i, j) of C
+// over F2 is the lowest bit of the integer sum.  The accumulators are folded
+// into integer parity bits every kFoldTiles k-tiles (4096 of the inner
+// dimension) and restarted from zero, so no partial sum exceeds 4096 = 2^12:
+// its lowest bit survives even an accumulation that keeps only about 13
+// significant bits, whatever the tensor pipe's internal precision.  Because the
 // whole inner dimension is accumulated before anything is read back, the
 // unpacking (one bit per output) costs little; for the rank-64/128 updates of
 // the decomposition it would cost as much as the Four Russians lookups, so
@@ -28,6 +31,7 @@ constexpr int kMmaThreads = 256;
 constexpr int kTileBytes = kBM * kBK;  // one operand tile of one stage (16 KB)
 constexpr int kMmaSmem = kStages * 2 * kTileBytes;
 constexpr uint32_t kOne = 0x38;  // 1.0 in e4m3
+constexpr int kFoldTiles = 32;   // k-tiles between parity folds (32 x 128 = 4096 of the inner dimension)
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -132,6 +136,23 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_mma8(const uint8_t *__restri
         for (int b = 0; b < 4; ++b)
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+    // parities of this lane's sums so far, in the epilogue's bit positions:
+    // par[mt][hr] bit 8 nt + 2 t + c = lowest bit of acc[mt][nt][2 hr + c]
+    const int t = lane & 3;
+    uint32_t par[4][2] = {};
+    auto fold = [&]() {
+#pragma unroll
+        for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+            for (int hr = 0; hr < 2; ++hr)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        par[mt][hr] ^= (uint32_t)(__float2int_rn(acc[mt][nt][2 * hr + c]) & 1) << (8 * nt + 2 * t + c);
+                        acc[mt][nt][2 * hr + c] = 0.f;
+                    }
+    };
 
 #pragma unroll
     for (int s = 0; s < kStages - 1; ++s) {
@@ -170,11 +191,12 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_mma8(const uint8_t *__restri
 #pragma unroll
                 for (int nt = 0; nt < 4; ++nt) mma_e4m3(acc[mt][nt], af[mt], bf[nt][0], bf[nt][1]);
         }
+        if ((kt + 1) % kFoldTiles == 0 || kt + 1 == ktiles) fold();
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 
     // parities -> 32 columns per row in one 32-bit half word of C
-    const int g = lane >> 2, t = lane & 3;
+    const int g = lane >> 2;
     const int cbase = col0 + 32 * wn;  // multiple of 32: a low or high half of word cbase / 64
     const int q = cbase >> 6, half = (cbase >> 5) & 1;
     // a half past the last column is still written (zero bits) while its
@@ -185,12 +207,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_mma8(const uint8_t *__restri
     for (int mt = 0; mt < 4; ++mt) {
 #pragma unroll
         for (int hr = 0; hr < 2; ++hr) {  // rows g and g + 8 of the m16 tile
-            uint32_t bits = 0;
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                for (int c = 0; c < 2; ++c)
-                    bits |= (uint32_t)(__float2int_rn(acc[mt][nt][2 * hr + c]) & 1) << (8 * nt + 2 * t + c);
+            uint32_t bits = par[mt][hr];
             bits |= __shfl_xor_sync(0xffffffffu, bits, 1);
             bits |= __shfl_xor_sync(0xffffffffu, bits, 2);
             const int row = row0 + 64 * wm + 16 * mt + 8 * hr + g;

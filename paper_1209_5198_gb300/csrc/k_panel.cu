@@ -1,9 +1,15 @@
 // Panel kernel of the decomposition: one CTA runs the panel step of block j
 // (panel_core.cuh) on the SM that the persistent trailing update leaves free.
+#include <mutex>
+
 #include "panel_core.cuh"
 
 namespace gf2 {
 namespace {
+
+#ifdef GF2_TRACE
+__device__ unsigned long long g_panel_trace[kTrSlots * kTraceMaxPanels];  // the trace build's panel stamps
+#endif
 
 // Dynamic shared memory of the panel kernel (see kPanelReserveBytes): the
 // first kPanelListCap entries of the row list of the general path.
@@ -21,7 +27,12 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
     // attribute both are no-ops.
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#ifdef GF2_TRACE
+    if (threadIdx.x == 0 && j < kTraceMaxPanels) g_panel_trace[kTrPanelStart * kTraceMaxPanels + j] = trace_clock();
+    panel_block(c, j, sh, panel_dyn, kPanelListCap, j < kTraceMaxPanels ? g_panel_trace : nullptr);
+#else
     panel_block(c, j, sh, panel_dyn, kPanelListCap);
+#endif
 }
 
 // The dynamic shared memory also keeps a panel CTA off any SM holding a
@@ -35,16 +46,33 @@ static_assert(kPanelListCap * 12 <= kPanelReserveBytes, "row list in the reserve
 
 cudaError_t prepare_panel_kernel()
 {
+    // several host threads may launch panels at once (the serving engine's
+    // decomposition lanes, the entry point without allocation)
+    static std::mutex mu;
     static bool done[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
     if (done[dev]) return cudaSuccess;
     e = cudaFuncSetAttribute(k_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPanelReserveBytes);
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }
+
+#ifdef GF2_TRACE
+cudaError_t read_panel_trace(unsigned long long *out, bool reset)
+{
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_panel_trace, sizeof(g_panel_trace));
+    if (e == cudaSuccess && reset) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_panel_trace);
+        if (e == cudaSuccess) e = cudaMemset(p, 0, sizeof(g_panel_trace));
+    }
+    return e;
+}
+#endif
 
 cudaError_t launch_panel(const DecompCtx &c, int j, cudaStream_t s)
 {

@@ -36,6 +36,9 @@ namespace {
 #ifdef GF2_COUNT_OPS
 __device__ unsigned long long g_update_ops[kNumOps];  // the op-counting build's counters
 #endif
+#ifdef GF2_TRACE
+__device__ unsigned long long g_update_trace[kTrSlots * kTraceMaxPanels];  // the trace build's launch spans
+#endif
 
 // -------------------------------------------------------------------- k_next
 // Look-ahead of panel j over the rows still active before it (256 per CTA):
@@ -64,6 +67,9 @@ constexpr int kNextSmemWords = kNextTiles * (Tabs<kNextC>::Words + 64 * kTileWor
 __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
 {
     __shared__ __align__(16) uint64_t smem[kNextSmemWords];
+    GF2_TR(const int jt = j < kTraceMaxPanels ? j : kTraceMaxPanels - 1;
+           TraceSpan span(g_update_trace + kTrNextStart * kTraceMaxPanels + jt,
+                          g_update_trace + kTrNextEnd * kTraceMaxPanels + jt);)
     uint64_t *tab = smem;                                      // [tile][Tabs<4>::Words]
     uint64_t *crow = tab + kNextTiles * Tabs<kNextC>::Words;   // [tile][64 x kTileWords]
     uint64_t *zc = crow + kNextTiles * 64 * kTileWords;        // [g][x][y, lambda], 16 tables of 16 entries
@@ -300,6 +306,9 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
     // one be scheduled
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    GF2_TR(const int jt = j + NP - 1 < kTraceMaxPanels ? j + NP - 1 : kTraceMaxPanels - 1;
+           TraceSpan span(g_update_trace + kTrRestStart * kTraceMaxPanels + jt,
+                          g_update_trace + kTrRestEnd * kTraceMaxPanels + jt);)
     extern __shared__ __align__(16) uint64_t smem[];
     uint64_t *tab = smem;                          // [NP * K tables][X][kTileWords]
     uint64_t *crow = smem + NP * Tabs<C>::Words;   // [NP][crow_words]: 64 x kTileWords, skewed
@@ -490,6 +499,19 @@ cudaError_t read_update_ops(unsigned long long *acc, bool reset)
     if (reset) {
         const unsigned long long z[kNumOps] = {};
         e = cudaMemcpyToSymbol(g_update_ops, z, sizeof(z));
+    }
+    return e;
+}
+#endif
+
+#ifdef GF2_TRACE
+cudaError_t read_update_trace(unsigned long long *out, bool reset)
+{
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_update_trace, sizeof(g_update_trace));
+    if (e == cudaSuccess && reset) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_update_trace);
+        if (e == cudaSuccess) e = cudaMemset(p, 0, sizeof(g_update_trace));
     }
     return e;
 }

@@ -442,8 +442,9 @@ __device__ __forceinline__ bool fast_phase(FastCols &st, int nbits, int smax, bo
 // searches, warps 1..3 serve the scans of the general path).
 // zs / zcap: shared memory for the first zcap entries of the row list (zcap
 // words of raw rows, then zcap int32 positions), or none.
+// tr: the trace build's timeline of the decomposition (null: no stamps).
 __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShared &sh, uint64_t *zs = nullptr,
-                                            int zcap = 0)
+                                            int zcap = 0, unsigned long long *tr = nullptr)
 {
     const RowList L{zs, zs ? reinterpret_cast<int32_t *>(zs + zcap) : nullptr, zs ? zcap : 0};
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -646,6 +647,10 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
         uint64_t raw[3];
 #pragma unroll
         for (int u = 0; u < 3; ++u) raw[u] = (srw[u] >= 0 && pv.Fp) ? wv[u] ^ prev_update(sh, fv[u]) : wv[u];
+        GF2_TR(if (tr && lane == 0) {
+            asm volatile("" ::"l"(raw[0] ^ raw[1] ^ raw[2]));  // stamp after the loads arrived
+            tr[kTrPanelLoaded * kTraceMaxPanels + j] = trace_clock();
+        })
         FastCols st;
 #pragma unroll
         for (int u = 0; u < 3; ++u) {
@@ -837,6 +842,7 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
     if (lane == 0) sh.req = kReqDone;
     __syncwarp();
     bar_sync(1, kPanelThreads);
+    GF2_TR(if (tr && lane == 0) tr[kTrPanelLoop * kTraceMaxPanels + j] = trace_clock();)
 
     // ---- coordinate maps from E (bits EA/EB) and the raw pivot words B
     {
@@ -928,6 +934,7 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
         pi->prow[t] = sh.prow[t];
         c.pivcols[R + t] = 64 * j + sh.pb[t];
     }
+    GF2_TR(if (tr && lane == 0) tr[kTrPanelEnd * kTraceMaxPanels + j] = trace_clock();)
 }
 
 }  // namespace

@@ -1,14 +1,14 @@
-"""Parity at the benchmark's full sizes (n = m = 32768 and the 16384 fixed-rank
-and product configurations), in the launch configuration the benchmark times.
+"""Parity at the benchmark's full sizes (n = m = 32768, the 65536 and
+rectangular scale configurations, the fixed-rank products), in the launch
+configuration the benchmark times.
 
-The oracle cannot decompose a 32768 x 32768 matrix in seconds, so these tests
-check what it can compute and what holds at any size:
-  * the first 256 columns exactly: the oracle eliminates only those columns
-    (its column limit) and every decision it makes there is final -- the
-    first pivot columns, the rows at the first positions, the echelon rows of
-    those pivots and the L multipliers of every row for them;
-  * P*A = L*E by Freivalds' test with random vectors (a wrong bit anywhere in
-    L, E or P survives one vector with probability at most 1/2);
+Every decomposition here is compared element by element with a COMPLETE run
+of the oracle on the same input: rank, pivot columns, perm, L and E.  The
+factors are unique given the pivot rule (Lemma 4.1 and Section 4), so any
+difference is an error.  (The oracle's multithreaded elimination takes a few
+seconds at 32768 and under a minute at 65536 on the host cores.)  On top:
+  * P*A = L*E by Freivalds' test with 64 random vectors packed one word per
+    row (a wrong factor passes with probability at most 2^-64);
   * the unit lower-triangular / row-echelon invariants of every row;
   * the exact rank of products X*Y of known rank r (built on the CPU);
   * solves and products checked against the definition A X = B, C = A B.
@@ -46,17 +46,28 @@ def pack(bits: np.ndarray, words: int) -> np.ndarray:
     return out[:words]
 
 
-def random_vectors(count: int, m: int, seed: int):
-    return [f2gen.uniform(1, m, seed, 900 + i).reshape(-1) for i in range(count)]
+def freivalds64(A, perm, L, E, m, seed):
+    """P A X == L (E X) for a random m x 64 bit matrix X (64 vectors, one
+    word per row): a wrong factor passes with probability at most 2^-64."""
+    X = f2gen.uniform(m, 64, seed, 64)
+    kmax = E.shape[0]
+    AX = oracle.mmm(A, X, m, 64, nthreads=NTHREADS)[perm]
+    EX = oracle.mmm(E, X, m, 64, nthreads=NTHREADS)
+    LEX = oracle.mmm(L, EX, kmax, 64, nthreads=NTHREADS)
+    assert np.array_equal(AX, LEX), "P*A*X != L*(E*X)"
 
 
-def freivalds(A, perm, L, E, m, k, vectors):
-    """P A x == L (E x) for every vector x."""
-    for x in vectors:
-        ax = matvec_parity(A, x)[perm]
-        ex = matvec_parity(E, x)
-        lex = matvec_parity(L, pack(ex, L.shape[1]))
-        assert np.array_equal(ax, lex), "P*A*x != L*(E*x)"
+def matches_full_oracle(A, m, perm, piv, r, L, E):
+    """The oracle's complete decomposition of the same input, element by
+    element."""
+    ref = oracle.ple(A, m, want_L=True, want_E=True, nthreads=NTHREADS)
+    assert r == ref["rank"]
+    assert np.array_equal(piv[:r], ref["pivcols"])
+    assert (piv[r:] == -1).all()
+    assert np.array_equal(perm, ref["perm"]), "perm differs"
+    assert np.array_equal(L, ref["L"]), "L differs"
+    assert np.array_equal(E, ref["E"]), "E differs"
+    return ref
 
 
 def check_shapes(perm, piv, r, L, E, n, m):
@@ -105,45 +116,8 @@ def test_full_size_decomposition_32768():
     perm, piv, r, L, E, _ = gpu_factors(A, N)
     assert r >= N - 8  # a Bernoulli(1/2) square matrix has rank n - O(1)
     check_shapes(perm, piv, r, L, E, N, N)
-    # the first 256 columns: the oracle's decisions there are final
-    c = 256
-    ref = oracle.ple(A, N, want_L=True, want_E=True, col_limit=c, nthreads=NTHREADS)
-    rc = ref["rank"]
-    assert np.array_equal(piv[:rc], ref["pivcols"])
-    assert rc == int((piv[:r] < c).sum())
-    assert np.array_equal(perm[:rc], ref["perm"][:rc])
-    assert np.array_equal(E[:rc], ref["E"][:rc])
-    inv_gpu = np.empty(N, dtype=np.int64)
-    inv_gpu[perm] = np.arange(N)
-    inv_ref = np.empty(N, dtype=np.int64)
-    inv_ref[ref["perm"]] = np.arange(N)
-    w = (rc + 63) // 64
-    mask = np.full(w, ~np.uint64(0), dtype=np.uint64)
-    if rc % 64:
-        mask[-1] = (np.uint64(1) << np.uint64(rc % 64)) - np.uint64(1)
-    assert np.array_equal(L[inv_gpu, :w] & mask, ref["L"][inv_ref, :w] & mask)
-    freivalds(A, perm, L, E, N, N, random_vectors(8, N, 77))
-
-
-def first_columns_match_oracle(A, n, m, perm, piv, r, L, E, cols=256):
-    """The oracle run on the first `cols` columns only (every decision there is
-    final): pivot columns, the rows at the first positions, their echelon
-    rows, and every row's L multipliers for those pivots."""
-    ref = oracle.ple(A, m, want_L=True, want_E=True, col_limit=cols, nthreads=NTHREADS)
-    rc = ref["rank"]
-    assert np.array_equal(piv[:rc], ref["pivcols"])
-    assert rc == int((piv[:r] < cols).sum())
-    assert np.array_equal(perm[:rc], ref["perm"][:rc])
-    assert np.array_equal(E[:rc], ref["E"][:rc])
-    inv_gpu = np.empty(n, dtype=np.int64)
-    inv_gpu[perm] = np.arange(n)
-    inv_ref = np.empty(n, dtype=np.int64)
-    inv_ref[ref["perm"]] = np.arange(n)
-    w = (rc + 63) // 64
-    mask = np.full(w, ~np.uint64(0), dtype=np.uint64)
-    if rc % 64:
-        mask[-1] = (np.uint64(1) << np.uint64(rc % 64)) - np.uint64(1)
-    assert np.array_equal(L[inv_gpu, :w] & mask, ref["L"][inv_ref, :w] & mask)
+    matches_full_oracle(A, N, perm, piv, r, L, E)
+    freivalds64(A, perm, L, E, N, 77)
 
 
 @pytest.mark.parametrize("n,m", [(65536, 65536), (16384, 65536), (65536, 16384)])
@@ -153,19 +127,21 @@ def test_full_size_scale_configurations(n, m):
     perm, piv, r, L, E, _ = gpu_factors(A, m)
     assert r >= min(n, m) - 8 if n == m else r == min(n, m)
     check_shapes(perm, piv, r, L, E, n, m)
-    first_columns_match_oracle(A, n, m, perm, piv, r, L, E)
-    freivalds(A, perm, L, E, m, min(n, m), random_vectors(4, m, 83))
+    matches_full_oracle(A, m, perm, piv, r, L, E)
+    freivalds64(A, perm, L, E, m, 83)
 
 
-@pytest.mark.parametrize("r", [8192, 16384 - 64])
-def test_full_size_fixed_rank_16384(r):
-    n = 16384
+@pytest.mark.parametrize("n,r", [(16384, 8192), (16384, 16384 - 64), (32768, 16384), (32768, 32768 - 64)])
+def test_full_size_fixed_rank(n, r):
+    """Fixed-rank products X*Y (the scale configuration's r = n/2 and n - 64):
+    the known rank and the complete oracle decomposition."""
     X, Y = f2gen.fixed_rank_factors(n, n, r, 500 + r)
     A = oracle.mmm(X, Y, r, n, nthreads=NTHREADS)
     perm, piv, rk, L, E, _ = gpu_factors(A, n)
     assert rk == r
     check_shapes(perm, piv, rk, L, E, n, n)
-    freivalds(A, perm, L, E, n, n, random_vectors(6, n, 78))
+    matches_full_oracle(A, n, perm, piv, rk, L, E)
+    freivalds64(A, perm, L, E, n, 78)
 
 
 def test_full_size_solve_32768():
@@ -191,8 +167,9 @@ def test_full_size_solve_32768():
 
 @pytest.mark.parametrize("strassen", [False, True])
 def test_full_size_product_16384(strassen):
-    """C = A B at 16384 by Freivalds (C x = A (B x) for random x), with M4RM
-    alone and with two Strassen-Winograd levels (cutoff 8192 -> 4096)."""
+    """C = A B at 16384 against the oracle's product, element by element,
+    with M4RM alone and with two Strassen-Winograd levels (cutoff 8192 ->
+    4096)."""
     n = 16384
     Ah = f2gen.uniform(n, n, 80)
     Bh = f2gen.uniform(n, n, 81)
@@ -202,6 +179,4 @@ def test_full_size_product_16384(strassen):
         C = gf2.mmm(gf2.Mat.from_rowmajor(Ah, n), gf2.Mat.from_rowmajor(Bh, n)).to_rowmajor()
     finally:
         gf2.set_strassen_cutoff(old)
-    for x in random_vectors(6, n, 82):
-        bx = matvec_parity(Bh, x)
-        assert np.array_equal(matvec_parity(C, x), matvec_parity(Ah, pack(bx, Ah.shape[1])))
+    assert np.array_equal(C, oracle.mmm(Ah, Bh, n, n, nthreads=NTHREADS))

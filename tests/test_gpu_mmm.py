@@ -66,6 +66,24 @@ def test_product_dense_ones_exact():
             assert np.array_equal(Cd.to_rowmajor(), ref)
 
 
+@pytest.mark.parametrize("k", [16385, 32769, 65537])
+def test_product_long_inner_dimension_ones_exact(k):
+    """All-ones operands with sums far above what a low-precision
+    accumulation keeps exactly (k > 2^14): every entry is k mod 2 = 1.  The
+    tensor-core kernel folds its sums into parity bits every 4096 of the
+    inner dimension; both backends must match the oracle."""
+    n = m = 128
+    A = np.full((n, (k + 63) // 64), ~np.uint64(0), dtype=np.uint64)
+    A[:, -1] = (np.uint64(1) << np.uint64(k % 64)) - np.uint64(1)
+    B = np.full((k, (m + 63) // 64), ~np.uint64(0), dtype=np.uint64)
+    ref = oracle.mmm(A, B, k, m)
+    assert (ref == ~np.uint64(0)).all()  # k odd: every entry 1
+    for flags in (gf2.GF2_MMM_TABLES, gf2.GF2_MMM_TENSOR):
+        Cd = gf2.Mat.empty(n, m)
+        gf2.gf2_mmm(gf2.Mat.from_rowmajor(A, k), gf2.Mat.from_rowmajor(B, m), Cd, flags=flags)
+        assert np.array_equal(Cd.to_rowmajor(), ref), flags
+
+
 def test_product_padding_error_both_backends():
     A = f2gen.uniform(100, 300, 45)
     A[7, 4] |= np.uint64(1) << np.uint64(50)  # column 306 >= 300

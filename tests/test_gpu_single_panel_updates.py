@@ -1,5 +1,6 @@
 """The trailing updates one panel at a time (GF2_PAIRS=0) give the same
-decomposition as the oracle.  The library reads the switch when it loads, so
+decomposition as the oracle, with both table sizes of that update (8-bit
+tables while more than 4096 rows remain below the panel, 4-bit after).  The library reads the switch when it loads, so
 the cases run in a child process."""
 import os
 import subprocess
@@ -25,6 +26,10 @@ cases = [(f2gen.uniform(1024, 1024, f2gen.BASE_SEED, 0), 1024),
          (f2gen.sparse_rows(1000, 1000, 10, 14), 1000)]
 X, Y = f2gen.fixed_rank_factors(1024, 1024, 512, 20)
 cases.append((oracle.mmm(X, Y, 512, 1024), 1024))
+# more than 4096 rows below the panels: the 8-bit-table update of one panel
+# (the 4-bit one takes over once fewer rows remain)
+cases.append((f2gen.uniform(8192, 8192, f2gen.BASE_SEED, 3), 8192))
+cases.append((f2gen.uniform(12000, 1000, 6), 1000))
 for A, m in cases:
     assert_same_decomposition(A, m, gpu_decompose(A, m))
 print("single-panel updates ok")

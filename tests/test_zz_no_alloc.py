@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import f2gen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -43,6 +44,8 @@ def test_noalloc_rank_matches_gf2_rank_on_two_calls_in_a_row():
     want = [gf2.gf2_rank(A) for A in cases]
     assert got == want
     assert got[0] == 700
+    # and the oracle's rank of the same inputs
+    assert got == [oracle.rank(A.to_rowmajor(), A.cols, nthreads=oracle.max_threads()) for A in cases]
     # and once more in the other order
     assert [rank_noalloc(A) for A in reversed(cases)] == list(reversed(want))
 
@@ -53,3 +56,27 @@ def test_noalloc_rejects_sizes_beyond_the_static_scratch():
     lib.gf2_rank_noalloc.argtypes = [ctypes.POINTER(gf2._CMat), ctypes.c_void_p, ctypes.c_void_p]
     big = gf2._CMat(1, 4097, 100, 4097)
     assert lib.gf2_rank_noalloc(ctypes.byref(big), ctypes.c_void_p(8), None) == gf2.GF2_ERR_UNSUPPORTED
+
+
+def test_noalloc_rank_of_a_wide_matrix():
+    # fewer rows than columns: this entry point decomposes the matrix itself
+    # (gf2_rank goes through the transpose); both must give the known rank
+    X, Y = f2gen.fixed_rank_factors(700, 4096, 333, 63)
+    A = gf2.mmm(gf2.Mat.from_rowmajor(X, 333), gf2.Mat.from_rowmajor(Y, 4096))
+    got = rank_noalloc(A)
+    assert got == 333
+    assert got == gf2.gf2_rank(A)
+    assert got == oracle.rank(A.to_rowmajor(), 4096)
+
+
+def test_noalloc_reports_padding_bits():
+    # a bit beyond the last column (m = 100: bits 36..63 of word 1 are padding)
+    words = f2gen.uniform(100, 100, 64)
+    words[17, 1] |= np.uint64(1) << np.uint64(40)
+    A = gf2.Mat.from_rowmajor(words, 100)
+    with pytest.raises(gf2.Gf2Error) as e:
+        rank_noalloc(A)
+    assert e.value.status == gf2.GF2_ERR_PADDING
+    # the next call on a clean matrix is unaffected
+    clean = gf2.Mat.from_rowmajor(f2gen.uniform(100, 100, 65), 100)
+    assert rank_noalloc(clean) == gf2.gf2_rank(clean)
