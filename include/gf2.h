@@ -68,6 +68,52 @@ int gf2_version(void);
 int gf2_release_workspace(void);
 
 /* ------------------------------------------------------------------------
+ * Per-call options.  Every field 0 means "automatic": the library's default,
+ * or the process-wide setting of the matching setter below
+ * (gf2_mmm_set_strassen_cutoff, gf2_batched_set_c8_from), which are only
+ * defaults.  The entry points ending in _ex take a gf2_opts (NULL = all 0),
+ * so that callers on different threads can use different settings without
+ * touching shared state.  No field changes a result: every option gives the
+ * same bits (the factors are unique given the pivot rule, the product is
+ * exact); they change only speed and memory.
+ *   panel_w          decomposition: columns per trailing update (Section 5,
+ *                    the wide-panel form): 64 = one update per 64-column
+ *                    block, 128 = one update per pair of blocks (default).
+ *                    Other multiples of 64: GF2_ERR_UNSUPPORTED.
+ *   table_c          decomposition: bits per Four Russians table of the
+ *                    trailing update (Section 6): 4 or 8; 0 = 8, and 4 for a
+ *                    single-block update with fewer than 4096 rows below it.
+ *                    Other values up to 16: GF2_ERR_UNSUPPORTED.
+ *   tile_words       words per column tile of the working copy: 4 (the only
+ *                    one built; others GF2_ERR_UNSUPPORTED).
+ *   backend          product: GF2_BACKEND_AUTO (M4RM under Strassen-Winograd),
+ *                    GF2_BACKEND_TABLES (M4RM alone), GF2_BACKEND_TENSOR.
+ *   strassen_cutoff  product: the Strassen-Winograd cutoff, >= 128
+ *                    (GF2_STRASSEN_OFF: no recursion); 0 = the process one.
+ *   batched_c8_from  batched decomposition: the size from which a matrix
+ *                    uses 8-bit tables (gf2_batched_set_c8_from); 0 = the
+ *                    process one.
+ * Negative values and values the field does not know: GF2_ERR_ARG. */
+#define GF2_BACKEND_AUTO 0
+#define GF2_BACKEND_TABLES 1
+#define GF2_BACKEND_TENSOR 2
+#define GF2_STRASSEN_OFF ((int64_t)1 << 62)
+
+typedef struct gf2_opts {
+    int32_t panel_w;
+    int32_t table_c;
+    int32_t tile_words;
+    int32_t backend;
+    int64_t strassen_cutoff;
+    int64_t batched_c8_from;
+} gf2_opts;
+
+/* Checks a gf2_opts without using the GPU: GF2_OK, GF2_ERR_ARG or
+ * GF2_ERR_UNSUPPORTED, as an _ex call with it would return first.  NULL is
+ * valid (all automatic). */
+int gf2_opts_check(const gf2_opts *o);
+
+/* ------------------------------------------------------------------------
  * Product over F2 (Section 1 and Section 6 of the paper).
  *   C = A*B        (accumulate == 0)
  *   C = C xor A*B  (accumulate != 0)
@@ -96,6 +142,15 @@ int gf2_release_workspace(void);
 size_t gf2_mmm_workspace_bytes(int64_t n, int64_t k, int64_t m, unsigned flags);
 int gf2_mmm(const gf2_mat *A, const gf2_mat *B, gf2_mat *C, int accumulate, unsigned flags,
             void *workspace, size_t ws_bytes, void *stream);
+
+/* gf2_mmm with per-call options: opts->backend and opts->strassen_cutoff
+ * take the place of the backend flags and of the process-wide cutoff (flags
+ * may still hold GF2_NOCHECK; a backend flag together with a backend option
+ * is GF2_ERR_ARG).  Size the workspace with gf2_mmm_workspace_bytes_ex and
+ * the same options. */
+size_t gf2_mmm_workspace_bytes_ex(int64_t n, int64_t k, int64_t m, unsigned flags, const gf2_opts *opts);
+int gf2_mmm_ex(const gf2_mat *A, const gf2_mat *B, gf2_mat *C, int accumulate, unsigned flags,
+               const gf2_opts *opts, void *workspace, size_t ws_bytes, void *stream);
 
 /* The Strassen cutoff of the default product (a process-wide setting).
  * gf2_mmm_autotune times, on the current device, square products of size d
@@ -140,6 +195,13 @@ int gf2_decompose(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *ra
                   gf2_mat *L, gf2_mat *E, unsigned flags,
                   void *workspace, size_t ws_bytes, void *stream);
 
+/* gf2_decompose with per-call options (panel_w, table_c, tile_words; the
+ * product fields are ignored).  Same outputs, bit for bit, for every
+ * option. */
+int gf2_decompose_ex(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *rank,
+                     gf2_mat *L, gf2_mat *E, unsigned flags, const gf2_opts *opts,
+                     void *workspace, size_t ws_bytes, void *stream);
+
 /* Reduced row echelon form, in place (Gauss-Jordan: the paper names it
  * among the uses of the decomposition, Section 1, and leaves it to the
  * textbook).  E (k x m, column blocks, device) is an echelon factor as
@@ -182,6 +244,9 @@ int gf2_nullspace(const gf2_mat *R, const int32_t *pivcols, int64_t rank, gf2_ma
 size_t gf2_rank_workspace_bytes(int64_t n, int64_t m);
 int gf2_rank(const gf2_mat *A, int64_t *rank_host, unsigned flags,
              void *workspace, size_t ws_bytes, void *stream);
+/* gf2_rank with per-call options (those of gf2_decompose_ex). */
+int gf2_rank_ex(const gf2_mat *A, int64_t *rank_host, unsigned flags, const gf2_opts *opts,
+                void *workspace, size_t ws_bytes, void *stream);
 
 /* Rank of A (n x m, n <= 4096 and m <= 4096) without allocating anything.
  * No counterpart in the paper: this exists for callers that may not
@@ -236,6 +301,13 @@ size_t gf2_decompose_batched_workspace_bytes(int count, const int64_t *n, const 
 int gf2_decompose_batched(int count, const gf2_mat *A, int32_t *const *perm, int32_t *const *pivcols,
                           int64_t *rank, const gf2_mat *L, const gf2_mat *E, unsigned flags,
                           void *workspace, size_t ws_bytes, void *stream);
+/* The same with per-call options (batched_c8_from); size the workspace with
+ * gf2_decompose_batched_workspace_bytes_ex and the same options. */
+size_t gf2_decompose_batched_workspace_bytes_ex(int count, const int64_t *n, const int64_t *m, int want_factors,
+                                                const gf2_opts *opts);
+int gf2_decompose_batched_ex(int count, const gf2_mat *A, int32_t *const *perm, int32_t *const *pivcols,
+                             int64_t *rank, const gf2_mat *L, const gf2_mat *E, unsigned flags,
+                             const gf2_opts *opts, void *workspace, size_t ws_bytes, void *stream);
 
 /* The batched kernel's table size: matrices whose larger dimension is at
  * least c8_from use Four Russians tables of 8 bits (64 KB per CTA, three CTAs
@@ -281,6 +353,66 @@ size_t gf2_solve_workspace_bytes(int64_t n, int64_t m);
 int gf2_solve(const gf2_mat *L, const gf2_mat *E, const int32_t *perm, const int32_t *pivcols,
               const int64_t *rank, const gf2_mat *B, gf2_mat *X, uint64_t *consistent,
               unsigned flags, void *workspace, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Factor handle: the factors of one decomposition in device memory that the
+ * handle owns (Lemma 4.1 and Figure 1: P, the pivot columns, L, E, and the
+ * block form's per-block data -- Z, the within-block maps T_j and T_j^-1 --
+ * which the handle keeps opaquely), with the scratch its calls need, so
+ * that solves, reduced forms and null spaces take the handle instead of
+ * loose arrays and use no shared workspace.
+ *   n, m      the matrix size the handle was allocated for
+ *   rank      host copy of the rank: -1 until gf2_factors_rank reads it
+ *   perm      device int32[n]; pivcols device int32[min(n, m)]
+ *   rank_dev  device int64, written by gf2_factors_decompose
+ *   L, E      n x min(n, m) and min(n, m) x m column blocks in device
+ *             memory (w = NULL with GF2_FACTORS_RANK_ONLY)
+ *   flags     as given to gf2_factors_alloc
+ *   impl      library-owned; do not touch
+ * Calls on one handle must not overlap in time (issue them on one stream,
+ * or wait between streams); calls on different handles may.
+ * gf2_factors_alloc(F, n, m, flags): fills *F and allocates its device
+ * memory (cudaMalloc; about the size of A for the scratch, plus L and E).
+ *   GF2_ERR_ARG (F NULL, n or m < 0, unknown flag), GF2_ERR_UNSUPPORTED
+ *   (n or m >= 2^31), GF2_ERR_NOMEM.
+ * gf2_factors_free(F): releases it (waits for the device first) and zeroes
+ *   *F; a zeroed handle frees as a no-op.  GF2_ERR_ARG for F NULL.
+ * gf2_factors_decompose(F, A, flags, opts, stream): P*A = L*E of an n x m
+ *   A into the handle, as gf2_decompose_ex (flags: GF2_NOCHECK).
+ * gf2_factors_rank(F, rank_host, stream): synchronises the stream and reads
+ *   the rank (also into F->rank).
+ * gf2_factors_solve(F, B, X, consistent, flags, stream): as gf2_solve with
+ *   the handle's factors (needs L and E).
+ * gf2_factors_rref(F, R, stream): R (min(n, m) x m, the caller's) receives
+ *   the reduced row echelon form of E; the handle is unchanged.
+ * gf2_factors_nullspace(F, N, stream): N (m x (m - rank), the caller's)
+ *   receives the null-space basis of gf2_nullspace; synchronises the stream
+ *   once to read the rank, and the first call allocates the handle's copy
+ *   of the reduced form (kept until gf2_factors_free).
+ * Errors as the matching loose-array entry points, plus GF2_ERR_ARG for a
+ * handle without L and E where they are needed, and GF2_ERR_SHAPE for a
+ * matrix of another size than the handle's. */
+#define GF2_FACTORS_RANK_ONLY 1u
+
+typedef struct gf2_factors {
+    int64_t n, m;
+    int64_t rank;
+    int32_t *perm;
+    int32_t *pivcols;
+    int64_t *rank_dev;
+    gf2_mat L, E;
+    uint32_t flags;
+    void *impl;
+} gf2_factors;
+
+int gf2_factors_alloc(gf2_factors *F, int64_t n, int64_t m, unsigned flags);
+int gf2_factors_free(gf2_factors *F);
+int gf2_factors_decompose(gf2_factors *F, const gf2_mat *A, unsigned flags, const gf2_opts *opts, void *stream);
+int gf2_factors_rank(gf2_factors *F, int64_t *rank_host, void *stream);
+int gf2_factors_solve(const gf2_factors *F, const gf2_mat *B, gf2_mat *X, uint64_t *consistent, unsigned flags,
+                      void *stream);
+int gf2_factors_rref(const gf2_factors *F, gf2_mat *R, void *stream);
+int gf2_factors_nullspace(gf2_factors *F, gf2_mat *N, void *stream);
 
 /* ------------------------------------------------------------------------
  * Serving: a request engine for rank and solve requests on many matrices

@@ -133,6 +133,29 @@ def load() -> ctypes.CDLL:
     lib.gf2_launch_count.restype = ctypes.c_int64
     lib.gf2_op_counts.restype = ctypes.c_int
     lib.gf2_op_counts.argtypes = [P, ctypes.c_int, ctypes.c_int]
+    O = ctypes.POINTER(Opts)
+    F = ctypes.POINTER(_CFactors)
+    lib.gf2_opts_check.restype = ctypes.c_int
+    lib.gf2_opts_check.argtypes = [O]
+    lib.gf2_mmm_workspace_bytes_ex.restype = S
+    lib.gf2_mmm_workspace_bytes_ex.argtypes = [I64, I64, I64, ctypes.c_uint, O]
+    lib.gf2_mmm_ex.restype = ctypes.c_int
+    lib.gf2_mmm_ex.argtypes = [M, M, M, ctypes.c_int, ctypes.c_uint, O, P, S, P]
+    lib.gf2_decompose_ex.restype = ctypes.c_int
+    lib.gf2_decompose_ex.argtypes = [M, P, P, P, M, M, ctypes.c_uint, O, P, S, P]
+    lib.gf2_rank_ex.restype = ctypes.c_int
+    lib.gf2_rank_ex.argtypes = [M, ctypes.POINTER(ctypes.c_int64), ctypes.c_uint, O, P, S, P]
+    lib.gf2_decompose_batched_workspace_bytes_ex.restype = S
+    lib.gf2_decompose_batched_workspace_bytes_ex.argtypes = [ctypes.c_int, P, P, ctypes.c_int, O]
+    lib.gf2_decompose_batched_ex.restype = ctypes.c_int
+    lib.gf2_decompose_batched_ex.argtypes = [ctypes.c_int, M, P, P, P, M, M, ctypes.c_uint, O, P, S, P]
+    for name, args in (("gf2_factors_alloc", [F, I64, I64, ctypes.c_uint]), ("gf2_factors_free", [F]),
+                       ("gf2_factors_decompose", [F, M, ctypes.c_uint, O, P]),
+                       ("gf2_factors_rank", [F, ctypes.POINTER(ctypes.c_int64), P]),
+                       ("gf2_factors_solve", [F, M, M, P, ctypes.c_uint, P]), ("gf2_factors_rref", [F, M, P]),
+                       ("gf2_factors_nullspace", [F, M, P])):
+        getattr(lib, name).restype = ctypes.c_int
+        getattr(lib, name).argtypes = args
     lib.gf2_trace_read.restype = ctypes.c_int
     lib.gf2_trace_read.argtypes = [P, ctypes.c_int64, ctypes.c_int]
     lib.gf2_timing_enable.argtypes = [ctypes.c_int]
@@ -158,6 +181,20 @@ def _stream(stream) -> int:
 
 def _ptr(t) -> int | None:
     return None if t is None else t.data_ptr()
+
+
+class Opts(ctypes.Structure):
+    """gf2_opts of include/gf2.h: per-call options, 0 = automatic in every field."""
+    _fields_ = [("panel_w", ctypes.c_int32), ("table_c", ctypes.c_int32), ("tile_words", ctypes.c_int32),
+                ("backend", ctypes.c_int32), ("strassen_cutoff", ctypes.c_int64), ("batched_c8_from", ctypes.c_int64)]
+
+
+BACKEND_AUTO, BACKEND_TABLES, BACKEND_TENSOR = 0, 1, 2
+GF2_FACTORS_RANK_ONLY = 1
+
+
+def _opts(o):
+    return None if o is None else ctypes.byref(o)
 
 
 class Mat:
@@ -202,6 +239,120 @@ class Mat:
         return np.ascontiguousarray(host[: (self.cols + 63) // 64, : self.rows].T)
 
 
+class _CFactors(ctypes.Structure):
+    """gf2_factors of include/gf2.h."""
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("rank", ctypes.c_int64),
+                ("perm", ctypes.c_void_p), ("pivcols", ctypes.c_void_p), ("rank_dev", ctypes.c_void_p),
+                ("L", _CMat), ("E", _CMat), ("flags", ctypes.c_uint32), ("impl", ctypes.c_void_p)]
+
+
+class _DeviceView:
+    """__cuda_array_interface__ of library-owned device memory, so that torch
+    can view it without a copy (valid while its owner lives)."""
+
+    def __init__(self, ptr: int, shape: tuple, typestr: str):
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (int(ptr or 0), False),
+                                         "version": 2, "strides": None}
+
+
+def _view(ptr, shape, typestr, dtype) -> torch.Tensor:
+    if not ptr or 0 in shape:
+        return torch.zeros(shape, dtype=dtype, device="cuda")
+    return torch.as_tensor(_DeviceView(ptr, shape, typestr), device="cuda")
+
+
+class Factors:
+    """A gf2_factors handle: the factors of one n x m decomposition in device
+    memory the library owns (perm, pivcols, rank, L, E and the block form),
+    with the scratch of its calls.  The tensors it hands out are views of
+    that memory, valid until close()."""
+
+    def __init__(self, n: int, m: int, rank_only: bool = False):
+        self._f = _CFactors()
+        _check(load().gf2_factors_alloc(ctypes.byref(self._f), n, m, GF2_FACTORS_RANK_ONLY if rank_only else 0),
+               "gf2_factors_alloc")
+        self.n, self.m = int(n), int(m)
+
+    def close(self) -> None:
+        if self._f.impl:
+            _check(load().gf2_factors_free(ctypes.byref(self._f)), "gf2_factors_free")
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def decompose(self, A: Mat, opts: Opts | None = None, flags: int = 0, stream=None) -> "Factors":
+        a = A.c()
+        _check(load().gf2_factors_decompose(ctypes.byref(self._f), ctypes.byref(a), flags, _opts(opts),
+                                            _stream(stream)), "gf2_factors_decompose")
+        return self
+
+    def rank(self, stream=None) -> int:
+        r = ctypes.c_int64(0)
+        _check(load().gf2_factors_rank(ctypes.byref(self._f), ctypes.byref(r), _stream(stream)), "gf2_factors_rank")
+        return int(r.value)
+
+    @property
+    def perm(self) -> torch.Tensor:
+        return _view(self._f.perm, (self.n,), "<i4", torch.int32)
+
+    @property
+    def pivcols(self) -> torch.Tensor:
+        return _view(self._f.pivcols, (min(self.n, self.m),), "<i4", torch.int32)
+
+    def _mat(self, c: _CMat) -> Mat | None:
+        if not c.w and c.rows and c.cols:
+            return None
+        t = _view(c.w, ((c.cols + 63) // 64, c.ld), "<i8", torch.int64)
+        return Mat(t, c.rows, c.cols)
+
+    @property
+    def L(self) -> Mat | None:
+        return self._mat(self._f.L)
+
+    @property
+    def E(self) -> Mat | None:
+        return self._mat(self._f.E)
+
+    def solve(self, B: Mat, stream=None) -> dict:
+        """A X = B with the handle's factors: X (m x nrhs Mat) and the
+        consistency mask (synchronises the stream)."""
+        X = Mat.empty(self.m, B.cols, B.t.device)
+        ok = torch.zeros(1, dtype=torch.int64, device=B.t.device)
+        b, x = B.c(), X.c()
+        _check(load().gf2_factors_solve(ctypes.byref(self._f), ctypes.byref(b), ctypes.byref(x), ok.data_ptr(), 0,
+                                        _stream(stream)), "gf2_factors_solve")
+        return dict(X=X, consistent=int(ok.cpu().numpy().view(np.uint64)[0]))
+
+    def rref(self, stream=None) -> Mat:
+        """The reduced row echelon form of E, in a new Mat (E is unchanged)."""
+        R = Mat.empty(min(self.n, self.m), self.m)
+        r = R.c()
+        _check(load().gf2_factors_rref(ctypes.byref(self._f), ctypes.byref(r), _stream(stream)), "gf2_factors_rref")
+        return R
+
+    def nullspace(self, stream=None) -> Mat:
+        """The null-space basis (m x (m - rank)); synchronises once for the rank."""
+        N = Mat.empty(self.m, self.m - self.rank(stream))
+        nn = N.c()
+        _check(load().gf2_factors_nullspace(ctypes.byref(self._f), ctypes.byref(nn), _stream(stream)),
+               "gf2_factors_nullspace")
+        return N
+
+
+def opts_check(o: Opts | None) -> int:
+    """gf2_opts_check: the status an _ex call with these options returns first."""
+    return int(load().gf2_opts_check(_opts(o)))
+
+
 def _workspace(nbytes: int, device) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
 
@@ -232,6 +383,44 @@ def gf2_decompose(A: Mat, perm: torch.Tensor, pivcols: torch.Tensor, rank: torch
     _check(lib.gf2_decompose(ctypes.byref(a), _ptr(perm), _ptr(pivcols), _ptr(rank),
                              ctypes.byref(l) if l is not None else None, ctypes.byref(e) if e is not None else None,
                              flags, workspace.data_ptr(), workspace.numel(), _stream(stream)), "gf2_decompose")
+
+
+def gf2_mmm_ex(A: Mat, B: Mat, C: Mat, opts: Opts | None, accumulate: bool = False, flags: int = 0, workspace=None,
+               stream=None) -> None:
+    """gf2_mmm with per-call options (backend, Strassen cutoff)."""
+    lib = load()
+    if workspace is None:
+        workspace = _workspace(lib.gf2_mmm_workspace_bytes_ex(A.rows, A.cols, B.cols, flags, _opts(opts)), C.t.device)
+    a, b, c = A.c(), B.c(), C.c()
+    _check(lib.gf2_mmm_ex(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), int(accumulate), flags, _opts(opts),
+                          workspace.data_ptr(), workspace.numel(), _stream(stream)), "gf2_mmm_ex")
+
+
+def gf2_decompose_ex(A: Mat, perm: torch.Tensor, pivcols: torch.Tensor, rank: torch.Tensor, L: Mat | None,
+                     E: Mat | None, opts: Opts | None, flags: int = 0, workspace=None, stream=None) -> None:
+    """gf2_decompose with per-call options (panel width, table size, tile)."""
+    lib = load()
+    want = L is not None or E is not None
+    if workspace is None:
+        workspace = _workspace(lib.gf2_decompose_workspace_bytes(A.rows, A.cols, int(want)), A.t.device)
+    a = A.c()
+    l = L.c() if L is not None else None
+    e = E.c() if E is not None else None
+    _check(lib.gf2_decompose_ex(ctypes.byref(a), _ptr(perm), _ptr(pivcols), _ptr(rank),
+                                ctypes.byref(l) if l is not None else None, ctypes.byref(e) if e is not None else None,
+                                flags, _opts(opts), workspace.data_ptr(), workspace.numel(), _stream(stream)),
+           "gf2_decompose_ex")
+
+
+def gf2_rank_ex(A: Mat, opts: Opts | None, flags: int = 0, workspace=None, stream=None) -> int:
+    lib = load()
+    if workspace is None:
+        workspace = _workspace(lib.gf2_rank_workspace_bytes(A.rows, A.cols), A.t.device)
+    r = ctypes.c_int64(-1)
+    a = A.c()
+    _check(lib.gf2_rank_ex(ctypes.byref(a), ctypes.byref(r), flags, _opts(opts), workspace.data_ptr(),
+                           workspace.numel(), _stream(stream)), "gf2_rank_ex")
+    return int(r.value)
 
 
 def gf2_rref(E: Mat, pivcols: torch.Tensor, workspace=None, stream=None) -> None:

@@ -205,7 +205,7 @@ int side_resources(int nevents, SideResources **out, std::unique_lock<std::mutex
 // ------------------------------------------------------------ graph cache
 // One captured graph per (device, shape, every pointer the kernels see).
 struct GraphKey {
-    int dev;
+    int32_t dev, pair, tab_c, unused;  // (no padding: the key is compared bytewise)
     int64_t n, m, lda, ldl, lde;
     const void *a, *perm, *piv, *rank, *L, *E, *ws;
 };
@@ -229,6 +229,43 @@ const bool g_use_pairs = [] {
     const char *e = getenv("GF2_PAIRS");
     return !(e && e[0] == '0');
 }();
+
+// ------------------------------------------------------------ options
+// A gf2_opts checked and resolved for one call (0 = the process-wide value,
+// read where it is used).
+struct CallOpts {
+    int32_t pair;      // wide updates by pairs of panels (panel_w 128) or one panel (64)
+    int32_t tab_c;     // Four Russians table bits of the wide updates: 0 (automatic), 4 or 8
+    unsigned backend;  // product backend flag: 0, GF2_MMM_TABLES or GF2_MMM_TENSOR
+    int64_t cutoff;    // Strassen cutoff of the product, 0 = the process one
+    int64_t c8_from;   // batched: 8-bit tables from this size, 0 = the process one
+};
+
+int check_opts(const gf2_opts *o)
+{
+    if (!o) return GF2_OK;
+    if (o->panel_w < 0 || o->panel_w % 64) return GF2_ERR_ARG;
+    if (o->panel_w != 0 && o->panel_w != 64 && o->panel_w != 128) return GF2_ERR_UNSUPPORTED;
+    if (o->table_c < 0 || o->table_c > 16) return GF2_ERR_ARG;
+    if (o->table_c != 0 && o->table_c != 4 && o->table_c != 8) return GF2_ERR_UNSUPPORTED;
+    if (o->tile_words < 0) return GF2_ERR_ARG;
+    if (o->tile_words != 0 && o->tile_words != kTileWords) return GF2_ERR_UNSUPPORTED;
+    if (o->backend < GF2_BACKEND_AUTO || o->backend > GF2_BACKEND_TENSOR) return GF2_ERR_ARG;
+    if (o->strassen_cutoff < 0 || (o->strassen_cutoff > 0 && o->strassen_cutoff < 128)) return GF2_ERR_ARG;
+    if (o->batched_c8_from < 0) return GF2_ERR_ARG;
+    return GF2_OK;
+}
+
+CallOpts resolve_opts(const gf2_opts *o)
+{
+    CallOpts r{};
+    r.pair = (o && o->panel_w) ? (o->panel_w == 128) : (g_use_pairs ? 1 : 0);
+    r.tab_c = o ? o->table_c : 0;
+    r.backend = !o ? 0u : o->backend == GF2_BACKEND_TABLES ? GF2_MMM_TABLES : o->backend == GF2_BACKEND_TENSOR ? GF2_MMM_TENSOR : 0u;
+    r.cutoff = o ? o->strassen_cutoff : 0;
+    r.c8_from = o ? o->batched_c8_from : 0;
+    return r;
+}
 
 cudaGraphExec_t find_graph(const GraphKey &k, int64_t *kernels)
 {
@@ -420,7 +457,7 @@ DecompLayout decomp_layout(int64_t n, int64_t m, bool factors)
 }
 
 int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *rank, gf2_mat *L, gf2_mat *E,
-                   unsigned flags, void *workspace, size_t ws_bytes, cudaStream_t s)
+                   unsigned flags, const CallOpts &o, void *workspace, size_t ws_bytes, cudaStream_t s)
 {
     if (!mat_ok(A) || !perm || !rank || (flags & ~GF2_NOCHECK)) return GF2_ERR_ARG;
     const int64_t n = A->rows, m = A->cols;
@@ -457,7 +494,8 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
     c.m = (int32_t)m;
     c.mu = (int32_t)d.mu;
     c.kmax = (int32_t)kmax;
-    c.pair = g_use_pairs ? 1 : 0;
+    c.pair = o.pair;
+    c.tab_c = o.tab_c;
     uint32_t *flag = reinterpret_cast<uint32_t *>(base + d.oFlag);
 
     if (n == 0 || m == 0) {
@@ -490,6 +528,8 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
     CK(cudaStreamWaitEvent(side->main, evIn, 0));
     GraphKey key{};
     key.dev = side->device;
+    key.pair = c.pair;
+    key.tab_c = c.tab_c;
     key.n = n; key.m = m; key.a = A->w; key.lda = A->ld;
     key.perm = perm; key.piv = pivcols; key.rank = rank;
     key.L = L ? L->w : nullptr; key.ldl = L ? L->ld : 0;
@@ -636,9 +676,20 @@ size_t gf2_decompose_workspace_bytes(int64_t n, int64_t m, int want_factors)
 int gf2_decompose(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *rank, gf2_mat *L, gf2_mat *E,
                   unsigned flags, void *workspace, size_t ws_bytes, void *stream)
 {
-    return decompose_impl(A, perm, pivcols, rank, L, E, flags, workspace, ws_bytes,
+    return decompose_impl(A, perm, pivcols, rank, L, E, flags, resolve_opts(nullptr), workspace, ws_bytes,
                           static_cast<cudaStream_t>(stream));
 }
+
+int gf2_decompose_ex(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *rank, gf2_mat *L, gf2_mat *E,
+                     unsigned flags, const gf2_opts *opts, void *workspace, size_t ws_bytes, void *stream)
+{
+    const int st = check_opts(opts);
+    if (st) return st;
+    return decompose_impl(A, perm, pivcols, rank, L, E, flags, resolve_opts(opts), workspace, ws_bytes,
+                          static_cast<cudaStream_t>(stream));
+}
+
+int gf2_opts_check(const gf2_opts *o) { return check_opts(o); }
 
 size_t gf2_nullspace_workspace_bytes(int64_t m, int64_t rank)
 {
@@ -729,7 +780,8 @@ RankLayout rank_layout(int64_t n, int64_t m)
     return d;
 }
 
-int rank_impl(const gf2_mat *A, int64_t *rank_host, unsigned flags, void *workspace, size_t ws_bytes, cudaStream_t s)
+int rank_impl(const gf2_mat *A, int64_t *rank_host, unsigned flags, const CallOpts &o, void *workspace, size_t ws_bytes,
+              cudaStream_t s)
 {
     if (!A || !rank_host || (flags & ~GF2_NOCHECK) || !mat_ok(A)) return GF2_ERR_ARG;
     const int64_t n = A->rows, m = A->cols;
@@ -743,7 +795,7 @@ int rank_impl(const gf2_mat *A, int64_t *rank_host, unsigned flags, void *worksp
     int64_t *rk = reinterpret_cast<int64_t *>(base + d.oRank);
     const size_t dec = gf2_decompose_workspace_bytes(d.rows, d.cols, 0);
     if (!d.transposed) {
-        st = decompose_impl(A, perm, piv, rk, nullptr, nullptr, flags, base + d.oDec, dec, s);
+        st = decompose_impl(A, perm, piv, rk, nullptr, nullptr, flags, o, base + d.oDec, dec, s);
     } else {
         if (n >= (1ll << 31) - 64 || m >= (1ll << 31) - 64) return GF2_ERR_UNSUPPORTED;
         if (!(flags & GF2_NOCHECK) && (m % 64)) {
@@ -759,7 +811,7 @@ int rank_impl(const gf2_mat *A, int64_t *rank_host, unsigned flags, void *worksp
         uint64_t *T = reinterpret_cast<uint64_t *>(base + d.oT);
         LAUNCH(GF2_KCLASS_LAYOUT, launch_transpose_bits(A->w, A->ld, n, m, T, m, s));
         const gf2_mat At{T, m, n, m};
-        st = decompose_impl(&At, perm, piv, rk, nullptr, nullptr, flags | GF2_NOCHECK, base + d.oDec, dec, s);
+        st = decompose_impl(&At, perm, piv, rk, nullptr, nullptr, flags | GF2_NOCHECK, o, base + d.oDec, dec, s);
     }
     if (st) return st;
     CK(cudaMemcpyAsync(rank_host, rk, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -777,7 +829,15 @@ size_t gf2_rank_workspace_bytes(int64_t n, int64_t m)
 
 int gf2_rank(const gf2_mat *A, int64_t *rank_host, unsigned flags, void *workspace, size_t ws_bytes, void *stream)
 {
-    return rank_impl(A, rank_host, flags, workspace, ws_bytes, static_cast<cudaStream_t>(stream));
+    return rank_impl(A, rank_host, flags, resolve_opts(nullptr), workspace, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+int gf2_rank_ex(const gf2_mat *A, int64_t *rank_host, unsigned flags, const gf2_opts *opts, void *workspace,
+                size_t ws_bytes, void *stream)
+{
+    const int st = check_opts(opts);
+    if (st) return st;
+    return rank_impl(A, rank_host, flags, resolve_opts(opts), workspace, ws_bytes, static_cast<cudaStream_t>(stream));
 }
 
 size_t gf2_decompose_host_workspace_bytes(int64_t n, int64_t m, int want_factors)
@@ -831,8 +891,8 @@ int gf2_decompose_host(int64_t n, int64_t m, const uint64_t *A_host, int64_t lda
     gf2_mat A{Ad, n, m, n > 0 ? n : 1};
     gf2_mat L{Ld, n, kmax, n > 0 ? n : 1};
     gf2_mat E{Ed, kmax, m, kmax > 0 ? kmax : 1};
-    st = decompose_impl(&A, permd, pivd, rkd, factors ? &L : nullptr, factors ? &E : nullptr, flags | GF2_NOCHECK, p,
-                        dec, s);
+    st = decompose_impl(&A, permd, pivd, rkd, factors ? &L : nullptr, factors ? &E : nullptr, flags | GF2_NOCHECK,
+                        resolve_opts(nullptr), p, dec, s);
     if (st) return st;
     CK(cudaMemcpyAsync(rank_host, rkd, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     if (n > 0) CK(cudaMemcpyAsync(perm_host, permd, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
@@ -1021,20 +1081,42 @@ int batch_side(BatchSide **out)
 
 }  // namespace
 
+namespace gf2 {
+static int batched_with(int count, const BatchItem *items, bool factors, unsigned flags, void *workspace,
+                        size_t ws_bytes, cudaStream_t s, int64_t c8_from);
+}  // namespace gf2
+
 extern "C" {
+
+size_t gf2_decompose_batched_workspace_bytes_ex(int count, const int64_t *n, const int64_t *m, int want_factors,
+                                                const gf2_opts *opts)
+{
+    if (count < 0 || (count > 0 && (!n || !m)) || check_opts(opts)) return 0;
+    const int64_t from = resolve_opts(opts).c8_from;
+    BatchPlan P;
+    if (batch_plan(count, n, m, want_factors != 0, from > 0 ? from : g_batch_c8_from.load(), &P) != GF2_OK) return 0;
+    return P.total;
+}
 
 size_t gf2_decompose_batched_workspace_bytes(int count, const int64_t *n, const int64_t *m, int want_factors)
 {
-    if (count < 0 || (count > 0 && (!n || !m))) return 0;
-    BatchPlan P;
-    if (batch_plan(count, n, m, want_factors != 0, g_batch_c8_from.load(), &P) != GF2_OK) return 0;
-    return P.total;
+    return gf2_decompose_batched_workspace_bytes_ex(count, n, m, want_factors, nullptr);
 }
 
 int gf2_decompose_batched(int count, const gf2_mat *A, int32_t *const *perm, int32_t *const *pivcols, int64_t *rank,
                           const gf2_mat *L, const gf2_mat *E, unsigned flags, void *workspace, size_t ws_bytes,
                           void *stream)
 {
+    return gf2_decompose_batched_ex(count, A, perm, pivcols, rank, L, E, flags, nullptr, workspace, ws_bytes, stream);
+}
+
+int gf2_decompose_batched_ex(int count, const gf2_mat *A, int32_t *const *perm, int32_t *const *pivcols, int64_t *rank,
+                             const gf2_mat *L, const gf2_mat *E, unsigned flags, const gf2_opts *opts, void *workspace,
+                             size_t ws_bytes, void *stream)
+{
+    const int ost = check_opts(opts);
+    if (ost) return ost;
+    const int64_t from = resolve_opts(opts).c8_from;
     if (count < 0 || (flags & ~GF2_NOCHECK)) return GF2_ERR_ARG;
     if (count == 0) return GF2_OK;
     if (!A || !perm || !rank || (count > 0 && !pivcols)) return GF2_ERR_ARG;
@@ -1053,7 +1135,8 @@ int gf2_decompose_batched(int count, const gf2_mat *A, int32_t *const *perm, int
                              factors ? L[i].w : nullptr, factors ? L[i].ld : 0,
                              factors ? E[i].w : nullptr, factors ? E[i].ld : 0};
     }
-    return gf2::decompose_batched_items(count, items.data(), factors, flags, workspace, ws_bytes, stream);
+    return gf2::batched_with(count, items.data(), factors, flags, workspace, ws_bytes, static_cast<cudaStream_t>(stream),
+                             from > 0 ? from : g_batch_c8_from.load());
 }
 
 }  // extern "C"
@@ -1288,10 +1371,34 @@ bool mmm_use_tensor(int64_t k, unsigned flags)
     return (flags & GF2_MMM_TENSOR) && !(flags & GF2_MMM_TABLES) && k < (1ll << 24);
 }
 
-int mmm_levels(int64_t n, int64_t k, int64_t m, unsigned flags)
+// cutoff 0: the process-wide one
+int mmm_levels(int64_t n, int64_t k, int64_t m, unsigned flags, int64_t cutoff)
 {
     if (flags & (GF2_MMM_TABLES | GF2_MMM_TENSOR)) return 0;
-    return strassen_levels(n, k, words_of(m), g_strassen_cutoff.load());
+    return strassen_levels(n, k, words_of(m), cutoff > 0 ? cutoff : g_strassen_cutoff.load());
+}
+
+size_t mmm_bytes(int64_t n, int64_t k, int64_t m, unsigned flags, int64_t cutoff)
+{
+    if (n < 0 || k < 0 || m < 0) return 0;
+    if (mmm_use_tensor(k, flags)) return mmm_tensor_bytes(n, k, m);
+    return align_up(strassen_bytes(n, k, words_of(m), mmm_levels(n, k, m, flags, cutoff))) + kAlign;
+}
+
+int mmm_impl(const gf2_mat *A, const gf2_mat *B, gf2_mat *C, int accumulate, unsigned flags, int64_t cutoff,
+             void *workspace, size_t ws_bytes, void *stream);
+
+// a backend flag and a backend option together are an error; otherwise the
+// option's backend joins the flags
+int mmm_opts_flags(unsigned flags, const gf2_opts *opts, unsigned *out, int64_t *cutoff)
+{
+    const int st = check_opts(opts);
+    if (st) return st;
+    const CallOpts o = resolve_opts(opts);
+    if (o.backend && (flags & (GF2_MMM_TABLES | GF2_MMM_TENSOR))) return GF2_ERR_ARG;
+    *out = flags | o.backend;
+    *cutoff = o.cutoff;
+    return GF2_OK;
 }
 
 }  // namespace
@@ -1300,13 +1407,39 @@ extern "C" {
 
 size_t gf2_mmm_workspace_bytes(int64_t n, int64_t k, int64_t m, unsigned flags)
 {
-    if (n < 0 || k < 0 || m < 0) return 0;
-    if (mmm_use_tensor(k, flags)) return mmm_tensor_bytes(n, k, m);
-    return align_up(strassen_bytes(n, k, words_of(m), mmm_levels(n, k, m, flags))) + kAlign;
+    return mmm_bytes(n, k, m, flags, 0);
+}
+
+size_t gf2_mmm_workspace_bytes_ex(int64_t n, int64_t k, int64_t m, unsigned flags, const gf2_opts *opts)
+{
+    unsigned f = 0;
+    int64_t cutoff = 0;
+    if (mmm_opts_flags(flags, opts, &f, &cutoff)) return 0;
+    return mmm_bytes(n, k, m, f, cutoff);
 }
 
 int gf2_mmm(const gf2_mat *A, const gf2_mat *B, gf2_mat *C, int accumulate, unsigned flags, void *workspace,
             size_t ws_bytes, void *stream)
+{
+    return mmm_impl(A, B, C, accumulate, flags, 0, workspace, ws_bytes, stream);
+}
+
+int gf2_mmm_ex(const gf2_mat *A, const gf2_mat *B, gf2_mat *C, int accumulate, unsigned flags, const gf2_opts *opts,
+               void *workspace, size_t ws_bytes, void *stream)
+{
+    unsigned f = 0;
+    int64_t cutoff = 0;
+    const int st = mmm_opts_flags(flags, opts, &f, &cutoff);
+    if (st) return st;
+    return mmm_impl(A, B, C, accumulate, f, cutoff, workspace, ws_bytes, stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+int mmm_impl(const gf2_mat *A, const gf2_mat *B, gf2_mat *C, int accumulate, unsigned flags, int64_t cutoff,
+             void *workspace, size_t ws_bytes, void *stream)
 {
     if (!mat_ok(A) || !mat_ok(B) || !mat_ok(C) || (flags & ~(GF2_NOCHECK | GF2_MMM_TABLES | GF2_MMM_TENSOR)))
         return GF2_ERR_ARG;
@@ -1322,11 +1455,11 @@ int gf2_mmm(const gf2_mat *A, const gf2_mat *B, gf2_mat *C, int accumulate, unsi
         return GF2_OK;
     }
     void *ws = nullptr;
-    int st = get_workspace(workspace, ws_bytes, gf2_mmm_workspace_bytes(n, k, m, flags), &ws);
+    int st = get_workspace(workspace, ws_bytes, mmm_bytes(n, k, m, flags, cutoff), &ws);
     if (st) return st;
     char *p = static_cast<char *>(ws);
     const bool tensor = mmm_use_tensor(k, flags);
-    const int levels = tensor ? 0 : mmm_levels(n, k, m, flags);
+    const int levels = tensor ? 0 : mmm_levels(n, k, m, flags, cutoff);
     uint32_t *flag = reinterpret_cast<uint32_t *>(
         p + (tensor ? mmm_tensor_bytes(n, k, m) - kAlign : align_up(strassen_bytes(n, k, mw, levels))));
     if (!(flags & GF2_NOCHECK)) {
@@ -1349,6 +1482,10 @@ int gf2_mmm(const gf2_mat *A, const gf2_mat *B, gf2_mat *C, int accumulate, unsi
     return mmm_rec(CBView{C->w, C->ld}, CBView{A->w, A->ld}, CBView{B->w, B->ld}, n, k, mw, accumulate != 0, levels,
                    reinterpret_cast<uint64_t *>(p), s);
 }
+
+}  // namespace
+
+extern "C" {
 
 int gf2_mmm_set_strassen_cutoff(int64_t cutoff)
 {
@@ -1614,6 +1751,193 @@ int gf2_batched_autotune(int64_t max_dim, int64_t *c8_from, float *times_ms, voi
     g_batch_c8_from.store(chosen);
     *c8_from = chosen;
     return GF2_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ factor handle
+namespace {
+
+// What a gf2_factors owns: one device allocation holding perm, pivcols, the
+// rank, L, E, the per-block data of the last decomposition (the block form's
+// Z, T_j, T_j^-1, pivot rows and bits per 64-column block, as the
+// decomposition leaves them) and the scratch of its calls (the largest of
+// the decomposition's, the solve's, the reduced form's and the null
+// space's workspaces); and, once a null space was asked for, a copy of the
+// reduced form.
+struct FactorsImpl {
+    int device;
+    void *mem;
+    void *scratch;
+    size_t scratch_bytes;
+    PanelInfo *blocks;
+    int64_t nblocks;
+    size_t info_offset;  // of the decomposition's per-block data in its workspace
+    uint64_t *R;         // k x m reduced form (ld k), for the null space
+};
+
+bool factors_ok(const gf2_factors *F)
+{
+    return F && F->impl && F->n >= 0 && F->m >= 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gf2_factors_alloc(gf2_factors *F, int64_t n, int64_t m, unsigned flags)
+{
+    if (!F || n < 0 || m < 0 || (flags & ~GF2_FACTORS_RANK_ONLY)) return GF2_ERR_ARG;
+    if (n >= (1ll << 31) - 64 || m >= (1ll << 31) - 64) return GF2_ERR_UNSUPPORTED;
+    const bool factors = !(flags & GF2_FACTORS_RANK_ONLY);
+    const int64_t kmax = n < m ? n : m, mu = words_of(m), lw = words_of(kmax);
+    const int64_t ldl = n > 0 ? n : 1, lde = kmax > 0 ? kmax : 1;
+    size_t scratch = gf2_decompose_workspace_bytes(n, m, factors);
+    const size_t more[3] = {gf2_solve_workspace_bytes(n, m), gf2_rref_workspace_bytes(kmax, m),
+                            gf2_nullspace_workspace_bytes(m, 0)};
+    for (size_t x : more) scratch = x > scratch ? x : scratch;
+    size_t o = 0;
+    const size_t oPerm = o; o += align_up((size_t)(n > 0 ? n : 1) * 4);
+    const size_t oPiv = o; o += align_up((size_t)(kmax > 0 ? kmax : 1) * 4);
+    const size_t oRank = o; o += kAlign;
+    const size_t oL = o; if (factors) o += align_up((size_t)lw * ldl * 8);
+    const size_t oE = o; if (factors) o += align_up((size_t)mu * lde * 8);
+    const size_t oBlk = o; o += align_up((size_t)(mu > 0 ? mu : 1) * sizeof(PanelInfo));
+    const size_t oScr = o; o += align_up(scratch);
+    auto *impl = new (std::nothrow) FactorsImpl{};
+    if (!impl) return GF2_ERR_NOMEM;
+    if (cudaGetDevice(&impl->device) != cudaSuccess) {
+        delete impl;
+        return GF2_ERR_CUDA;
+    }
+    if (cudaMalloc(&impl->mem, o) != cudaSuccess) {
+        cudaGetLastError();
+        delete impl;
+        return GF2_ERR_NOMEM;
+    }
+    char *base = static_cast<char *>(impl->mem);
+    impl->scratch = base + oScr;
+    impl->scratch_bytes = align_up(scratch);
+    impl->blocks = reinterpret_cast<PanelInfo *>(base + oBlk);
+    impl->nblocks = mu;
+    impl->info_offset = decomp_layout(n, m, factors).oInfo;
+    impl->R = nullptr;
+    gf2_factors f{};
+    f.n = n;
+    f.m = m;
+    f.rank = -1;
+    f.perm = reinterpret_cast<int32_t *>(base + oPerm);
+    f.pivcols = reinterpret_cast<int32_t *>(base + oPiv);
+    f.rank_dev = reinterpret_cast<int64_t *>(base + oRank);
+    f.L = gf2_mat{factors ? reinterpret_cast<uint64_t *>(base + oL) : nullptr, n, kmax, ldl};
+    f.E = gf2_mat{factors ? reinterpret_cast<uint64_t *>(base + oE) : nullptr, kmax, m, lde};
+    f.flags = flags;
+    f.impl = impl;
+    // (zero factors: a decomposition writes them all; this keeps the padding
+    // of L and E defined)
+    if (cudaMemset(impl->mem, 0, o) != cudaSuccess) {
+        cudaFree(impl->mem);
+        delete impl;
+        return GF2_ERR_CUDA;
+    }
+    *F = f;
+    return GF2_OK;
+}
+
+int gf2_factors_free(gf2_factors *F)
+{
+    if (!F) return GF2_ERR_ARG;
+    auto *impl = static_cast<FactorsImpl *>(F->impl);
+    if (impl) {
+        int cur = 0;
+        const bool have = cudaGetDevice(&cur) == cudaSuccess;
+        cudaSetDevice(impl->device);
+        cudaDeviceSynchronize();
+        cudaFree(impl->R);
+        cudaFree(impl->mem);
+        if (have) cudaSetDevice(cur);
+        delete impl;
+    }
+    *F = gf2_factors{};
+    return GF2_OK;
+}
+
+int gf2_factors_decompose(gf2_factors *F, const gf2_mat *A, unsigned flags, const gf2_opts *opts, void *stream)
+{
+    if (!factors_ok(F) || !A) return GF2_ERR_ARG;
+    int st = check_opts(opts);
+    if (st) return st;
+    if (A->rows != F->n || A->cols != F->m) return GF2_ERR_SHAPE;
+    auto *impl = static_cast<FactorsImpl *>(F->impl);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool factors = F->L.w != nullptr;
+    F->rank = -1;
+    st = decompose_impl(A, F->perm, F->pivcols, F->rank_dev, factors ? &F->L : nullptr, factors ? &F->E : nullptr,
+                        flags, resolve_opts(opts), impl->scratch, impl->scratch_bytes, s);
+    if (st) return st;
+    if (impl->nblocks > 0 && F->n > 0)
+        CK(cudaMemcpyAsync(impl->blocks, static_cast<char *>(impl->scratch) + impl->info_offset,
+                           (size_t)impl->nblocks * sizeof(PanelInfo), cudaMemcpyDeviceToDevice, s));
+    return GF2_OK;
+}
+
+int gf2_factors_rank(gf2_factors *F, int64_t *rank_host, void *stream)
+{
+    if (!factors_ok(F) || !rank_host) return GF2_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaMemcpyAsync(rank_host, F->rank_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    F->rank = *rank_host;
+    return GF2_OK;
+}
+
+int gf2_factors_solve(const gf2_factors *F, const gf2_mat *B, gf2_mat *X, uint64_t *consistent, unsigned flags,
+                      void *stream)
+{
+    if (!factors_ok(F) || !F->L.w || !F->E.w || !B || !X) return GF2_ERR_ARG;
+    if (B->rows != F->n || X->rows != F->m) return GF2_ERR_SHAPE;
+    auto *impl = static_cast<FactorsImpl *>(F->impl);
+    return gf2_solve(&F->L, &F->E, F->perm, F->pivcols, F->rank_dev, B, X, consistent, flags, impl->scratch,
+                     impl->scratch_bytes, stream);
+}
+
+int gf2_factors_rref(const gf2_factors *F, gf2_mat *R, void *stream)
+{
+    if (!factors_ok(F) || !F->E.w || !R || !mat_ok(R)) return GF2_ERR_ARG;
+    const int64_t k = F->E.rows, m = F->m;
+    if (R->rows != k || R->cols != m) return GF2_ERR_SHAPE;
+    if (k == 0 || m == 0) return GF2_OK;
+    if (!R->w) return GF2_ERR_ARG;
+    auto *impl = static_cast<FactorsImpl *>(F->impl);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaMemcpy2DAsync(R->w, (size_t)R->ld * 8, F->E.w, (size_t)F->E.ld * 8, (size_t)k * 8, (size_t)words_of(m),
+                         cudaMemcpyDeviceToDevice, s));
+    return gf2_rref(R, F->pivcols, impl->scratch, impl->scratch_bytes, stream);
+}
+
+int gf2_factors_nullspace(gf2_factors *F, gf2_mat *N, void *stream)
+{
+    if (!factors_ok(F) || !F->E.w || !N) return GF2_ERR_ARG;
+    auto *impl = static_cast<FactorsImpl *>(F->impl);
+    int64_t r = 0;
+    int st = gf2_factors_rank(F, &r, stream);
+    if (st) return st;
+    const int64_t k = F->E.rows, m = F->m;
+    if (!mat_ok(N) || N->rows != m || N->cols != m - r) return GF2_ERR_SHAPE;
+    if (m == 0 || m == r) return GF2_OK;
+    if (!impl->R && k > 0) {
+        if (cudaMalloc(&impl->R, (size_t)k * words_of(m) * 8) != cudaSuccess) {
+            cudaGetLastError();
+            impl->R = nullptr;
+            return GF2_ERR_NOMEM;
+        }
+    }
+    gf2_mat R{impl->R, k, m, k > 0 ? k : 1};
+    if (k > 0) {
+        st = gf2_factors_rref(F, &R, stream);
+        if (st) return st;
+    }
+    return gf2_nullspace(&R, F->pivcols, r, N, impl->scratch, impl->scratch_bytes, stream);
 }
 
 }  // extern "C"

@@ -76,6 +76,7 @@ struct DecompCtx {
     uint64_t *zraw;     // [n] their raw panel words (both null: the panel scans without a list)
     int32_t pair;       // wide updates by pairs of panels (j even, j+1)
     int32_t info_ring;  // info holds only panels j-1 and j (info[j % 2]): the batched form
+    int32_t tab_c;      // table bits of the wide updates: 4, 8, or 0 (8; 4 for one panel with < 4096 rows)
 };
 
 // The PanelInfo of panel j.

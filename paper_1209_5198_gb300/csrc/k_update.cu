@@ -485,6 +485,7 @@ cudaError_t prepare_update_kernels()
     if (done[dev]) return cudaSuccess;
     e = allow_smem(k_rest<8, kRestU, 1>, rest_smem_bytes<8, 1>());
     if (e == cudaSuccess) e = allow_smem(k_rest<8, kRest2U, 2>, rest_smem_bytes<8, 2>());
+    if (e == cudaSuccess) e = allow_smem(k_rest<4, kRest2U, 2>, rest_smem_bytes<4, 2>());
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }
@@ -558,11 +559,18 @@ cudaError_t launch_rest(const DecompCtx &c, int j, int np, int est_active_rows, 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    // table size: the caller's choice (c.tab_c), else 8 bits, and 4 bits
+    // for one panel with few rows below it (fewer rows to amortise the
+    // tables over)
     if (np == 2) {
+        if (c.tab_c == 4) {
+            cfg.dynamicSmemBytes = rest_smem_bytes<4, 2>();
+            return cudaLaunchKernelEx(&cfg, k_rest<4, kRest2U, 2>, c, j, tile_first, ntiles);
+        }
         cfg.dynamicSmemBytes = rest_smem_bytes<8, 2>();
         return cudaLaunchKernelEx(&cfg, k_rest<8, kRest2U, 2>, c, j, tile_first, ntiles);
     }
-    if (est_active_rows >= 4096) {
+    if (c.tab_c == 8 || (c.tab_c == 0 && est_active_rows >= 4096)) {
         cfg.dynamicSmemBytes = rest_smem_bytes<8, 1>();
         return cudaLaunchKernelEx(&cfg, k_rest<8, kRestU, 1>, c, j, tile_first, ntiles);
     }

@@ -191,3 +191,89 @@ def test_reduced_form_null_space_and_rank_workspaces_without_gpu(lib):
     assert lib.gf2_op_counts(None, 9, 0) == 1
     assert lib.gf2_op_counts(out, -1, 0) == 1
     assert lib.gf2_op_counts(out, 9, 0) == 7  # GF2_ERR_UNSUPPORTED: the release build counts nothing
+
+
+def test_options_and_factor_structs_match_the_c_layout(tmp_path):
+    """gf2_opts and gf2_factors of the binding have the C structs' sizes and
+    field offsets."""
+    import shutil
+    import subprocess
+
+    import paper_1209_5198_gb300 as g
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = {"gf2_opts": g.Opts, "gf2_factors": g._CFactors}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gf2.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        lines += [f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));' for f, _ in py._fields_]
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout2.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout2"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)
+
+
+def test_options_are_validated_without_gpu(lib):
+    """gf2_opts_check and every _ex entry point reject bad options before any
+    device work (so these run without a GPU)."""
+    import paper_1209_5198_gb300 as g
+    ok = g.Opts()
+    assert g.opts_check(None) == g.GF2_OK
+    assert g.opts_check(ok) == g.GF2_OK
+    good = [dict(panel_w=64), dict(panel_w=128), dict(table_c=4), dict(table_c=8), dict(tile_words=4),
+            dict(backend=g.BACKEND_TABLES), dict(backend=g.BACKEND_TENSOR), dict(strassen_cutoff=128),
+            dict(strassen_cutoff=g.STRASSEN_OFF), dict(batched_c8_from=512),
+            dict(panel_w=64, table_c=4, tile_words=4, backend=1, strassen_cutoff=4096, batched_c8_from=1)]
+    bad_arg = [dict(panel_w=-64), dict(panel_w=96), dict(table_c=-1), dict(table_c=17), dict(tile_words=-4),
+               dict(backend=3), dict(backend=-1), dict(strassen_cutoff=-1), dict(strassen_cutoff=127),
+               dict(batched_c8_from=-5)]
+    unsupported = [dict(panel_w=192), dict(panel_w=256), dict(table_c=6), dict(table_c=16), dict(tile_words=2),
+                   dict(tile_words=8)]
+    for kw in good:
+        assert g.opts_check(g.Opts(**kw)) == g.GF2_OK, kw
+    for kw in bad_arg:
+        assert g.opts_check(g.Opts(**kw)) == g.GF2_ERR_ARG, kw
+    for kw in unsupported:
+        assert g.opts_check(g.Opts(**kw)) == g.GF2_ERR_UNSUPPORTED, kw
+    # the _ex entry points return the same status before touching the device
+    bad = ctypes.byref(g.Opts(panel_w=96))
+    a = g._CMat(1, 64, 64, 64)  # (never dereferenced)
+    assert lib.gf2_decompose_ex(ctypes.byref(a), None, None, None, None, None, 0, bad, None, 0, None) == g.GF2_ERR_ARG
+    assert lib.gf2_rank_ex(ctypes.byref(a), ctypes.byref(ctypes.c_int64()), 0, bad, None, 0, None) == g.GF2_ERR_ARG
+    assert lib.gf2_mmm_ex(ctypes.byref(a), ctypes.byref(a), ctypes.byref(a), 0, 0, bad, None, 0, None) == g.GF2_ERR_ARG
+    assert lib.gf2_decompose_batched_ex(1, ctypes.byref(a), None, None, None, None, None, 0,
+                                        ctypes.byref(g.Opts(tile_words=8)), None, 0, None) == g.GF2_ERR_UNSUPPORTED
+    assert lib.gf2_mmm_workspace_bytes_ex(64, 64, 64, 0, bad) == 0
+    # a backend flag and a backend option together
+    both = ctypes.byref(g.Opts(backend=g.BACKEND_TENSOR))
+    assert lib.gf2_mmm_ex(ctypes.byref(a), ctypes.byref(a), ctypes.byref(a), 0, g.GF2_MMM_TABLES, both, None, 0,
+                          None) == g.GF2_ERR_ARG
+
+
+def test_factor_handle_argument_errors_without_gpu(lib):
+    """gf2_factors_* reject bad arguments before any allocation, and a zeroed
+    handle frees as a no-op."""
+    import paper_1209_5198_gb300 as g
+    F = g._CFactors()
+    assert lib.gf2_factors_alloc(None, 4, 4, 0) == g.GF2_ERR_ARG
+    assert lib.gf2_factors_alloc(ctypes.byref(F), -1, 4, 0) == g.GF2_ERR_ARG
+    assert lib.gf2_factors_alloc(ctypes.byref(F), 4, -1, 0) == g.GF2_ERR_ARG
+    assert lib.gf2_factors_alloc(ctypes.byref(F), 4, 4, 8) == g.GF2_ERR_ARG
+    assert lib.gf2_factors_alloc(ctypes.byref(F), 1 << 31, 4, 0) == g.GF2_ERR_UNSUPPORTED
+    assert lib.gf2_factors_free(None) == g.GF2_ERR_ARG
+    assert lib.gf2_factors_free(ctypes.byref(F)) == g.GF2_OK  # zeroed: nothing to free
+    a = g._CMat(None, 4, 4, 4)
+    r = ctypes.c_int64()
+    assert lib.gf2_factors_decompose(ctypes.byref(F), ctypes.byref(a), 0, None, None) == g.GF2_ERR_ARG
+    assert lib.gf2_factors_rank(ctypes.byref(F), ctypes.byref(r), None) == g.GF2_ERR_ARG
+    assert lib.gf2_factors_solve(ctypes.byref(F), ctypes.byref(a), ctypes.byref(a), None, 0, None) == g.GF2_ERR_ARG
+    assert lib.gf2_factors_rref(ctypes.byref(F), ctypes.byref(a), None) == g.GF2_ERR_ARG
+    assert lib.gf2_factors_nullspace(ctypes.byref(F), ctypes.byref(a), None) == g.GF2_ERR_ARG
