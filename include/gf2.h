@@ -88,6 +88,18 @@ int gf2_release_workspace(void);
  *                    one built; others GF2_ERR_UNSUPPORTED).
  *   backend          product: GF2_BACKEND_AUTO (M4RM under Strassen-Winograd),
  *                    GF2_BACKEND_TABLES (M4RM alone), GF2_BACKEND_TENSOR.
+ *   schedule         decomposition by pairs of panels: GF2_SCHEDULE_PERSISTENT
+ *                    runs it as one cooperative persistent launch (one CTA
+ *                    per SM: CTA 0 runs the panel chain, the others the
+ *                    look-ahead and the trailing updates, ordered by device
+ *                    counters); GF2_SCHEDULE_STREAMS as separate launches on
+ *                    three streams (one CTA per panel); AUTO picks the
+ *                    persistent launch from 4096 rows on when the device can
+ *                    hold one CTA per SM, the streams otherwise (and always
+ *                    with panel_w 64).  A persistent run whose bounded device
+ *                    waits give up writes rank -1 (the other outputs are then
+ *                    undefined); the calls that read the rank back return
+ *                    GF2_ERR_TIMEOUT.
  *   strassen_cutoff  product: the Strassen-Winograd cutoff, >= 128
  *                    (GF2_STRASSEN_OFF: no recursion); 0 = the process one.
  *   batched_c8_from  batched decomposition: the size from which a matrix
@@ -99,11 +111,17 @@ int gf2_release_workspace(void);
 #define GF2_BACKEND_TENSOR 2
 #define GF2_STRASSEN_OFF ((int64_t)1 << 62)
 
+#define GF2_SCHEDULE_AUTO 0
+#define GF2_SCHEDULE_STREAMS 1
+#define GF2_SCHEDULE_PERSISTENT 2
+
 typedef struct gf2_opts {
     int32_t panel_w;
     int32_t table_c;
     int32_t tile_words;
     int32_t backend;
+    int32_t schedule;
+    int32_t reserved;         /* must be 0 */
     int64_t strassen_cutoff;
     int64_t batched_c8_from;
 } gf2_opts;
@@ -507,7 +525,8 @@ int gf2_server_destroy(gf2_server *server);
 #define GF2_KCLASS_UPDATE 2  /* wide trailing update / product pass (M4RM)   */
 #define GF2_KCLASS_LAYOUT 3  /* layout conversions and final outputs         */
 #define GF2_KCLASS_SOLVE 4   /* forward / back substitution (gf2_solve)      */
-#define GF2_NUM_KCLASSES 5
+#define GF2_KCLASS_FACTOR 5  /* the whole decomposition in one persistent launch */
+#define GF2_NUM_KCLASSES 6
 int64_t gf2_launch_count(void);
 int gf2_timing_enable(int on);
 int gf2_timing_reset(void);

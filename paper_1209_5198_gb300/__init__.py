@@ -44,7 +44,7 @@ GF2_ERR_TIMEOUT = 6
 GF2_ERR_UNSUPPORTED = 7
 GF2_NOCHECK = 1
 GF2_SERVE_SERIAL = 1
-KCLASS = {"panel": 0, "next": 1, "update": 2, "layout": 3, "solve": 4}
+KCLASS = {"panel": 0, "next": 1, "update": 2, "layout": 3, "solve": 4, "factor": 5}
 
 
 class Gf2Error(RuntimeError):
@@ -186,10 +186,12 @@ def _ptr(t) -> int | None:
 class Opts(ctypes.Structure):
     """gf2_opts of include/gf2.h: per-call options, 0 = automatic in every field."""
     _fields_ = [("panel_w", ctypes.c_int32), ("table_c", ctypes.c_int32), ("tile_words", ctypes.c_int32),
-                ("backend", ctypes.c_int32), ("strassen_cutoff", ctypes.c_int64), ("batched_c8_from", ctypes.c_int64)]
+                ("backend", ctypes.c_int32), ("schedule", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("strassen_cutoff", ctypes.c_int64), ("batched_c8_from", ctypes.c_int64)]
 
 
 BACKEND_AUTO, BACKEND_TABLES, BACKEND_TENSOR = 0, 1, 2
+SCHEDULE_AUTO, SCHEDULE_STREAMS, SCHEDULE_PERSISTENT = 0, 1, 2
 GF2_FACTORS_RANK_ONLY = 1
 
 

@@ -236,6 +236,7 @@ const bool g_use_pairs = [] {
 struct CallOpts {
     int32_t pair;      // wide updates by pairs of panels (panel_w 128) or one panel (64)
     int32_t tab_c;     // Four Russians table bits of the wide updates: 0 (automatic), 4 or 8
+    int32_t schedule;  // GF2_SCHEDULE_*
     unsigned backend;  // product backend flag: 0, GF2_MMM_TABLES or GF2_MMM_TENSOR
     int64_t cutoff;    // Strassen cutoff of the product, 0 = the process one
     int64_t c8_from;   // batched: 8-bit tables from this size, 0 = the process one
@@ -251,6 +252,7 @@ int check_opts(const gf2_opts *o)
     if (o->tile_words < 0) return GF2_ERR_ARG;
     if (o->tile_words != 0 && o->tile_words != kTileWords) return GF2_ERR_UNSUPPORTED;
     if (o->backend < GF2_BACKEND_AUTO || o->backend > GF2_BACKEND_TENSOR) return GF2_ERR_ARG;
+    if (o->schedule < GF2_SCHEDULE_AUTO || o->schedule > GF2_SCHEDULE_PERSISTENT || o->reserved) return GF2_ERR_ARG;
     if (o->strassen_cutoff < 0 || (o->strassen_cutoff > 0 && o->strassen_cutoff < 128)) return GF2_ERR_ARG;
     if (o->batched_c8_from < 0) return GF2_ERR_ARG;
     return GF2_OK;
@@ -261,6 +263,7 @@ CallOpts resolve_opts(const gf2_opts *o)
     CallOpts r{};
     r.pair = (o && o->panel_w) ? (o->panel_w == 128) : (g_use_pairs ? 1 : 0);
     r.tab_c = o ? o->table_c : 0;
+    r.schedule = o ? o->schedule : GF2_SCHEDULE_AUTO;
     r.backend = !o ? 0u : o->backend == GF2_BACKEND_TABLES ? GF2_MMM_TABLES : o->backend == GF2_BACKEND_TENSOR ? GF2_MMM_TENSOR : 0u;
     r.cutoff = o ? o->strassen_cutoff : 0;
     r.c8_from = o ? o->batched_c8_from : 0;
@@ -351,6 +354,30 @@ void drop_graphs()
 //     j = 4k+2, the one before for j = 4k); next(j+1) follows next(j);
 //     rest(j, j+1) waits for next(j+1); a lone last panel is updated alone.
 // So panel j+1 runs while next(j) and the updates of earlier panels run.
+// The factors out of the working buffers and the rank (after either schedule).
+int enqueue_outputs(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat *E, cudaStream_t s)
+{
+    LAUNCH(GF2_KCLASS_LAYOUT, launch_finish_scalars(c, rank, s));
+    if (E) LAUNCH(GF2_KCLASS_LAYOUT, launch_finish_E(c, E->w, E->ld, s));
+    if (L)
+        LAUNCH(GF2_KCLASS_LAYOUT, launch_colblocks_from_rowmajor(c.Lint, c.ldl, c.perm, c.n, (int32_t)words_of(c.kmax),
+                                                                   L->w, L->ld, s));
+    return GF2_OK;
+}
+
+// The persistent schedule: the counters cleared, one cooperative launch of
+// the whole factorization (csrc/k_factor.cu), then the outputs; all on s.
+// cudaErrorNotSupported (nothing enqueued): the device cannot hold it.
+cudaError_t enqueue_persistent(DecompCtx c, int32_t *progress, int64_t *rank, gf2_mat *L, gf2_mat *E, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(progress, 0, (size_t)factor_progress_ints(c.mu) * 4, s);
+    if (e != cudaSuccess) return e;
+    e = launch(GF2_KCLASS_FACTOR, s, [&]() { return launch_factor(c, progress, s); });
+    if (e != cudaSuccess) return e;
+    c.fail = factor_fail_word(progress);
+    return enqueue_outputs(c, rank, L, E, s) == GF2_OK ? cudaSuccess : cudaErrorUnknown;
+}
+
 int enqueue_factorization(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat *E, SideResources *side)
 {
     cudaStream_t s = side->main, P = side->stream, N = side->next;
@@ -419,17 +446,15 @@ int enqueue_factorization(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat
     CK(cudaStreamWaitEvent(s, evJoinP, 0));
     CK(cudaEventRecord(evJoinN, N));
     CK(cudaStreamWaitEvent(s, evJoinN, 0));
-    LAUNCH(GF2_KCLASS_LAYOUT, launch_finish_scalars(c, rank, s));
-    if (E) LAUNCH(GF2_KCLASS_LAYOUT, launch_finish_E(c, E->w, E->ld, s));
-    if (L)
-        LAUNCH(GF2_KCLASS_LAYOUT, launch_colblocks_from_rowmajor(c.Lint, c.ldl, c.perm, c.n, (int32_t)words_of(c.kmax),
-                                                                   L->w, L->ld, s));
-    return GF2_OK;
+    return enqueue_outputs(c, rank, L, E, s);
 }
+
+// the automatic schedule's switch to the persistent launch (rows)
+constexpr int64_t kPersistentFromRows = 4096;
 
 struct DecompLayout {
     int64_t mu, ldw, kmax, ldl;
-    size_t oW, oY, oF, oAct, oNact, oPP, oInfo, oZpos, oZraw, oLint, oEint, oFlag, total;
+    size_t oW, oY, oF, oAct, oNact, oPP, oInfo, oZpos, oZraw, oLint, oEint, oFlag, oProg, total;
 };
 
 DecompLayout decomp_layout(int64_t n, int64_t m, bool factors)
@@ -452,6 +477,7 @@ DecompLayout decomp_layout(int64_t n, int64_t m, bool factors)
     d.oLint = o; if (factors) o += align_up((size_t)n * d.ldl * 8);
     d.oEint = o; if (factors) o += align_up((size_t)d.kmax * d.ldw * 8);
     d.oFlag = o; o += kAlign;
+    d.oProg = o; o += align_up((size_t)factor_progress_ints((int)d.mu) * 4);  // the persistent run's counters
     d.total = o;
     return d;
 }
@@ -513,6 +539,19 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
     }
     if (c.Lint) CK(cudaMemsetAsync(c.Lint, 0, (size_t)n * d.ldl * 8, s));
     CK(cudaMemsetAsync(c.nact, 0, (size_t)c.mu * sizeof(int32_t), s));  // the active-list counts
+
+    // By pairs of panels, from kPersistentFromRows rows on (or when asked):
+    // the whole factorization as one cooperative persistent launch on the
+    // caller's stream (csrc/k_factor.cu); a device that cannot hold one CTA
+    // per SM falls back to the separate launches below.
+    const bool persistent = c.pair && (o.schedule == GF2_SCHEDULE_PERSISTENT ||
+                                       (o.schedule == GF2_SCHEDULE_AUTO && n >= kPersistentFromRows));
+    if (persistent) {
+        const cudaError_t e = enqueue_persistent(c, reinterpret_cast<int32_t *>(base + d.oProg), rank, L, E, s);
+        if (e == cudaSuccess) return GF2_OK;
+        cudaGetLastError();
+        if (e != cudaErrorNotSupported) return GF2_ERR_CUDA;
+    }
 
     // The factorization runs on the library's three streams of this device
     // (M: wide updates and outputs, P: the panel chain, N: the look-ahead
@@ -816,7 +855,7 @@ int rank_impl(const gf2_mat *A, int64_t *rank_host, unsigned flags, const CallOp
     if (st) return st;
     CK(cudaMemcpyAsync(rank_host, rk, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    return GF2_OK;
+    return *rank_host < 0 ? GF2_ERR_TIMEOUT : GF2_OK;  // (-1: a persistent run's device wait gave up)
 }
 }  // namespace
 extern "C" {
@@ -900,7 +939,7 @@ int gf2_decompose_host(int64_t n, int64_t m, const uint64_t *A_host, int64_t lda
     if (L_host && lw > 0) CK(cudaMemcpyAsync(L_host, Ld, (size_t)lw * n * 8, cudaMemcpyDeviceToHost, s));
     if (E_host && kmax > 0) CK(cudaMemcpyAsync(E_host, Ed, (size_t)mu * kmax * 8, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    return GF2_OK;
+    return *rank_host < 0 ? GF2_ERR_TIMEOUT : GF2_OK;
 }
 
 // ------------------------------------------------------------ solve
@@ -1587,7 +1626,8 @@ int gf2_op_counts(uint64_t *out, int count, int reset)
 #ifdef GF2_COUNT_OPS
     if (cudaDeviceSynchronize() != cudaSuccess) return GF2_ERR_CUDA;
     unsigned long long acc[kNumOps] = {};
-    if (read_update_ops(acc, reset != 0) != cudaSuccess || read_mmm_ops(acc, reset != 0) != cudaSuccess)
+    if (read_update_ops(acc, reset != 0) != cudaSuccess || read_mmm_ops(acc, reset != 0) != cudaSuccess ||
+        read_factor_ops(acc, reset != 0) != cudaSuccess)
         return GF2_ERR_CUDA;
     for (int i = 0; i < count && i < kNumOps; ++i) out[i] = acc[i];
     return GF2_OK;
@@ -1602,15 +1642,20 @@ int gf2_trace_read(uint64_t *out, int64_t count, int reset)
     if (!out || count < 0) return GF2_ERR_ARG;
 #ifdef GF2_TRACE
     if (cudaDeviceSynchronize() != cudaSuccess) return GF2_ERR_CUDA;
-    std::vector<unsigned long long> a(kTrSlots * kTraceMaxPanels), b(kTrSlots * kTraceMaxPanels);
-    if (read_panel_trace(a.data(), reset != 0) != cudaSuccess || read_update_trace(b.data(), reset != 0) != cudaSuccess)
+    std::vector<unsigned long long> a(kTrSlots * kTraceMaxPanels), b(kTrSlots * kTraceMaxPanels),
+        f(kTrSlots * kTraceMaxPanels);
+    if (read_panel_trace(a.data(), reset != 0) != cudaSuccess || read_update_trace(b.data(), reset != 0) != cudaSuccess ||
+        read_factor_trace(f.data(), reset != 0) != cudaSuccess)
         return GF2_ERR_CUDA;
-    // each slot lives in one translation unit: the panel phases in the
-    // panel's, the launch spans in the update kernels'; start slots are kept
+    // each slot lives in one translation unit per schedule: the panel phases
+    // in the panel kernel's, the launch spans in the update kernels', and
+    // everything of a persistent run in its kernel's (a run writes one of
+    // them; the larger value is the one written); start slots are kept
     // complemented on the device
     for (int64_t i = 0; i < count && i < (int64_t)a.size(); ++i) {
         const int slot = (int)(i / kTraceMaxPanels);
         unsigned long long v = slot <= kTrPanelEnd ? a[i] : b[i];
+        if (f[i] > v) v = f[i];
         if ((slot == kTrNextStart || slot == kTrRestStart) && v) v = ~v;
         out[i] = v;
     }
@@ -1888,7 +1933,7 @@ int gf2_factors_rank(gf2_factors *F, int64_t *rank_host, void *stream)
     CK(cudaMemcpyAsync(rank_host, F->rank_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     F->rank = *rank_host;
-    return GF2_OK;
+    return *rank_host < 0 ? GF2_ERR_TIMEOUT : GF2_OK;
 }
 
 int gf2_factors_solve(const gf2_factors *F, const gf2_mat *B, gf2_mat *X, uint64_t *consistent, unsigned flags,

@@ -77,6 +77,7 @@ struct DecompCtx {
     int32_t pair;       // wide updates by pairs of panels (j even, j+1)
     int32_t info_ring;  // info holds only panels j-1 and j (info[j % 2]): the batched form
     int32_t tab_c;      // table bits of the wide updates: 4, 8, or 0 (8; 4 for one panel with < 4096 rows)
+    const int32_t *fail;  // nonzero after the run: a bounded device wait gave up (the rank reads -1); or null
 };
 
 // The PanelInfo of panel j.
@@ -173,6 +174,14 @@ cudaError_t launch_colblocks_from_rowmajor(const uint64_t *R, int64_t ldr, const
 cudaError_t launch_finish_E(const DecompCtx &c, uint64_t *E, int64_t lde, cudaStream_t s);
 cudaError_t launch_finish_scalars(const DecompCtx &c, int64_t *rank, cudaStream_t s);
 cudaError_t launch_panel(const DecompCtx &c, int j, cudaStream_t s);
+// The whole factorization (pairs of panels) in one cooperative persistent
+// launch (csrc/k_factor.cu): `progress` is factor_progress_ints(mu) int32 of
+// zeroed device memory; it receives the run's failure word (c.fail points
+// into it).  Returns cudaErrorNotSupported when the kernel cannot have one
+// CTA resident on every SM.
+int64_t factor_progress_ints(int mu);
+cudaError_t launch_factor(const DecompCtx &c, int32_t *progress, cudaStream_t s);
+const int32_t *factor_fail_word(const int32_t *progress);
 cudaError_t launch_next(const DecompCtx &c, int j, cudaStream_t s);
 // the wide update of panel j (np = 1) or of the pair j, j+1 (np = 2)
 // the wide update of panel j (np = 1) or of panels j, j+1 (np = 2) on its
@@ -289,6 +298,7 @@ struct TraceSpan {
 };
 cudaError_t read_panel_trace(unsigned long long *out, bool reset);   // csrc/k_panel.cu
 cudaError_t read_update_trace(unsigned long long *out, bool reset);  // csrc/k_update.cu
+cudaError_t read_factor_trace(unsigned long long *out, bool reset);  // csrc/k_factor.cu
 #else
 #define GF2_TR(...)
 #endif
@@ -296,6 +306,7 @@ cudaError_t read_update_trace(unsigned long long *out, bool reset);  // csrc/k_u
 #ifdef GF2_COUNT_OPS
 #define GF2_OPS(...) __VA_ARGS__
 cudaError_t read_update_ops(unsigned long long *acc, bool reset);  // csrc/k_update.cu
+cudaError_t read_factor_ops(unsigned long long *acc, bool reset);  // csrc/k_factor.cu
 cudaError_t read_mmm_ops(unsigned long long *acc, bool reset);     // csrc/k_mmm.cu
 #else
 #define GF2_OPS(...)

@@ -1,0 +1,458 @@
+// The whole decomposition P*A = L*E in one persistent, cooperative launch
+// (pairs of 64-column panels; Section 4's block elimination with the
+// wide-panel update of Section 5).
+//
+// Why one launch.  The panel step of block j (Procedure buildZ, Sections
+// 4.1-4.4) is a serial chain of 64 pivot decisions that no other work can
+// shorten, and panel j+2 cannot start before the look-ahead of panel j has
+// applied panel j to the next two column blocks.  As separate launches each
+// of the mu panels pays a kernel launch and the placement of its CTA, and
+// one panel CTA's shared memory keeps the next one from being resident
+// early.  Here CTA 0 runs the panel chain for the whole decomposition on an
+// SM it never gives up, and the other CTAs (the workers) run the look-ahead
+// and the trailing updates as the chain releases them.
+//
+// Work and its order (the same dependencies as the separate launches):
+//   PANEL(j)  CTA 0, threads 0..127; after NEXT(j-2).
+//   NEXT(j)   the look-ahead of panel j (next_body, csrc/update_core.cuh), in
+//             chunks of 512 list entries; after PANEL(j) and NEXT(j-1) (its
+//             input list and F word), after the last pair update that covers
+//             the tile holding word j+2 has finished that tile, and after the
+//             pair update that read Y and the active list of panel j-8 (the
+//             ring of eight buffers) has finished.
+//   REST(p)   the update of the pair (2p, 2p+1) (rest_prepare / rest_pass),
+//             after NEXT(2p+1); in slots of (tile, range of 256-entry
+//             chunks); a slot on tile T starts after the previous pair that
+//             updates T has finished T (two updates of one word are ordered).
+// The look-ahead is the critical path: a worker looks for a look-ahead
+// chunk before each batch of update chunks (kFBatch of them, a few
+// microseconds), and its update tables live in shared memory apart from the
+// look-ahead's, so it resumes its slot without rebuilding them.
+//
+// Progress counters in global memory order the work.  A producer's threads
+// finish their writes, the CTA synchronises, and thread 0 fences and then
+// increments (release); a consumer's thread 0 reads with acquire and fences,
+// then the CTA synchronises before it touches the data.  Nothing is read
+// through the read-only path.  Every wait polls with a short sleep and gives
+// up after kFSpinLimit polls: it then sets the failure word, every CTA
+// leaves, and the rank reads -1.  The cooperative launch puts all CTAs on
+// the GPU at once, so a wait only ever waits for CTAs that are running.
+#include <mutex>
+
+#include "panel_core.cuh"
+#include "update_core.cuh"
+
+namespace gf2 {
+namespace {
+
+constexpr int kFThreads = 512;
+constexpr int kFNextRows = 512;           // list entries per look-ahead chunk (one per thread)
+constexpr int kFRestU = 4;                // row groups of 16 rows per warp and pass iteration
+constexpr int kFBatch = 8;                // update chunks between looks at the look-ahead queue
+constexpr int kFSmemBytes = 200 * 1024;   // dynamic shared memory of every CTA (one per SM)
+constexpr long long kFSpinLimit = 1ll << 22;  // polls of one wait (~64-500 ns each) before it gives up
+
+// progress words (int32, zeroed before the launch): a header, then the
+// per-panel, per-pair and per-(pair, tile) counters
+enum { kPgPanelDone = 0, kPgNextComplete = 1, kPgFail = 2, kPgHeader = 8 };
+
+struct Progress {
+    int32_t *hdr;
+    int32_t *next_claim, *next_done;                          // [mu]: chunks claimed / finished
+    int32_t *pair_claim, *pair_done;                          // [npairs]: slots claimed, chunks finished
+    int32_t *pair_tf, *pair_nt, *pair_nch, *pair_prev;        // [npairs]: shape, published with NEXT(2p+1)
+    int32_t *tile_done;                                       // [npairs][ntw]: chunks finished per tile
+    int npairs, ntw;
+};
+
+__host__ __device__ inline Progress progress_at(int32_t *base, int mu)
+{
+    Progress g;
+    g.npairs = mu / 2;
+    g.ntw = (mu + kTileWords - 1) / kTileWords;
+    g.hdr = base;
+    int32_t *p = base + kPgHeader;
+    g.next_claim = p; p += mu;
+    g.next_done = p; p += mu;
+    g.pair_claim = p; p += g.npairs;
+    g.pair_done = p; p += g.npairs;
+    g.pair_tf = p; p += g.npairs;
+    g.pair_nt = p; p += g.npairs;
+    g.pair_nch = p; p += g.npairs;
+    g.pair_prev = p; p += g.npairs;
+    g.tile_done = p;
+    return g;
+}
+
+__device__ __forceinline__ int ld_acquire(const int32_t *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed(const int32_t *p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int32_t *p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0: polls until *p >= v.  false: the run failed (here or elsewhere).
+__device__ __forceinline__ bool wait_geq(const int32_t *p, int v, const Progress &g)
+{
+    for (long long it = 0;; ++it) {
+        if (ld_acquire(p) >= v) return true;
+        if (ld_relaxed(g.hdr + kPgFail)) return false;
+        if (it >= kFSpinLimit) {
+            atomicExch(g.hdr + kPgFail, 1);
+            return false;
+        }
+        __nanosleep(64);
+    }
+}
+
+// Look-ahead chunks of panel j: one per kFNextRows entries of the list of
+// the rows active before it, at least one (chunk 0 also writes the pivot
+// rows' factors).
+__device__ __forceinline__ int next_chunks(const DecompCtx &c, int j)
+{
+    const int cnt = j == 0 ? c.n : ld_relaxed(c.nact + j - 1);
+    return max(1, (cnt + kFNextRows - 1) / kFNextRows);
+}
+
+// Slots of pair p: each of its tiles in `parts` ranges of chunks, about two
+// slots per worker while the chunks last.
+__device__ __forceinline__ int pair_parts(const Progress &g, int p, int workers)
+{
+    const int nt = ld_relaxed(g.pair_nt + p), nch = ld_relaxed(g.pair_nch + p);
+    if (nt <= 0 || nch <= 0) return 0;
+    const int want = (2 * workers + nt - 1) / nt;
+    return max(1, min(want, nch));
+}
+
+// Thread 0, after NEXT(2p+1) finished: the shape of pair p's update and the
+// latest earlier pair with an update (its tiles are ordered before p's).
+__device__ __forceinline__ void publish_pair(const DecompCtx &c, const Progress &g, int p)
+{
+    const int tf = (2 * p + 1 + 2) / kTileWords + 1;
+    const int nt = max(0, g.ntw - tf);
+    const int r0 = c.info[2 * p].r, r1 = c.info[2 * p + 1].r;
+    const int nact = ld_relaxed(c.nact + 2 * p + 1);
+    int nch = 0;
+    if ((r0 | r1) && nt > 0) nch = max((nact + kRestChunk - 1) / kRestChunk, c.Eint ? 1 : 0);
+    g.pair_tf[p] = tf;
+    g.pair_nt[p] = nch > 0 ? nt : 0;
+    g.pair_nch[p] = nch;
+    g.pair_prev[p] = p == 0 ? -1 : (ld_relaxed(g.pair_nch + p - 1) > 0 ? p - 1 : ld_relaxed(g.pair_prev + p - 1));
+}
+
+// Thread 0: may NEXT(j) start?  (Never waits.)
+__device__ __forceinline__ bool next_ready(const DecompCtx &c, const Progress &g, int j)
+{
+    if (ld_acquire(g.hdr + kPgPanelDone) <= j) return false;
+    if (ld_acquire(g.hdr + kPgNextComplete) < j) return false;
+    // the ring of Y buffers and active lists: the update that read panel
+    // j-8's has finished
+    if (j >= 8) {
+        const int q = (j - 8) / 2;
+        const int nch = ld_relaxed(g.pair_nch + q);
+        if (nch > 0 && ld_acquire(g.pair_done + q) < nch * ld_relaxed(g.pair_nt + q)) return false;
+    }
+    // the tile holding word j+2: the last pair update that covers it (pairs
+    // up to (j-2, j-1)) has finished it
+    if (j + 2 < c.mu && j >= 2) {
+        const int T = (j + 2) / kTileWords;
+        int q = (j - 2) / 2;
+        if (ld_relaxed(g.pair_nch + q) == 0) q = ld_relaxed(g.pair_prev + q);
+        while (q >= 0 && ld_relaxed(g.pair_tf + q) > T) q = ld_relaxed(g.pair_prev + q);
+        if (q >= 0 && ld_acquire(g.tile_done + (int64_t)q * g.ntw + T) < ld_relaxed(g.pair_nch + q)) return false;
+    }
+    return true;
+}
+
+#ifdef GF2_TRACE
+__device__ unsigned long long g_factor_trace[kTrSlots * kTraceMaxPanels];  // the trace build's stamps
+#endif
+
+// what a worker CTA does next (decided by thread 0)
+enum { kDoIdle = 0, kDoNext = 1, kDoRest = 2, kDoQuit = 3 };
+struct WorkerCmd {
+    int kind, j, chunk, p, tile, rb, re, prepare, first;
+};
+
+template <int C>
+__global__ void __launch_bounds__(kFThreads, 1) k_factor(DecompCtx c, int32_t *progress)
+{
+    extern __shared__ __align__(16) unsigned char fsmem[];
+    const Progress g = progress_at(progress, c.mu);
+    const int tid = threadIdx.x;
+    UpdOps ops;
+
+    if (blockIdx.x == 0) {
+        // ---------------------------------------------------- the panel chain
+        if (tid >= kPanelThreads) return;
+        PanelShared &sh = *reinterpret_cast<PanelShared *>(fsmem);
+        constexpr int kShBytes = (int)((sizeof(PanelShared) + 15) / 16 * 16);
+        constexpr int kListCap = (kFSmemBytes - kShBytes) / 12 / 8 * 8;
+        uint64_t *zs = reinterpret_cast<uint64_t *>(fsmem + kShBytes);
+        __shared__ int quit;
+        for (int j = 0; j < c.mu; ++j) {
+            if (tid == 0) {
+                quit = (j >= 2 && !wait_geq(g.hdr + kPgNextComplete, j - 1, g)) ? 1 : 0;
+                __threadfence();
+                GF2_TR(if (j < kTraceMaxPanels) g_factor_trace[kTrPanelStart * kTraceMaxPanels + j] = trace_clock();)
+            }
+            panel_sync();
+            if (quit) return;
+#ifdef GF2_TRACE
+            panel_block(c, j, sh, zs, kListCap, j < kTraceMaxPanels ? g_factor_trace : nullptr);
+#else
+            panel_block(c, j, sh, zs, kListCap);
+#endif
+            panel_sync();
+            if (tid == 0) {
+                __threadfence();
+                st_release(g.hdr + kPgPanelDone, j + 1);
+            }
+        }
+        return;
+    }
+
+    // -------------------------------------------------------------- workers
+    // shared memory: the update's tables and staged rows, then the
+    // look-ahead's (apart, so that a look-ahead chunk leaves the tables of
+    // the slot in progress intact)
+    uint64_t *rest_smem = reinterpret_cast<uint64_t *>(fsmem);
+    uint64_t *next_smem = reinterpret_cast<uint64_t *>(fsmem + rest_smem_bytes<C, 2>());
+    int *keep_row = reinterpret_cast<int *>(next_smem + kNextSmemWords);
+    int *keep_warp = keep_row + kFNextRows;
+    __shared__ WorkerCmd cmd;
+    const int workers = gridDim.x - 1;
+    // thread 0's state: the look-ahead cursor, the pair cursor, the slot
+    int jn = 0, pr = 0;
+    int sp = -1, stile = 0, scur = 0, send = 0, sfirst = 0, sprep = 0;
+    long long idle = 0;
+    for (;;) {
+        if (tid == 0) {
+            WorkerCmd w{};
+            w.kind = kDoIdle;
+            if (ld_relaxed(g.hdr + kPgFail)) {
+                w.kind = kDoQuit;
+            } else {
+                // 1. a look-ahead chunk
+                while (jn < c.mu && next_ready(c, g, jn)) {
+                    const int nch = next_chunks(c, jn);
+                    if (ld_relaxed(g.next_claim + jn) >= nch) {
+                        ++jn;
+                        continue;
+                    }
+                    const int t = atomicAdd(g.next_claim + jn, 1);
+                    if (t < nch) {
+                        w.kind = kDoNext;
+                        w.j = jn;
+                        w.chunk = t;
+                        break;
+                    }
+                    ++jn;
+                }
+                // 2. update chunks: the slot in progress, or a new slot
+                if (w.kind == kDoIdle && sp < 0) {
+                    while (pr < g.npairs && ld_acquire(g.hdr + kPgNextComplete) >= 2 * pr + 2) {
+                        const int parts = pair_parts(g, pr, workers);
+                        const int nslots = parts * ld_relaxed(g.pair_nt + pr);
+                        if (ld_relaxed(g.pair_claim + pr) >= nslots) {
+                            ++pr;
+                            continue;
+                        }
+                        const int s = atomicAdd(g.pair_claim + pr, 1);
+                        if (s >= nslots) {
+                            ++pr;
+                            continue;
+                        }
+                        const int nch = ld_relaxed(g.pair_nch + pr), part = s % parts;
+                        sp = pr;
+                        stile = ld_relaxed(g.pair_tf + pr) + s / parts;
+                        scur = (int)((int64_t)part * nch / parts);
+                        send = (int)((int64_t)(part + 1) * nch / parts);
+                        sfirst = part == 0;
+                        sprep = 1;
+                        // two updates of one word are ordered: the previous
+                        // pair with an update has finished this tile
+                        const int q = ld_relaxed(g.pair_prev + pr);
+                        if (q >= 0 && !wait_geq(g.tile_done + (int64_t)q * g.ntw + stile, ld_relaxed(g.pair_nch + q), g))
+                            w.kind = kDoQuit;
+                        break;
+                    }
+                }
+                if (w.kind == kDoIdle && sp >= 0) {
+                    w.kind = kDoRest;
+                    w.p = sp;
+                    w.tile = stile;
+                    w.prepare = sprep;
+                    w.first = sfirst;
+                    const int nact = ld_relaxed(c.nact + 2 * sp + 1);
+                    const int e = min(send, scur + kFBatch);
+                    w.rb = scur * kRestChunk;
+                    w.re = min(nact, e * kRestChunk);
+                    w.chunk = e - scur;  // chunks of this batch
+                    sprep = 0;
+                    scur = e;
+                    if (scur >= send) sp = -1;
+                }
+                if (w.kind == kDoIdle && jn >= c.mu && pr >= g.npairs && sp < 0) w.kind = kDoQuit;
+            }
+            if (w.kind != kDoIdle) __threadfence();
+            cmd = w;
+        }
+        __syncthreads();
+        const WorkerCmd w = cmd;
+        if (w.kind == kDoQuit) break;
+        if (w.kind == kDoIdle) {
+            if (tid == 0) {
+                if (++idle > kFSpinLimit) atomicExch(g.hdr + kPgFail, 1);
+                __nanosleep(128);
+            }
+            __syncthreads();
+            continue;
+        }
+        idle = 0;
+        if (w.kind == kDoNext) {
+            GF2_TR(if (tid == 0 && w.j < kTraceMaxPanels)
+                       atomicMax(g_factor_trace + kTrNextStart * kTraceMaxPanels + w.j, ~trace_clock());)
+            next_body<kFThreads, kFNextRows>(c, w.j, w.chunk, next_smem, keep_row, keep_warp);
+            __syncthreads();
+            if (tid == 0) {
+                GF2_TR(if (w.j < kTraceMaxPanels) atomicMax(g_factor_trace + kTrNextEnd * kTraceMaxPanels + w.j, trace_clock());)
+                __threadfence();
+                const int nch = next_chunks(c, w.j);
+                if (atomicAdd(g.next_done + w.j, 1) == nch - 1) {
+                    // the last chunk: NEXT(j) is complete
+                    __threadfence();
+                    if (w.j & 1) publish_pair(c, g, w.j / 2);
+                    __threadfence();
+                    st_release(g.hdr + kPgNextComplete, w.j + 1);
+                }
+            }
+        } else {  // kDoRest
+            const int j = 2 * w.p;
+            GF2_TR(if (tid == 0 && j + 1 < kTraceMaxPanels)
+                       atomicMax(g_factor_trace + kTrRestStart * kTraceMaxPanels + j + 1, ~trace_clock());)
+            if (w.prepare) rest_prepare<C, 2, kFThreads>(c, j, w.tile, w.first != 0, rest_smem, ops);
+            if (w.rb < w.re) rest_pass<C, kFRestU, 2, kFThreads>(c, j, w.tile, w.rb, w.re, rest_smem, ops);
+            __syncthreads();
+            if (tid == 0) {
+                GF2_TR(if (j + 1 < kTraceMaxPanels) atomicMax(g_factor_trace + kTrRestEnd * kTraceMaxPanels + j + 1, trace_clock());)
+                __threadfence();
+                atomicAdd(g.tile_done + (int64_t)w.p * g.ntw + w.tile, w.chunk);
+                atomicAdd(g.pair_done + w.p, w.chunk);
+            }
+        }
+    }
+    GF2_OPS(add_ops(g_update_ops, kOpUpdates, ops.upd); add_ops(g_update_ops, C == 8 ? kOpLookups8 : kOpLookups4, ops.lk);
+            add_ops(g_update_ops, C == 8 ? kOpTable8 : kOpTable4, ops.tab);)
+}
+
+static_assert(rest_smem_bytes<8, 2>() + kNextSmemWords * 8 + (kFNextRows + kFThreads / 32 + 1) * 4 <= kFSmemBytes,
+              "worker shared memory");
+
+std::mutex g_factor_mutex;
+int g_factor_ready[64];  // per device: 0 unknown, 1 usable, -1 not (one CTA per SM does not fit)
+
+template <int C>
+cudaError_t factor_prepare(int dev)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_factor<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmemBytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor<C>, kFThreads, kFSmemBytes);
+    if (e != cudaSuccess) return e;
+    int coop = 0;
+    e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e != cudaSuccess) return e;
+    return (per_sm >= 1 && coop) ? cudaSuccess : cudaErrorNotSupported;
+}
+
+}  // namespace
+
+int64_t factor_progress_ints(int mu)
+{
+    const int64_t npairs = mu / 2, ntw = (mu + kTileWords - 1) / kTileWords;
+    return kPgHeader + 2 * (int64_t)mu + 6 * npairs + npairs * ntw;
+}
+
+const int32_t *factor_fail_word(const int32_t *progress) { return progress + kPgFail; }
+
+cudaError_t launch_factor(const DecompCtx &c0, int32_t *progress, cudaStream_t s)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lock(g_factor_mutex);
+        if (g_factor_ready[dev] == 0) {
+            e = factor_prepare<8>(dev);
+            if (e == cudaSuccess) e = factor_prepare<4>(dev);
+            g_factor_ready[dev] = e == cudaSuccess ? 1 : -1;
+            if (e != cudaSuccess && e != cudaErrorNotSupported) {
+                g_factor_ready[dev] = 0;
+                return e;
+            }
+        }
+        if (g_factor_ready[dev] < 0) return cudaErrorNotSupported;
+    }
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (sms < 2) return cudaErrorNotSupported;
+    DecompCtx c = c0;
+    c.fail = progress + kPgFail;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(sms);
+    cfg.blockDim = dim3(kFThreads);
+    cfg.dynamicSmemBytes = kFSmemBytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (c.tab_c == 4) return cudaLaunchKernelEx(&cfg, k_factor<4>, c, progress);
+    return cudaLaunchKernelEx(&cfg, k_factor<8>, c, progress);
+}
+
+#ifdef GF2_COUNT_OPS
+cudaError_t read_factor_ops(unsigned long long *acc, bool reset)
+{
+    unsigned long long h[kNumOps];
+    cudaError_t e = cudaMemcpyFromSymbol(h, g_update_ops, sizeof(h));
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < kNumOps; ++i) acc[i] += h[i];
+    if (reset) {
+        const unsigned long long z[kNumOps] = {};
+        e = cudaMemcpyToSymbol(g_update_ops, z, sizeof(z));
+    }
+    return e;
+}
+#endif
+
+#ifdef GF2_TRACE
+cudaError_t read_factor_trace(unsigned long long *out, bool reset)
+{
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_factor_trace, sizeof(g_factor_trace));
+    if (e == cudaSuccess && reset) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_factor_trace);
+        if (e == cudaSuccess) e = cudaMemset(p, 0, sizeof(g_factor_trace));
+    }
+    return e;
+}
+#endif
+
+}  // namespace gf2

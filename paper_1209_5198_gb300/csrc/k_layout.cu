@@ -110,9 +110,9 @@ __global__ void k_finish_E(const uint64_t *__restrict__ Eint, int64_t ldw,
 }
 
 __global__ void k_finish_scalars(const PanelInfo *__restrict__ last, int32_t *__restrict__ pivcols,
-                                 int32_t kmax, int64_t *__restrict__ rank_out)
+                                 int32_t kmax, int64_t *__restrict__ rank_out, const int32_t *fail)
 {
-    const int rank = last->R + last->r;
+    const int rank = (fail && *fail) ? -1 : last->R + last->r;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0 && rank_out) *rank_out = rank;
     if (t < kmax && t >= rank) pivcols[t] = -1;
@@ -163,7 +163,7 @@ cudaError_t launch_finish_scalars(const DecompCtx &c, int64_t *rank, cudaStream_
 {
     const int threads = 256;
     const int blocks = (c.kmax + threads - 1) / threads > 0 ? (c.kmax + threads - 1) / threads : 1;
-    k_finish_scalars<<<blocks, threads, 0, s>>>(c.info + (c.mu - 1), c.pivcols, c.kmax, rank);
+    k_finish_scalars<<<blocks, threads, 0, s>>>(c.info + (c.mu - 1), c.pivcols, c.kmax, rank, c.fail);
     return cudaGetLastError();
 }
 

@@ -47,6 +47,27 @@ __device__ __forceinline__ void bar_sync(int id, int nthreads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// Barrier of the panel's kPanelThreads threads (named barrier kBarPanel).
+// The panel step synchronises its own threads only, so that it also runs in
+// the first kPanelThreads threads of a larger CTA (the persistent
+// decomposition kernel, whose other warps of that CTA have left).
+constexpr int kBarPanel = 3;
+
+__device__ __forceinline__ void panel_sync() { bar_sync(kBarPanel, kPanelThreads); }
+
+// panel_sync that also returns whether any of the panel's threads passed p != 0
+__device__ __forceinline__ int panel_sync_or(int p)
+{
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred pin, pout;\n\tsetp.ne.s32 pin, %1, 0;\n\t"
+        "bar.red.or.pred pout, %2, %3, pin;\n\tselp.s32 %0, 1, 0, pout;\n\t}"
+        : "=r"(r)
+        : "r"(p), "n"(kBarPanel), "n"(kPanelThreads)
+        : "memory");
+    return r;
+}
+
 __device__ __forceinline__ uint64_t warp_or(uint64_t v)
 {
 #pragma unroll
@@ -146,7 +167,7 @@ __device__ __forceinline__ void build_reduction_tables(PanelShared &sh)
             if ((x >> b) & 1) acc ^= sh.pred[8 * g + b];
         sh.tab[e] = acc;
     }
-    __syncthreads();
+    panel_sync();
 }
 
 __device__ __forceinline__ uint64_t reduce_word(const PanelShared &sh, uint64_t v)
@@ -230,7 +251,7 @@ __device__ __noinline__ void scan_find(const DecompCtx &c, const uint64_t *Wj, c
                     hit = 1;
                 }
             }
-            if (__syncthreads_or(hit)) break;
+            if (panel_sync_or(hit)) break;
         }
         acc = warp_or(acc);
         if (lane == 0 && acc) atomicOr(&sh.orv, (unsigned long long)acc);
@@ -248,7 +269,7 @@ __device__ __noinline__ void scan_find(const DecompCtx &c, const uint64_t *Wj, c
         while (h < sh.zn && list_pos(c, L, h) < from) ++h;
         sh.zhead = h;
     }
-    __syncthreads();
+    panel_sync();
     bool found = false;
     {
         // (2 entries per thread between barriers: the qualifying row is
@@ -269,7 +290,7 @@ __device__ __noinline__ void scan_find(const DecompCtx &c, const uint64_t *Wj, c
                     }
                 }
             }
-            found = __syncthreads_or(hit);
+            found = panel_sync_or(hit);
         }
     }
     // the rows behind the list, appended in position order
@@ -289,13 +310,13 @@ __device__ __noinline__ void scan_find(const DecompCtx &c, const uint64_t *Wj, c
 #pragma unroll
         for (int u = 0; u < U; ++u) any |= v[u];
         int hit = 0;
-        if (__syncthreads_or(any != 0)) {
+        if (panel_sync_or(any != 0)) {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const bool nz = v[u] != 0;
                 const unsigned bal = __ballot_sync(kFull, nz);
                 if (lane == 0) sh.wcnt[warp] = __popc(bal);
-                __syncthreads();
+                panel_sync();
                 int off = sh.zn, total = 0;
 #pragma unroll
                 for (int w = 0; w < kPanelThreads / 32; ++w) {
@@ -310,12 +331,12 @@ __device__ __noinline__ void scan_find(const DecompCtx &c, const uint64_t *Wj, c
                         hit = 1;
                     }
                 }
-                __syncthreads();  // every thread has read sh.zn and the counts
+                panel_sync();  // every thread has read sh.zn and the counts
                 if (tid == 0) sh.zn += total;
             }
         }
         if (tid == 0) sh.zto = min(base + kPanelThreads * U, n);
-        found = __syncthreads_or(hit);
+        found = panel_sync_or(hit);
     }
     // no row qualifies: every nonzero row behind the window is now listed, so
     // their OR comes from the list (only this case needs the reduction
@@ -327,7 +348,7 @@ __device__ __noinline__ void scan_find(const DecompCtx &c, const uint64_t *Wj, c
         acc = warp_or(acc);
         if (lane == 0 && acc) atomicOr(&sh.orv, (unsigned long long)acc);
     }
-    __syncthreads();
+    panel_sync();
     if (tid == 0 && found) {
         sh.found = list_pos(c, L, sh.found_idx);
         sh.found_raw = list_raw(c, L, sh.found_idx);
@@ -499,7 +520,7 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
             sh.T[tid] = pp->Zp[tid];
             sh.TI[tid] = tid < rp ? Wj[(int64_t)pp->prow[tid] * kTileWords] : 0;
         }
-        __syncthreads();
+        panel_sync();
         for (int e = tid; e < 256; e += kPanelThreads) {
             const int g = e >> 4, x = e & 15;
             uint64_t a = 0, b = 0;
@@ -512,7 +533,7 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
             sh.zt[e] = a;
             sh.ct[e] = b;
         }
-        __syncthreads();
+        panel_sync();
     }
 
     if (warp != 0) {  // helpers: serve scan requests of warp 0

@@ -358,8 +358,13 @@ int plain_decompose(gf2_server *S, Entry *e, int lane)
     gf2_mat A{reinterpret_cast<uint64_t *>(S->arena.at(e->a_off)), e->n, e->m, e->n};
     gf2_mat L{e->L, e->n, k, e->n};
     gf2_mat E{e->E, k, e->m, k > 0 ? k : 1};
-    return gf2_decompose(&A, e->perm, e->piv, e->rank, &L, &E, GF2_NOCHECK, S->dec_ws[lane], S->dec_ws_bytes,
-                         S->dec_stream[lane]);
+    // separate launches: the engine overlaps up to four decompositions and
+    // its solve launches on the GPU, which a launch holding every SM would
+    // serialise
+    gf2_opts o{};
+    o.schedule = GF2_SCHEDULE_STREAMS;
+    return gf2_decompose_ex(&A, e->perm, e->piv, e->rank, &L, &E, GF2_NOCHECK, &o, S->dec_ws[lane], S->dec_ws_bytes,
+                            S->dec_stream[lane]);
 }
 
 void fail_entry(Entry *e, int status)
