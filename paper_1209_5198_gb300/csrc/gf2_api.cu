@@ -365,20 +365,20 @@ int enqueue_outputs(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat *E, c
     return GF2_OK;
 }
 
-// The persistent schedule: the counters cleared, one cooperative launch of
-// the whole factorization (csrc/k_factor.cu), then the outputs; all on s.
-// cudaErrorNotSupported (nothing enqueued): the device cannot hold it.
-cudaError_t enqueue_persistent(DecompCtx c, int32_t *progress, int64_t *rank, gf2_mat *L, gf2_mat *E, cudaStream_t s)
+// The panels from j_start (even) on in one cooperative persistent launch
+// (csrc/k_factor.cu) on s, after its progress words are set up.
+int enqueue_persistent(const DecompCtx &c, int32_t *progress, int j_start, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(progress, 0, (size_t)factor_progress_ints(c.mu) * 4, s);
-    if (e != cudaSuccess) return e;
-    e = launch(GF2_KCLASS_FACTOR, s, [&]() { return launch_factor(c, progress, s); });
-    if (e != cudaSuccess) return e;
-    c.fail = factor_fail_word(progress);
-    return enqueue_outputs(c, rank, L, E, s) == GF2_OK ? cudaSuccess : cudaErrorUnknown;
+    CK(launch_factor_init(progress, c.mu, j_start, s));
+    LAUNCH(GF2_KCLASS_FACTOR, launch_factor(c, progress, j_start, s));
+    return GF2_OK;
 }
 
-int enqueue_factorization(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat *E, SideResources *side)
+// The factorization: panels [0, jend) as separate launches on the library's
+// streams (below), then, when jend < mu, the panels from jend on in one
+// persistent launch (progress: its counters; jend even), then the outputs.
+int enqueue_factorization(DecompCtx c, int64_t *rank, gf2_mat *L, gf2_mat *E, SideResources *side, int jend,
+                          int32_t *progress)
 {
     cudaStream_t s = side->main, P = side->stream, N = side->next;
     const int mu = c.mu;
@@ -394,7 +394,7 @@ int enqueue_factorization(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat
     CK(cudaEventRecord(evFork, s));
     CK(cudaStreamWaitEvent(P, evFork, 0));
     CK(cudaStreamWaitEvent(N, evFork, 0));
-    for (int j = 0; j < mu; ++j) {
+    for (int j = 0; j < jend; ++j) {
         if (j >= 2) CK(cudaStreamWaitEvent(P, evNext[j - 2], 0));
         LAUNCH_ON(GF2_KCLASS_PANEL, P, launch_panel(c, j, P));
         CK(cudaEventRecord(evPanel[j], P));
@@ -446,6 +446,11 @@ int enqueue_factorization(const DecompCtx &c, int64_t *rank, gf2_mat *L, gf2_mat
     CK(cudaStreamWaitEvent(s, evJoinP, 0));
     CK(cudaEventRecord(evJoinN, N));
     CK(cudaStreamWaitEvent(s, evJoinN, 0));
+    if (jend < mu) {
+        const int st = enqueue_persistent(c, progress, jend, s);
+        if (st) return st;
+        c.fail = factor_fail_word(progress);
+    }
     return enqueue_outputs(c, rank, L, E, s);
 }
 
@@ -540,18 +545,23 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
     if (c.Lint) CK(cudaMemsetAsync(c.Lint, 0, (size_t)n * d.ldl * 8, s));
     CK(cudaMemsetAsync(c.nact, 0, (size_t)c.mu * sizeof(int32_t), s));  // the active-list counts
 
-    // By pairs of panels, from kPersistentFromRows rows on (or when asked):
-    // the whole factorization as one cooperative persistent launch on the
-    // caller's stream (csrc/k_factor.cu); a device that cannot hold one CTA
-    // per SM falls back to the separate launches below.
-    const bool persistent = c.pair && (o.schedule == GF2_SCHEDULE_PERSISTENT ||
-                                       (o.schedule == GF2_SCHEDULE_AUTO && n >= kPersistentFromRows));
-    if (persistent) {
-        const cudaError_t e = enqueue_persistent(c, reinterpret_cast<int32_t *>(base + d.oProg), rank, L, E, s);
-        if (e == cudaSuccess) return GF2_OK;
+    // Which panels run as separate launches ([0, jend)) and which in one
+    // persistent launch (csrc/k_factor.cu), by pairs of panels only:
+    // PERSISTENT all of them; AUTO, from kPersistentFromRows rows on, the
+    // second half -- the first half is bound by the trailing updates, which
+    // the separate launches run beside the look-ahead kernels on the same
+    // SMs; the second half is bound by the serial panel chain, which the
+    // persistent launch keeps on one SM without a launch between panels.
+    // A device that cannot hold one CTA per SM keeps the separate launches.
+    int jend = c.mu;
+    if (c.pair && (o.schedule == GF2_SCHEDULE_PERSISTENT ||
+                   (o.schedule == GF2_SCHEDULE_AUTO && n >= kPersistentFromRows))) {
+        const cudaError_t e = factor_available();
+        if (e == cudaSuccess) jend = o.schedule == GF2_SCHEDULE_PERSISTENT ? 0 : 2 * (c.mu / 4);
+        else if (e != cudaErrorNotSupported) return GF2_ERR_CUDA;
         cudaGetLastError();
-        if (e != cudaErrorNotSupported) return GF2_ERR_CUDA;
     }
+    int32_t *progress = reinterpret_cast<int32_t *>(base + d.oProg);
 
     // The factorization runs on the library's three streams of this device
     // (M: wide updates and outputs, P: the panel chain, N: the look-ahead
@@ -574,8 +584,9 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
     key.L = L ? L->w : nullptr; key.ldl = L ? L->ld : 0;
     key.E = E ? E->w : nullptr; key.lde = E ? E->ld : 0;
     key.ws = ws;
-    if (g_timing.load() || !g_use_graphs) {
-        st = enqueue_factorization(c, rank, L, E, side);
+    // (a persistent launch is not captured into the graph)
+    if (g_timing.load() || !g_use_graphs || jend < c.mu) {
+        st = enqueue_factorization(c, rank, L, E, side, jend, progress);
         if (st) return st;
     } else {
         bool replayed = false, seen = false;
@@ -599,11 +610,11 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
             // first call with this shape and these buffers: enqueue directly
             // (a capture and instantiation cost more than one run; a repeat
             // call is captured and every later one replays the graph)
-            st = enqueue_factorization(c, rank, L, E, side);
+            st = enqueue_factorization(c, rank, L, E, side, jend, progress);
             if (st) return st;
         } else {
             if (cudaStreamBeginCapture(side->main, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GF2_ERR_CUDA;
-            st = enqueue_factorization(c, rank, L, E, side);
+            st = enqueue_factorization(c, rank, L, E, side, jend, progress);
             cudaGraph_t graph = nullptr;
             const cudaError_t ec = cudaStreamEndCapture(side->main, &graph);
             if (st || ec != cudaSuccess) {

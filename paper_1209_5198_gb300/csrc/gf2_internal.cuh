@@ -174,13 +174,17 @@ cudaError_t launch_colblocks_from_rowmajor(const uint64_t *R, int64_t ldr, const
 cudaError_t launch_finish_E(const DecompCtx &c, uint64_t *E, int64_t lde, cudaStream_t s);
 cudaError_t launch_finish_scalars(const DecompCtx &c, int64_t *rank, cudaStream_t s);
 cudaError_t launch_panel(const DecompCtx &c, int j, cudaStream_t s);
-// The whole factorization (pairs of panels) in one cooperative persistent
-// launch (csrc/k_factor.cu): `progress` is factor_progress_ints(mu) int32 of
-// zeroed device memory; it receives the run's failure word (c.fail points
-// into it).  Returns cudaErrorNotSupported when the kernel cannot have one
-// CTA resident on every SM.
+// The factorization (pairs of panels) from panel j_start (even) on in one
+// cooperative persistent launch (csrc/k_factor.cu): the panels before it,
+// their look-aheads and pair updates done; `progress` is
+// factor_progress_ints(mu) int32 of device memory, set up by
+// launch_factor_init on the same stream; it receives the run's failure word
+// (c.fail points into it).  Returns cudaErrorNotSupported when the kernel
+// cannot have one CTA resident on every SM.
 int64_t factor_progress_ints(int mu);
-cudaError_t launch_factor(const DecompCtx &c, int32_t *progress, cudaStream_t s);
+cudaError_t launch_factor_init(int32_t *progress, int mu, int j_start, cudaStream_t s);
+cudaError_t launch_factor(const DecompCtx &c, int32_t *progress, int j_start, cudaStream_t s);
+cudaError_t factor_available();  // cudaErrorNotSupported: the device cannot hold one CTA per SM
 const int32_t *factor_fail_word(const int32_t *progress);
 cudaError_t launch_next(const DecompCtx &c, int j, cudaStream_t s);
 // the wide update of panel j (np = 1) or of the pair j, j+1 (np = 2)

@@ -21,9 +21,11 @@
 //             pair update that read Y and the active list of panel j-8 (the
 //             ring of eight buffers) has finished.
 //   REST(p)   the update of the pair (2p, 2p+1) (rest_prepare / rest_pass),
-//             after NEXT(2p+1); in slots of (tile, range of 256-entry
-//             chunks); a slot on tile T starts after the previous pair that
-//             updates T has finished T (two updates of one word are ordered).
+//             after NEXT(2p+1) and after the previous pair's update has
+//             finished (two updates of one word are ordered); in slots of
+//             (tile, range of 256-entry chunks), each owned by one worker.
+//             The first tile of the pair, which the next look-aheads wait
+//             for, is split over every worker and claimed first.
 // The look-ahead is the critical path: a worker looks for a look-ahead
 // chunk before each batch of update chunks (kFBatch of them, a few
 // microseconds), and its update tables live in shared memory apart from the
@@ -46,9 +48,10 @@ namespace gf2 {
 namespace {
 
 constexpr int kFThreads = 512;
-constexpr int kFNextRows = 512;           // list entries per look-ahead chunk (one per thread)
+constexpr int kFNextRows = 512;           // list entries per look-ahead round (one per thread)
+constexpr int kFNextRounds = 1;           // rounds per look-ahead chunk (one table setup per chunk)
 constexpr int kFRestU = 4;                // row groups of 16 rows per warp and pass iteration
-constexpr int kFBatch = 8;                // update chunks between looks at the look-ahead queue
+constexpr int kFBatch = 16;               // update chunks between looks at the look-ahead queue
 constexpr int kFSmemBytes = 200 * 1024;   // dynamic shared memory of every CTA (one per SM)
 constexpr long long kFSpinLimit = 1ll << 22;  // polls of one wait (~64-500 ns each) before it gives up
 
@@ -123,17 +126,32 @@ __device__ __forceinline__ bool wait_geq(const int32_t *p, int v, const Progress
 __device__ __forceinline__ int next_chunks(const DecompCtx &c, int j)
 {
     const int cnt = j == 0 ? c.n : ld_relaxed(c.nact + j - 1);
-    return max(1, (cnt + kFNextRows - 1) / kFNextRows);
+    return max(1, (cnt + kFNextRows * kFNextRounds - 1) / (kFNextRows * kFNextRounds));
 }
 
-// Slots of pair p: each of its tiles in `parts` ranges of chunks, about two
-// slots per worker while the chunks last.
-__device__ __forceinline__ int pair_parts(const Progress &g, int p, int workers)
+// Slots of pair p: ranges of its items, (tile, 256-entry chunk) in
+// tile-major order.  Its first tile (tile_first), which the next
+// look-aheads wait for, is split into `head` slots claimed first; the other
+// tiles' items are split into one equal range per worker (about as the
+// separate update launch splits them over its CTAs), so that a worker builds
+// its tables once or twice per pair.
+constexpr int kFHeadSlots = 16;
+
+struct PairSlots {
+    int head, body, nslots;
+    int64_t items;  // tiles x chunks
+};
+
+__device__ __forceinline__ PairSlots pair_slots(const Progress &g, int p, int workers)
 {
+    PairSlots ps{0, 0, 0, 0};
     const int nt = ld_relaxed(g.pair_nt + p), nch = ld_relaxed(g.pair_nch + p);
-    if (nt <= 0 || nch <= 0) return 0;
-    const int want = (2 * workers + nt - 1) / nt;
-    return max(1, min(want, nch));
+    if (nt <= 0 || nch <= 0) return ps;
+    ps.items = (int64_t)nt * nch;
+    ps.head = min(nch, kFHeadSlots);
+    ps.body = nt > 1 ? workers : 0;
+    ps.nslots = ps.head + ps.body;
+    return ps;
 }
 
 // Thread 0, after NEXT(2p+1) finished: the shape of pair p's update and the
@@ -152,17 +170,25 @@ __device__ __forceinline__ void publish_pair(const DecompCtx &c, const Progress 
     g.pair_prev[p] = p == 0 ? -1 : (ld_relaxed(g.pair_nch + p - 1) > 0 ? p - 1 : ld_relaxed(g.pair_prev + p - 1));
 }
 
-// Thread 0: may NEXT(j) start?  (Never waits.)
-__device__ __forceinline__ bool next_ready(const DecompCtx &c, const Progress &g, int j)
+// Thread 0: may NEXT(j) start?  (Never waits.)  When not, *wp / *wv name
+// the first unmet condition, "*wp >= *wv": the caller polls that one word
+// instead of testing everything again.
+__device__ __forceinline__ bool next_ready(const DecompCtx &c, const Progress &g, int j, const int32_t **wp, int *wv)
 {
-    if (ld_acquire(g.hdr + kPgPanelDone) <= j) return false;
-    if (ld_acquire(g.hdr + kPgNextComplete) < j) return false;
+    *wp = g.hdr + kPgPanelDone;
+    *wv = j + 1;
+    if (ld_acquire(*wp) < *wv) return false;
+    *wp = g.hdr + kPgNextComplete;
+    *wv = j;
+    if (ld_acquire(*wp) < *wv) return false;
     // the ring of Y buffers and active lists: the update that read panel
     // j-8's has finished
     if (j >= 8) {
         const int q = (j - 8) / 2;
         const int nch = ld_relaxed(g.pair_nch + q);
-        if (nch > 0 && ld_acquire(g.pair_done + q) < nch * ld_relaxed(g.pair_nt + q)) return false;
+        *wp = g.pair_done + q;
+        *wv = nch * ld_relaxed(g.pair_nt + q);
+        if (nch > 0 && ld_acquire(*wp) < *wv) return false;
     }
     // the tile holding word j+2: the last pair update that covers it (pairs
     // up to (j-2, j-1)) has finished it
@@ -171,8 +197,13 @@ __device__ __forceinline__ bool next_ready(const DecompCtx &c, const Progress &g
         int q = (j - 2) / 2;
         if (ld_relaxed(g.pair_nch + q) == 0) q = ld_relaxed(g.pair_prev + q);
         while (q >= 0 && ld_relaxed(g.pair_tf + q) > T) q = ld_relaxed(g.pair_prev + q);
-        if (q >= 0 && ld_acquire(g.tile_done + (int64_t)q * g.ntw + T) < ld_relaxed(g.pair_nch + q)) return false;
+        if (q >= 0) {
+            *wp = g.tile_done + (int64_t)q * g.ntw + T;
+            *wv = ld_relaxed(g.pair_nch + q);
+            if (ld_acquire(*wp) < *wv) return false;
+        }
     }
+    *wp = nullptr;
     return true;
 }
 
@@ -186,8 +217,10 @@ struct WorkerCmd {
     int kind, j, chunk, p, tile, rb, re, prepare, first;
 };
 
+// Panels j_start.. (even j_start): the earlier panels, their look-aheads
+// and the updates of their pairs are done (launch_factor_init marks them).
 template <int C>
-__global__ void __launch_bounds__(kFThreads, 1) k_factor(DecompCtx c, int32_t *progress)
+__global__ void __launch_bounds__(kFThreads, 1) k_factor(DecompCtx c, int32_t *progress, int j_start)
 {
     extern __shared__ __align__(16) unsigned char fsmem[];
     const Progress g = progress_at(progress, c.mu);
@@ -202,7 +235,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_factor(DecompCtx c, int32_t *p
         constexpr int kListCap = (kFSmemBytes - kShBytes) / 12 / 8 * 8;
         uint64_t *zs = reinterpret_cast<uint64_t *>(fsmem + kShBytes);
         __shared__ int quit;
-        for (int j = 0; j < c.mu; ++j) {
+        for (int j = j_start; j < c.mu; ++j) {
             if (tid == 0) {
                 quit = (j >= 2 && !wait_geq(g.hdr + kPgNextComplete, j - 1, g)) ? 1 : 0;
                 __threadfence();
@@ -227,17 +260,31 @@ __global__ void __launch_bounds__(kFThreads, 1) k_factor(DecompCtx c, int32_t *p
     // -------------------------------------------------------------- workers
     // shared memory: the update's tables and staged rows, then the
     // look-ahead's (apart, so that a look-ahead chunk leaves the tables of
-    // the slot in progress intact)
+    // the segment in progress intact)
     uint64_t *rest_smem = reinterpret_cast<uint64_t *>(fsmem);
     uint64_t *next_smem = reinterpret_cast<uint64_t *>(fsmem + rest_smem_bytes<C, 2>());
     int *keep_row = reinterpret_cast<int *>(next_smem + kNextSmemWords);
     int *keep_warp = keep_row + kFNextRows;
     __shared__ WorkerCmd cmd;
+    __shared__ int kw[kFThreads / 32];  // per warp: the next iteration of the segment in progress
+    __shared__ int stop;                // set by thread 0: leave the update pass (look-ahead work)
     const int workers = gridDim.x - 1;
-    // thread 0's state: the look-ahead cursor, the pair cursor, the slot
-    int jn = 0, pr = 0;
-    int sp = -1, stile = 0, scur = 0, send = 0, sfirst = 0, sprep = 0;
+    const int wid = blockIdx.x - 1;
+    // every worker takes look-ahead chunks; the last kFHeadSlots also take
+    // the head slots of every pair
+    const int head_slot = wid - (workers - kFHeadSlots);  // >= 0: this worker's head slot
+    // thread 0's state: the look-ahead cursor; the pair cursor, its phase
+    // (0: head slot, 1: body slot) and the slot in progress (items [si, se),
+    // tile-major, of pair sp; sprep: the tables of item si's tile are not
+    // built yet)
+    int jn = j_start, pr = j_start / 2, phase = head_slot >= 0 ? 0 : 1;
+    int sp = -1, sprep = 0, s_tf = 0, s_nch = 1, s_nact = 0;
+    int64_t si = 0, se = 0, seg_end = 0;
     long long idle = 0;
+    // the condition NEXT(jn) waits for ("*watch >= watch_val"; null: test
+    // everything) and its value, read before the previous work ran
+    const int32_t *watch = nullptr;
+    int watch_val = 0, watched = 0;
     for (;;) {
         if (tid == 0) {
             WorkerCmd w{};
@@ -245,8 +292,10 @@ __global__ void __launch_bounds__(kFThreads, 1) k_factor(DecompCtx c, int32_t *p
             if (ld_relaxed(g.hdr + kPgFail)) {
                 w.kind = kDoQuit;
             } else {
-                // 1. a look-ahead chunk
-                while (jn < c.mu && next_ready(c, g, jn)) {
+                // 1. a look-ahead chunk (only once the condition it last
+                // waited for holds)
+                // (a worker without a slot in progress tests everything)
+                while (jn < c.mu && (!watch || watched >= watch_val || sp < 0) && next_ready(c, g, jn, &watch, &watch_val)) {
                     const int nch = next_chunks(c, jn);
                     if (ld_relaxed(g.next_claim + jn) >= nch) {
                         ++jn;
@@ -261,54 +310,67 @@ __global__ void __launch_bounds__(kFThreads, 1) k_factor(DecompCtx c, int32_t *p
                     }
                     ++jn;
                 }
-                // 2. update chunks: the slot in progress, or a new slot
-                if (w.kind == kDoIdle && sp < 0) {
-                    while (pr < g.npairs && ld_acquire(g.hdr + kPgNextComplete) >= 2 * pr + 2) {
-                        const int parts = pair_parts(g, pr, workers);
-                        const int nslots = parts * ld_relaxed(g.pair_nt + pr);
-                        if (ld_relaxed(g.pair_claim + pr) >= nslots) {
-                            ++pr;
-                            continue;
-                        }
-                        const int s = atomicAdd(g.pair_claim + pr, 1);
-                        if (s >= nslots) {
-                            ++pr;
-                            continue;
-                        }
-                        const int nch = ld_relaxed(g.pair_nch + pr), part = s % parts;
-                        sp = pr;
-                        stile = ld_relaxed(g.pair_tf + pr) + s / parts;
-                        scur = (int)((int64_t)part * nch / parts);
-                        send = (int)((int64_t)(part + 1) * nch / parts);
-                        sfirst = part == 0;
+                // 2. this worker's slots of the pairs in order: its head slot
+                // (if it has one), then its range of the other tiles, once the
+                // pair's look-ahead is done
+                while (w.kind == kDoIdle && sp < 0 && pr < g.npairs &&
+                       ld_acquire(g.hdr + kPgNextComplete) >= 2 * pr + 2) {
+                    const int p_this = pr;
+                    const PairSlots ps = pair_slots(g, p_this, workers);
+                    const int64_t nch = ld_relaxed(g.pair_nch + p_this);
+                    si = se = 0;
+                    if (ps.nslots > 0 && phase == 0 && head_slot < ps.head) {
+                        si = nch * head_slot / ps.head;
+                        se = nch * (head_slot + 1) / ps.head;
+                    } else if (ps.nslots > 0 && phase == 1 && ps.body > 0) {
+                        si = nch + (ps.items - nch) * wid / ps.body;
+                        se = nch + (ps.items - nch) * (wid + 1) / ps.body;
+                    }
+                    // the next slot of this worker: the body slot of this
+                    // pair after its head slot, else the next pair
+                    if (phase == 0) {
+                        phase = 1;
+                    } else {
+                        phase = head_slot >= 0 ? 0 : 1;
+                        ++pr;
+                    }
+                    if (si < se) {
+                        sp = p_this;
+                        s_tf = ld_relaxed(g.pair_tf + sp);
+                        s_nch = (int)nch;
+                        s_nact = ld_relaxed(c.nact + 2 * sp + 1);
                         sprep = 1;
-                        // two updates of one word are ordered: the previous
-                        // pair with an update has finished this tile
-                        const int q = ld_relaxed(g.pair_prev + pr);
-                        if (q >= 0 && !wait_geq(g.tile_done + (int64_t)q * g.ntw + stile, ld_relaxed(g.pair_nch + q), g))
-                            w.kind = kDoQuit;
-                        break;
                     }
                 }
                 if (w.kind == kDoIdle && sp >= 0) {
-                    w.kind = kDoRest;
-                    w.p = sp;
-                    w.tile = stile;
-                    w.prepare = sprep;
-                    w.first = sfirst;
-                    const int nact = ld_relaxed(c.nact + 2 * sp + 1);
-                    const int e = min(send, scur + kFBatch);
-                    w.rb = scur * kRestChunk;
-                    w.re = min(nact, e * kRestChunk);
-                    w.chunk = e - scur;  // chunks of this batch
-                    sprep = 0;
-                    scur = e;
-                    if (scur >= send) sp = -1;
+                    // the rest of item si's tile in this slot; a new tile
+                    // first waits until the previous pair with an update has
+                    // finished it (two updates of one word are ordered)
+                    const int64_t t = si / s_nch, c0 = si % s_nch;
+                    seg_end = min(se, (t + 1) * s_nch);
+                    const int tile = s_tf + (int)t;
+                    const int q = sprep ? ld_relaxed(g.pair_prev + sp) : -1;
+                    if (q >= 0 && !wait_geq(g.tile_done + (int64_t)q * g.ntw + tile, ld_relaxed(g.pair_nch + q), g)) {
+                        w.kind = kDoQuit;
+                    } else {
+                        w.kind = kDoRest;
+                        w.p = sp;
+                        w.tile = tile;
+                        w.prepare = sprep;
+                        w.first = c0 == 0;
+                        w.rb = (int)(c0 * kRestChunk);
+                        w.re = min(s_nact, (int)(((seg_end - 1) % s_nch + 1) * kRestChunk));
+                        w.chunk = (int)(seg_end - si);  // chunks of this segment
+                    }
                 }
                 if (w.kind == kDoIdle && jn >= c.mu && pr >= g.npairs && sp < 0) w.kind = kDoQuit;
             }
             if (w.kind != kDoIdle) __threadfence();
             cmd = w;
+            stop = 0;
+            // the watched word, loaded now and used at the next decision:
+            // its latency overlaps the work of this one
+            if (watch) watched = ld_relaxed(watch);
         }
         __syncthreads();
         const WorkerCmd w = cmd;
@@ -325,7 +387,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_factor(DecompCtx c, int32_t *p
         if (w.kind == kDoNext) {
             GF2_TR(if (tid == 0 && w.j < kTraceMaxPanels)
                        atomicMax(g_factor_trace + kTrNextStart * kTraceMaxPanels + w.j, ~trace_clock());)
-            next_body<kFThreads, kFNextRows>(c, w.j, w.chunk, next_smem, keep_row, keep_warp);
+            next_body<kFThreads, kFNextRows, kFNextRounds>(c, w.j, w.chunk, next_smem, keep_row, keep_warp);
             __syncthreads();
             if (tid == 0) {
                 GF2_TR(if (w.j < kTraceMaxPanels) atomicMax(g_factor_trace + kTrNextEnd * kTraceMaxPanels + w.j, trace_clock());)
@@ -343,14 +405,28 @@ __global__ void __launch_bounds__(kFThreads, 1) k_factor(DecompCtx c, int32_t *p
             const int j = 2 * w.p;
             GF2_TR(if (tid == 0 && j + 1 < kTraceMaxPanels)
                        atomicMax(g_factor_trace + kTrRestStart * kTraceMaxPanels + j + 1, ~trace_clock());)
-            if (w.prepare) rest_prepare<C, 2, kFThreads>(c, j, w.tile, w.first != 0, rest_smem, ops);
-            if (w.rb < w.re) rest_pass<C, kFRestU, 2, kFThreads>(c, j, w.tile, w.rb, w.re, rest_smem, ops);
-            __syncthreads();
+            if (w.prepare) {
+                rest_prepare<C, 2, kFThreads>(c, j, w.tile, w.first != 0, rest_smem, ops);
+                if (tid < kFThreads / 32) kw[tid] = 0;
+                __syncthreads();
+            }
+            // (thread 0 of a look-ahead worker polls the word its look-ahead
+            // waits for and stops the pass when it changes)
+            const int done = w.rb < w.re ? rest_pass_from<C, kFRestU, 2, kFThreads>(c, j, w.tile, w.rb, w.re, rest_smem,
+                                                                                     ops, kw, &stop, watch, watch_val)
+                                         : 1;
             if (tid == 0) {
                 GF2_TR(if (j + 1 < kTraceMaxPanels) atomicMax(g_factor_trace + kTrRestEnd * kTraceMaxPanels + j + 1, trace_clock());)
-                __threadfence();
-                atomicAdd(g.tile_done + (int64_t)w.p * g.ntw + w.tile, w.chunk);
-                atomicAdd(g.pair_done + w.p, w.chunk);
+                if (done) {
+                    __threadfence();
+                    atomicAdd(g.tile_done + (int64_t)w.p * g.ntw + w.tile, w.chunk);
+                    atomicAdd(g.pair_done + w.p, w.chunk);
+                    si = seg_end;
+                    sprep = 1;
+                    if (si >= se) sp = -1;
+                } else {
+                    sprep = 0;  // stopped: the tables and kw stay for the resumption
+                }
             }
         }
     }
@@ -378,7 +454,24 @@ cudaError_t factor_prepare(int dev)
     return (per_sm >= 1 && coop) ? cudaSuccess : cudaErrorNotSupported;
 }
 
+// The progress words before a run from panel j_start: all zero (the pairs
+// before j_start / 2 read as having no update, which is complete), then
+// j_start panels and look-aheads done.
+__global__ void k_factor_init(int32_t *progress, int64_t ints, int j_start)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ints; i += (int64_t)gridDim.x * blockDim.x)
+        progress[i] = i == kPgPanelDone || i == kPgNextComplete ? j_start : 0;
+}
+
 }  // namespace
+
+cudaError_t launch_factor_init(int32_t *progress, int mu, int j_start, cudaStream_t s)
+{
+    const int64_t ints = factor_progress_ints(mu);
+    const int blocks = (int)((ints + 255) / 256 < 1024 ? (ints + 255) / 256 : 1024);
+    k_factor_init<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(progress, ints, j_start);
+    return cudaGetLastError();
+}
 
 int64_t factor_progress_ints(int mu)
 {
@@ -388,7 +481,7 @@ int64_t factor_progress_ints(int mu)
 
 const int32_t *factor_fail_word(const int32_t *progress) { return progress + kPgFail; }
 
-cudaError_t launch_factor(const DecompCtx &c0, int32_t *progress, cudaStream_t s)
+cudaError_t factor_available()
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -410,6 +503,19 @@ cudaError_t launch_factor(const DecompCtx &c0, int32_t *progress, cudaStream_t s
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    return sms < 2 ? cudaErrorNotSupported : cudaSuccess;
+}
+
+cudaError_t launch_factor(const DecompCtx &c0, int32_t *progress, int j_start, cudaStream_t s)
+{
+    cudaError_t e = factor_available();
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
     if (sms < 2) return cudaErrorNotSupported;
     DecompCtx c = c0;
     c.fail = progress + kPgFail;
@@ -423,8 +529,8 @@ cudaError_t launch_factor(const DecompCtx &c0, int32_t *progress, cudaStream_t s
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (c.tab_c == 4) return cudaLaunchKernelEx(&cfg, k_factor<4>, c, progress);
-    return cudaLaunchKernelEx(&cfg, k_factor<8>, c, progress);
+    if (c.tab_c == 4) return cudaLaunchKernelEx(&cfg, k_factor<4>, c, progress, j_start);
+    return cudaLaunchKernelEx(&cfg, k_factor<8>, c, progress, j_start);
 }
 
 #ifdef GF2_COUNT_OPS

@@ -40,8 +40,10 @@ constexpr int kNextSmemWords = kNextTiles * (Tabs<kNextC>::Words + 64 * kTileWor
 __device__ unsigned long long g_update_ops[kNumOps];  // the op-counting build's counters (per unit)
 #endif
 
+// One chunk of ROUNDS x ROWS list entries: the tables once, then ROUNDS
+// rounds of ROWS entries (one per thread).
 // smem: kNextSmemWords words; keep_row: ROWS ints; keep_warp: THREADS / 32 + 1 ints.
-template <int THREADS, int ROWS>
+template <int THREADS, int ROWS, int ROUNDS = 1>
 __device__ __forceinline__ void next_body(const DecompCtx &c, int j, int chunk, uint64_t *smem, int *keep_row,
                                           int *keep_warp)
 {
@@ -70,12 +72,16 @@ __device__ __forceinline__ void next_body(const DecompCtx &c, int j, int chunk, 
     // panel j (every storage row for j = 0)
     const int cnt = j == 0 ? c.n : c.nact[j - 1];
     const int32_t *lst = j == 0 ? nullptr : c.act + (int64_t)((j - 1) % kRing) * c.n;
-    const int rb = chunk * ROWS, re = min(cnt, rb + ROWS);
-    const bool rows_here = rb < re;
-    if (!rows_here && chunk != 0) return;
+    const int cbase = chunk * ROUNDS * ROWS;
+    if (cbase >= cnt && chunk != 0) return;
     const uint64_t *Fj = c.F + (int64_t)(j & 1) * c.n;
     uint64_t *Fn = c.F + (int64_t)((j + 1) & 1) * c.n;
     constexpr int U = ROWS / (kRowsPerWarp * (THREADS / 32));  // row groups per warp
+    const int ng = tables_used<kNextC>(r);
+    GF2_OPS(unsigned long long n_upd = 0, n_y = 0, n_lk = 0, n_tab = 0;)
+    for (int round = 0; round < ROUNDS; ++round) {
+    const int rb = cbase + round * ROWS, re = min(cnt, rb + ROWS);
+    if (round > 0 && rb >= re) break;
 
     // 1. every load of this thread's rows, issued before anything waits
     int rows[U];
@@ -99,8 +105,9 @@ __device__ __forceinline__ void next_body(const DecompCtx &c, int j, int chunk, 
         w1[u] = (in && has_f && wp == 0) ? c.W[widx(c, rr, j + 1)] : 0;
         a[u] = (in && live_hi) ? *reinterpret_cast<const ulonglong2 *>(c.W + widx(c, rr, col)) : make_ulonglong2(0, 0);
     }
-    // 2. tables of (Zp, Comp) for y and lambda, of word j+1 of the pivot
-    // rows, and of C for the tiles
+    // 2. (once) tables of (Zp, Comp) for y and lambda, of word j+1 of the
+    // pivot rows, and of C for the tiles
+    if (round == 0) {
     if (r > 0) {
         if (tid < 256) {  // 16 tables of 16 entries
         const int g = tid >> 4, x = tid & 15;
@@ -124,13 +131,15 @@ __device__ __forceinline__ void next_body(const DecompCtx &c, int j, int chunk, 
     if (r > 0)
         for (int tt = 0; tt < nt; ++tt)
             build_tables<kNextC, THREADS>(tab + tt * Tabs<kNextC>::Words, crow + tt * 64 * kTileWords);
-    GF2_OPS(unsigned long long n_upd = 0, n_y = 0, n_lk = 0, n_tab = 0;
-            if (tid == 0 && r > 0) {
+    GF2_OPS(if (tid == 0 && r > 0) {
                 constexpr int E4 = Tabs<kNextC>::X - 1;
                 n_tab += has_f ? 16 * E4 : 0;  // the tables of word j+1 (c1)
                 for (int tt = 0; tt < nt; ++tt)
                     n_tab += (unsigned long long)Tabs<kNextC>::K * E4 * live_words(q0 + tt * kTileWords, c.mu);
             })
+    } else {
+        __syncthreads();  // this round's keep_row entries are written
+    }
     // the rows that stay active, appended to the list of panel j in list order
     const int kept_row = keep_row[tid];
     const unsigned kept_mask = __ballot_sync(0xffffffffu, kept_row >= 0);
@@ -154,7 +163,6 @@ __device__ __forceinline__ void next_body(const DecompCtx &c, int j, int chunk, 
     // 3. compute and store
     const ulonglong2 *zc2 = reinterpret_cast<const ulonglong2 *>(zc);
     const ulonglong2 *tab2 = reinterpret_cast<const ulonglong2 *>(tab);
-    const int ng = tables_used<kNextC>(r);
     uint64_t *Ynext = c.Y + (int64_t)(j % kRing) * c.n;
     uint64_t yv[U];
 #pragma unroll
@@ -217,6 +225,7 @@ __device__ __forceinline__ void next_body(const DecompCtx &c, int j, int chunk, 
                     n_lk += (unsigned long long)ng * lw;)
         }
     }
+    }  // rounds
     GF2_OPS(add_ops(g_update_ops, kOpUpdates, n_upd); add_ops(g_update_ops, kOpYRows, n_y);
             add_ops(g_update_ops, kOpLookups4, n_lk); add_ops(g_update_ops, kOpTable4, n_tab);)
 
@@ -414,6 +423,115 @@ __device__ __forceinline__ void rest_pass(const DecompCtx &c, int j, int tile, i
                     if (NP == 2 && y1[u]) { ops.upd += lw; ops.lk += (unsigned long long)ng1 * lw; }
                 })
     }
+}
+
+// rest_pass that can stop between iterations and resume: warp w starts at
+// its iteration kw[w] (iterations of STEP list entries from rb) and, before
+// each iteration, leaves if *stop is set.  Thread 0 sets *stop itself once
+// the word it polls here reaches poll_val (poll: the condition its caller
+// waits for; null: never).  On return kw[w] = the first iteration warp w
+// has not done; the result is 1 when every warp has finished [rb, re).
+template <int C, int U, int NP, int THREADS>
+__device__ __forceinline__ int rest_pass_from(const DecompCtx &c, int j, int tile, int rb, int re,
+                                              const uint64_t *smem, UpdOps &ops, int *kw, volatile int *stop,
+                                              const int32_t *poll, int poll_val)
+{
+    constexpr int K = Tabs<C>::K;
+    const PanelInfo *pi0 = c.info + j;
+    const PanelInfo *pi1 = c.info + j + NP - 1;
+    const int r0 = pi0->r, r1 = NP == 2 ? pi1->r : 0;
+    const int ng0 = tables_used<C>(r0), ng1 = NP == 2 ? tables_used<C>(r1) : 0;
+    const int jl = j + NP - 1;
+    const int32_t *act = c.act + (int64_t)(jl % kRing) * c.n;
+    const uint64_t *Y0 = c.Y + (int64_t)(j % kRing) * c.n;
+    const uint64_t *Y1 = c.Y + (int64_t)((j + 1) % kRing) * c.n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int rs = lane / kLanesPerRow, wp = lane % kLanesPerRow, swp = rs & 3;
+    constexpr int NW = THREADS / 32;
+    const ulonglong2 *tab2 = reinterpret_cast<const ulonglong2 *>(smem);
+    const int q0 = tile * kTileWords;
+    (void)ops;
+    (void)q0;
+    (void)K;
+    uint64_t *Wt = c.W + (int64_t)tile * c.tstride + 2 * wp;
+    constexpr int STEP = kRowsPerWarp * U * NW;
+    int k = kw[warp];
+    int base = rb + warp * kRowsPerWarp * U + k * STEP;
+    uint64_t yn0[U], yn1[U];
+    int rown[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int e = base + u * kRowsPerWarp + rs;
+        rown[u] = e < re ? act[e] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        yn0[u] = rown[u] >= 0 ? Y0[rown[u]] : 0;
+        yn1[u] = (NP == 2 && rown[u] >= 0) ? Y1[rown[u]] : 0;
+    }
+    int polled = -1;  // thread 0: the polled word, read one iteration ahead
+    for (; base < re; base += STEP, ++k) {
+        if (tid == 0 && poll) {
+            if (polled >= poll_val) *stop = 1;
+            int v;
+            asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(poll) : "memory");
+            polled = v;
+        }
+        if (__shfl_sync(0xffffffffu, lane == 0 ? *stop : 0, 0)) break;
+        uint64_t y0[U], y1[U];
+        int row[U];
+        ulonglong2 a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            y0[u] = yn0[u];
+            y1[u] = yn1[u];
+            row[u] = rown[u];
+            const int e = base + STEP + u * kRowsPerWarp + rs;
+            rown[u] = e < re ? act[e] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            yn0[u] = rown[u] >= 0 ? Y0[rown[u]] : 0;
+            yn1[u] = (NP == 2 && rown[u] >= 0) ? Y1[rown[u]] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            a[u] = make_ulonglong2(0, 0);
+            if (y0[u] | y1[u]) a[u] = *reinterpret_cast<const ulonglong2 *>(Wt + (int64_t)row[u] * kTileWords);
+        }
+        for (int g = 0; g < ng0; ++g) {
+            const int gg = g ^ swp;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int x = (int)((y0[u] >> (C * gg)) & (Tabs<C>::X - 1));
+                const ulonglong2 t = tab2[tab_entry<C>(gg, x) * (kTileWords / 2) + wp];
+                a[u].x ^= t.x;
+                a[u].y ^= t.y;
+            }
+        }
+        if (NP == 2) {
+            for (int g = 0; g < ng1; ++g) {
+                const int gg = g ^ swp;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int x = (int)((y1[u] >> (C * gg)) & (Tabs<C>::X - 1));
+                    const ulonglong2 t = tab2[tab_entry<C>(K + gg, x) * (kTileWords / 2) + wp];
+                    a[u].x ^= t.x;
+                    a[u].y ^= t.y;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (y0[u] | y1[u]) *reinterpret_cast<ulonglong2 *>(Wt + (int64_t)row[u] * kTileWords) = a[u];
+        GF2_OPS(const int lw = (q0 + 2 * wp < c.mu) + (q0 + 2 * wp + 1 < c.mu);
+                for (int u = 0; u < U; ++u) {
+                    if (y0[u]) { ops.upd += lw; ops.lk += (unsigned long long)ng0 * lw; }
+                    if (NP == 2 && y1[u]) { ops.upd += lw; ops.lk += (unsigned long long)ng1 * lw; }
+                })
+    }
+    if (lane == 0) kw[warp] = k;
+    return __syncthreads_and(base >= re);
 }
 
 }  // namespace

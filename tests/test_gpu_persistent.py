@@ -108,3 +108,28 @@ def test_auto_picks_the_persistent_schedule_from_4096_rows():
     finally:
         gf2.timing(False)
     assert big == 1 and small == 0
+
+
+@pytest.mark.parametrize("name", ["tall", "square", "rank", "sparse", "wide"])
+def test_auto_schedule_hybrid_matches_oracle(name):
+    """AUTO from 4096 rows: the first half of the panels as separate
+    launches, the second half in the persistent launch."""
+    if name == "tall":
+        A, m = f2gen.uniform(9000, 1400, 110), 1400
+    elif name == "square":
+        A, m = f2gen.uniform(6000, 6000, 111), 6000
+    elif name == "rank":
+        X, Y = f2gen.fixed_rank_factors(5000, 5000, 2500, 112)
+        A, m = oracle.mmm(X, Y, 2500, 5000, nthreads=NT), 5000
+    elif name == "sparse":
+        A, m = f2gen.sparse_rows(5000, 5000, 3, 113), 5000
+    else:
+        A, m = f2gen.uniform(4096, 7000, 114), 7000
+    gf2.timing(True)
+    try:
+        got = run(A, m, None)
+        t = gf2.timing_read()
+    finally:
+        gf2.timing(False)
+    assert t["factor"][1] == 1 and t["panel"][1] > 0, "not the split schedule"
+    assert_same_decomposition(A, m, got)
