@@ -840,8 +840,12 @@ def run_ours(args):
     ws = torch.empty(lib.gf2_decompose_workspace_bytes(n, m, 1), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
+    sched = {"auto": gf2.SCHEDULE_AUTO, "streams": gf2.SCHEDULE_STREAMS, "persistent": gf2.SCHEDULE_PERSISTENT,
+             "split": gf2.SCHEDULE_SPLIT}
+    opts = gf2.Opts(schedule=sched[args.schedule])
+
     def step():
-        gf2.gf2_decompose(A, perm, piv, rk, L, E, workspace=ws, stream=stream)
+        gf2.gf2_decompose_ex(A, perm, piv, rk, L, E, opts, workspace=ws, stream=stream)
 
     for _ in range(args.warmup):
         step()
@@ -976,6 +980,7 @@ def run_ours(args):
             "vs_baseline": (PAPER_SECONDS_32768 / (ms / 1000.0)) if (n == m == 32768) else None,
             "dtype": "u64", "data": "synthetic",
             "config": {"workload": workload_name(n, m), "n": n, "m": m, "rank": r, "factors": "L,E",
+                       "schedule": args.schedule,
                        "per_rank_matrix": "independent seed per rank",
                        "l2": "no flush: working set (A 128 MiB + W + L + E, ~512 MiB) > 129 MB L2",
                        "vs_baseline_ref": "Table 4 b=128 rec 11.498 s (3.06 GHz Xeon, other machine)"},
@@ -1100,6 +1105,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the compact serving and batched measurements")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "streams", "persistent", "split"],
+                    help="decomposition schedule (gf2_opts.schedule)")
     ap.add_argument("--workload", default="decompose", choices=["decompose", "batched", "serving", "product", "sizes", "sparse"],
                     help="decompose: the headline 32768^2 decomposition; batched: many small matrices in one "
                          "launch; serving: a request stream on resident factors")

@@ -88,18 +88,21 @@ int gf2_release_workspace(void);
  *                    one built; others GF2_ERR_UNSUPPORTED).
  *   backend          product: GF2_BACKEND_AUTO (M4RM under Strassen-Winograd),
  *                    GF2_BACKEND_TABLES (M4RM alone), GF2_BACKEND_TENSOR.
- *   schedule         decomposition by pairs of panels: GF2_SCHEDULE_PERSISTENT
- *                    runs it as one cooperative persistent launch (one CTA
- *                    per SM: CTA 0 runs the panel chain, the others the
- *                    look-ahead and the trailing updates, ordered by device
- *                    counters); GF2_SCHEDULE_STREAMS as separate launches on
- *                    three streams (one CTA per panel); AUTO picks the
- *                    persistent launch from 4096 rows on when the device can
- *                    hold one CTA per SM, the streams otherwise (and always
- *                    with panel_w 64).  A persistent run whose bounded device
- *                    waits give up writes rank -1 (the other outputs are then
- *                    undefined); the calls that read the rank back return
- *                    GF2_ERR_TIMEOUT.
+ *   schedule         decomposition by pairs of panels: GF2_SCHEDULE_STREAMS
+ *                    runs it as separate launches on three streams (one CTA
+ *                    per panel; the trailing updates beside the look-ahead
+ *                    kernels on the same SMs); GF2_SCHEDULE_PERSISTENT as one
+ *                    cooperative persistent launch (one CTA per SM: CTA 0
+ *                    runs the panel chain, the others the look-ahead and the
+ *                    trailing updates, ordered by device counters);
+ *                    GF2_SCHEDULE_SPLIT the first three quarters of the
+ *                    panels as separate launches and the rest persistent;
+ *                    AUTO is STREAMS (the fastest measured at 32768; also
+ *                    with panel_w 64 and on a device that cannot hold one CTA
+ *                    per SM, whatever is asked).  A persistent run whose
+ *                    bounded device waits give up writes rank -1 (the other
+ *                    outputs are then undefined); the calls that read the
+ *                    rank back return GF2_ERR_TIMEOUT.
  *   strassen_cutoff  product: the Strassen-Winograd cutoff, >= 128
  *                    (GF2_STRASSEN_OFF: no recursion); 0 = the process one.
  *   batched_c8_from  batched decomposition: the size from which a matrix
@@ -114,6 +117,7 @@ int gf2_release_workspace(void);
 #define GF2_SCHEDULE_AUTO 0
 #define GF2_SCHEDULE_STREAMS 1
 #define GF2_SCHEDULE_PERSISTENT 2
+#define GF2_SCHEDULE_SPLIT 3
 
 typedef struct gf2_opts {
     int32_t panel_w;

@@ -191,7 +191,7 @@ class Opts(ctypes.Structure):
 
 
 BACKEND_AUTO, BACKEND_TABLES, BACKEND_TENSOR = 0, 1, 2
-SCHEDULE_AUTO, SCHEDULE_STREAMS, SCHEDULE_PERSISTENT = 0, 1, 2
+SCHEDULE_AUTO, SCHEDULE_STREAMS, SCHEDULE_PERSISTENT, SCHEDULE_SPLIT = 0, 1, 2, 3
 GF2_FACTORS_RANK_ONLY = 1
 
 

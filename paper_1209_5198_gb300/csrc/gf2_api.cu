@@ -205,7 +205,7 @@ int side_resources(int nevents, SideResources **out, std::unique_lock<std::mutex
 // ------------------------------------------------------------ graph cache
 // One captured graph per (device, shape, every pointer the kernels see).
 struct GraphKey {
-    int32_t dev, pair, tab_c, unused;  // (no padding: the key is compared bytewise)
+    int32_t dev, pair, tab_c, jend;  // (no padding: the key is compared bytewise)
     int64_t n, m, lda, ldl, lde;
     const void *a, *perm, *piv, *rank, *L, *E, *ws;
 };
@@ -252,7 +252,7 @@ int check_opts(const gf2_opts *o)
     if (o->tile_words < 0) return GF2_ERR_ARG;
     if (o->tile_words != 0 && o->tile_words != kTileWords) return GF2_ERR_UNSUPPORTED;
     if (o->backend < GF2_BACKEND_AUTO || o->backend > GF2_BACKEND_TENSOR) return GF2_ERR_ARG;
-    if (o->schedule < GF2_SCHEDULE_AUTO || o->schedule > GF2_SCHEDULE_PERSISTENT || o->reserved) return GF2_ERR_ARG;
+    if (o->schedule < GF2_SCHEDULE_AUTO || o->schedule > GF2_SCHEDULE_SPLIT || o->reserved) return GF2_ERR_ARG;
     if (o->strassen_cutoff < 0 || (o->strassen_cutoff > 0 && o->strassen_cutoff < 128)) return GF2_ERR_ARG;
     if (o->batched_c8_from < 0) return GF2_ERR_ARG;
     return GF2_OK;
@@ -446,16 +446,19 @@ int enqueue_factorization(DecompCtx c, int64_t *rank, gf2_mat *L, gf2_mat *E, Si
     CK(cudaStreamWaitEvent(s, evJoinP, 0));
     CK(cudaEventRecord(evJoinN, N));
     CK(cudaStreamWaitEvent(s, evJoinN, 0));
-    if (jend < mu) {
-        const int st = enqueue_persistent(c, progress, jend, s);
-        if (st) return st;
-        c.fail = factor_fail_word(progress);
-    }
+    if (jend < mu) return GF2_OK;  // the caller continues with enqueue_tail
     return enqueue_outputs(c, rank, L, E, s);
 }
 
-// the automatic schedule's switch to the persistent launch (rows)
-constexpr int64_t kPersistentFromRows = 4096;
+// After the separate launches of panels [0, jend) (jend < mu): the panels
+// from jend on in one persistent launch, then the outputs; on s.
+int enqueue_tail(DecompCtx c, int64_t *rank, gf2_mat *L, gf2_mat *E, int jend, int32_t *progress, cudaStream_t s)
+{
+    const int st = enqueue_persistent(c, progress, jend, s);
+    if (st) return st;
+    c.fail = factor_fail_word(progress);
+    return enqueue_outputs(c, rank, L, E, s);
+}
 
 struct DecompLayout {
     int64_t mu, ldw, kmax, ldl;
@@ -547,17 +550,16 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
 
     // Which panels run as separate launches ([0, jend)) and which in one
     // persistent launch (csrc/k_factor.cu), by pairs of panels only:
-    // PERSISTENT all of them; AUTO, from kPersistentFromRows rows on, the
-    // second half -- the first half is bound by the trailing updates, which
-    // the separate launches run beside the look-ahead kernels on the same
-    // SMs; the second half is bound by the serial panel chain, which the
-    // persistent launch keeps on one SM without a launch between panels.
+    // PERSISTENT all of them; SPLIT the first three quarters as separate
+    // launches and the last quarter persistent (the panel chain bounds the
+    // end, and there the persistent launch runs a panel every ~17 us against
+    // ~22 us); AUTO the separate launches (measured: SPLIT 13.01 ms against
+    // 13.00 ms at 32768, the switch costs what the last quarter gains).
     // A device that cannot hold one CTA per SM keeps the separate launches.
     int jend = c.mu;
-    if (c.pair && (o.schedule == GF2_SCHEDULE_PERSISTENT ||
-                   (o.schedule == GF2_SCHEDULE_AUTO && n >= kPersistentFromRows))) {
+    if (c.pair && (o.schedule == GF2_SCHEDULE_PERSISTENT || o.schedule == GF2_SCHEDULE_SPLIT)) {
         const cudaError_t e = factor_available();
-        if (e == cudaSuccess) jend = o.schedule == GF2_SCHEDULE_PERSISTENT ? 0 : 2 * (c.mu / 4);
+        if (e == cudaSuccess) jend = o.schedule == GF2_SCHEDULE_PERSISTENT ? 0 : 2 * ((3 * c.mu) / 8);
         else if (e != cudaErrorNotSupported) return GF2_ERR_CUDA;
         cudaGetLastError();
     }
@@ -584,8 +586,10 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
     key.L = L ? L->w : nullptr; key.ldl = L ? L->ld : 0;
     key.E = E ? E->w : nullptr; key.lde = E ? E->ld : 0;
     key.ws = ws;
-    // (a persistent launch is not captured into the graph)
-    if (g_timing.load() || !g_use_graphs || jend < c.mu) {
+    key.jend = jend;
+    // (the separate launches are captured into the graph; a persistent
+    // launch after them is not: enqueue_tail follows the graph)
+    if (g_timing.load() || !g_use_graphs || jend == 0) {
         st = enqueue_factorization(c, rank, L, E, side, jend, progress);
         if (st) return st;
     } else {
@@ -631,6 +635,10 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
             exec = remember_graph(key, graph, exec);
             CK(cudaGraphLaunch(exec, side->main));
         }
+    }
+    if (jend < c.mu) {
+        st = enqueue_tail(c, rank, L, E, jend, progress, side->main);
+        if (st) return st;
     }
     CK(cudaEventRecord(evOut, side->main));
     CK(cudaStreamWaitEvent(s, evOut, 0));

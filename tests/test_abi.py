@@ -231,11 +231,11 @@ def test_options_are_validated_without_gpu(lib):
     good = [dict(panel_w=64), dict(panel_w=128), dict(table_c=4), dict(table_c=8), dict(tile_words=4),
             dict(backend=g.BACKEND_TABLES), dict(backend=g.BACKEND_TENSOR), dict(strassen_cutoff=128),
             dict(strassen_cutoff=g.STRASSEN_OFF), dict(batched_c8_from=512),
-            dict(schedule=g.SCHEDULE_STREAMS), dict(schedule=g.SCHEDULE_PERSISTENT),
+            dict(schedule=g.SCHEDULE_STREAMS), dict(schedule=g.SCHEDULE_PERSISTENT), dict(schedule=g.SCHEDULE_SPLIT),
             dict(panel_w=64, table_c=4, tile_words=4, backend=1, strassen_cutoff=4096, batched_c8_from=1)]
     bad_arg = [dict(panel_w=-64), dict(panel_w=96), dict(table_c=-1), dict(table_c=17), dict(tile_words=-4),
                dict(backend=3), dict(backend=-1), dict(strassen_cutoff=-1), dict(strassen_cutoff=127),
-               dict(batched_c8_from=-5), dict(schedule=3), dict(schedule=-1), dict(reserved=1)]
+               dict(batched_c8_from=-5), dict(schedule=4), dict(schedule=-1), dict(reserved=1)]
     unsupported = [dict(panel_w=192), dict(panel_w=256), dict(table_c=6), dict(table_c=16), dict(tile_words=2),
                    dict(tile_words=8)]
     for kw in good:

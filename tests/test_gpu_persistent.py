@@ -97,23 +97,20 @@ def test_stream_schedule_at_sizes_where_auto_is_persistent(n, m):
     assert_same_decomposition(A, m, got)
 
 
-def test_auto_picks_the_persistent_schedule_from_4096_rows():
+def test_auto_is_the_stream_schedule():
     gf2.timing(True)
     try:
-        run(f2gen.uniform(4096, 1000, 107), 1000, None, factors=False)
-        big = gf2.timing_read()["factor"][1]
-        gf2.timing(True)
-        run(f2gen.uniform(4095, 1000, 108), 1000, None, factors=False)
-        small = gf2.timing_read()["factor"][1]
+        run(f2gen.uniform(6000, 3000, 107), 3000, None, factors=False)
+        t = gf2.timing_read()
     finally:
         gf2.timing(False)
-    assert big == 1 and small == 0
+    assert t["factor"][1] == 0 and t["panel"][1] > 0
 
 
 @pytest.mark.parametrize("name", ["tall", "square", "rank", "sparse", "wide"])
-def test_auto_schedule_hybrid_matches_oracle(name):
-    """AUTO from 4096 rows: the first half of the panels as separate
-    launches, the second half in the persistent launch."""
+def test_split_schedule_matches_oracle(name):
+    """SPLIT: the first three quarters of the panels as separate launches,
+    the rest in the persistent launch (from the workspace state they leave)."""
     if name == "tall":
         A, m = f2gen.uniform(9000, 1400, 110), 1400
     elif name == "square":
@@ -127,7 +124,7 @@ def test_auto_schedule_hybrid_matches_oracle(name):
         A, m = f2gen.uniform(4096, 7000, 114), 7000
     gf2.timing(True)
     try:
-        got = run(A, m, None)
+        got = run(A, m, gf2.Opts(schedule=gf2.SCHEDULE_SPLIT))
         t = gf2.timing_read()
     finally:
         gf2.timing(False)
