@@ -649,7 +649,7 @@ def op_counts(reset: bool = False) -> dict:
 
 TRACE_PANELS = 4096
 TRACE_SLOTS = ("panel_start", "panel_loaded", "panel_loop", "panel_end", "next_start", "next_end", "rest_start",
-               "rest_end")
+               "rest_end", "panel_uinv", "panel_t", "panel_tinv", "panel_zp")
 
 
 def trace_read(reset: bool = False) -> dict:

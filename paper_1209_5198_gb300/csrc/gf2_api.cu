@@ -1673,7 +1673,7 @@ int gf2_trace_read(uint64_t *out, int64_t count, int reset)
     // complemented on the device
     for (int64_t i = 0; i < count && i < (int64_t)a.size(); ++i) {
         const int slot = (int)(i / kTraceMaxPanels);
-        unsigned long long v = slot <= kTrPanelEnd ? a[i] : b[i];
+        unsigned long long v = trace_panel_slot(slot) ? a[i] : b[i];
         if (f[i] > v) v = f[i];
         if ((slot == kTrNextStart || slot == kTrRestStart) && v) v = ~v;
         out[i] = v;

@@ -276,8 +276,14 @@ enum TraceSlot {
     kTrNextEnd = 5,
     kTrRestStart = 6,   // every update launch of panel j (pair: j = the second panel)
     kTrRestEnd = 7,
-    kTrSlots = 8
+    // the panel's end phase, step by step (between kTrPanelLoop and kTrPanelEnd)
+    kTrPanelUinv = 8,   // U^-1 (backward sweep) and Comp
+    kTrPanelT = 9,      // T = lambda(B)
+    kTrPanelTinv = 10,  // T^-1 (backward sweep)
+    kTrPanelZp = 11,    // Zp = Comp T^-1 (before the stores)
+    kTrSlots = 12
 };
+__host__ __device__ constexpr bool trace_panel_slot(int slot) { return slot <= kTrPanelEnd || slot >= kTrPanelUinv; }
 #ifdef GF2_TRACE
 #define GF2_TR(...) __VA_ARGS__
 __device__ __forceinline__ unsigned long long trace_clock()

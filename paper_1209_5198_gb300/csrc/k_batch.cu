@@ -20,6 +20,8 @@
 // The host routes each matrix by its size (gf2_batched_autotune measures the
 // crossover on the device) and runs the two kernels side by side.
 #include "m4rm_core.cuh"
+#include <mutex>
+
 #include "panel_core.cuh"
 
 namespace gf2 {
@@ -250,10 +252,14 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_batch(BatchCtx b)
 template <int C>
 cudaError_t prepare_batch()
 {
+    // (several host threads may launch batches at once: the serving engine's
+    // lanes and callers on other streams)
+    static std::mutex mu;
     static bool done[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
     if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
     e = cudaFuncSetAttribute(k_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BatchShared<C>));
     if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;

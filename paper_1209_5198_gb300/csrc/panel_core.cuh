@@ -125,6 +125,8 @@ struct PanelShared {
     int zn, zfrom, zto, zhead, found_idx;
     uint64_t found_raw;  // the raw word of the row found (with the list)
     int wcnt[kPanelThreads / 32];
+    uint64_t basis[64];  // end phase: the 8-bit blocks' basis effects of a triangular sweep
+    int ns;              // end phase: pivots found in the panel
 };
 
 // Word j of storage row i with the updates of every panel < j.  W holds it
@@ -459,6 +461,156 @@ __device__ __forceinline__ bool fast_phase(FastCols &st, int nbits, int smax, bo
     return false;
 }
 
+// ---------------------------------------------------------------- end phase
+// The coordinate maps of a panel, from E (rows in sh.E), U = E at the pivot
+// columns (columns in sh.Ucol, unit upper triangular) and the raw pivot
+// words B (sh.B):
+//   Comp = rows of U^-1 at the pivot bits (lambda(d) = d Comp),
+//   T    = B Comp (lambda of every pivot word, unit lower triangular),
+//   T^-1, and Zp = Comp T^-1 (the paper's Z: y(d) = d Zp).
+// Every map is linear over F2 and taken 8 bits at a time with 256-entry
+// tables (Section 6's Four Russians method on 64 x 64 matrices): a product
+// is 8 independent lookups per row; a triangular solve (M x = e_c, M unit
+// upper triangular with column t in Mcol[t]) is 8 dependent lookups, one
+// per 8-row block from the top: the backward sweep of one block (for t in
+// the block, downwards: if x_t then x ^= the part of column t above the
+// diagonal) changes x by a linear function of the block's 8 entries of x,
+// tabulated from its 8 basis effects.  All kPanelThreads threads take part.
+
+// tab[256 g + x] = XOR of basis[8 g + i] over the bits i of x, for the 8
+// tables g: thread (g, q) fills entries 16 q .. 16 q + 15 of table g by a
+// Gray walk (one XOR per entry) that starts at position q of the cyclic
+// 4-bit Gray sequence, so that at every step the 16 threads of one table
+// write 16 different bank pairs (no shared-memory bank conflicts).
+__device__ __forceinline__ void fill_tables(const uint64_t *basis, uint64_t *tab)
+{
+    static_assert(kPanelThreads == 128, "8 tables x 16 threads");
+    const int tid = threadIdx.x;
+    const int g = tid >> 4, q = tid & 15;
+    const uint64_t *bs = basis + 8 * g;
+    uint64_t v = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        if ((q >> i) & 1) v ^= bs[4 + i];
+    const int gq = q ^ (q >> 1);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        if ((gq >> i) & 1) v ^= bs[i];
+    uint64_t *tb = tab + 256 * g + 16 * q;
+    tb[gq] = v;
+#pragma unroll 4
+    for (int step = 1; step < 16; ++step) {
+        const int p = (q + step) & 15;
+        v ^= bs[p ? __ffs(p) - 1 : 3];  // (from 15 to 0 the cyclic sequence changes bit 3)
+        tb[p ^ (p >> 1)] = v;
+    }
+}
+
+// Tables of the block sweeps of M (columns Mcol, zero past the rank) in tab.
+__device__ __forceinline__ void sweep_tables(const uint64_t *Mcol, PanelShared &sh)
+{
+    const int tid = threadIdx.x;
+    if (tid < 64) {  // the effect of entry tid alone in its block
+        const int lo = tid & ~7;
+        uint64_t x = 1ull << tid;
+        for (int t = tid; t >= lo; --t)
+            if ((x >> t) & 1) x ^= Mcol[t] & ((1ull << t) - 1);
+        sh.basis[tid] = x ^ (1ull << tid);
+    }
+    panel_sync();
+    fill_tables(sh.basis, sh.tab);
+    panel_sync();
+}
+
+// x = M^-1 x by the block sweeps (tables of sweep_tables)
+__device__ __forceinline__ uint64_t sweep_apply(const PanelShared &sh, uint64_t x)
+{
+#pragma unroll
+    for (int b = 7; b >= 0; --b) x ^= sh.tab[256 * b + (int)((x >> (8 * b)) & 255)];
+    return x;
+}
+
+// Tables of the rows R[0..64): tab[256 g + x] = XOR of R[8 g + i] over the bits i of x.
+__device__ __forceinline__ void product_tables(const uint64_t *R, PanelShared &sh)
+{
+    fill_tables(R, sh.tab);
+    panel_sync();
+}
+
+// w R (the XOR of the rows R[p] over the bits p of w), tables of product_tables
+__device__ __forceinline__ uint64_t product_apply(const PanelShared &sh, uint64_t w)
+{
+    uint64_t r = 0;
+#pragma unroll
+    for (int g = 0; g < 8; ++g) r ^= sh.tab[256 * g + (int)((w >> (8 * g)) & 255)];
+    return r;
+}
+
+__device__ __forceinline__ void panel_end_phase(const DecompCtx &c, int j, int R, PanelInfo *pi, PanelShared &sh,
+                                                unsigned long long *tr)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int s = sh.ns;
+    (void)tr;
+    // U^-1 by columns (warp 0: columns lane, lane + 32), then its rows and Comp
+    sweep_tables(sh.Ucol, sh);
+    if (warp == 0) {
+        uint64_t x[2];
+        x[0] = sweep_apply(sh, lane < s ? 1ull << lane : 0);
+        x[1] = sweep_apply(sh, lane + 32 < s ? 1ull << (lane + 32) : 0);
+        transpose64(x, lane);  // x[h] = row lane + 32h of U^-1
+        sh.TI[lane] = x[0];
+        sh.TI[lane + 32] = x[1];
+        __syncwarp();
+        const int t0 = sh.sidx[lane], t1 = sh.sidx[lane + 32];
+        sh.Comp[lane] = t0 >= 0 ? sh.TI[t0] : 0;
+        sh.Comp[lane + 32] = t1 >= 0 ? sh.TI[t1] : 0;
+    }
+    panel_sync();
+    GF2_TR(if (tr && tid == 0) tr[kTrPanelUinv * kTraceMaxPanels + j] = trace_clock();)
+    // T[t] = lambda(B_t) = B_t Comp
+    product_tables(sh.Comp, sh);
+    uint64_t Tt = 0;
+    if (tid < 64) Tt = tid < s ? product_apply(sh, sh.B[tid]) : 0;
+    panel_sync();  // (every lookup into the tables done)
+    if (tid < 64) sh.T[tid] = Tt;
+    panel_sync();
+    GF2_TR(if (tr && tid == 0) tr[kTrPanelT * kTraceMaxPanels + j] = trace_clock();)
+    // T^-1 by rows: T^T y = e_c (column t of T^T = row t of T) gives row c
+    sweep_tables(sh.T, sh);
+    uint64_t Yc = 0;
+    if (tid < 64) Yc = sweep_apply(sh, tid < s ? 1ull << tid : 0);
+    panel_sync();
+    if (tid < 64) sh.TI[tid] = Yc;
+    panel_sync();
+    GF2_TR(if (tr && tid == 0) tr[kTrPanelTinv * kTraceMaxPanels + j] = trace_clock();)
+    // Zp = Comp T^-1
+    product_tables(sh.TI, sh);
+    if (tid < 64) {
+        const uint64_t m = sh.Comp[tid];
+        const uint64_t z = product_apply(sh, m);
+        GF2_TR(if (tr && tid == 0) {
+            asm volatile("" ::"l"(z));
+            tr[kTrPanelZp * kTraceMaxPanels + j] = trace_clock();
+        })
+        pi->Zp[tid] = z;
+        pi->Comp[tid] = m;
+    }
+    if (tid == 0) {
+        pi->R = R;
+        pi->r = s;
+    }
+    for (int t = tid; t < s; t += kPanelThreads) {
+        pi->Tinv[t] = sh.TI[t];
+        pi->T[t] = sh.T[t];
+        pi->Erow[t] = sh.E[t];
+        pi->pivbit[t] = sh.pb[t];
+        pi->prow[t] = sh.prow[t];
+        c.pivcols[R + t] = 64 * j + sh.pb[t];
+    }
+    GF2_TR(if (tr && tid == 0) tr[kTrPanelEnd * kTraceMaxPanels + j] = trace_clock();)
+}
+
 // The panel step of block j, run by one CTA of kPanelThreads threads (warp 0
 // searches, warps 1..3 serve the scans of the general path).
 // zs / zcap: shared memory for the first zcap entries of the row list (zcap
@@ -540,13 +692,14 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
         for (;;) {
             bar_sync(1, kPanelThreads);
             const int req = sh.req;
-            if (req == kReqDone) return;
+            if (req == kReqDone) break;  // (to the end phase, with warp 0)
             scan_find(c, Wj, pv, sh, L);
             bar_sync(2, kPanelThreads);
         }
     }
 
     // ---------------------------------------------------------------- warp 0
+    if (warp == 0) {
     uint64_t A = 0, B = 0;    // columns lane and lane+32 over the window slots
     uint64_t EA = 0, EB = 0;  // bit s: entry (s, column) of E_s
     uint64_t valid = 0;       // window slots holding a row
@@ -859,103 +1012,30 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
         ++k;
     }
     replay();
-    // release the helpers
-    if (lane == 0) sh.req = kReqDone;
-    __syncwarp();
-    bar_sync(1, kPanelThreads);
-    GF2_TR(if (tr && lane == 0) tr[kTrPanelLoop * kTraceMaxPanels + j] = trace_clock();)
-
-    // ---- coordinate maps from E (bits EA/EB) and the raw pivot words B
+    // E (rows) and U (columns: U = E at the pivot columns, unit upper
+    // triangular; zero past s) into shared memory for the end phase
     {
         uint64_t e2[2] = {EA, EB};
         transpose64(e2, lane);
         sh.E[lane] = e2[0];
         sh.E[lane + 32] = e2[1];
+        sh.Ucol[lane] = 0;
+        sh.Ucol[lane + 32] = 0;
+        __syncwarp();
         // column s' of U = column pb[s'] of E
         const int sa = sh.sidx[lane], sb = sh.sidx[lane + 32];
         if (sa >= 0) sh.Ucol[sa] = EA;
         if (sb >= 0) sh.Ucol[sb] = EB;
+        if (lane == 0) sh.ns = s;
     }
+    // release the helpers (they join the end phase)
+    if (lane == 0) sh.req = kReqDone;
     __syncwarp();
-    const int c0 = lane, c1 = lane + 32;
-    // Both triangular inverses by a backward column sweep over a unit upper
-    // triangular M (column t in Mcol[t], bits <= t): x = e_c; for t from the
-    // top down, x[t] is final once the columns above it have been removed,
-    // and column t leaves the right-hand side when x[t] = 1.  Two test-and-
-    // XOR steps per column, no parity chain.  U x = e_c gives column c of
-    // U^-1; T^T y = e_c (column t of T^T = row t of T) gives row c of T^-1.
-    auto sweep = [&](const uint64_t *Mcol, uint64_t x[2]) {
-        x[0] = c0 < s ? (1ull << c0) : 0;
-        x[1] = c1 < s ? (1ull << c1) : 0;
-#pragma unroll 4
-        for (int t = 63; t > 0; --t) {
-            const uint64_t u = Mcol[t] & ((1ull << t) - 1);
-            if ((x[0] >> t) & 1) x[0] ^= u;
-            if ((x[1] >> t) & 1) x[1] ^= u;
-        }
-    };
-    // rows of U^-1 (staged in TI), then Comp at the pivot bits
-    {
-        uint64_t x[2];
-        sweep(sh.Ucol, x);
-        transpose64(x, lane);  // x[h] = row lane + 32h of U^-1
-        sh.TI[c0] = x[0];
-        sh.TI[c1] = x[1];
-        __syncwarp();
-        const int t0 = sh.sidx[c0], t1 = sh.sidx[c1];
-        sh.Comp[c0] = t0 >= 0 ? sh.TI[t0] : 0;
-        sh.Comp[c1] = t1 >= 0 ? sh.TI[t1] : 0;
-    }
-    __syncwarp();
-    // T[t] = lambda(B_t) = XOR over the bits p of B_t of Comp[p]
-    {
-        const uint64_t b0 = c0 < s ? sh.B[c0] : 0, b1 = c1 < s ? sh.B[c1] : 0;
-        uint64_t a0 = 0, a1 = 0;
-#pragma unroll 8
-        for (int p = 0; p < 64; ++p) {
-            const uint64_t cp = sh.Comp[p];
-            if ((b0 >> p) & 1) a0 ^= cp;
-            if ((b1 >> p) & 1) a1 ^= cp;
-        }
-        sh.T[c0] = a0;
-        sh.T[c1] = a1;
-    }
-    __syncwarp();
-    {
-        uint64_t y[2];
-        sweep(sh.T, y);  // y[h] = row lane + 32h of T^-1
-        __syncwarp();
-        sh.TI[c0] = y[0];
-        sh.TI[c1] = y[1];
-    }
-    __syncwarp();
-    if (lane == 0) {
-        pi->R = R;
-        pi->r = s;
-    }
-    {
-        const uint64_t m0 = sh.Comp[c0], m1 = sh.Comp[c1];
-        uint64_t z0 = 0, z1 = 0;
-#pragma unroll 8
-        for (int t = 0; t < 64; ++t) {
-            const uint64_t ti = sh.TI[t];
-            if ((m0 >> t) & 1) z0 ^= ti;
-            if ((m1 >> t) & 1) z1 ^= ti;
-        }
-        pi->Zp[c0] = z0;
-        pi->Zp[c1] = z1;
-        pi->Comp[c0] = m0;
-        pi->Comp[c1] = m1;
-    }
-    for (int t = lane; t < s; t += 32) {
-        pi->Tinv[t] = sh.TI[t];
-        pi->T[t] = sh.T[t];
-        pi->Erow[t] = sh.E[t];
-        pi->pivbit[t] = sh.pb[t];
-        pi->prow[t] = sh.prow[t];
-        c.pivcols[R + t] = 64 * j + sh.pb[t];
-    }
-    GF2_TR(if (tr && lane == 0) tr[kTrPanelEnd * kTraceMaxPanels + j] = trace_clock();)
+    bar_sync(1, kPanelThreads);
+    GF2_TR(if (tr && lane == 0) tr[kTrPanelLoop * kTraceMaxPanels + j] = trace_clock();)
+    }  // warp 0
+
+    panel_end_phase(c, j, R, pi, sh, tr);
 }
 
 }  // namespace
