@@ -490,6 +490,8 @@ typedef struct gf2_server_stats {
     int64_t completed, hits, misses, evictions;
     int64_t solve_launches, batched_decompositions, plain_decompositions;
     int64_t max_batch, resident_bytes, arena_bytes;
+    int64_t admitted_in_flight;   /* requests admitted while a launch of the engine was on the GPU */
+    int64_t overlapped_launches;  /* solve launches enqueued while another launch was on the GPU   */
 } gf2_server_stats;
 
 /* Creates an engine on the current device.  device_bytes: the device memory
@@ -601,6 +603,16 @@ int gf2_op_counts(uint64_t *out, int count, int reset);
  * reset) synchronises the current device and writes min(count, 12 * 4096)
  * values.  Returns GF2_OK, GF2_ERR_ARG (out null or count < 0),
  * GF2_ERR_UNSUPPORTED (every other build) or GF2_ERR_CUDA. */
+/* The number of polls after which a bounded device-side wait gives up
+ * (the grid-wide barriers of gf2_solve, the progress counters of the
+ * persistent decomposition), for every later call in the process; 0
+ * restores each wait's default (about a second).  No counterpart in the
+ * paper: it exists so that a test can make a wait run out (GF2_ERR_TIMEOUT
+ * from gf2_solve; rank -1 and GF2_ERR_TIMEOUT from the calls that read the
+ * rank of a persistent decomposition) and check that the GPU context stays
+ * usable.  Errors: GF2_ERR_ARG (polls < 0 or >= 2^32). */
+int gf2_debug_set_wait_limit(int64_t polls);
+
 #define GF2_TRACE_PANELS 4096
 #define GF2_TRACE_SLOTS 12
 int gf2_trace_read(uint64_t *out, int64_t count, int reset);

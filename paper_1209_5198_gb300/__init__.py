@@ -156,6 +156,8 @@ def load() -> ctypes.CDLL:
                        ("gf2_factors_nullspace", [F, M, P])):
         getattr(lib, name).restype = ctypes.c_int
         getattr(lib, name).argtypes = args
+    lib.gf2_debug_set_wait_limit.restype = ctypes.c_int
+    lib.gf2_debug_set_wait_limit.argtypes = [ctypes.c_int64]
     lib.gf2_trace_read.restype = ctypes.c_int
     lib.gf2_trace_read.argtypes = [P, ctypes.c_int64, ctypes.c_int]
     lib.gf2_timing_enable.argtypes = [ctypes.c_int]
@@ -647,6 +649,12 @@ def op_counts(reset: bool = False) -> dict:
     return {k: int(v) for k, v in zip(OPS, out)}
 
 
+def set_wait_limit(polls: int) -> None:
+    """gf2_debug_set_wait_limit: polls after which a bounded device wait gives
+    up (0: the defaults); for tests that make a wait run out."""
+    _check(load().gf2_debug_set_wait_limit(int(polls)), "gf2_debug_set_wait_limit")
+
+
 TRACE_PANELS = 4096
 TRACE_SLOTS = ("panel_start", "panel_loaded", "panel_loop", "panel_end", "next_start", "next_end", "rest_start",
                "rest_end", "panel_uinv", "panel_t", "panel_tinv", "panel_zp")
@@ -692,7 +700,8 @@ COMPLETION_DTYPE = np.dtype([("id", "<u8"), ("status", "<i4"), ("hit", "<i4"), (
                              ("consistent", "<u8"), ("arrival_us", "<f8"), ("admit_us", "<f8"),
                              ("done_us", "<f8")], align=True)
 STATS_FIELDS = ("completed", "hits", "misses", "evictions", "solve_launches", "batched_decompositions",
-                "plain_decompositions", "max_batch", "resident_bytes", "arena_bytes")
+                "plain_decompositions", "max_batch", "resident_bytes", "arena_bytes", "admitted_in_flight",
+                "overlapped_launches")
 
 
 class Server:

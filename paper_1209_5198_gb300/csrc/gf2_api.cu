@@ -102,6 +102,7 @@ bool mat_ok(const gf2_mat *M)
 // ------------------------------------------------------------ diagnostics
 std::atomic<int64_t> g_launches{0};
 std::atomic<bool> g_timing{false};
+std::atomic<int64_t> g_wait_limit{0};  // polls of a bounded device wait (0: each wait's default)
 std::mutex g_timing_mutex;
 struct TimedLaunch {
     int cls;
@@ -1010,6 +1011,7 @@ int gf2_solve(const gf2_mat *L, const gf2_mat *E, const int32_t *perm, const int
     c.n = (int32_t)n;
     c.m = (int32_t)m;
     c.check = (flags & GF2_NOCHECK) ? 0 : 1;
+    c.wait_limit = (uint32_t)device_wait_limit(1ll << 24);
     CK(cudaMemsetAsync(p, 0, kAlign, s));
     LAUNCH(GF2_KCLASS_SOLVE, launch_solve(c, s));
     // the status of the bounded waits and of the padding check
@@ -1303,6 +1305,12 @@ int decompose_batched_items(int count, const BatchItem *items, bool factors, uns
 }
 
 void add_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+int64_t device_wait_limit(int64_t dflt)
+{
+    const int64_t v = g_wait_limit.load();
+    return v > 0 ? v : dflt;
+}
 
 }  // namespace gf2
 
@@ -1654,6 +1662,13 @@ int gf2_op_counts(uint64_t *out, int count, int reset)
     (void)reset;
     return GF2_ERR_UNSUPPORTED;
 #endif
+}
+
+int gf2_debug_set_wait_limit(int64_t polls)
+{
+    if (polls < 0 || polls > UINT32_MAX) return GF2_ERR_ARG;
+    g_wait_limit.store(polls);
+    return GF2_OK;
 }
 
 int gf2_trace_read(uint64_t *out, int64_t count, int reset)

@@ -149,6 +149,7 @@ struct SolveCtx {
     uint64_t *bad;                    // one word: OR of the residual rows
     int32_t n, m;
     int32_t check;                    // report right-hand-side bits beyond nrhs
+    uint32_t wait_limit;              // polls after which a grid-wide wait gives up
 };
 
 // One solve of a serving batch: the operands, where its rank goes and the
@@ -185,6 +186,9 @@ int64_t factor_progress_ints(int mu);
 cudaError_t launch_factor_init(int32_t *progress, int mu, int j_start, cudaStream_t s);
 cudaError_t launch_factor(const DecompCtx &c, int32_t *progress, int j_start, cudaStream_t s);
 cudaError_t factor_available();  // cudaErrorNotSupported: the device cannot hold one CTA per SM
+// The polls after which a bounded device wait gives up: the value set by
+// gf2_debug_set_wait_limit, else `dflt` (csrc/gf2_api.cu).
+int64_t device_wait_limit(int64_t dflt);
 const int32_t *factor_fail_word(const int32_t *progress);
 cudaError_t launch_next(const DecompCtx &c, int j, cudaStream_t s);
 // the wide update of panel j (np = 1) or of the pair j, j+1 (np = 2)

@@ -53,7 +53,7 @@ constexpr int kFNextRounds = 1;           // rounds per look-ahead chunk (one ta
 constexpr int kFRestU = 4;                // row groups of 16 rows per warp and pass iteration
 constexpr int kFBatch = 16;               // update chunks between looks at the look-ahead queue
 constexpr int kFSmemBytes = 200 * 1024;   // dynamic shared memory of every CTA (one per SM)
-constexpr long long kFSpinLimit = 1ll << 22;  // polls of one wait (~64-500 ns each) before it gives up
+constexpr long long kFSpinLimit = 1ll << 22;  // default polls of one wait (~64-500 ns each) before it gives up
 
 // progress words (int32, zeroed before the launch): a header, then the
 // per-panel, per-pair and per-(pair, tile) counters
@@ -66,6 +66,7 @@ struct Progress {
     int32_t *pair_tf, *pair_nt, *pair_nch, *pair_prev;        // [npairs]: shape, published with NEXT(2p+1)
     int32_t *tile_done;                                       // [npairs][ntw]: chunks finished per tile
     int npairs, ntw;
+    long long limit;                                          // polls of one wait before it gives up
 };
 
 __host__ __device__ inline Progress progress_at(int32_t *base, int mu)
@@ -75,6 +76,7 @@ __host__ __device__ inline Progress progress_at(int32_t *base, int mu)
     g.ntw = (mu + kTileWords - 1) / kTileWords;
     g.hdr = base;
     int32_t *p = base + kPgHeader;
+    g.limit = kFSpinLimit;
     g.next_claim = p; p += mu;
     g.next_done = p; p += mu;
     g.pair_claim = p; p += g.npairs;
@@ -112,7 +114,7 @@ __device__ __forceinline__ bool wait_geq(const int32_t *p, int v, const Progress
     for (long long it = 0;; ++it) {
         if (ld_acquire(p) >= v) return true;
         if (ld_relaxed(g.hdr + kPgFail)) return false;
-        if (it >= kFSpinLimit) {
+        if (it >= g.limit) {
             atomicExch(g.hdr + kPgFail, 1);
             return false;
         }
@@ -220,10 +222,12 @@ struct WorkerCmd {
 // Panels j_start.. (even j_start): the earlier panels, their look-aheads
 // and the updates of their pairs are done (launch_factor_init marks them).
 template <int C>
-__global__ void __launch_bounds__(kFThreads, 1) k_factor(DecompCtx c, int32_t *progress, int j_start)
+__global__ void __launch_bounds__(kFThreads, 1) k_factor(DecompCtx c, int32_t *progress, int j_start,
+                                                           long long wait_limit)
 {
     extern __shared__ __align__(16) unsigned char fsmem[];
-    const Progress g = progress_at(progress, c.mu);
+    Progress g = progress_at(progress, c.mu);
+    g.limit = wait_limit;
     const int tid = threadIdx.x;
     UpdOps ops;
 
@@ -377,7 +381,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_factor(DecompCtx c, int32_t *p
         if (w.kind == kDoQuit) break;
         if (w.kind == kDoIdle) {
             if (tid == 0) {
-                if (++idle > kFSpinLimit) atomicExch(g.hdr + kPgFail, 1);
+                if (++idle > g.limit) atomicExch(g.hdr + kPgFail, 1);
                 __nanosleep(128);
             }
             __syncthreads();
@@ -529,8 +533,9 @@ cudaError_t launch_factor(const DecompCtx &c0, int32_t *progress, int j_start, c
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (c.tab_c == 4) return cudaLaunchKernelEx(&cfg, k_factor<4>, c, progress, j_start);
-    return cudaLaunchKernelEx(&cfg, k_factor<8>, c, progress, j_start);
+    const long long limit = (long long)device_wait_limit(kFSpinLimit);
+    if (c.tab_c == 4) return cudaLaunchKernelEx(&cfg, k_factor<4>, c, progress, j_start, limit);
+    return cudaLaunchKernelEx(&cfg, k_factor<8>, c, progress, j_start, limit);
 }
 
 #ifdef GF2_COUNT_OPS

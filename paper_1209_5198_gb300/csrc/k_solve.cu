@@ -31,7 +31,7 @@ namespace {
 
 constexpr int kSolveThreads = 256;
 constexpr int kSolveWarps = kSolveThreads / 32;
-constexpr uint32_t kSpinLimit = 1u << 24;  // ~1-2 s of 100 ns sleeps
+constexpr uint32_t kSpinLimit = 1u << 24;  // default polls of a grid-wide wait (~1-2 s of 100 ns sleeps)
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
 {
@@ -42,7 +42,7 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
 
 // Grid-wide barrier (all CTAs are co-resident: cooperative launch).  Returns
 // false, in every thread, once any CTA has given up waiting.
-__device__ bool grid_barrier(uint32_t *count, uint32_t *err, uint32_t &epoch, int *s_ok)
+__device__ bool grid_barrier(uint32_t *count, uint32_t *err, uint32_t &epoch, int *s_ok, uint32_t limit)
 {
     __syncthreads();
     ++epoch;
@@ -53,7 +53,7 @@ __device__ bool grid_barrier(uint32_t *count, uint32_t *err, uint32_t &epoch, in
         uint32_t it = 0;
         while (ld_acquire(count) < target) {
             if (ld_acquire(err) & 1u) break;
-            if (++it > kSpinLimit) {
+            if (++it > limit) {
                 atomicOr(err, 1u);
                 break;
             }
@@ -71,7 +71,8 @@ struct GridSync {
     uint32_t *count, *err;
     uint32_t epoch;
     int *s_ok;
-    __device__ bool operator()() { return grid_barrier(count, err, epoch, s_ok); }
+    uint32_t limit;
+    __device__ bool operator()() { return grid_barrier(count, err, epoch, s_ok, limit); }
 };
 struct CtaSync {
     __device__ bool operator()()
@@ -201,7 +202,7 @@ __device__ void solve_body(const SolveCtx &c, int b, int G, Sync &bar, SolveShar
 __global__ void __launch_bounds__(kSolveThreads) k_solve(SolveCtx c)
 {
     __shared__ SolveShared sh;
-    GridSync bar{c.sync, c.sync + 1, 0, &sh.s_ok};
+    GridSync bar{c.sync, c.sync + 1, 0, &sh.s_ok, c.wait_limit};
     solve_body(c, blockIdx.x, gridDim.x, bar, sh);
 }
 

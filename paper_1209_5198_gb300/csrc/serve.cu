@@ -438,10 +438,20 @@ bool retire_slots(gf2_server *S)
 }
 
 // ---- step 3: admission in arrival order
+bool gpu_busy(const gf2_server *S);
+
 bool admit(gf2_server *S)
 {
     bool progress = false, miss_blocked = false;
     const double now = S->now();
+    // (continuous batching: a request may be admitted while earlier work of
+    // the engine is still on the GPU)
+    const bool in_flight = gpu_busy(S);
+    auto count_admission = [&]() {
+        if (!in_flight) return;
+        std::lock_guard<std::mutex> lock(S->mu);
+        ++S->stats.admitted_in_flight;
+    };
     for (auto it = S->waiting.begin(); it != S->waiting.end();) {
         Req *q = *it;
         auto f = S->cache.find(q->r.matrix);
@@ -465,6 +475,7 @@ bool admit(gf2_server *S)
             q->hit = 1;
             q->admit = now;
             S->admitted.push_back(q);
+            count_admission();
             it = S->waiting.erase(it);
             progress = true;
             continue;
@@ -492,6 +503,7 @@ bool admit(gf2_server *S)
         q->hit = 0;
         q->admit = now;
         S->admitted.push_back(q);
+        count_admission();
         S->to_build.push_back(e);
         it = S->waiting.erase(it);
         progress = true;
@@ -722,6 +734,7 @@ bool launch_solves(gf2_server *S)
                 return true;
             }
             add_launches(launches);
+            const bool overlapped = gpu_busy(S);  // (before this slot counts as busy)
             sl->busy = true;
             sl->dev_off = off;
             sl->dev_bytes = in_bytes + scratch;
@@ -730,6 +743,7 @@ bool launch_solves(gf2_server *S)
             sl->remaining = (int)cnt;
             std::lock_guard<std::mutex> lock(S->mu);
             ++S->stats.solve_launches;
+            if (overlapped) ++S->stats.overlapped_launches;
             if ((int64_t)cnt > S->stats.max_batch) S->stats.max_batch = (int64_t)cnt;
             return true;
         }

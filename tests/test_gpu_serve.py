@@ -145,6 +145,39 @@ def test_poisson_arrivals_overlap_and_match_oracle():
         st = s.stats()
     w.check(got)
     assert st["max_batch"] >= 1
+    # continuous batching: requests were admitted while earlier launches of
+    # the engine were on the GPU, and solve launches were enqueued while
+    # others ran -- and every result still equals the oracle's (the same as
+    # running the request alone)
+    assert st["admitted_in_flight"] > 0, st
+    assert st["overlapped_launches"] > 0, st
+
+
+def test_a_request_the_arena_can_never_hold_fails_alone():
+    """Factors larger than the whole factor arena (a 1 MiB budget): those
+    requests complete with GF2_ERR_NOMEM, every other request is served and
+    equals the oracle."""
+    sizes = [(128, 128), (300, 256), (2000, 2000)]
+    w = Workload(24, seed=15, sizes=sizes)
+    big = 2  # key of the 2000 x 2000 matrix
+    with gf2.Server(1 << 20, 2048, 2048, max_batch=16) as s:
+        req = w.req.copy()
+        for X in w.X:
+            X[:] = 0
+        s.submit(req)
+        done = s.wait_all(len(req), timeout_s=300)
+    exp = w.expected()
+    seen = 0
+    for c in done:
+        i = int(c["id"])
+        if int(w.req[i]["matrix"]) == big:
+            assert c["status"] == gf2.GF2_ERR_NOMEM, (i, int(c["status"]))
+            continue
+        assert c["status"] == gf2.GF2_OK, (i, gf2.status_string(int(c["status"])))
+        rank, cons, X = exp[i]
+        assert int(c["rank"]) == rank and int(c["consistent"]) == cons and np.array_equal(w.X[i], X), i
+        seen += 1
+    assert seen > 0 and len(done) == len(w.req)
 
 
 def test_eviction_under_a_small_budget():
