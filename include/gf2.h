@@ -587,7 +587,7 @@ int gf2_op_counts(uint64_t *out, int count, int reset);
 /* Device timeline of the decomposition's kernels, in the trace build only
  * (libgf2_trace.so, compiled with -DGF2_TRACE; the kernels read the GPU's
  * global timer).  No counterpart in the paper: it measures where the time
- * of the serial panel chain goes.  Per panel j < 4096 it keeps twelve
+ * of the serial panel chain goes.  Per panel j < 4096 it keeps thirteen
  * nanosecond stamps, slot-major (out[slot * 4096 + j]):
  *   0 panel kernel released, 1 its rows loaded and the previous panel's
  *   update applied, 2 pivot loop done, 3 coordinate maps written (end),
@@ -595,12 +595,13 @@ int gf2_op_counts(uint64_t *out, int count, int reset);
  *   6 / 7 first start / last end of the trailing update(s) of panel j (a
  *   pair's update is filed under its second panel), and the panel's end
  *   phase step by step: 8 U^-1 and Comp done, 9 T done, 10 T^-1 done,
- *   11 Zp done (before the stores).
+ *   11 Zp done (before the stores), and 12 panel kernel entered (before
+ *   it waits for the previous panel; separate launches only).
  * 0 = not recorded.  The panel stamps are overwritten by every run; the
  * launch spans accumulate (earliest start, latest end) until a read with
  * reset = 1 clears every stamp, so clear them right before the
  * decomposition to trace.  gf2_trace_read(out, count,
- * reset) synchronises the current device and writes min(count, 12 * 4096)
+ * reset) synchronises the current device and writes min(count, 13 * 4096)
  * values.  Returns GF2_OK, GF2_ERR_ARG (out null or count < 0),
  * GF2_ERR_UNSUPPORTED (every other build) or GF2_ERR_CUDA. */
 /* The number of polls after which a bounded device-side wait gives up

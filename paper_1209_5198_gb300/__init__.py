@@ -657,7 +657,7 @@ def set_wait_limit(polls: int) -> None:
 
 TRACE_PANELS = 4096
 TRACE_SLOTS = ("panel_start", "panel_loaded", "panel_loop", "panel_end", "next_start", "next_end", "rest_start",
-               "rest_end", "panel_uinv", "panel_t", "panel_tinv", "panel_zp")
+               "rest_end", "panel_uinv", "panel_t", "panel_tinv", "panel_zp", "panel_entry")
 
 
 def trace_read(reset: bool = False) -> dict:

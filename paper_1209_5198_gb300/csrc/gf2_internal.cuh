@@ -285,7 +285,8 @@ enum TraceSlot {
     kTrPanelT = 9,      // T = lambda(B)
     kTrPanelTinv = 10,  // T^-1 (backward sweep)
     kTrPanelZp = 11,    // Zp = Comp T^-1 (before the stores)
-    kTrSlots = 12
+    kTrPanelEntry = 12, // panel kernel entered (before griddepcontrol.wait)
+    kTrSlots = 13
 };
 __host__ __device__ constexpr bool trace_panel_slot(int slot) { return slot <= kTrPanelEnd || slot >= kTrPanelUinv; }
 #ifdef GF2_TRACE

@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4) k_panel(DecompCtx c, int j)
 {
     __shared__ PanelShared sh;
     extern __shared__ __align__(16) uint64_t panel_dyn[];
+    GF2_TR(if (threadIdx.x == 0 && j < kTraceMaxPanels) g_panel_trace[kTrPanelEntry * kTraceMaxPanels + j] = trace_clock();)
     // Launched as a programmatic dependent of the previous panel: wait until
     // that launch has completed and its writes are visible, then let the
     // next panel be scheduled (it waits here in turn).  Without the launch

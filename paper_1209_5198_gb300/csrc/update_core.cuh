@@ -332,66 +332,82 @@ __device__ __forceinline__ void rest_prepare(const DecompCtx &c, int j, int tile
     }
 }
 
-// W ^= y_j C_j (+ y_j+1 C_j+1) on `tile` for the list entries [rb, re), with
-// the tables rest_prepare built; U row groups of 16 rows per warp and
-// iteration, y and the next rows' indices prefetched one iteration ahead.
-template <int C, int U, int NP, int THREADS>
-__device__ __forceinline__ void rest_pass(const DecompCtx &c, int j, int tile, int rb, int re, const uint64_t *smem,
-                                          UpdOps &ops)
+// -------------------------------------------------------------------- lookups
+// The 8-bit table lookups of the wide update with their addresses reduced
+// to two integer operations.  At step g a lane reads table g ^ swp (swp = its
+// row slot & 3: the four rows of a quarter-warp read the four 32-byte
+// quarters of the bank space), entry x = byte g ^ swp of its multiplier y.
+// Entry (t, x) of the [quad][x][quarter][kTileWords] layout is at byte
+// ((t >> 2) * 256 + x) * 128 + (t & 3) * 32 of the tables, the lane's word
+// pair 16 bytes further for wp = 1.  So with q = g & 3:
+//   x    = the low byte of __byte_perm(half g >> 2 of y, 0, sel[q]),
+//          sel[q] = 0x4440 | (q ^ swp)
+//   addr = base[q] + 128 x + (g >> 2) * 32768
+//          base[q] = tables + (q ^ swp) * 32 + wp * 16.
+struct Lk8 {
+    uint32_t base[4];  // shared-window byte addresses
+    uint32_t sel[4];
+};
+
+__device__ __forceinline__ Lk8 lk8_lane(const uint64_t *tab, int swp, int wp)
+{
+    Lk8 l;
+    const uint32_t t = (uint32_t)__cvta_generic_to_shared(tab);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        l.base[q] = t + (uint32_t)(((q ^ swp) << 5) + (wp << 4));
+        l.sel[q] = 0x4440u | (uint32_t)(q ^ swp);
+    }
+    return l;
+}
+
+// acc[u] ^= y[u] * C for the NG tables from table G0 (compile time; G0 a
+// multiple of 8: tables G0.. belong to one panel and take bytes 0.. of y).
+template <int G0, int NG, int U>
+__device__ __forceinline__ void lk8_rows(const Lk8 &l, const uint64_t (&y)[U], ulonglong2 (&acc)[U])
+{
+    static_assert(G0 % 8 == 0 && (NG == 4 || NG == 8), "whole quads of one panel's tables");
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t h = g < 4 ? (uint32_t)y[u] : (uint32_t)(y[u] >> 32);
+            const uint32_t x = __byte_perm(h, 0u, l.sel[g & 3]);
+            const uint32_t addr = l.base[g & 3] + (x << 7) + (uint32_t)(((G0 + g) >> 2) * 256 * 128);
+            uint64_t tx, ty;
+            asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(tx), "=l"(ty) : "r"(addr));
+            acc[u].x ^= tx;
+            acc[u].y ^= ty;
+        }
+    }
+}
+
+// One iteration of the wide update for U row groups: W ^= y0 C_j (+ y1
+// C_j+1) on this lane's word pair of the rows row[u] (-1: none; a row with
+// y0 = y1 = 0 is neither read nor written).  The row words, like the
+// multipliers and the list entries, are cached in L2 only (.cg): nothing
+// re-reads them from L1, and an L1 fill would take cycles of the data
+// pipe that the table lookups are bound by.
+template <int C, int U, int NP>
+__device__ __forceinline__ void rest_rows(const Lk8 &lk, const ulonglong2 *tab2, int swp, int wp, int ng0, int ng1,
+                                          const uint64_t (&y0)[U], const uint64_t (&y1)[U], const int (&row)[U],
+                                          uint64_t *Wt)
 {
     constexpr int K = Tabs<C>::K;
-    const PanelInfo *pi0 = c.info + j;
-    const PanelInfo *pi1 = c.info + j + NP - 1;
-    const int r0 = pi0->r, r1 = NP == 2 ? pi1->r : 0;
-    const int ng0 = tables_used<C>(r0), ng1 = NP == 2 ? tables_used<C>(r1) : 0;
-    const int jl = j + NP - 1;
-    const int32_t *act = c.act + (int64_t)(jl % kRing) * c.n;
-    const uint64_t *Y0 = c.Y + (int64_t)(j % kRing) * c.n;
-    const uint64_t *Y1 = c.Y + (int64_t)((j + 1) % kRing) * c.n;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int rs = lane / kLanesPerRow, wp = lane % kLanesPerRow, swp = rs & 3;
-    constexpr int NW = THREADS / 32;
-    const ulonglong2 *tab2 = reinterpret_cast<const ulonglong2 *>(smem);
-    const int q0 = tile * kTileWords;
-    (void)ops;
-    (void)q0;
-    (void)K;
-    uint64_t *Wt = c.W + (int64_t)tile * c.tstride + 2 * wp;  // this lane's word pair of the tile
-    constexpr int STEP = kRowsPerWarp * U * NW;
-    uint64_t yn0[U], yn1[U];
-    int rown[U];
+    ulonglong2 a[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        const int k = rb + warp * kRowsPerWarp * U + u * kRowsPerWarp + rs;
-        rown[u] = k < re ? act[k] : -1;
+        a[u] = make_ulonglong2(0, 0);
+        if (y0[u] | y1[u]) a[u] = __ldcg(reinterpret_cast<const ulonglong2 *>(Wt + (int64_t)row[u] * kTileWords));
     }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        yn0[u] = rown[u] >= 0 ? Y0[rown[u]] : 0;
-        yn1[u] = (NP == 2 && rown[u] >= 0) ? Y1[rown[u]] : 0;
-    }
-    for (int base = rb + warp * kRowsPerWarp * U; base < re; base += STEP) {
-        uint64_t y0[U], y1[U];
-        int row[U];
-        ulonglong2 a[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            y0[u] = yn0[u];
-            y1[u] = yn1[u];
-            row[u] = rown[u];
-            const int k = base + STEP + u * kRowsPerWarp + rs;
-            rown[u] = k < re ? act[k] : -1;
+    if (C == 8) {
+        if (ng0 == 8) lk8_rows<0, 8, U>(lk, y0, a);
+        else if (ng0 == 4) lk8_rows<0, 4, U>(lk, y0, a);
+        if (NP == 2) {
+            if (ng1 == 8) lk8_rows<8, 8, U>(lk, y1, a);
+            else if (ng1 == 4) lk8_rows<8, 4, U>(lk, y1, a);
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            yn0[u] = rown[u] >= 0 ? Y0[rown[u]] : 0;
-            yn1[u] = (NP == 2 && rown[u] >= 0) ? Y1[rown[u]] : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            a[u] = make_ulonglong2(0, 0);
-            if (y0[u] | y1[u]) a[u] = *reinterpret_cast<const ulonglong2 *>(Wt + (int64_t)row[u] * kTileWords);
-        }
+    } else {
         for (int g = 0; g < ng0; ++g) {
             const int gg = g ^ swp;
 #pragma unroll
@@ -414,9 +430,68 @@ __device__ __forceinline__ void rest_pass(const DecompCtx &c, int j, int tile, i
                 }
             }
         }
+    }
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (y0[u] | y1[u]) *reinterpret_cast<ulonglong2 *>(Wt + (int64_t)row[u] * kTileWords) = a[u];
+    for (int u = 0; u < U; ++u)
+        if (y0[u] | y1[u]) __stcg(reinterpret_cast<ulonglong2 *>(Wt + (int64_t)row[u] * kTileWords), a[u]);
+}
+
+// W ^= y_j C_j (+ y_j+1 C_j+1) on `tile` for the list entries [rb, re), with
+// the tables rest_prepare built; U row groups of 16 rows per warp and
+// iteration, y and the next rows' indices prefetched one iteration ahead.
+template <int C, int U, int NP, int THREADS>
+__device__ __forceinline__ void rest_pass(const DecompCtx &c, int j, int tile, int rb, int re, const uint64_t *smem,
+                                          UpdOps &ops)
+{
+    constexpr int K = Tabs<C>::K;
+    const PanelInfo *pi0 = c.info + j;
+    const PanelInfo *pi1 = c.info + j + NP - 1;
+    const int r0 = pi0->r, r1 = NP == 2 ? pi1->r : 0;
+    const int ng0 = tables_used<C>(r0), ng1 = NP == 2 ? tables_used<C>(r1) : 0;
+    const int jl = j + NP - 1;
+    const int32_t *act = c.act + (int64_t)(jl % kRing) * c.n;
+    const uint64_t *Y0 = c.Y + (int64_t)(j % kRing) * c.n;
+    const uint64_t *Y1 = c.Y + (int64_t)((j + 1) % kRing) * c.n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int rs = lane / kLanesPerRow, wp = lane % kLanesPerRow, swp = rs & 3;
+    constexpr int NW = THREADS / 32;
+    const ulonglong2 *tab2 = reinterpret_cast<const ulonglong2 *>(smem);
+    const Lk8 lk = lk8_lane(smem, swp, wp);
+    const int q0 = tile * kTileWords;
+    (void)ops;
+    (void)q0;
+    (void)K;
+    uint64_t *Wt = c.W + (int64_t)tile * c.tstride + 2 * wp;  // this lane's word pair of the tile
+    constexpr int STEP = kRowsPerWarp * U * NW;
+    uint64_t yn0[U], yn1[U];
+    int rown[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int k = rb + warp * kRowsPerWarp * U + u * kRowsPerWarp + rs;
+        rown[u] = k < re ? __ldcg(act + k) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        yn0[u] = rown[u] >= 0 ? __ldcg(Y0 + rown[u]) : 0;
+        yn1[u] = (NP == 2 && rown[u] >= 0) ? __ldcg(Y1 + rown[u]) : 0;
+    }
+    for (int base = rb + warp * kRowsPerWarp * U; base < re; base += STEP) {
+        uint64_t y0[U], y1[U];
+        int row[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            y0[u] = yn0[u];
+            y1[u] = yn1[u];
+            row[u] = rown[u];
+            const int k = base + STEP + u * kRowsPerWarp + rs;
+            rown[u] = k < re ? __ldcg(act + k) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            yn0[u] = rown[u] >= 0 ? __ldcg(Y0 + rown[u]) : 0;
+            yn1[u] = (NP == 2 && rown[u] >= 0) ? __ldcg(Y1 + rown[u]) : 0;
+        }
+        rest_rows<C, U, NP>(lk, tab2, swp, wp, ng0, ng1, y0, y1, row, Wt);
         GF2_OPS(const int lw = (q0 + 2 * wp < c.mu) + (q0 + 2 * wp + 1 < c.mu);
                 for (int u = 0; u < U; ++u) {
                     if (y0[u]) { ops.upd += lw; ops.lk += (unsigned long long)ng0 * lw; }
@@ -449,6 +524,7 @@ __device__ __forceinline__ int rest_pass_from(const DecompCtx &c, int j, int til
     const int rs = lane / kLanesPerRow, wp = lane % kLanesPerRow, swp = rs & 3;
     constexpr int NW = THREADS / 32;
     const ulonglong2 *tab2 = reinterpret_cast<const ulonglong2 *>(smem);
+    const Lk8 lk = lk8_lane(smem, swp, wp);
     const int q0 = tile * kTileWords;
     (void)ops;
     (void)q0;
@@ -462,12 +538,12 @@ __device__ __forceinline__ int rest_pass_from(const DecompCtx &c, int j, int til
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int e = base + u * kRowsPerWarp + rs;
-        rown[u] = e < re ? act[e] : -1;
+        rown[u] = e < re ? __ldcg(act + e) : -1;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        yn0[u] = rown[u] >= 0 ? Y0[rown[u]] : 0;
-        yn1[u] = (NP == 2 && rown[u] >= 0) ? Y1[rown[u]] : 0;
+        yn0[u] = rown[u] >= 0 ? __ldcg(Y0 + rown[u]) : 0;
+        yn1[u] = (NP == 2 && rown[u] >= 0) ? __ldcg(Y1 + rown[u]) : 0;
     }
     int polled = -1;  // thread 0: the polled word, read one iteration ahead
     for (; base < re; base += STEP, ++k) {
@@ -480,50 +556,20 @@ __device__ __forceinline__ int rest_pass_from(const DecompCtx &c, int j, int til
         if (__shfl_sync(0xffffffffu, lane == 0 ? *stop : 0, 0)) break;
         uint64_t y0[U], y1[U];
         int row[U];
-        ulonglong2 a[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             y0[u] = yn0[u];
             y1[u] = yn1[u];
             row[u] = rown[u];
             const int e = base + STEP + u * kRowsPerWarp + rs;
-            rown[u] = e < re ? act[e] : -1;
+            rown[u] = e < re ? __ldcg(act + e) : -1;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            yn0[u] = rown[u] >= 0 ? Y0[rown[u]] : 0;
-            yn1[u] = (NP == 2 && rown[u] >= 0) ? Y1[rown[u]] : 0;
+            yn0[u] = rown[u] >= 0 ? __ldcg(Y0 + rown[u]) : 0;
+            yn1[u] = (NP == 2 && rown[u] >= 0) ? __ldcg(Y1 + rown[u]) : 0;
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            a[u] = make_ulonglong2(0, 0);
-            if (y0[u] | y1[u]) a[u] = *reinterpret_cast<const ulonglong2 *>(Wt + (int64_t)row[u] * kTileWords);
-        }
-        for (int g = 0; g < ng0; ++g) {
-            const int gg = g ^ swp;
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int x = (int)((y0[u] >> (C * gg)) & (Tabs<C>::X - 1));
-                const ulonglong2 t = tab2[tab_entry<C>(gg, x) * (kTileWords / 2) + wp];
-                a[u].x ^= t.x;
-                a[u].y ^= t.y;
-            }
-        }
-        if (NP == 2) {
-            for (int g = 0; g < ng1; ++g) {
-                const int gg = g ^ swp;
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int x = (int)((y1[u] >> (C * gg)) & (Tabs<C>::X - 1));
-                    const ulonglong2 t = tab2[tab_entry<C>(K + gg, x) * (kTileWords / 2) + wp];
-                    a[u].x ^= t.x;
-                    a[u].y ^= t.y;
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (y0[u] | y1[u]) *reinterpret_cast<ulonglong2 *>(Wt + (int64_t)row[u] * kTileWords) = a[u];
+        rest_rows<C, U, NP>(lk, tab2, swp, wp, ng0, ng1, y0, y1, row, Wt);
         GF2_OPS(const int lw = (q0 + 2 * wp < c.mu) + (q0 + 2 * wp + 1 < c.mu);
                 for (int u = 0; u < U; ++u) {
                     if (y0[u]) { ops.upd += lw; ops.lk += (unsigned long long)ng0 * lw; }
