@@ -152,9 +152,13 @@ int gf2_opts_check(const gf2_opts *o);
  *       even number of words.  The cutoff is off until gf2_mmm_autotune or
  *       gf2_mmm_set_strassen_cutoff sets it.
  *   GF2_MMM_TABLES: M4RM alone (no recursion).
- *   GF2_MMM_TENSOR: the tensor cores (every entry an e4m3 0 or 1, integer
- *       sums in fp32 folded into parity bits every 4096 of the inner
- *       dimension, entry = lowest bit; k < 2^24, else M4RM).
+ *   GF2_MMM_TENSOR: the fifth-generation tensor cores (tcgen05.mma of
+ *       kind::f8f6f4 with operands loaded by TMA, accumulators in tensor
+ *       memory): every entry an e4m3 0 or 1, the integer sums in fp32
+ *       folded into parity bits every 4096 of the inner dimension, entry =
+ *       lowest bit; k < 2^24, else M4RM.  This backend synchronises the
+ *       stream once before it returns, to read its error word: a device
+ *       wait that gave up returns GF2_ERR_TIMEOUT.
  * The workspace depends on the backend and the recursion depth: size it
  * with the same flags (and after the same cutoff setting).
  * Errors: GF2_ERR_ARG (NULL, both backend flags), GF2_ERR_SHAPE (A.cols !=
@@ -185,6 +189,16 @@ int gf2_mmm_ex(const gf2_mat *A, const gf2_mat *B, gf2_mat *C, int accumulate, u
  * (>= 128; 2^62 turns the recursion off).  Errors: GF2_ERR_ARG,
  * GF2_ERR_NOMEM, GF2_ERR_CUDA. */
 int gf2_mmm_autotune(int64_t max_dim, int64_t *cutoff, void *stream);
+
+/* A measurement aid with no counterpart in the paper: the rate of the
+ * tensor pipe for the MMA shape the tensor backend issues (tcgen05.mma
+ * kind::f8f6f4, 128 x 256 x 32, e4m3 in, fp32 out) from shared memory, with
+ * no loads: one CTA per SM issues iters x 4 MMAs into one accumulator.
+ * *tflops receives dense TFLOP/s (2 flops per multiply-add) on the current
+ * device, timed by CUDA events on the stream, which it synchronises.
+ * Errors: GF2_ERR_ARG (iters < 1, tflops NULL), GF2_ERR_TIMEOUT,
+ * GF2_ERR_CUDA. */
+int gf2_tensor_peak(int64_t iters, double *tflops, void *stream);
 int gf2_mmm_set_strassen_cutoff(int64_t cutoff);
 int64_t gf2_mmm_strassen_cutoff(void);
 

@@ -87,6 +87,8 @@ def load() -> ctypes.CDLL:
     lib.gf2_batched_c8_from.restype = I64
     lib.gf2_mmm_autotune.restype = ctypes.c_int
     lib.gf2_mmm_autotune.argtypes = [I64, ctypes.POINTER(I64), P]
+    lib.gf2_tensor_peak.restype = ctypes.c_int
+    lib.gf2_tensor_peak.argtypes = [I64, ctypes.POINTER(ctypes.c_double), P]
     lib.gf2_mmm_set_strassen_cutoff.restype = ctypes.c_int
     lib.gf2_mmm_set_strassen_cutoff.argtypes = [I64]
     lib.gf2_mmm_strassen_cutoff.restype = I64
@@ -593,6 +595,14 @@ def mmm_autotune(max_dim: int = 32768, stream=None) -> int:
     out = ctypes.c_int64(0)
     _check(load().gf2_mmm_autotune(int(max_dim), ctypes.byref(out), _stream(stream)), "gf2_mmm_autotune")
     return int(out.value)
+
+
+def tensor_peak(iters: int = 4096, stream=None) -> float:
+    """Dense TFLOP/s of the tensor pipe for the tensor backend's MMA shape
+    (tcgen05 kind::f8f6f4, 128 x 256 x 32) from shared memory, one CTA per SM."""
+    out = ctypes.c_double(0)
+    _check(load().gf2_tensor_peak(int(iters), ctypes.byref(out), _stream(stream)), "gf2_tensor_peak")
+    return float(out.value)
 
 
 def batched_autotune(max_dim: int = 4096, stream=None, times: dict | None = None) -> int:

@@ -1538,12 +1538,19 @@ int mmm_impl(const gf2_mat *A, const gf2_mat *B, gf2_mat *C, int accumulate, uns
         if (st) return st;
     }
     if (tensor) {
+        // expand to e4m3 bytes, then the tcgen05 product; its device waits
+        // are bounded and report through the word after the padding flag,
+        // read back with one synchronisation of the stream
         const size_t kp = (size_t)mma_pad(k);
         uint8_t *A8 = reinterpret_cast<uint8_t *>(p);
         uint8_t *B8 = A8 + align_up((size_t)mma_pad(n) * kp);
-        LAUNCH(GF2_KCLASS_UPDATE, launch_mma_product(A->w, A->ld, B->w, B->ld, C->w, C->ld, (int)n, (int)k, (int)m,
-                                                     accumulate, A8, B8, s));
-        return GF2_OK;
+        uint32_t *err = flag + 1;
+        CK(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
+        LAUNCH(GF2_KCLASS_LAYOUT, launch_expand_operands(A->w, A->ld, B->w, B->ld, (int)n, (int)k, (int)m, A8, B8, s));
+        LAUNCH(GF2_KCLASS_UPDATE, launch_umma_product(A8, B8, (int)mma_pad(n), (int)mma_pad(m), (int)kp, C->w, C->ld,
+                                                      (int)n, (int)m, accumulate, err, s));
+        st = check_flag(err, s);
+        return st == GF2_ERR_PADDING ? GF2_ERR_TIMEOUT : st;
     }
     return mmm_rec(CBView{C->w, C->ld}, CBView{A->w, A->ld}, CBView{B->w, B->ld}, n, k, mw, accumulate != 0, levels,
                    reinterpret_cast<uint64_t *>(p), s);
@@ -1601,6 +1608,35 @@ int time_product(uint64_t *A, uint64_t *B, uint64_t *C, uint64_t *tmp, int64_t d
 }  // namespace
 
 extern "C" {
+
+int gf2_tensor_peak(int64_t iters, double *tflops, void *stream)
+{
+    if (iters < 1 || iters > (1 << 30) || !tflops) return GF2_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    uint32_t *err = nullptr;
+    CK(cudaMalloc(&err, sizeof(uint32_t)));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int st = GF2_OK;
+    if (cudaMemsetAsync(err, 0, sizeof(uint32_t), s) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess || launch_umma_peak(sms, 16, err, s) != cudaSuccess ||
+        cudaEventRecord(e0, s) != cudaSuccess || launch_umma_peak(sms, (int)iters, err, s) != cudaSuccess ||
+        cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+        st = GF2_ERR_CUDA;
+    float ms = 0.f;
+    if (!st && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = GF2_ERR_CUDA;
+    if (!st) {
+        st = check_flag(err, s);
+        if (st == GF2_ERR_PADDING) st = GF2_ERR_TIMEOUT;
+    }
+    if (!st) *tflops = (double)sms * (double)iters * umma_peak_flops_per_iter() / ((double)ms * 1e-3) / 1e12;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(err);
+    return st;
+}
 
 int gf2_mmm_autotune(int64_t max_dim, int64_t *cutoff, void *stream)
 {

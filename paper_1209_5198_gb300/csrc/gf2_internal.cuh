@@ -215,12 +215,21 @@ constexpr int kServeClusterCTAs = 8;
 bool serve_by_cluster(int64_t n);
 cudaError_t launch_serve_cluster(const ServeItem *items, int count, int64_t max_n, cudaStream_t s);
 int batch_ctas_per_sm(int c);  // c = 4 or 8: the batched kernel's table size
-// the product on the tensor cores (k < 2^24): A8, B8 are n_pad x k_pad and
-// m_pad x k_pad bytes (dimensions rounded up to mma_pad)
+// the product on the tensor cores (k < 2^24, csrc/k_umma.cu): A8 = A and
+// B8 = B^T as e4m3 bytes 0 / 1.0, K contiguous, n_pad x k_pad and m_pad x
+// k_pad bytes (dimensions rounded up to mma_pad)
 int64_t mma_pad(int64_t x);
-cudaError_t launch_mma_product(const uint64_t *A, int64_t lda, const uint64_t *B, int64_t ldb, uint64_t *C,
-                               int64_t ldc, int n, int k, int m, int accumulate, uint8_t *A8, uint8_t *B8,
-                               cudaStream_t s);
+cudaError_t launch_expand_operands(const uint64_t *A, int64_t lda, const uint64_t *B, int64_t ldb, int n, int k, int m,
+                                   uint8_t *A8, uint8_t *B8, cudaStream_t s);
+// the tcgen05 product from the expanded operands; err: ORed with 1 when a
+// device wait gave up
+cudaError_t launch_umma_product(const uint8_t *A8, const uint8_t *B8, int n_pad, int m_pad, int k_pad, uint64_t *C,
+                                int64_t ldc, int n, int m, int accumulate, uint32_t *err, cudaStream_t s);
+// the tensor pipe's kind::f8f6f4 rate: ctas CTAs issue iters x 4 MMAs of
+// 128 x 256 x 32 each (umma_peak_flops_per_iter() flops per iteration)
+cudaError_t launch_umma_peak(int ctas, int iters, uint32_t *err, cudaStream_t s);
+double umma_peak_flops_per_iter();
+// rows words of the last column block with a bit outside mask -> *err |= 1
 cudaError_t launch_check_last_block(const uint64_t *last, int rows, uint64_t mask, uint32_t *err, cudaStream_t s);
 cudaError_t launch_batch(const BatchCtx &b, int grid, int c, cudaStream_t s);
 // T = A^T for A n x m in column blocks (T: m x n, ld ldt >= m; csrc/k_transpose.cu)

@@ -118,3 +118,15 @@ def test_product_of_fixed_rank_factors_has_that_rank():
     X, Y = f2gen.fixed_rank_factors(n, m, r, 44)
     A = gf2.mmm(gf2.Mat.from_rowmajor(X, r), gf2.Mat.from_rowmajor(Y, m))
     assert gf2.gf2_rank(A) == r
+
+
+def test_tensor_peak_probe_runs():
+    """The tensor pipe probe (the tensor backend's MMA shape from shared
+    memory) returns a positive dense rate and leaves the context usable."""
+    tf = gf2.tensor_peak(256)
+    assert tf > 0.0
+    A = f2gen.uniform(256, 256, 50)
+    B = f2gen.uniform(256, 300, 51)
+    Cd = gf2.Mat.empty(256, 300)
+    gf2.gf2_mmm(gf2.Mat.from_rowmajor(A, 256), gf2.Mat.from_rowmajor(B, 300), Cd, flags=gf2.GF2_MMM_TENSOR)
+    assert np.array_equal(Cd.to_rowmajor(), oracle.mmm(A, B, 256, 300))
