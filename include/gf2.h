@@ -154,7 +154,7 @@ int gf2_opts_check(const gf2_opts *o);
  *   GF2_MMM_TABLES: M4RM alone (no recursion).
  *   GF2_MMM_TENSOR: the fifth-generation tensor cores (tcgen05.mma of
  *       kind::f8f6f4 with operands loaded by TMA, accumulators in tensor
- *       memory): every entry an e4m3 0 or 1, the integer sums in fp32
+ *       memory): every entry an e2m1 0 or 1, the integer sums in fp32
  *       folded into parity bits every 4096 of the inner dimension, entry =
  *       lowest bit; k < 2^24, else M4RM.  This backend synchronises the
  *       stream once before it returns, to read its error word: a device
@@ -192,7 +192,7 @@ int gf2_mmm_autotune(int64_t max_dim, int64_t *cutoff, void *stream);
 
 /* A measurement aid with no counterpart in the paper: the rate of the
  * tensor pipe for the MMA shape the tensor backend issues (tcgen05.mma
- * kind::f8f6f4, 128 x 256 x 32, e4m3 in, fp32 out) from shared memory, with
+ * kind::f8f6f4, 128 x 256 x 32, 8-bit operands in, fp32 out) from shared memory, with
  * no loads: one CTA per SM issues iters x 4 MMAs into one accumulator.
  * *tflops receives dense TFLOP/s (2 flops per multiply-add) on the current
  * device, timed by CUDA events on the stream, which it synchronises.

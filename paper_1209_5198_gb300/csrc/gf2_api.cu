@@ -1426,8 +1426,8 @@ int mmm_rec(CBView C, CBView A, CBView B, int64_t n, int64_t k, int64_t mw, bool
 
 size_t mmm_tensor_bytes(int64_t n, int64_t k, int64_t m)
 {
-    const size_t kp = (size_t)mma_pad(k > 0 ? k : 1);
-    return align_up((size_t)mma_pad(n > 0 ? n : 1) * kp) + align_up((size_t)mma_pad(m > 0 ? m : 1) * kp) + kAlign;
+    const size_t rb = (size_t)mma_row_bytes(mma_pad(k > 0 ? k : 1));
+    return align_up((size_t)mma_pad(n > 0 ? n : 1) * rb) + align_up((size_t)mma_pad(m > 0 ? m : 1) * rb) + kAlign;
 }
 
 // the tensor-core product only when the flags ask for it: measured on the
@@ -1538,12 +1538,12 @@ int mmm_impl(const gf2_mat *A, const gf2_mat *B, gf2_mat *C, int accumulate, uns
         if (st) return st;
     }
     if (tensor) {
-        // expand to e4m3 bytes, then the tcgen05 product; its device waits
+        // expand to e2m1 entries, then the tcgen05 product; its device waits
         // are bounded and report through the word after the padding flag,
         // read back with one synchronisation of the stream
         const size_t kp = (size_t)mma_pad(k);
         uint8_t *A8 = reinterpret_cast<uint8_t *>(p);
-        uint8_t *B8 = A8 + align_up((size_t)mma_pad(n) * kp);
+        uint8_t *B8 = A8 + align_up((size_t)mma_pad(n) * (size_t)mma_row_bytes((int64_t)kp));
         uint32_t *err = flag + 1;
         CK(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
         LAUNCH(GF2_KCLASS_LAYOUT, launch_expand_operands(A->w, A->ld, B->w, B->ld, (int)n, (int)k, (int)m, A8, B8, s));

@@ -216,9 +216,10 @@ bool serve_by_cluster(int64_t n);
 cudaError_t launch_serve_cluster(const ServeItem *items, int count, int64_t max_n, cudaStream_t s);
 int batch_ctas_per_sm(int c);  // c = 4 or 8: the batched kernel's table size
 // the product on the tensor cores (k < 2^24, csrc/k_umma.cu): A8 = A and
-// B8 = B^T as e4m3 bytes 0 / 1.0, K contiguous, n_pad x k_pad and m_pad x
-// k_pad bytes (dimensions rounded up to mma_pad)
+// B8 = B^T as e2m1 entries 0 / 1.0, K contiguous, n_pad and m_pad rows of
+// mma_row_bytes(k_pad) bytes (dimensions rounded up to mma_pad)
 int64_t mma_pad(int64_t x);
+int64_t mma_row_bytes(int64_t k_pad);  // bytes of one expanded operand row of k_pad entries
 cudaError_t launch_expand_operands(const uint64_t *A, int64_t lda, const uint64_t *B, int64_t ldb, int n, int k, int m,
                                    uint8_t *A8, uint8_t *B8, cudaStream_t s);
 // the tcgen05 product from the expanded operands; err: ORed with 1 when a

@@ -43,7 +43,8 @@ def test_host_only_entry_points(lib):
     # the product: M4RM needs only a status word; the tensor path the byte
     # expansions of A and B; the recursion one level's temporaries per level
     assert 0 < lib.gf2_mmm_workspace_bytes(1000, 2000, 3000, 0) <= 4096
-    assert lib.gf2_mmm_workspace_bytes(1000, 2000, 3000, 4) >= 1024 * 2048 + 3072 * 2048
+    # tensor backend: both operands expanded to e2m1 entries, two per byte
+    assert lib.gf2_mmm_workspace_bytes(1000, 2000, 3000, 4) >= (1024 * 2048 + 3072 * 2048) // 2
     import paper_1209_5198_gb300 as g
     old = g.strassen_cutoff()
     try:
