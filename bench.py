@@ -843,6 +843,16 @@ def run_ours(args):
     sched = {"auto": gf2.SCHEDULE_AUTO, "streams": gf2.SCHEDULE_STREAMS, "persistent": gf2.SCHEDULE_PERSISTENT,
              "split": gf2.SCHEDULE_SPLIT}
     opts = gf2.Opts(schedule=sched[args.schedule])
+    tuned = None
+    if args.schedule == "auto" and not args.no_tune:
+        # the library's autotuner times the speed-only options (update width,
+        # table size, schedule) on this GPU for this shape; the automatic
+        # options of every later call then take its choice
+        best = gf2.decompose_autotune(n, m, factors=True, stream=stream)
+        tuned = {"panel_w": best.opts.panel_w, "table_c": best.opts.table_c,
+                 "schedule": {1: "streams", 2: "persistent", 3: "split"}.get(best.opts.schedule, "auto"),
+                 "tuned_ms": round(best.ms, 4), "bucket": [best.bucket_n, best.bucket_m],
+                 "device": best.device.decode()}
 
     def step():
         gf2.gf2_decompose_ex(A, perm, piv, rk, L, E, opts, workspace=ws, stream=stream)
@@ -980,7 +990,7 @@ def run_ours(args):
             "vs_baseline": (PAPER_SECONDS_32768 / (ms / 1000.0)) if (n == m == 32768) else None,
             "dtype": "u64", "data": "synthetic",
             "config": {"workload": workload_name(n, m), "n": n, "m": m, "rank": r, "factors": "L,E",
-                       "schedule": args.schedule,
+                       "schedule": args.schedule, "tuned": tuned,
                        "per_rank_matrix": "independent seed per rank",
                        "l2": "no flush: working set (A 128 MiB + W + L + E, ~512 MiB) > 129 MB L2",
                        "vs_baseline_ref": "Table 4 b=128 rec 11.498 s (3.06 GHz Xeon, other machine)"},
@@ -1105,6 +1115,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the compact serving and batched measurements")
+    ap.add_argument("--no-tune", action="store_true", help="skip the decomposition autotuner (library defaults)")
     ap.add_argument("--schedule", default="auto", choices=["auto", "streams", "persistent", "split"],
                     help="decomposition schedule (gf2_opts.schedule)")
     ap.add_argument("--workload", default="decompose", choices=["decompose", "batched", "serving", "product", "sizes", "sparse"],

@@ -238,6 +238,63 @@ int gf2_decompose_ex(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t 
                      gf2_mat *L, gf2_mat *E, unsigned flags, const gf2_opts *opts,
                      void *workspace, size_t ws_bytes, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Autotuner of the decomposition (the paper tunes its block size b and
+ * table size c by hand for one CPU, Sections 6.1 and 7).  Options that
+ * change only speed -- panel_w 64 or 128 (Section 5's wide panel), table_c
+ * 4 or 8 (Section 6), and for panel_w 128 the three schedules -- are timed
+ * on the current device and the fastest is kept per (device, shape bucket).
+ * The shape bucket of an n x m matrix is the pair of powers of two at or
+ * above n and m (at least 64 each).  Every later gf2_decompose,
+ * gf2_decompose_ex, gf2_rank, gf2_decompose_host or gf2_factors_decompose
+ * call whose options leave panel_w, table_c and schedule at 0 (or NULL)
+ * uses the entry of its bucket on its device, when there is one; options
+ * never change a result.  The entries are process-wide, guarded by a lock;
+ * gf2_tune_save / gf2_tune_load write and merge them as a JSON file:
+ *   {"gf2_tune": 1, "entries": [{"device": "...", "kind": "decompose",
+ *    "bucket_n": N, "bucket_m": M, "panel_w": .., "table_c": ..,
+ *    "tile_words": .., "backend": .., "schedule": .., "strassen_cutoff": ..,
+ *    "batched_c8_from": .., "ms": ..}, ...]}
+ * (any key order and whitespace; a file of another shape is GF2_ERR_ARG and
+ * loads nothing). */
+#define GF2_TUNE_DECOMPOSE 0
+
+typedef struct gf2_tune_entry {
+    char device[64];   /* device key, as gf2_tune_device_key writes it (no quotes or backslashes) */
+    int32_t kind;      /* GF2_TUNE_DECOMPOSE */
+    int32_t reserved;  /* must be 0 */
+    int64_t bucket_n;  /* shape bucket: powers of two >= 64 */
+    int64_t bucket_m;
+    gf2_opts opts;     /* the fastest options measured for the bucket */
+    double ms;         /* their time, milliseconds per decomposition */
+} gf2_tune_entry;
+
+/* The key of the current device: its name, SM count and compute capability.
+ * Errors: GF2_ERR_ARG (out NULL or len too small), GF2_ERR_CUDA. */
+int gf2_tune_device_key(char *out, int64_t len);
+/* Inserts an entry, replacing the one of the same device, kind and bucket.
+ * Host only.  Errors: GF2_ERR_ARG (NULL, empty or unterminated device key,
+ * a key with '"', '\\' or control characters, a bucket that is not a power of
+ * two >= 64, reserved != 0, ms < 0, options gf2_opts_check rejects). */
+int gf2_tune_put(const gf2_tune_entry *e);
+/* The entry of (device, kind) for the bucket of n x m: *found = 1 and *out
+ * filled, or *found = 0.  Host only.  Errors: GF2_ERR_ARG. */
+int gf2_tune_lookup(const char *device, int32_t kind, int64_t n, int64_t m, gf2_tune_entry *out, int *found);
+int64_t gf2_tune_count(void);
+int gf2_tune_clear(void);
+/* JSON file of every entry / merge of a file's entries (GF2_ERR_ARG when the
+ * file cannot be opened or does not have the shape above). */
+int gf2_tune_save(const char *path);
+int gf2_tune_load(const char *path);
+/* Times every candidate (3 untimed calls, then the best of 3, CUDA events on
+ * `stream`) on a seeded uniform random n x m matrix made on the device, with
+ * L and E when want_factors, and stores the fastest as the entry of the
+ * bucket of n x m on the current device; *best receives it.  It allocates
+ * the matrix, the outputs and a workspace, synchronises the stream and frees
+ * them before it returns.  Errors: GF2_ERR_ARG (best NULL, n or m < 1 or
+ * >= 2^31), GF2_ERR_NOMEM, GF2_ERR_TIMEOUT, GF2_ERR_CUDA. */
+int gf2_decompose_autotune(int64_t n, int64_t m, int want_factors, gf2_tune_entry *best, void *stream);
+
 /* Reduced row echelon form, in place (Gauss-Jordan: the paper names it
  * among the uses of the decomposition, Section 1, and leaves it to the
  * textbook).  E (k x m, column blocks, device) is an echelon factor as

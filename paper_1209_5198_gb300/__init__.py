@@ -139,6 +139,21 @@ def load() -> ctypes.CDLL:
     F = ctypes.POINTER(_CFactors)
     lib.gf2_opts_check.restype = ctypes.c_int
     lib.gf2_opts_check.argtypes = [O]
+    T = ctypes.POINTER(TuneEntry)
+    lib.gf2_tune_device_key.restype = ctypes.c_int
+    lib.gf2_tune_device_key.argtypes = [ctypes.c_char_p, I64]
+    lib.gf2_tune_put.restype = ctypes.c_int
+    lib.gf2_tune_put.argtypes = [T]
+    lib.gf2_tune_lookup.restype = ctypes.c_int
+    lib.gf2_tune_lookup.argtypes = [ctypes.c_char_p, ctypes.c_int32, I64, I64, T, ctypes.POINTER(ctypes.c_int)]
+    lib.gf2_tune_count.restype = I64
+    lib.gf2_tune_clear.restype = ctypes.c_int
+    lib.gf2_tune_save.restype = ctypes.c_int
+    lib.gf2_tune_save.argtypes = [ctypes.c_char_p]
+    lib.gf2_tune_load.restype = ctypes.c_int
+    lib.gf2_tune_load.argtypes = [ctypes.c_char_p]
+    lib.gf2_decompose_autotune.restype = ctypes.c_int
+    lib.gf2_decompose_autotune.argtypes = [I64, I64, ctypes.c_int, T, P]
     lib.gf2_mmm_workspace_bytes_ex.restype = S
     lib.gf2_mmm_workspace_bytes_ex.argtypes = [I64, I64, I64, ctypes.c_uint, O]
     lib.gf2_mmm_ex.restype = ctypes.c_int
@@ -193,6 +208,15 @@ class Opts(ctypes.Structure):
                 ("backend", ctypes.c_int32), ("schedule", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("strassen_cutoff", ctypes.c_int64), ("batched_c8_from", ctypes.c_int64)]
 
+
+class TuneEntry(ctypes.Structure):
+    """gf2_tune_entry of include/gf2.h: the autotuner's choice for one
+    (device, shape bucket)."""
+    _fields_ = [("device", ctypes.c_char * 64), ("kind", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("bucket_n", ctypes.c_int64), ("bucket_m", ctypes.c_int64), ("opts", Opts), ("ms", ctypes.c_double)]
+
+
+GF2_TUNE_DECOMPOSE = 0
 
 BACKEND_AUTO, BACKEND_TABLES, BACKEND_TENSOR = 0, 1, 2
 SCHEDULE_AUTO, SCHEDULE_STREAMS, SCHEDULE_PERSISTENT, SCHEDULE_SPLIT = 0, 1, 2, 3
@@ -595,6 +619,51 @@ def mmm_autotune(max_dim: int = 32768, stream=None) -> int:
     out = ctypes.c_int64(0)
     _check(load().gf2_mmm_autotune(int(max_dim), ctypes.byref(out), _stream(stream)), "gf2_mmm_autotune")
     return int(out.value)
+
+
+def tune_device_key() -> str:
+    """The current device's key in the autotuner's table."""
+    buf = ctypes.create_string_buffer(64)
+    _check(load().gf2_tune_device_key(buf, 64), "gf2_tune_device_key")
+    return buf.value.decode()
+
+
+def tune_put(entry: TuneEntry) -> None:
+    _check(load().gf2_tune_put(ctypes.byref(entry)), "gf2_tune_put")
+
+
+def tune_lookup(device: str, n: int, m: int, kind: int = GF2_TUNE_DECOMPOSE):
+    """The entry of (device, kind) for the shape bucket of n x m, or None."""
+    out, found = TuneEntry(), ctypes.c_int(0)
+    _check(load().gf2_tune_lookup(device.encode(), kind, int(n), int(m), ctypes.byref(out), ctypes.byref(found)),
+           "gf2_tune_lookup")
+    return out if found.value else None
+
+
+def tune_count() -> int:
+    return int(load().gf2_tune_count())
+
+
+def tune_clear() -> None:
+    _check(load().gf2_tune_clear(), "gf2_tune_clear")
+
+
+def tune_save(path: str) -> None:
+    _check(load().gf2_tune_save(os.fsencode(path)), "gf2_tune_save")
+
+
+def tune_load(path: str) -> None:
+    _check(load().gf2_tune_load(os.fsencode(path)), "gf2_tune_load")
+
+
+def decompose_autotune(n: int, m: int, factors: bool = True, stream=None) -> TuneEntry:
+    """Times the decomposition's speed-only options on this device for an
+    n x m matrix, records the fastest for its shape bucket (used by later
+    calls with automatic options) and returns it."""
+    out = TuneEntry()
+    _check(load().gf2_decompose_autotune(int(n), int(m), int(bool(factors)), ctypes.byref(out), _stream(stream)),
+           "gf2_decompose_autotune")
+    return out
 
 
 def tensor_peak(iters: int = 4096, stream=None) -> float:

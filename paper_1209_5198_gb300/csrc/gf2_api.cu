@@ -12,6 +12,11 @@
 #include "../../include/gf2.h"
 #include "gf2_internal.cuh"
 
+namespace gf2 {
+// the autotuner's entry for (this device, the shape bucket of n x m), if any (csrc/tune.cu)
+bool tuned_decompose_opts(int64_t n, int64_t m, gf2_opts *out);
+}  // namespace gf2
+
 using namespace gf2;
 
 namespace {
@@ -235,6 +240,7 @@ const bool g_use_pairs = [] {
 // A gf2_opts checked and resolved for one call (0 = the process-wide value,
 // read where it is used).
 struct CallOpts {
+    int32_t automatic; // no decomposition option was given: the autotuner's entry applies, if any
     int32_t pair;      // wide updates by pairs of panels (panel_w 128) or one panel (64)
     int32_t tab_c;     // Four Russians table bits of the wide updates: 0 (automatic), 4 or 8
     int32_t schedule;  // GF2_SCHEDULE_*
@@ -262,6 +268,7 @@ int check_opts(const gf2_opts *o)
 CallOpts resolve_opts(const gf2_opts *o)
 {
     CallOpts r{};
+    r.automatic = !o || (o->panel_w == 0 && o->table_c == 0 && o->schedule == GF2_SCHEDULE_AUTO);
     r.pair = (o && o->panel_w) ? (o->panel_w == 128) : (g_use_pairs ? 1 : 0);
     r.tab_c = o ? o->table_c : 0;
     r.schedule = o ? o->schedule : GF2_SCHEDULE_AUTO;
@@ -492,10 +499,20 @@ DecompLayout decomp_layout(int64_t n, int64_t m, bool factors)
 }
 
 int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *rank, gf2_mat *L, gf2_mat *E,
-                   unsigned flags, const CallOpts &o, void *workspace, size_t ws_bytes, cudaStream_t s)
+                   unsigned flags, const CallOpts &o_in, void *workspace, size_t ws_bytes, cudaStream_t s)
 {
     if (!mat_ok(A) || !perm || !rank || (flags & ~GF2_NOCHECK)) return GF2_ERR_ARG;
     const int64_t n = A->rows, m = A->cols;
+    CallOpts o = o_in;
+    if (o.automatic) {
+        // automatic options: the autotuner's choice for this shape bucket, when it has one
+        gf2_opts t{};
+        if (tuned_decompose_opts(n, m, &t)) {
+            if (t.panel_w) o.pair = t.panel_w == 128;
+            o.tab_c = t.table_c;
+            o.schedule = t.schedule;
+        }
+    }
     if (n >= (1ll << 31) - 64 || m >= (1ll << 31) - 64) return GF2_ERR_UNSUPPORTED;
     const int64_t kmax = n < m ? n : m;
     if (kmax > 0 && !pivcols) return GF2_ERR_ARG;
