@@ -471,7 +471,29 @@ def run_product(args):
         "gpu_launches": main.get("launches_per_step"),
         "clocks": main.get("clocks"),
     }
+    # the tcgen05 backend against the tensor pipe: the probe of its MMA shape
+    # (kind::f8f6f4 128 x 256 x 32 from shared memory) and the measured bf16
+    # GEMM rate x 2 (the nominal fp8 / bf16 ratio)
+    if main.get("tensor_ms"):
+        probe = gf2.tensor_peak(4096)
+        tflops = 2.0 * n ** 3 / (main["tensor_ms"] / 1000) / 1e12
+        bf16 = measured_peaks().get("bf16_tflops")
+        line["tensor_roofline"] = {
+            "kernel": "k_umma (tcgen05 kind::f8f6f4, e2m1 operands by TMA, fp32 accumulators in tensor memory)",
+            "bound": "tensor", "achieved": tflops, "unit": "TFLOP/s", "peak": probe, "frac": tflops / probe,
+            "peak_source": "gf2_tensor_peak probe on this GPU (its MMA shape from shared memory, no loads)",
+            "fp8_from_measured_bf16": (2.0 * bf16) if bf16 else None,
+            "frac_of_fp8_from_measured_bf16": (tflops / (2.0 * bf16)) if bf16 else None,
+            "ms": main["tensor_ms"], "includes": "operand expansion (two kernels) + the tcgen05 kernel"}
     print(json.dumps(line), flush=True)
+
+
+def measured_peaks() -> dict:
+    """The measured peaks of this machine's GPUs ({} when absent)."""
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
 
 
 def product_cpu_sample(n: int, seconds: float):
