@@ -203,6 +203,40 @@ def rhs_from_solution(n_rhs: int, m: int, seed: int = BASE_SEED, *tags: int) -> 
     return uniform(m, n_rhs, seed, 5, *tags)
 
 
+# ---------------------------------------------------------------- F_p
+
+def fp_uniform(n: int, m: int, p: int, seed: int = BASE_SEED, *tags: int) -> np.ndarray:
+    """n x m matrix of residues mod p (int64), entry (i, j) = the high 32 bits
+    of draw i*m + j, times p, over 2^32 (uniform up to a bias below p/2^32)."""
+    assert 2 <= p < 2 ** 31
+    key = stream_key(seed, 20, n, m, p, *tags)
+    hi = (draws(key, 0, n * m) >> np.uint64(32)).astype(np.uint64)
+    return ((hi * np.uint64(p)) >> np.uint64(32)).astype(np.int64).reshape(n, m)
+
+
+def fp_fixed_rank_factors(n: int, m: int, r: int, p: int, seed: int = BASE_SEED, *tags: int):
+    """Factors X (n x r) and Y (r x m) of full rank r over F_p (int64 residues):
+    X = P1 [T; G] with T unit lower triangular, Y = [U H] P2 with U unit upper
+    triangular, G, H and the off-diagonal entries uniform, P1 / P2 random row /
+    column permutations.  X Y mod p has rank exactly r; the product is left to
+    the caller."""
+    assert 0 <= r <= min(n, m)
+    key = stream_key(seed, 21, n, m, r, p, *tags)
+    tg = fp_uniform(n, r, p, key, 1)
+    i = np.arange(r)
+    if r:
+        tg[:r] = np.where(i[None, :] < i[:, None], tg[:r], 0)
+        tg[i, i] = 1
+    X = np.ascontiguousarray(tg[permutation(n, stream_key(key, 2))])
+    uh = fp_uniform(r, m, p, key, 3)
+    if r:
+        cols = np.arange(m)
+        uh[:, :r] = np.where(cols[None, :r] > i[:, None], uh[:, :r], 0)
+        uh[i, i] = 1
+    Y = np.ascontiguousarray(uh[:, permutation(m, stream_key(key, 4))])
+    return X, Y
+
+
 # ---------------------------------------------------------------- packing
 
 def pack_bits(bits: np.ndarray, b: int = 64) -> np.ndarray:
