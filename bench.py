@@ -655,6 +655,55 @@ def run_sparse(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ F_p
+
+FP_METRIC = "decomposition over F_p: multiply-adds mod p per second (P*A = L*E, uniform residues)"
+
+
+def run_fp(args):
+    """The decomposition over a prime field F_p (the remark after eq.
+    (cond:nonsing:Bk)): uniform residues mod p from the seeded generator, n x n
+    for n in --fp-sizes, p = 65521 and 2^31 - 1; time per decomposition (L and
+    E), and multiply-adds per second counted as sum over pivots t of
+    (n - t - 1)(m - q_t).  value = the largest n with p = 65521."""
+    import torch
+
+    import f2gen
+    import paper_1209_5198_gb300 as gf2
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    lib = gf2.load()
+    rows = []
+    for n in args.fp_sizes:
+        for p in (65521, 2147483647):
+            A = torch.from_numpy(f2gen.fp_uniform(n, n, p, f2gen.BASE_SEED, 30).astype(np.int32)).to(dev)
+            ws = torch.empty(lib.gf2_fp_decompose_workspace_bytes(n, n), dtype=torch.uint8, device=dev)
+            fn = lambda: gf2.fp_decompose(A, p, flags=gf2.GF2_NOCHECK, workspace=ws, stream=stream)
+            for _ in range(max(1, args.warmup)):
+                out = fn()
+            ms = time_calls(fn, 2, stream)
+            out = fn()
+            torch.cuda.synchronize()
+            rank = int(out["rank"].item())
+            piv = out["pivcols"].cpu().numpy()[:rank].astype(np.float64)
+            t = np.arange(rank, dtype=np.float64)
+            madds = float(np.sum((n - t - 1) * (n - piv)))
+            rows.append({"n": n, "p": p, "rank": rank, "ms": ms, "madds_per_s": madds / (ms / 1000)})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+            del A, ws, out
+            torch.cuda.empty_cache()
+    main = max((x for x in rows if x["p"] == 65521), key=lambda x: x["n"])
+    line = {
+        "metric": FP_METRIC, "value": main["madds_per_s"], "unit": "madd/s", "n_gpus": 1, "steps": 2,
+        "warmup": max(1, args.warmup), "ms_per_step": main["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32 mod p", "data": "synthetic",
+        "config": {"workload": f"decomposition over F_p of n x n uniform residues; value = n {main['n']}, "
+                               f"p = {main['p']}", "configs": rows},
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ serving
 
 SERVE_METRIC = "served solves/s (rank + solve requests on resident factors, continuous batching)"
@@ -1138,9 +1187,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the compact serving and batched measurements")
     ap.add_argument("--no-tune", action="store_true", help="skip the decomposition autotuner (library defaults)")
+    ap.add_argument("--fp-sizes", type=int, nargs="+", default=[1024, 4096, 8192], help="n of the F_p workload")
     ap.add_argument("--schedule", default="auto", choices=["auto", "streams", "persistent", "split"],
                     help="decomposition schedule (gf2_opts.schedule)")
-    ap.add_argument("--workload", default="decompose", choices=["decompose", "batched", "serving", "product", "sizes", "sparse"],
+    ap.add_argument("--workload", default="decompose", choices=["decompose", "batched", "serving", "product", "sizes", "sparse", "fp"],
                     help="decompose: the headline 32768^2 decomposition; batched: many small matrices in one "
                          "launch; serving: a request stream on resident factors")
     ap.add_argument("--requests", type=int, default=20000, help="requests in the serving trace")
@@ -1158,6 +1208,8 @@ def main():
         run_serving(args)
     elif args.workload == "product":
         run_product(args)
+    elif args.workload == "fp":
+        run_fp(args)
     elif args.workload == "sparse":
         run_sparse(args)
     elif args.workload == "sizes":

@@ -190,6 +190,36 @@ int gf2_mmm_ex(const gf2_mat *A, const gf2_mat *B, gf2_mat *C, int accumulate, u
  * GF2_ERR_NOMEM, GF2_ERR_CUDA. */
 int gf2_mmm_autotune(int64_t max_dim, int64_t *cutoff, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Decomposition over a prime field F_p (the remark after eq.
+ * (cond:nonsing:Bk), Section 4.2: over F_q the pivot condition becomes "the
+ * reduced entry beta is nonzero" and beta stays on the diagonal).  A is n x
+ * m, row-major 32-bit residues (entry (i, j) at A[i*lda + j], device, read
+ * only, every entry < p), p a prime with 2 <= p < 2^31.  Column by column,
+ * the first row in the current order whose reduced entry is nonzero is
+ * exchanged into the pivot slot and the rows after it are eliminated; no
+ * column is exchanged.  Outputs (device, owned by the caller):
+ *   perm[n]      (P A)[i] = A[perm[i]]
+ *   pivcols[k]   the r pivot columns, increasing, then -1 (k = min(n, m))
+ *   *rank        r (int64; -1 if a bounded device wait gave up)
+ *   L (optional) n x k row-major (ldl >= k): unit lower trapezoidal, columns
+ *                >= r zero
+ *   E (optional) k x m row-major (lde >= m): row echelon, E[t][pivcols[t]] =
+ *                beta_t != 0, zero before it; rows >= r zero
+ * with P A = L E (mod p); for p = 2 the factors equal gf2_decompose's.
+ * Asynchronous on `stream`, except the entry check (skipped with
+ * GF2_NOCHECK), which synchronises it once.  Workspace:
+ * gf2_fp_decompose_workspace_bytes(n, m) (about 4 n m bytes), or NULL for the
+ * library's own.  Errors: GF2_ERR_ARG (p not a prime in [2, 2^31), NULL
+ * pointers, an entry >= p), GF2_ERR_SHAPE (lda < m, ldl < k, lde < m),
+ * GF2_ERR_NOMEM, GF2_ERR_UNSUPPORTED (n or m >= 2^31, or no cooperative
+ * launch), GF2_ERR_CUDA. */
+size_t gf2_fp_decompose_workspace_bytes(int64_t n, int64_t m);
+int gf2_fp_is_prime(uint32_t p);
+int gf2_fp_decompose(const uint32_t *A, int64_t lda, int64_t n, int64_t m, uint32_t p, int32_t *perm,
+                     int32_t *pivcols, int64_t *rank, uint32_t *L, int64_t ldl, uint32_t *E, int64_t lde,
+                     unsigned flags, void *workspace, size_t ws_bytes, void *stream);
+
 /* A measurement aid with no counterpart in the paper: the rate of the
  * tensor pipe for the MMA shape the tensor backend issues (tcgen05.mma
  * kind::f8f6f4, 128 x 256 x 32, 8-bit operands in, fp32 out) from shared memory, with

@@ -89,6 +89,12 @@ def load() -> ctypes.CDLL:
     lib.gf2_mmm_autotune.argtypes = [I64, ctypes.POINTER(I64), P]
     lib.gf2_tensor_peak.restype = ctypes.c_int
     lib.gf2_tensor_peak.argtypes = [I64, ctypes.POINTER(ctypes.c_double), P]
+    lib.gf2_fp_decompose_workspace_bytes.restype = S
+    lib.gf2_fp_decompose_workspace_bytes.argtypes = [I64, I64]
+    lib.gf2_fp_is_prime.restype = ctypes.c_int
+    lib.gf2_fp_is_prime.argtypes = [ctypes.c_uint32]
+    lib.gf2_fp_decompose.restype = ctypes.c_int
+    lib.gf2_fp_decompose.argtypes = [P, I64, I64, I64, ctypes.c_uint32, P, P, P, P, I64, P, I64, ctypes.c_uint, P, S, P]
     lib.gf2_mmm_set_strassen_cutoff.restype = ctypes.c_int
     lib.gf2_mmm_set_strassen_cutoff.argtypes = [I64]
     lib.gf2_mmm_strassen_cutoff.restype = I64
@@ -664,6 +670,34 @@ def decompose_autotune(n: int, m: int, factors: bool = True, stream=None) -> Tun
     _check(load().gf2_decompose_autotune(int(n), int(m), int(bool(factors)), ctypes.byref(out), _stream(stream)),
            "gf2_decompose_autotune")
     return out
+
+
+def fp_decompose(A: torch.Tensor, p: int, factors: bool = True, flags: int = 0, workspace=None, stream=None) -> dict:
+    """P A = L E over the prime field F_p (gf2_fp_decompose): A is an n x m
+    int32 CUDA tensor of residues (row-major, rows contiguous).  Returns perm,
+    pivcols, rank (int64 tensor; -1 when a bounded device wait gave up) and,
+    with factors, L (n x k) and E (k x m) as int32 tensors of residues."""
+    if A.dtype != torch.int32 or A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("expected a 2-d int32 tensor with contiguous rows")
+    n, m = A.shape
+    k = min(n, m)
+    dev = A.device
+    lib = load()
+    perm = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    piv = torch.empty(max(k, 1), dtype=torch.int32, device=dev)
+    rank = torch.zeros(1, dtype=torch.int64, device=dev)
+    L = torch.empty((n, k), dtype=torch.int32, device=dev) if factors else None
+    E = torch.empty((k, m), dtype=torch.int32, device=dev) if factors else None
+    if workspace is None:
+        workspace = _workspace(lib.gf2_fp_decompose_workspace_bytes(n, m), dev)
+    _check(lib.gf2_fp_decompose(A.data_ptr() if A.numel() else None, max(A.stride(0), m), n, m, int(p), perm.data_ptr(),
+                                piv.data_ptr(), rank.data_ptr(), _ptr(L), max(k, 1), _ptr(E), max(m, 1), flags,
+                                workspace.data_ptr(), workspace.numel(), _stream(stream)), "gf2_fp_decompose")
+    return dict(perm=perm[:n], pivcols=piv[:k], rank=rank, L=L, E=E)
+
+
+def fp_is_prime(p: int) -> bool:
+    return bool(load().gf2_fp_is_prime(int(p)))
 
 
 def tensor_peak(iters: int = 4096, stream=None) -> float:

@@ -15,6 +15,11 @@
 namespace gf2 {
 // the autotuner's entry for (this device, the shape bucket of n x m), if any (csrc/tune.cu)
 bool tuned_decompose_opts(int64_t n, int64_t m, gf2_opts *out);
+// the decomposition over F_p (csrc/k_gfp.cu)
+size_t fp_workspace_bytes(int64_t n, int64_t m);
+int fp_decompose(const uint32_t *A, int64_t lda, int64_t n, int64_t m, uint32_t p, int32_t *perm, int32_t *pivcols,
+                 int64_t *rank, uint32_t *L, int64_t ldl, uint32_t *E, int64_t lde, bool check, void *ws,
+                 uint32_t wait_limit, cudaStream_t s);
 }  // namespace gf2
 
 using namespace gf2;
@@ -1625,6 +1630,39 @@ int time_product(uint64_t *A, uint64_t *B, uint64_t *C, uint64_t *tmp, int64_t d
 }  // namespace
 
 extern "C" {
+
+size_t gf2_fp_decompose_workspace_bytes(int64_t n, int64_t m)
+{
+    if (n < 0 || m < 0) return 0;
+    return fp_workspace_bytes(n, m);
+}
+
+int gf2_fp_is_prime(uint32_t p)
+{
+    if (p < 2) return 0;
+    for (uint32_t d = 2; (uint64_t)d * d <= p; ++d)
+        if (p % d == 0) return 0;
+    return 1;
+}
+
+int gf2_fp_decompose(const uint32_t *A, int64_t lda, int64_t n, int64_t m, uint32_t p, int32_t *perm,
+                     int32_t *pivcols, int64_t *rank, uint32_t *L, int64_t ldl, uint32_t *E, int64_t lde,
+                     unsigned flags, void *workspace, size_t ws_bytes, void *stream)
+{
+    if (n < 0 || m < 0 || !rank || (flags & ~GF2_NOCHECK)) return GF2_ERR_ARG;
+    if (p < 2 || p >= (1u << 31) || !gf2_fp_is_prime(p)) return GF2_ERR_ARG;
+    if (n >= (1ll << 31) || m >= (1ll << 31)) return GF2_ERR_UNSUPPORTED;
+    const int64_t k = n < m ? n : m;
+    if ((n > 0 && !perm) || (k > 0 && !pivcols) || (n > 0 && m > 0 && !A)) return GF2_ERR_ARG;
+    if (n > 0 && m > 0 && lda < m) return GF2_ERR_SHAPE;
+    if (L && k > 0 && ldl < k) return GF2_ERR_SHAPE;
+    if (E && k > 0 && lde < m) return GF2_ERR_SHAPE;
+    void *ws = nullptr;
+    int st = get_workspace(workspace, ws_bytes, fp_workspace_bytes(n, m), &ws);
+    if (st) return st;
+    return fp_decompose(A, lda, n, m, p, perm, pivcols, rank, L, ldl, E, lde, !(flags & GF2_NOCHECK), ws,
+                        (uint32_t)device_wait_limit(1ll << 24), static_cast<cudaStream_t>(stream));
+}
 
 int gf2_tensor_peak(int64_t iters, double *tflops, void *stream)
 {
