@@ -212,8 +212,8 @@ int gf2_mmm_autotune(int64_t max_dim, int64_t *cutoff, void *stream);
  * gf2_fp_decompose_workspace_bytes(n, m) (about 4 n m bytes), or NULL for the
  * library's own.  Errors: GF2_ERR_ARG (p not a prime in [2, 2^31), NULL
  * pointers, an entry >= p), GF2_ERR_SHAPE (lda < m, ldl < k, lde < m),
- * GF2_ERR_NOMEM, GF2_ERR_UNSUPPORTED (n or m >= 2^31, or no cooperative
- * launch), GF2_ERR_CUDA. */
+ * GF2_ERR_NOMEM, GF2_ERR_UNSUPPORTED (n or m >= 2^31, n above 1024 rows per
+ * SM of the device, or no cooperative launch), GF2_ERR_CUDA. */
 size_t gf2_fp_decompose_workspace_bytes(int64_t n, int64_t m);
 int gf2_fp_is_prime(uint32_t p);
 int gf2_fp_decompose(const uint32_t *A, int64_t lda, int64_t n, int64_t m, uint32_t p, int32_t *perm,

@@ -14,15 +14,18 @@
 // Block columns of kFpB = 32 columns:
 //   k_fp_load     the block column of every row into a column-major panel
 //                 buffer (a column of the block is contiguous over the rows);
-//   k_fp_panel    one cooperative launch for the block: per column, every
-//                 CTA finds its first candidate (min position with a nonzero
-//                 entry among the non-pivot rows, one 64-bit atomicMin of
-//                 (position, row)), a grid barrier, then every non-pivot row
-//                 takes its multiplier l = entry * beta^-1 (stored in place:
-//                 the L entry) and subtracts l x the pivot row from its
-//                 later block columns; thread 0 of CTA 0 records the
-//                 exchange; a second barrier.  Every wait is bounded and a
-//                 give-up sets the error word (GF2_ERR_TIMEOUT);
+//   k_fp_panel    one cooperative launch for the block (at most one CTA per
+//                 SM, each keeping its rows' block entries, pivot marks and
+//                 positions in shared memory), one grid barrier per column:
+//                 every CTA posts its first candidate (min position with a
+//                 nonzero entry among its non-pivot rows, one 64-bit
+//                 atomicMin of (position, row)) and copies that row's entries
+//                 to its slot; after the barrier every CTA reads the winner's
+//                 slot (the pivot row), eliminates its non-pivot rows
+//                 (multiplier l = entry * beta^-1, stored in place: the L
+//                 entry) and applies the exchange to the rows it owns, while
+//                 thread 0 of CTA 0 records it in global memory.  Every wait
+//                 is bounded and a give-up leaves rank -1;
 //   k_fp_store    the block back into the working copy;
 //   k_fp_trsm     the block's pivot rows on the trailing columns: forward
 //                 substitution with the block's unit lower multipliers;
@@ -44,7 +47,7 @@ namespace {
 
 constexpr int kFpB = 32;           // columns per block column
 constexpr int kFpThreads = 256;
-constexpr int kFpRowsPerCta = 64;  // rows per CTA of the cooperative panel launch, at most one CTA per SM
+constexpr int kFpMaxRowsPerCta = 1024;  // rows one panel CTA keeps in shared memory (128 KB of the block)
 
 struct FpCtx {
     uint32_t *W;        // [n][ldw] working copy, row-major by storage row
@@ -56,6 +59,8 @@ struct FpCtx {
     int32_t *pivcols;   // [k] pivot columns (-1 past the rank)
     int32_t *rank;      // [0] pivots so far, [1] pivots before the current block column
     unsigned long long *found;  // [kFpB] per block column: (position << 32 | row) of its pivot, ~0 = none
+    uint32_t *cand;     // [2][grid][kFpB] per column parity and panel CTA: the block entries of its candidate
+                        // row (two slots: a CTA writes the next column's while others may still read this one's)
     uint32_t *sync;     // [0] barrier count (zeroed before every panel launch), [1] error word
     int32_t n, m, k;
     uint32_t p;
@@ -167,64 +172,109 @@ __global__ void k_fp_store(FpCtx c, int j0, int bw)
 }
 
 // The pivot steps of the block column [j0, j0 + bw) (cooperative launch).
-__global__ void __launch_bounds__(kFpThreads) k_fp_panel(FpCtx c, int j0, int bw)
+// CTA b owns the rows [b rpc, (b+1) rpc): their block entries, pivot marks
+// and positions live in its shared memory for the whole launch.  Per column,
+// one grid barrier: before it every CTA posts its first candidate (the
+// smallest (position, row) among its non-pivot rows with a nonzero entry:
+// one 64-bit atomicMin) and copies that row's block entries to its slot of
+// c.cand; after it every CTA reads the winner's slot (the pivot row), takes
+// l = entry beta^-1 for each of its non-pivot rows (stored in place: the L
+// entry) and subtracts l x the pivot row from the later block columns, and
+// applies the exchange to the rows it owns (the row at position R, found by
+// its position, moves to the pivot's; the pivot row takes position R).  The
+// global positions, pivot marks and perm are written back at the end, each
+// CTA for its own rows, so nothing global is read while another CTA writes it.
+__global__ void __launch_bounds__(kFpThreads) k_fp_panel(FpCtx c, int j0, int bw, int rpc)
 {
+    extern __shared__ uint32_t fp_smem[];
+    uint32_t *vals = fp_smem;                                   // [kFpB][rpc]
+    int32_t *spiv = reinterpret_cast<int32_t *>(vals + kFpB * rpc);  // [rpc]
+    int32_t *spos = spiv + rpc;                                 // [rpc]
+    __shared__ uint32_t pivrow[kFpB];
     __shared__ unsigned long long s_min;
+    __shared__ uint32_t s_inv;
     __shared__ int s_ok;
     uint32_t epoch = 0;
+    const int tid = threadIdx.x;
+    const int row0 = blockIdx.x * rpc;
+    const int nr = max(0, min(rpc, c.n - row0));
     // the same in every CTA: CTA 0 writes it only at the end, after every CTA
     // has passed the barriers (all read it before their first one)
     int R = c.rank[0];
-    if (blockIdx.x == 0 && threadIdx.x == 0) c.rank[1] = R;
-    const int stride = gridDim.x * blockDim.x;
-    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0 && tid == 0) c.rank[1] = R;
+    for (int e = tid; e < bw * nr; e += kFpThreads) {
+        const int cc = e / nr, r = e % nr;
+        vals[cc * rpc + r] = c.P[(int64_t)cc * c.n + row0 + r];
+    }
+    for (int r = tid; r < nr; r += kFpThreads) {
+        spiv[r] = c.piv[row0 + r];
+        spos[r] = c.pos[row0 + r];
+    }
+    __syncthreads();
     for (int col = 0; col < bw && R < c.k; ++col) {
-        // first candidate: the smallest position among the non-pivot rows with a nonzero entry
-        if (threadIdx.x == 0) s_min = ~0ull;
-        __syncthreads();
-        // (positions, pivot marks and the pivot row's entries are written by
-        // other CTAs during the launch: read through L2, never from L1)
+        // this CTA's first candidate, and its row's block entries to its slot
         unsigned long long best = ~0ull;
-        const uint32_t *Pc = c.P + (int64_t)col * c.n;
-        for (int i = t0; i < c.n; i += stride)
-            if (__ldcg(c.piv + i) < 0 && __ldcg(Pc + i) != 0) {
-                const unsigned long long key = ((unsigned long long)(uint32_t)__ldcg(c.pos + i) << 32) | (uint32_t)i;
+        for (int r = tid; r < nr; r += kFpThreads)
+            if (spiv[r] < 0 && vals[col * rpc + r] != 0) {
+                const unsigned long long key = ((unsigned long long)(uint32_t)spos[r] << 32) | (uint32_t)(row0 + r);
                 best = key < best ? key : best;
             }
+        if (tid == 0) s_min = ~0ull;
+        __syncthreads();
         if (best != ~0ull) atomicMin(&s_min, best);
         __syncthreads();
-        if (threadIdx.x == 0 && s_min != ~0ull) atomicMin(c.found + col, s_min);
+        const unsigned long long mine = s_min;
+        if (mine != ~0ull) {
+            const int rl = (int)(mine & 0xFFFFFFFFu) - row0;
+            if (tid >= col && tid < bw)
+                c.cand[((int64_t)(col & 1) * gridDim.x + blockIdx.x) * kFpB + tid] = vals[tid * rpc + rl];
+            if (tid == 0) atomicMin(c.found + col, mine);
+        }
         if (!fp_barrier(c, epoch, &s_ok)) return;
         const unsigned long long f = *reinterpret_cast<volatile unsigned long long *>(c.found + col);
-        if (f == ~0ull) continue;  // no pivot in this column (every CTA sees the same)
+        if (f == ~0ull) continue;  // no pivot in this column (every CTA sees the same); nothing moved
         const int fpos = (int)(f >> 32), prow = (int)(f & 0xFFFFFFFFu);
-        const uint32_t beta = __ldcg(Pc + prow);
-        const uint32_t inv = inv_p(beta, c.p, c.pinv);
-        for (int i = t0; i < c.n; i += stride) {
-            if (i == prow || __ldcg(c.piv + i) >= 0) continue;
-            const uint32_t a = __ldcg(Pc + i);
+        const int owner = prow / rpc;
+        if (tid >= col && tid < bw) pivrow[tid] = __ldcg(c.cand + ((int64_t)(col & 1) * gridDim.x + owner) * kFpB + tid);
+        __syncthreads();
+        if (tid == 0) s_inv = inv_p(pivrow[col], c.p, c.pinv);
+        __syncthreads();
+        const uint32_t inv = s_inv;
+        const int prl = prow - row0;  // the pivot row's local index (if this CTA owns it)
+        for (int r = tid; r < nr; r += kFpThreads) {
+            if (r == prl || spiv[r] >= 0) continue;
+            const uint32_t a = vals[col * rpc + r];
             if (a == 0) continue;  // multiplier 0: nothing to subtract (the entry already holds it)
             const uint32_t l = mul_p(a, inv, c.p, c.pinv);
-            for (int cc = col + 1; cc < bw; ++cc) {
-                uint32_t *Pi = c.P + (int64_t)cc * c.n;
-                Pi[i] = sub_p(__ldcg(Pi + i), mul_p(l, __ldcg(Pi + prow), c.p, c.pinv), c.p);
-            }
-            c.P[(int64_t)col * c.n + i] = l;  // the L entry, in place of the eliminated one
+            for (int cc = col + 1; cc < bw; ++cc)
+                vals[cc * rpc + r] = sub_p(vals[cc * rpc + r], mul_p(l, pivrow[cc], c.p, c.pinv), c.p);
+            vals[col * rpc + r] = l;  // the L entry, in place of the eliminated one
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            // exchange positions R and fpos; the pivot row becomes pivot R
-            const int rowR = __ldcg(c.perm + R);
-            c.perm[R] = prow;
-            c.perm[fpos] = rowR;
-            c.pos[prow] = R;
-            c.pos[rowR] = fpos;
-            c.piv[prow] = R;
-            c.pivcols[R] = j0 + col;
+        // the exchange of positions R and fpos, on the rows this CTA owns: the
+        // row at position R moves to fpos, the pivot row becomes pivot R
+        __syncthreads();
+        for (int r = tid; r < nr; r += kFpThreads)
+            if (r != prl && spos[r] == R) spos[r] = fpos;
+        if (tid == 0 && prl >= 0 && prl < nr) {
+            spiv[prl] = R;
+            spos[prl] = R;
         }
+        if (blockIdx.x == 0 && tid == 0) c.pivcols[R] = j0 + col;
+        __syncthreads();
         ++R;
-        if (!fp_barrier(c, epoch, &s_ok)) return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) c.rank[0] = R;
+    // the block entries, pivot marks and positions of this CTA's rows back
+    // to global memory (every position is some row's: perm stays a permutation)
+    for (int e = tid; e < bw * nr; e += kFpThreads) {
+        const int cc = e / nr, r = e % nr;
+        c.P[(int64_t)cc * c.n + row0 + r] = vals[cc * rpc + r];
+    }
+    for (int r = tid; r < nr; r += kFpThreads) {
+        c.piv[row0 + r] = spiv[r];
+        c.pos[row0 + r] = spos[r];
+        c.perm[spos[r]] = row0 + r;
+    }
+    if (blockIdx.x == 0 && tid == 0) c.rank[0] = R;
 }
 
 // The pivot rows of the block (positions R0 .. R1-1: the ranks before and
@@ -342,7 +392,7 @@ size_t fp_workspace_bytes(int64_t n, int64_t m)
     const int64_t k = n < m ? n : m;
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     return al((size_t)n * m * 4) + al((size_t)kFpB * n * 4) + 3 * al((size_t)n * 4) + al((size_t)(k > 0 ? k : 1) * 4) +
-           al(8) + al(kFpB * 8) + al(16) + al(4);
+           al(8) + al(kFpB * 8) + al(16) + al(4) + al((size_t)2 * 1024 * kFpB * 4);
 }
 
 int fp_decompose(const uint32_t *A, int64_t lda, int64_t n, int64_t m, uint32_t p, int32_t *perm, int32_t *pivcols,
@@ -364,7 +414,8 @@ int fp_decompose(const uint32_t *A, int64_t lda, int64_t n, int64_t m, uint32_t 
     c.rank = reinterpret_cast<int32_t *>(b); b += al(8);
     c.found = reinterpret_cast<unsigned long long *>(b); b += al(kFpB * 8);
     c.sync = reinterpret_cast<uint32_t *>(b); b += al(16);
-    uint32_t *bad = reinterpret_cast<uint32_t *>(b);
+    uint32_t *bad = reinterpret_cast<uint32_t *>(b); b += al(4);
+    c.cand = reinterpret_cast<uint32_t *>(b);  // room for 2 x 1024 CTAs
     c.ldw = m;
     c.n = (int32_t)n;
     c.m = (int32_t)m;
@@ -374,14 +425,21 @@ int fp_decompose(const uint32_t *A, int64_t lda, int64_t n, int64_t m, uint32_t 
     c.two64 = (uint32_t)((((unsigned __int128)1) << 64) % p);
     c.wait_limit = wait_limit;
 
+    // the panel launch: one CTA per SM at most, rpc rows each in shared memory
     int dev = 0, sms = 1, coop = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fp_panel, kFpThreads, 0) != cudaSuccess)
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess)
+        return GF2_ERR_CUDA;
+    if (sms > 1024) sms = 1024;
+    int grid = (int)((n + kFpThreads - 1) / kFpThreads);  // at least a row per thread
+    grid = grid < 1 ? 1 : (grid > sms ? sms : grid);
+    const int rpc = (int)((n + grid - 1) / grid);
+    if (rpc > kFpMaxRowsPerCta) return GF2_ERR_UNSUPPORTED;
+    const size_t smem = (size_t)rpc * (kFpB + 2) * 4;
+    if (cudaFuncSetAttribute(k_fp_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fp_panel, kFpThreads, smem) != cudaSuccess)
         return GF2_ERR_CUDA;
     if (!coop || per_sm < 1) return GF2_ERR_UNSUPPORTED;
-    int grid = (int)((n + kFpRowsPerCta - 1) / kFpRowsPerCta);
-    grid = grid < 1 ? 1 : (grid > sms ? sms : grid);
 
     if (cudaMemsetAsync(c.rank, 0, 8, s) != cudaSuccess || cudaMemsetAsync(c.sync, 0, 16, s) != cudaSuccess ||
         cudaMemsetAsync(bad, 0, 4, s) != cudaSuccess)
@@ -404,10 +462,10 @@ int fp_decompose(const uint32_t *A, int64_t lda, int64_t n, int64_t m, uint32_t 
         // the grid barrier counts from zero in every panel launch (the error word stays)
         if (cudaMemsetAsync(c.sync, 0, sizeof(uint32_t), s) != cudaSuccess) return GF2_ERR_CUDA;
         FpCtx arg = c;
-        int j0i = (int)j0, bwi = bw;
-        void *args[] = {&arg, &j0i, &bwi};
-        if (cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_fp_panel), dim3(grid), dim3(kFpThreads), args, 0,
-                                        s) != cudaSuccess)
+        int j0i = (int)j0, bwi = bw, rpci = rpc;
+        void *args[] = {&arg, &j0i, &bwi, &rpci};
+        if (cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_fp_panel), dim3(grid), dim3(kFpThreads), args,
+                                        smem, s) != cudaSuccess)
             return GF2_ERR_CUDA;
         k_fp_store<<<blocks_for((int64_t)n * bw, 256), 256, 0, s>>>(c, (int)j0, bw);
         const int jt = (int)(j0 + bw);

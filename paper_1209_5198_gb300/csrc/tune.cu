@@ -218,6 +218,10 @@ __global__ void k_tune_fill(uint64_t *A, int64_t n, int64_t mu, uint64_t last_ma
 
 bool tuned_decompose_opts(int64_t n, int64_t m, gf2_opts *out)
 {
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        if (g_tune.empty()) return false;  // nothing tuned: no device query at all
+    }
     gf2_tune_entry key{};
     if (gf2_tune_device_key(key.device, sizeof(key.device)) != GF2_OK) return false;
     key.kind = GF2_TUNE_DECOMPOSE;
@@ -241,17 +245,30 @@ extern "C" {
 int gf2_tune_device_key(char *out, int64_t len)
 {
     if (!out || len < 1) return GF2_ERR_ARG;
-    int dev = 0, sms = 0;
-    cudaDeviceProp prop;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    // the key of each device is made once (reading the device properties is
+    // slow) and then copied: every decomposition with automatic options asks
+    constexpr int kMaxDev = 64;
+    static std::mutex mu;
+    static char keys[kMaxDev][sizeof(((gf2_tune_entry *)nullptr)->device)] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
         cudaGetLastError();
         return GF2_ERR_CUDA;
     }
-    char buf[sizeof(((gf2_tune_entry *)nullptr)->device)];
-    snprintf(buf, sizeof(buf), "%s sm%d cc%d.%d", prop.name, sms, prop.major, prop.minor);
-    for (char *c = buf; *c; ++c)
-        if (*c == '"' || *c == '\\') *c = '_';  // nothing the JSON file would have to escape
+    std::lock_guard<std::mutex> lock(mu);
+    char *buf = keys[dev];
+    if (!buf[0]) {
+        int sms = 0;
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return GF2_ERR_CUDA;
+        }
+        snprintf(buf, sizeof(keys[0]), "%s sm%d cc%d.%d", prop.name, sms, prop.major, prop.minor);
+        for (char *c = buf; *c; ++c)
+            if (*c == '"' || *c == '\\' || (unsigned char)*c < 0x20) *c = '_';  // nothing the JSON file would escape
+    }
     if ((int64_t)strlen(buf) >= len) return GF2_ERR_ARG;
     memcpy(out, buf, strlen(buf) + 1);
     return GF2_OK;
