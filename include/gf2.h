@@ -253,6 +253,14 @@ int64_t gf2_mmm_strassen_cutoff(void);
  * The factors are the bit-level PLE form (remark after Lemma 4.1: the block
  * decomposition with b = 1 is PLE); P, pivcols and r are the same for every
  * block size.  Exact over F2: P*A = L*E bit for bit.
+ * Asynchronous on `stream` (after the padding check, which synchronises it
+ * once unless GF2_NOCHECK).  The second call with the same shape and buffers
+ * captures the launch sequence into a CUDA graph on the library's streams
+ * (thread-local capture mode) and later calls replay it; while a call
+ * captures, a device-wide synchronisation from another host thread
+ * (cudaDeviceSynchronize, torch.cuda.synchronize) fails with
+ * cudaErrorStreamCaptureUnsupported, so multi-threaded callers synchronise
+ * their own streams instead.
  * Errors: GF2_ERR_ARG, GF2_ERR_SHAPE (ld < rows, L or E of the wrong size),
  * GF2_ERR_PADDING, GF2_ERR_NOMEM, GF2_ERR_UNSUPPORTED (n >= 2^31), GF2_ERR_CUDA.
  */

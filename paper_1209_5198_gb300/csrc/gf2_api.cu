@@ -475,7 +475,7 @@ int enqueue_tail(DecompCtx c, int64_t *rank, gf2_mat *L, gf2_mat *E, int jend, i
 
 struct DecompLayout {
     int64_t mu, ldw, kmax, ldl;
-    size_t oW, oY, oF, oAct, oNact, oPP, oInfo, oZpos, oZraw, oLint, oEint, oFlag, oProg, total;
+    size_t oW, oY, oF, oAct, oNact, oOrw, oPP, oInfo, oZpos, oZraw, oLint, oEint, oFlag, oProg, total;
 };
 
 DecompLayout decomp_layout(int64_t n, int64_t m, bool factors)
@@ -491,6 +491,7 @@ DecompLayout decomp_layout(int64_t n, int64_t m, bool factors)
     d.oF = o; o += align_up((size_t)n * 2 * 8);
     d.oAct = o; o += align_up((size_t)n * kRing * 4);
     d.oNact = o; o += align_up((size_t)(d.mu > 0 ? d.mu : 1) * 4);
+    d.oOrw = o; o += align_up((size_t)(d.mu > 0 ? d.mu : 1) * 4);
     d.oPP = o; o += align_up((size_t)n * 4);
     d.oInfo = o; o += align_up((size_t)(d.mu > 0 ? d.mu : 1) * sizeof(PanelInfo));
     d.oZpos = o; o += align_up((size_t)(n > 0 ? n : 1) * 4);
@@ -541,6 +542,7 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
     c.F = reinterpret_cast<uint64_t *>(base + d.oF);
     c.act = reinterpret_cast<int32_t *>(base + d.oAct);
     c.nact = reinterpret_cast<int32_t *>(base + d.oNact);
+    c.orw = reinterpret_cast<int32_t *>(base + d.oOrw);
     c.pivpanel = reinterpret_cast<int32_t *>(base + d.oPP);
     c.zpos = reinterpret_cast<int32_t *>(base + d.oZpos);
     c.zraw = reinterpret_cast<uint64_t *>(base + d.oZraw);
@@ -570,6 +572,7 @@ int decompose_impl(const gf2_mat *A, int32_t *perm, int32_t *pivcols, int64_t *r
     }
     if (c.Lint) CK(cudaMemsetAsync(c.Lint, 0, (size_t)n * d.ldl * 8, s));
     CK(cudaMemsetAsync(c.nact, 0, (size_t)c.mu * sizeof(int32_t), s));  // the active-list counts
+    CK(cudaMemsetAsync(c.orw, 0, (size_t)c.mu * sizeof(int32_t), s));   // the look-ahead's zero-block flags
 
     // Which panels run as separate launches ([0, jend)) and which in one
     // persistent launch (csrc/k_factor.cu), by pairs of panels only:

@@ -68,6 +68,10 @@ struct DecompCtx {
     int32_t *act;       // [kRing][n] act[j % kRing]: the storage rows that are not pivots of panels <= j
                         // (ascending within each 256-entry piece), written by the look-ahead of panel j
     int32_t *nact;      // [mu] number of entries of act after panel j (zero before the run)
+    int32_t *orw;       // [mu] set by the look-ahead of panel j-2 after a rank-deficient panel: bit 1 =
+                        // looked, bit 0 = some row not a pivot of panels <= j-2 has a nonzero word j
+                        // after the updates of panels <= j-2 (zero before the run); or null.  With
+                        // r_{j-1} = 0, orw[j] == 2 means panel j has no pivot
     uint64_t *Lint;     // [n x ldl] per storage row, or null (rank only)
     int64_t ldl;
     uint64_t *Eint;     // [k x lde] per pivot index (row-major), or null

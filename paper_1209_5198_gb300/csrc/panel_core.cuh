@@ -628,7 +628,13 @@ __device__ __forceinline__ void panel_block(const DecompCtx &c, int j, PanelShar
     const uint64_t *Wj = c.W + (int64_t)(j / kTileWords) * c.tstride + (j % kTileWords);  // word j of row i: Wj[T i]
 
     if (tid == 0) sh.zfrom = -1;  // no row list yet in this panel
-    if (R >= n || nbits <= 0) {
+    // no pivot: no rows or columns left, or (panel j-1 had none and the
+    // look-ahead of panel j-2 looked and saw only zero words j in the rows
+    // still active) every row's word j is zero -- the rank is used up,
+    // nothing to scan
+    const bool zero_block = c.orw && j >= 2 && panel_info(c, j - 1)->r == 0 &&
+                            *reinterpret_cast<volatile const int32_t *>(c.orw + j) == 2;
+    if (R >= n || nbits <= 0 || zero_block) {
         if (tid == 0) {
             pi->R = R;
             pi->r = 0;

@@ -85,7 +85,8 @@ __device__ __forceinline__ void next_body(const DecompCtx &c, int j, int chunk, 
 
     // 1. every load of this thread's rows, issued before anything waits
     int rows[U];
-    uint32_t active = 0;  // bit u: row u is not a pivot of panels <= j
+    uint32_t active = 0;  // bit u: row u is not a pivot of panels <= j (and r > 0)
+    uint32_t keepm = 0;   // bit u: row u is not a pivot of panels <= j
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int k = rb + (warp * U + u) * kRowsPerWarp + rs;
@@ -99,6 +100,7 @@ __device__ __forceinline__ void next_body(const DecompCtx &c, int j, int chunk, 
         const bool in = row >= 0;
         const int64_t rr = in ? row : 0;
         const bool keep = in && c.pivpanel[row] > j;
+        if (keep) keepm |= 1u << u;
         if (keep && r > 0) active |= 1u << u;
         if (wp == 0) keep_row[(warp * U + u) * kRowsPerWarp + rs] = keep ? row : -1;
         d[u] = !in ? 0 : (j == 0 ? c.W[widx(c, rr, 0)] : Fj[rr]);
@@ -205,6 +207,25 @@ __device__ __forceinline__ void next_body(const DecompCtx &c, int j, int chunk, 
             uint64_t *dst = c.W + widx(c, row, col);
             if (live_lo) *reinterpret_cast<ulonglong2 *>(dst) = a[u];
             else dst[1] = a[u].y;
+        }
+    }
+    // After a rank-deficient panel (the rank may be used up): whether any row
+    // that stays active has a nonzero word j+2 now (every panel <= j
+    // applied).  orw[j+2] bit 1: computed (by the first chunk), bit 0: some
+    // nonzero word seen.  With no pivot in panel j+1 either, "computed and
+    // none" tells panel j+2 that its block has no pivot.
+    if (c.orw && j + 2 < c.mu && r < 64) {
+        uint64_t o = 0;
+        if (wp == ((j + 2) & 3) >> 1)  // this lane's word pair holds word j+2
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (!((keepm >> u) & 1)) continue;
+                o |= live_hi ? (((j + 2) & 1) ? a[u].y : a[u].x) : c.W[widx(c, rows[u], j + 2)];
+            }
+        const int any = __syncthreads_or(o != 0);
+        if (tid == 0) {  // one atomic per CTA at most
+            const int v = (any ? 1 : 0) | ((chunk == 0 && round == 0) ? 2 : 0);
+            if (v && (*reinterpret_cast<volatile int32_t *>(c.orw + j + 2) & v) != v) atomicOr(c.orw + j + 2, v);
         }
     }
     // the second tile of a pair's range: every word of it

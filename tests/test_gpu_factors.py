@@ -32,8 +32,14 @@ def cases():
             ("sparse", f2gen.sparse_rows(1200, 1200, 3, 74), 1200)]
 
 
-def handle_factors(F: "gf2.Factors") -> dict:
-    torch.cuda.synchronize()
+def handle_factors(F: "gf2.Factors", stream=None) -> dict:
+    """The handle's factors on the host.  With a stream, only that stream is
+    synchronised: a device-wide synchronisation fails while another thread's
+    decomposition captures its CUDA graph."""
+    if stream is None:
+        torch.cuda.synchronize()
+    else:
+        stream.synchronize()
     return dict(perm=F.perm.cpu().numpy(), pivcols=F.pivcols.cpu().numpy(), rank=F.rank(),
                 L=F.L.to_rowmajor(), E=F.E.to_rowmajor())
 
@@ -136,7 +142,7 @@ def test_two_threads_with_different_options():
                     C = gf2.Mat.empty(1024, 1024)
                     gf2.gf2_mmm_ex(Pd, Qd, C, mopt, stream=s)
                     s.synchronize()
-                    got = handle_factors(F)
+                    got = handle_factors(F, s)
                     ref = refs[i]
                     assert got["rank"] == ref["rank"]
                     assert np.array_equal(got["perm"], ref["perm"])
