@@ -74,20 +74,23 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
     // a programmatic dependent of the previous update on this stream: wait
     // for it to complete (and its writes to be visible), then let the next
     // one be scheduled
+    // The panels' results and the active list come from kernels of the
+    // other streams, which this launch waits for in full: they are read
+    // before the wait.
+    const PanelInfo *pi0 = c.info + j;
+    const PanelInfo *pi1 = c.info + j + NP - 1;
+    const int r0 = pi0->r, r1 = NP == 2 ? pi1->r : 0;
+    // the rows to update: the list of the rows that are not pivots of
+    // panels <= j + NP - 1 (the rows that are have y = 0)
+    const int jl = j + NP - 1;
+    const int nact = c.nact[jl];
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     GF2_TR(const int jt = j + NP - 1 < kTraceMaxPanels ? j + NP - 1 : kTraceMaxPanels - 1;
            TraceSpan span(g_update_trace + kTrRestStart * kTraceMaxPanels + jt,
                           g_update_trace + kTrRestEnd * kTraceMaxPanels + jt);)
     extern __shared__ __align__(16) uint64_t smem[];
-    const PanelInfo *pi0 = c.info + j;
-    const PanelInfo *pi1 = c.info + j + NP - 1;
-    const int r0 = pi0->r, r1 = NP == 2 ? pi1->r : 0;
     if (r0 == 0 && r1 == 0) return;
-    // the rows to update: the list of the rows that are not pivots of
-    // panels <= j + NP - 1 (the rows that are have y = 0)
-    const int jl = j + NP - 1;
-    const int nact = c.nact[jl];
     // (with no row left the tiles are still visited when E is wanted: the
     // pivot rows' echelon words come from the same tables)
     const int nchunks = max((nact + kRestChunk - 1) / kRestChunk, c.Eint ? 1 : 0);
