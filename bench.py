@@ -369,6 +369,60 @@ def time_calls(fn, steps: int, stream) -> float:
     return e0.elapsed_time(e1) / steps
 
 
+def run_wide(args):
+    """The wide-panel question (Section 5's wider blocks, Table 4's "rec"
+    columns): the trailing update by w = 64 s columns at once is the product
+    C ^= Y P with an n x w multiplier matrix Y and w pivot rows P.  Timed
+    here with the M4RM kernel alone (C in registers over the inner
+    dimension, so C is read and written once per call) at n = m = --n and
+    w = 64 .. 1024: the time per 64 columns of w falls while fixed costs per
+    call (table builds, C's loads) are amortised and levels off once the
+    table lookups (8 of 8 B per output word and 64 columns of w) bound it."""
+    import torch
+
+    import paper_1209_5198_gb300 as gf2
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    lib = gf2.load()
+    n = args.n
+    g = torch.Generator(device=dev).manual_seed(0x1209)
+    props = torch.cuda.get_device_properties(0)
+    fl = gf2.GF2_MMM_TABLES | gf2.GF2_NOCHECK
+    C = gf2.Mat(rand_words(n, n, g, dev), n, n)
+    rows = []
+    sampler = ClockSampler(0)
+    sampler.start()
+    for w in (64, 128, 256, 512, 1024):
+        Y = gf2.Mat(rand_words(n, w, g, dev), n, w)
+        P = gf2.Mat(rand_words(w, n, g, dev), w, n)
+        ws = torch.empty(max(1, lib.gf2_mmm_workspace_bytes(n, w, n, fl)), dtype=torch.uint8, device=dev)
+        fn = lambda: gf2.gf2_mmm(Y, P, C, accumulate=True, flags=fl, workspace=ws, stream=stream)
+        for _ in range(args.warmup):
+            fn()
+        ms = time_calls(fn, args.steps, stream)
+        words = n * (n // 64)
+        rows.append({"w": w, "ms": ms, "ms_per_64_columns": ms / (w // 64),
+                     "c_gbs": 16.0 * words / (ms / 1000) / 1e9,
+                     "lookup_gbs": 8.0 * 8 * (w // 64) * words / (ms / 1000) / 1e9})
+    clocks = sampler.stop()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    clk = clocks.get("sm_mhz") or 2070.0
+    line = {"metric": "wide-panel trailing update: ms per 64 columns of w (C ^= Y P, M4RM)",
+            "value": rows[2]["ms_per_64_columns"], "unit": "ms", "higher_is_better": False,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"C ^= Y P over F2, C {n} x {n}, Y {n} x w, P w x {n}, w = 64..1024 "
+                                   "(Bernoulli(1/2)); value = w = 256", "rows": rows,
+                       "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                       "lookup_peak_gbs": 128.0 * props.multi_processor_count * clk * 1e6 / 1e9},
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def run_product(args):
     import torch
 
@@ -1190,7 +1244,7 @@ def main():
     ap.add_argument("--fp-sizes", type=int, nargs="+", default=[1024, 4096, 8192], help="n of the F_p workload")
     ap.add_argument("--schedule", default="auto", choices=["auto", "streams", "persistent", "split"],
                     help="decomposition schedule (gf2_opts.schedule)")
-    ap.add_argument("--workload", default="decompose", choices=["decompose", "batched", "serving", "product", "sizes", "sparse", "fp"],
+    ap.add_argument("--workload", default="decompose", choices=["decompose", "batched", "serving", "product", "sizes", "sparse", "fp", "wide"],
                     help="decompose: the headline 32768^2 decomposition; batched: many small matrices in one "
                          "launch; serving: a request stream on resident factors")
     ap.add_argument("--requests", type=int, default=20000, help="requests in the serving trace")
@@ -1214,6 +1268,8 @@ def main():
         run_sparse(args)
     elif args.workload == "sizes":
         run_sizes(args)
+    elif args.workload == "wide":
+        run_wide(args)
     else:
         run_ours(args)
 
