@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(kNextThreads, 4) k_next(DecompCtx c, int j)
 constexpr int kRestThreads = 512;
 constexpr int kRestU = 6;   // row groups of 16 rows per warp and iteration (one panel)
 constexpr int kRest2U = 4;  // the same for a pair
+constexpr int kRestHeadU = 1;  // the same for a pair's one-tile head launch (256-row items: every warp busy)
 
 template <int C, int U, int NP>
 // at most 96 registers: 512 x 96 leaves room on the SM for a k_next CTA
@@ -84,31 +85,51 @@ __global__ void __maxnreg__(96) k_rest(DecompCtx c, int j, int tile_first, int n
     // panels <= j + NP - 1 (the rows that are have y = 0)
     const int jl = j + NP - 1;
     const int nact = c.nact[jl];
+    // (with no row left the tiles are still visited when E is wanted: the
+    // pivot rows' echelon words come from the same tables)
+    const int nchunks = max((nact + kRestChunk - 1) / kRestChunk, c.Eint ? 1 : 0);
+    const int64_t items = (int64_t)ntiles * nchunks;
+    const int64_t i0 = items * blockIdx.x / gridDim.x, i1 = items * (blockIdx.x + 1) / gridDim.x;
+    const bool work = (r0 != 0 || r1 != 0) && i0 < i1;
+    // The one-row-group variant (the head launches: one tile, one chunk per
+    // CTA, a serial latency chain) also loads its pivot rows' storage rows,
+    // their multipliers and its first rows before the wait.
+    constexpr bool PRE = U == 1;
+    RestPre<NP, kRestThreads> pre{};
+    RestIter<U> first{};
+    if (PRE && work) {
+        rest_preload<NP, kRestThreads>(c, j, r0, r1, pre);
+        const int chunk = (int)(i0 % nchunks);
+        const int chunk_end = (int)((min(i1, (i0 / nchunks + 1) * nchunks) - 1) % nchunks) + 1;
+        rest_iter_load<U, NP>(c, j, chunk * kRestChunk + (int)(threadIdx.x >> 5) * kRowsPerWarp * U,
+                              min(nact, chunk_end * kRestChunk), first);
+    }
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     GF2_TR(const int jt = j + NP - 1 < kTraceMaxPanels ? j + NP - 1 : kTraceMaxPanels - 1;
            TraceSpan span(g_update_trace + kTrRestStart * kTraceMaxPanels + jt,
                           g_update_trace + kTrRestEnd * kTraceMaxPanels + jt);)
     extern __shared__ __align__(16) uint64_t smem[];
-    if (r0 == 0 && r1 == 0) return;
-    // (with no row left the tiles are still visited when E is wanted: the
-    // pivot rows' echelon words come from the same tables)
-    const int nchunks = max((nact + kRestChunk - 1) / kRestChunk, c.Eint ? 1 : 0);
-    const int64_t items = (int64_t)ntiles * nchunks;
-    if (items == 0) return;
-    const int64_t i0 = items * blockIdx.x / gridDim.x, i1 = items * (blockIdx.x + 1) / gridDim.x;
+    if (!work) return;
     UpdOps ops;
     // The item range is split into segments of one tile each: one table
     // build per segment, then one pipelined pass over its rows.
     for (int64_t it = i0; it < i1;) {
+        const bool seg0 = it == i0;
         const int tile = tile_first + (int)(it / nchunks);
         const int chunk = (int)(it % nchunks);
         const int64_t seg_end = min(i1, (int64_t)(tile - tile_first + 1) * nchunks);
         const int chunk_end = (int)((seg_end - 1) % nchunks) + 1;
         it = seg_end;
-        rest_prepare<C, NP, kRestThreads>(c, j, tile, chunk == 0, smem, ops);
-        rest_pass<C, U, NP, kRestThreads>(c, j, tile, chunk * kRestChunk, min(nact, chunk_end * kRestChunk), smem,
-                                          ops);
+        const int rb = chunk * kRestChunk, re = min(nact, chunk_end * kRestChunk);
+        if (PRE) {
+            rest_prepare<C, NP, kRestThreads, PRE>(c, j, tile, chunk == 0, smem, ops, pre);
+            if (seg0) rest_pass<C, U, NP, kRestThreads, PRE>(c, j, tile, rb, re, smem, ops, first);
+            else rest_pass<C, U, NP, kRestThreads>(c, j, tile, rb, re, smem, ops);
+        } else {
+            rest_prepare<C, NP, kRestThreads>(c, j, tile, chunk == 0, smem, ops);
+            rest_pass<C, U, NP, kRestThreads>(c, j, tile, rb, re, smem, ops);
+        }
     }
     GF2_OPS(add_ops(g_update_ops, kOpUpdates, ops.upd); add_ops(g_update_ops, C == 8 ? kOpLookups8 : kOpLookups4, ops.lk);
             add_ops(g_update_ops, C == 8 ? kOpTable8 : kOpTable4, ops.tab);)
@@ -150,6 +171,7 @@ cudaError_t prepare_update_kernels()
     e = allow_smem(k_rest<8, kRestU, 1>, rest_smem_bytes<8, 1>());
     if (e == cudaSuccess) e = allow_smem(k_rest<8, kRest2U, 2>, rest_smem_bytes<8, 2>());
     if (e == cudaSuccess) e = allow_smem(k_rest<4, kRest2U, 2>, rest_smem_bytes<4, 2>());
+    if (e == cudaSuccess) e = allow_smem(k_rest<8, kRestHeadU, 2>, rest_smem_bytes<8, 2>());
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }
@@ -232,6 +254,8 @@ cudaError_t launch_rest(const DecompCtx &c, int j, int np, int est_active_rows, 
             return cudaLaunchKernelEx(&cfg, k_rest<4, kRest2U, 2>, c, j, tile_first, ntiles);
         }
         cfg.dynamicSmemBytes = rest_smem_bytes<8, 2>();
+        if (limit == 1 && skip == 0 && ntiles == 1)  // a head
+            return cudaLaunchKernelEx(&cfg, k_rest<8, kRestHeadU, 2>, c, j, tile_first, ntiles);
         return cudaLaunchKernelEx(&cfg, k_rest<8, kRest2U, 2>, c, j, tile_first, ntiles);
     }
     if (c.tab_c == 8 || (c.tab_c == 0 && est_active_rows >= 4096)) {

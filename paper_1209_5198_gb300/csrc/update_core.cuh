@@ -309,9 +309,40 @@ struct UpdOps {  // the op-counting build's tallies of one thread
 // j+1's tables are built from them (their words in W are not read again: the
 // echelon rows come from these tables).  first: the CTA that takes the
 // tile's first chunk also writes the pivot rows' echelon words of the tile.
-template <int C, int NP, int THREADS>
+// rest_prepare's loads that do not read W, the same for every tile (entry e
+// as below; row -1 past the panel's pivots): the head launches make them
+// before their grid-dependency wait.
+template <int NP, int THREADS>
+struct RestPre {
+    static constexpr int NE = NP * 64 * kTileWords;
+    static constexpr int RPT = (NE + THREADS - 1) / THREADS;
+    int row[RPT];
+    uint64_t yv[RPT];
+};
+
+template <int NP, int THREADS>
+__device__ __forceinline__ void rest_preload(const DecompCtx &c, int j, int r0, int r1, RestPre<NP, THREADS> &p)
+{
+    const PanelInfo *pi0 = c.info + j;
+    const PanelInfo *pi1 = c.info + j + NP - 1;
+    const uint64_t *Y0 = c.Y + (int64_t)(j % kRing) * c.n;
+#pragma unroll
+    for (int k = 0; k < RestPre<NP, THREADS>::RPT; ++k) {
+        const int e = threadIdx.x + k * THREADS, t = (e & 255) / kTileWords;
+        const bool p1 = e >= 64 * kTileWords;
+        p.row[k] = -1;
+        p.yv[k] = 0;
+        if (e < RestPre<NP, THREADS>::NE && t < (p1 ? r1 : r0)) {
+            p.row[k] = (p1 ? pi1 : pi0)->prow[t];
+            if (p1) p.yv[k] = Y0[p.row[k]];
+        }
+    }
+}
+
+// PRE: the loads of rest_preload are in pre.
+template <int C, int NP, int THREADS, bool PRE = false>
 __device__ __forceinline__ void rest_prepare(const DecompCtx &c, int j, int tile, bool first, uint64_t *smem,
-                                             UpdOps &ops)
+                                             UpdOps &ops, const RestPre<NP, THREADS> &pre = RestPre<NP, THREADS>{})
 {
     constexpr int K = Tabs<C>::K;
     uint64_t *tab = smem;                          // [NP * K tables][X][kTileWords]
@@ -337,7 +368,10 @@ __device__ __forceinline__ void rest_prepare(const DecompCtx &c, int j, int tile
         const bool p1 = e >= 64 * kTileWords;
         v[k] = 0;
         yv[k] = 0;
-        if (e < NE && t < (p1 ? r1 : r0)) {
+        if constexpr (PRE) {
+            yv[k] = pre.yv[k];
+            if (pre.row[k] >= 0) v[k] = c.W[widx(c, pre.row[k], q0 + idx % kTileWords)];
+        } else if (e < NE && t < (p1 ? r1 : r0)) {
             const int row = (p1 ? pi1 : pi0)->prow[t];
             v[k] = c.W[widx(c, row, q0 + idx % kTileWords)];
             if (p1) yv[k] = Y0[row];
@@ -483,9 +517,38 @@ __device__ __forceinline__ void rest_rows(const Lk8 &lk, const ulonglong2 *tab2,
 // W ^= y_j C_j (+ y_j+1 C_j+1) on `tile` for the list entries [rb, re), with
 // the tables rest_prepare built; U row groups of 16 rows per warp and
 // iteration, y and the next rows' indices prefetched one iteration ahead.
-template <int C, int U, int NP, int THREADS>
+// The loads of rest_pass's first iteration (list entries, then
+// multipliers; no W) for the warp whose rows start at base: row -1 past re.
+template <int U>
+struct RestIter {
+    int row[U];
+    uint64_t y0[U], y1[U];
+};
+
+template <int U, int NP>
+__device__ __forceinline__ void rest_iter_load(const DecompCtx &c, int j, int base, int re, RestIter<U> &it)
+{
+    const int32_t *act = c.act + (int64_t)((j + NP - 1) % kRing) * c.n;
+    const uint64_t *Y0 = c.Y + (int64_t)(j % kRing) * c.n;
+    const uint64_t *Y1 = c.Y + (int64_t)((j + 1) % kRing) * c.n;
+    const int rs = (threadIdx.x & 31) / kLanesPerRow;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int k = base + u * kRowsPerWarp + rs;
+        it.row[u] = k < re ? __ldcg(act + k) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        it.y0[u] = it.row[u] >= 0 ? __ldcg(Y0 + it.row[u]) : 0;
+        it.y1[u] = (NP == 2 && it.row[u] >= 0) ? __ldcg(Y1 + it.row[u]) : 0;
+    }
+}
+
+// PRE: the first iteration's loads are in first (rest_iter_load with base =
+// rb + warp * kRowsPerWarp * U).
+template <int C, int U, int NP, int THREADS, bool PRE = false>
 __device__ __forceinline__ void rest_pass(const DecompCtx &c, int j, int tile, int rb, int re, const uint64_t *smem,
-                                          UpdOps &ops)
+                                          UpdOps &ops, const RestIter<U> &first = RestIter<U>{})
 {
     constexpr int K = Tabs<C>::K;
     const PanelInfo *pi0 = c.info + j;
@@ -509,15 +572,24 @@ __device__ __forceinline__ void rest_pass(const DecompCtx &c, int j, int tile, i
     constexpr int STEP = kRowsPerWarp * U * NW;
     uint64_t yn0[U], yn1[U];
     int rown[U];
+    if constexpr (PRE) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const int k = rb + warp * kRowsPerWarp * U + u * kRowsPerWarp + rs;
-        rown[u] = k < re ? __ldcg(act + k) : -1;
-    }
+        for (int u = 0; u < U; ++u) {
+            rown[u] = first.row[u];
+            yn0[u] = first.y0[u];
+            yn1[u] = first.y1[u];
+        }
+    } else {
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-        yn0[u] = rown[u] >= 0 ? __ldcg(Y0 + rown[u]) : 0;
-        yn1[u] = (NP == 2 && rown[u] >= 0) ? __ldcg(Y1 + rown[u]) : 0;
+        for (int u = 0; u < U; ++u) {
+            const int k = rb + warp * kRowsPerWarp * U + u * kRowsPerWarp + rs;
+            rown[u] = k < re ? __ldcg(act + k) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            yn0[u] = rown[u] >= 0 ? __ldcg(Y0 + rown[u]) : 0;
+            yn1[u] = (NP == 2 && rown[u] >= 0) ? __ldcg(Y1 + rown[u]) : 0;
+        }
     }
     for (int base = rb + warp * kRowsPerWarp * U; base < re; base += STEP) {
         uint64_t y0[U], y1[U];
