@@ -254,7 +254,9 @@ cudaError_t launch_rest(const DecompCtx &c, int j, int np, int est_active_rows, 
             return cudaLaunchKernelEx(&cfg, k_rest<4, kRest2U, 2>, c, j, tile_first, ntiles);
         }
         cfg.dynamicSmemBytes = rest_smem_bytes<8, 2>();
-        if (limit == 1 && skip == 0 && ntiles == 1)  // a head
+        // a head with at most one item per CTA (where CTAs take two or more,
+        // the deeper row groups of kRest2U do better)
+        if (limit == 1 && skip == 0 && ntiles == 1 && (est_active_rows + kRestChunk - 1) / kRestChunk <= num_sms() - 1)
             return cudaLaunchKernelEx(&cfg, k_rest<8, kRestHeadU, 2>, c, j, tile_first, ntiles);
         return cudaLaunchKernelEx(&cfg, k_rest<8, kRest2U, 2>, c, j, tile_first, ntiles);
     }

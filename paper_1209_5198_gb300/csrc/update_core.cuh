@@ -356,52 +356,62 @@ __device__ __forceinline__ void rest_prepare(const DecompCtx &c, int j, int tile
     const int q0 = tile * kTileWords;
     const uint64_t *Y0 = c.Y + (int64_t)(j % kRing) * c.n;
     (void)ops;
-    // One round of loads: the pivot rows' tile words of both panels and,
-    // for the second panel's rows, panel j's multipliers (entry e: panel
-    // e / 256, row (e % 256) / kTileWords, word e % kTileWords).
-    constexpr int NE = NP * 64 * kTileWords;
-    constexpr int RPT = (NE + THREADS - 1) / THREADS;
-    uint64_t v[RPT], yv[RPT];
+    if constexpr (PRE) {
+        // one round of loads, from rest_preload's storage rows: the pivot
+        // rows' tile words of both panels (entry e: panel e / 256, row
+        // (e % 256) / kTileWords, word e % kTileWords)
+        constexpr int NE = RestPre<NP, THREADS>::NE, RPT = RestPre<NP, THREADS>::RPT;
+        uint64_t v[RPT];
 #pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-        const int e = tid + k * THREADS, idx = e & 255, t = idx / kTileWords;
-        const bool p1 = e >= 64 * kTileWords;
-        v[k] = 0;
-        yv[k] = 0;
-        if constexpr (PRE) {
-            yv[k] = pre.yv[k];
-            if (pre.row[k] >= 0) v[k] = c.W[widx(c, pre.row[k], q0 + idx % kTileWords)];
-        } else if (e < NE && t < (p1 ? r1 : r0)) {
-            const int row = (p1 ? pi1 : pi0)->prow[t];
-            v[k] = c.W[widx(c, row, q0 + idx % kTileWords)];
-            if (p1) yv[k] = Y0[row];
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-        const int e = tid + k * THREADS, idx = e & 255, t = idx / kTileWords;
-        if (e < NE) (e >= 64 * kTileWords ? crow1 : crow)[idx + kRestPad * (t / C)] = v[k];
-    }
-    __syncthreads();
-    build_tables<C, THREADS, kRestPad>(tab, crow);
-    GF2_OPS(if (tid == 0) ops.tab += (unsigned long long)NP * K * (Tabs<C>::X - 1) * live_words(q0, c.mu);)
-    if (NP == 2) {
+        for (int k = 0; k < RPT; ++k)
+            v[k] = pre.row[k] >= 0 ? c.W[widx(c, pre.row[k], q0 + (tid + k * THREADS) % kTileWords)] : 0;
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
-            const int e = tid + k * THREADS, idx = e & 255;
-            if (e < 64 * kTileWords || e >= NE || !yv[k]) continue;
-            const uint64_t y = yv[k];
-            uint64_t acc = 0;
-            for (int g = 0; g < ng0; ++g)
-                acc ^= tab[tab_entry<C>(g, (int)((y >> (C * g)) & (Tabs<C>::X - 1))) * kTileWords + idx % kTileWords];
-            crow1[idx + kRestPad * (idx / kTileWords / C)] ^= acc;
-            // (every CTA that shares the tile redoes this; counted once, by the one with chunk 0)
-            GF2_OPS(if (first && q0 + idx % kTileWords < c.mu) { ops.upd += 1; ops.lk += ng0; })
+            const int e = tid + k * THREADS, idx = e & 255, t = idx / kTileWords;
+            if (e < NE) (e >= 64 * kTileWords ? crow1 : crow)[idx + kRestPad * (t / C)] = v[k];
         }
         __syncthreads();
-        build_tables<C, THREADS, kRestPad>(tab, crow1, K);
+        build_tables<C, THREADS, kRestPad>(tab, crow);
+        GF2_OPS(if (tid == 0) ops.tab += (unsigned long long)NP * K * (Tabs<C>::X - 1) * live_words(q0, c.mu);)
+        if (NP == 2) {
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const int e = tid + k * THREADS, idx = e & 255;
+                if (e < 64 * kTileWords || e >= NE || !pre.yv[k]) continue;
+                const uint64_t y = pre.yv[k];
+                uint64_t acc = 0;
+                for (int g = 0; g < ng0; ++g)
+                    acc ^= tab[tab_entry<C>(g, (int)((y >> (C * g)) & (Tabs<C>::X - 1))) * kTileWords + idx % kTileWords];
+                crow1[idx + kRestPad * (idx / kTileWords / C)] ^= acc;
+                GF2_OPS(if (first && q0 + idx % kTileWords < c.mu) { ops.upd += 1; ops.lk += ng0; })
+            }
+            __syncthreads();
+            build_tables<C, THREADS, kRestPad>(tab, crow1, K);
+        }
+    } else {
+        __syncthreads();
+        load_pivot_rows<THREADS, C, kRestPad>(c, pi0->prow, r0, q0, crow);
+        if (NP == 2) load_pivot_rows<THREADS, C, kRestPad>(c, pi1->prow, r1, q0, crow1);
+        __syncthreads();
+        build_tables<C, THREADS, kRestPad>(tab, crow);
+        GF2_OPS(if (tid == 0) ops.tab += (unsigned long long)NP * K * (Tabs<C>::X - 1) * live_words(q0, c.mu);)
+        if (NP == 2) {
+            __syncthreads();
+            for (int idx = tid; idx < r1 * kTileWords; idx += THREADS) {
+                const uint64_t y = Y0[pi1->prow[idx / kTileWords]];
+                if (!y) continue;
+                uint64_t acc = 0;
+                for (int g = 0; g < ng0; ++g)
+                    acc ^= tab[tab_entry<C>(g, (int)((y >> (C * g)) & (Tabs<C>::X - 1))) * kTileWords + idx % kTileWords];
+                crow1[idx + kRestPad * (idx / kTileWords / C)] ^= acc;
+                // (every CTA that shares the tile redoes this; counted once, by the one with chunk 0)
+                GF2_OPS(if (first && q0 + idx % kTileWords < c.mu) { ops.upd += 1; ops.lk += ng0; })
+            }
+            __syncthreads();
+            build_tables<C, THREADS, kRestPad>(tab, crow1, K);
+        }
     }
     __syncthreads();
     if (c.Eint && first) {
