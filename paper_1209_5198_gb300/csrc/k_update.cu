@@ -64,6 +64,7 @@ constexpr int kRestThreads = 512;
 constexpr int kRestU = 6;   // row groups of 16 rows per warp and iteration (one panel)
 constexpr int kRest2U = 4;  // the same for a pair
 constexpr int kRestHeadU = 1;  // the same for a pair's one-tile head launch (256-row items: every warp busy)
+constexpr int kRestHeadMinRows = 16384;  // rows below the pair from which a head runs with kRestHeadU
 
 template <int C, int U, int NP>
 // at most 96 registers: 512 x 96 leaves room on the SM for a k_next CTA
@@ -255,8 +256,13 @@ cudaError_t launch_rest(const DecompCtx &c, int j, int np, int est_active_rows, 
         }
         cfg.dynamicSmemBytes = rest_smem_bytes<8, 2>();
         // a head with at most one item per CTA (where CTAs take two or more,
-        // the deeper row groups of kRest2U do better)
-        if (limit == 1 && skip == 0 && ntiles == 1 && (est_active_rows + kRestChunk - 1) / kRestChunk <= num_sms() - 1)
+        // the deeper row groups of kRest2U do better), and with at least
+        // kRestHeadMinRows rows below the pair: there the update stream bounds
+        // the decomposition and the head's latency delays the look-ahead
+        // (measured: below, e.g. all of a 16384 x 16384 decomposition, the
+        // deeper row groups do better here too)
+        if (limit == 1 && skip == 0 && ntiles == 1 && est_active_rows >= kRestHeadMinRows &&
+            (est_active_rows + kRestChunk - 1) / kRestChunk <= num_sms() - 1)
             return cudaLaunchKernelEx(&cfg, k_rest<8, kRestHeadU, 2>, c, j, tile_first, ntiles);
         return cudaLaunchKernelEx(&cfg, k_rest<8, kRest2U, 2>, c, j, tile_first, ntiles);
     }
